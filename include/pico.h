@@ -1,0 +1,180 @@
+/*
+ * pico.h -- C ABI of libpico, the GPU hot path of PICO (Probing Image-space
+ * COvariance) voxelwise noise-variance estimation for linear MRI
+ * reconstructions (Dalmaz et al., "Fast Voxelwise SNR Estimation for
+ * Iterative MRI Reconstructions").
+ *
+ * Problem (Sec. 2.1): pre-whitened multi-coil data b_w = A x + n_w with
+ * n_w ~ CN(0, I) (Eq. 3), Tikhonov CG-SENSE reconstruction
+ * x = (A^H A + lam I)^-1 A^H b_w (Eqs. 4-6), image-domain noise covariance
+ * Sigma = (M + lam I)^-1 M (M + lam I)^-1 with M = A^H A (Eq. 8), variance
+ * map diag(Sigma) (Eq. 10).  PICO (Alg. 1) estimates diag(Sigma) by
+ * averaging Re(conj(v) . Sigma v) over random-phase probe images v (Eq. 20);
+ * Sigma v is applied with CG on the normal equations (Sec. 2.2.3).  PMR
+ * (Sec. 1) re-solves with synthetic k-space noise for comparison.
+ *
+ * Conventions (all entry points):
+ *  - Images are complex64 (interleaved float re, im), row-major [ny][nx],
+ *    voxel (y, x); batches are contiguous [nbatch][ny][nx].
+ *  - "_dev" pointers are CUDA device pointers owned by the caller; they must
+ *    stay valid until the work is finished (pico_sync).  Host pointers are
+ *    read during the call only.
+ *  - All GPU work is stream-ordered on the stream given to pico_init; results
+ *    are valid after pico_sync (or any later synchronisation of that stream).
+ *  - Every call returns a pico_status; no exceptions cross the ABI.  On error
+ *    pico_last_error(ctx) describes the cause.  A failed call leaves the
+ *    context usable unless the status is PICO_E_CUDA.
+ *  - Results are deterministic: identical inputs give identical bits,
+ *    independent of how probes are split into calls (probe_begin/accumulate).
+ */
+#ifndef PICO_H
+#define PICO_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pico_ctx pico_ctx;
+
+typedef enum {
+  PICO_OK = 0,
+  PICO_E_INVALID = 1,     /* bad argument or descriptor                            */
+  PICO_E_OOM = 2,         /* footprint above hbm_budget, or cudaMalloc failed      */
+  PICO_E_CUDA = 3,        /* a CUDA runtime error; the context should be destroyed */
+  PICO_E_TIMEOUT = 4,     /* a bounded device-side wait gave up                    */
+  PICO_E_BREAKDOWN = 5,   /* CG met p^H (M + lam) p <= 0 for some right-hand side  */
+  PICO_E_UNSUPPORTED = 6  /* valid request this build does not implement           */
+} pico_status;
+
+typedef enum { PICO_CARTESIAN = 0, PICO_SPIRAL = 1 } pico_kind;
+
+/* Probe families of Sec. 2.2.4: random phase (Eq. 20), real Rademacher
+ * (Eq. 19), complex Gaussian (Eq. 18). */
+typedef enum { PICO_PROBE_PHASE = 0, PICO_PROBE_RADEMACHER = 1, PICO_PROBE_GAUSS = 2 } pico_probe;
+
+/* Acquisition and reconstruction description (Sec. 2.1.1-2.1.3). */
+typedef struct {
+  int32_t kind;             /* pico_kind                                                     */
+  int32_t ny, nx;           /* image matrix                                                   */
+  int32_t ncoils;           /* receive channels                                               */
+  const void* smaps;        /* host complex64 [ncoils][ny][nx] coil sensitivities (copied)    */
+  const double* noise_cov;  /* host complex128 [ncoils][ncoils] Hermitian PD channel noise
+                               covariance Sigma_n (Eq. 2), or NULL for white noise; folded
+                               into the sensitivities as L^-1 S with L L^H = Sigma_n (Eq. 3) */
+  const uint8_t* mask;      /* Cartesian: host [ny] phase-encode mask, natural DFT order
+                               (index ky, 0 = DC); every kx of a kept line is sampled        */
+  int32_t mask_2d;          /* must be 0 (2-D Cartesian masks: PICO_E_UNSUPPORTED)            */
+  const float* traj;        /* spiral: host [nsamp][2] (kx, ky) in cycles/FOV                 */
+  int64_t nsamp;            /* spiral samples                                                 */
+  float oversamp;           /* spiral gridding oversampling (2.0)                             */
+  int32_t kb_width;         /* spiral Kaiser-Bessel width (6)                                 */
+  double lambda;            /* Tikhonov weight relative to the spectrally normalised operator:
+                               lam_phys = lambda * power_margin * lambda_max(A^H A) (Sec. 3.3);
+                               with power_iters == 0, lambda is taken as physical            */
+  int32_t power_iters;      /* power-method steps for lambda_max (15 in the paper), 0 = none  */
+  double power_margin;      /* safety factor on lambda_max (1.01 in the paper)                */
+  int32_t max_batch;        /* right-hand sides solved together (0 = 64)                      */
+  int32_t max_iter_cap;     /* largest max_iter accepted later (0 = 128)                      */
+} pico_operator_desc;
+
+typedef struct {
+  double lambda_max;        /* power-method estimate (0 if power_iters == 0)                  */
+  double lambda_phys;       /* Tikhonov weight applied to A^H A                               */
+  int32_t kind, ny, nx, ncoils, max_batch, max_iter_cap;
+  int64_t nsamp;
+  uint64_t device_bytes;    /* device memory held by the context                              */
+} pico_info;
+
+/* Create a context: validates the descriptor, whitens the sensitivities,
+ * uploads the operator, sizes the workspace for max_batch right-hand sides
+ * and runs the power method (Sec. 3.3).  cuda_stream: a cudaStream_t (NULL =
+ * legacy default stream).  hbm_budget: bytes the context may hold on the
+ * device, 0 = unlimited; PICO_E_OOM is returned before any allocation if the
+ * footprint exceeds it.  Synchronises the stream before returning.
+ * On failure *out may still receive a context that only carries the error
+ * text (pico_last_error); release it with pico_destroy. */
+pico_status pico_init(const pico_operator_desc* desc, void* cuda_stream, size_t hbm_budget, pico_ctx** out);
+
+/* Operator sizes and the normalisation actually used. */
+pico_status pico_get_info(const pico_ctx* ctx, pico_info* info);
+
+/* y = (A^H A + lam_phys I) x for nbatch images (Eq. 6 left-hand side).
+ * x_dev, y_dev: device complex64 [nbatch][ny][nx]; must not overlap. */
+pico_status pico_apply_normal(pico_ctx* ctx, const void* x_dev, void* y_dev, int32_t nbatch);
+
+/* Solve (A^H A + lam_phys I) x = rhs by CG from x0 = 0 for nbatch right-hand
+ * sides (Eq. 6, CG-SENSE).  Each system stops after max_iter updates or once
+ * ||r|| <= rtol ||rhs|| (rtol = 0: exactly max_iter updates).  Inner products
+ * are accumulated in FP64.  rhs_dev, x_dev: device complex64 [nbatch][ny][nx].
+ * iters_out (int32 [nbatch]) and relres_out (double [nbatch]) are HOST arrays
+ * or NULL; if either is given the call synchronises the stream.
+ * max_iter must be in [0, max_iter_cap]. */
+pico_status pico_cg_batch(pico_ctx* ctx, const void* rhs_dev, void* x_dev, int32_t nbatch, int32_t max_iter,
+                          double rtol, int32_t* iters_out, double* relres_out);
+
+/* PICO running sums (Alg. 1) over probes probe_begin .. probe_begin+nprobes-1
+ * drawn under seed (probe_kind: pico_probe):
+ *   sum_dev[k]   (+)= sum_i Re(conj(v_i[k]) (Sigma v_i)[k])
+ *   sumsq_dev[k] (+)= sum_i Re(...)^2                (nullable)
+ * Sigma v is one CG solve when lam_phys == 0, else solve / apply A^H A /
+ * solve (Sec. 2.2.3).  sum_dev, sumsq_dev: device float64 [ny][nx];
+ * accumulate = 0 overwrites them, 1 adds to them (checkpoint/resume and
+ * splitting probes across calls give bit-identical totals).
+ * The variance map is sum / (number of probes); see pico_finalize. */
+pico_status pico_variance_map(pico_ctx* ctx, uint64_t seed, int64_t probe_begin, int32_t nprobes,
+                              int32_t probe_kind, int32_t max_iter, double rtol, double* sum_dev,
+                              double* sumsq_dev, int32_t accumulate);
+
+/* PMR running sums (Sec. 1; Sec. 3.2.2): replica i draws whitened k-space
+ * noise n_i ~ CN(0, sigma^2 I) on the sampled positions, solves
+ * x_i = (A^H A + lam_phys I)^-1 A^H n_i by CG and accumulates
+ *   sum_dev[k] (+)= |x_i[k]|^2 / sigma^2,  sumsq_dev[k] (+)= (|x_i[k]|^2/sigma^2)^2.
+ * Arguments as for pico_variance_map. */
+pico_status pico_pmr(pico_ctx* ctx, uint64_t seed, int64_t rep_begin, int32_t nreps, double sigma,
+                     int32_t max_iter, double rtol, double* sum_dev, double* sumsq_dev, int32_t accumulate);
+
+/* Finalise running sums over `count` samples (Alg. 1 output; Sec. 4
+ * "per-voxel standard error of the running mean"):
+ *   var_dev[k] = sum[k] / count                                   (float32, nullable)
+ *   stderr_dev[k] = sqrt((sumsq/count - (sum/count)^2) / (count-1)) (float32, nullable;
+ *                                                                   needs sumsq_dev) */
+pico_status pico_finalize(pico_ctx* ctx, const double* sum_dev, const double* sumsq_dev, int64_t count,
+                          float* var_dev, float* stderr_dev);
+
+/* g-factor map g = sigma_acc / (sqrt(R) sigma_ref) (Eq. 11) from two variance
+ * maps (device float32 [ny][nx]); R is the acceleration factor. */
+pico_status pico_gfactor(pico_ctx* ctx, const float* var_acc_dev, const float* var_ref_dev, double R,
+                         float* g_dev);
+
+/* Device timing of this context's kernels by class, from CUDA events recorded
+ * on the context stream around every launch while profiling is enabled.
+ * pico_profile(ctx, 1) clears the totals and starts recording, (ctx, 0) stops.
+ * Classes: 0 = SENSE normal operator (incl. the fused CG direction update),
+ * 1 = CG init/update vector kernels, 2 = PMR noise + adjoint, 3 = accumulate /
+ * finalize / small kernels.  pico_profile_read synchronises the stream and
+ * returns the summed milliseconds and the number of launches of a class. */
+pico_status pico_profile(pico_ctx* ctx, int32_t enable);
+pico_status pico_profile_read(pico_ctx* ctx, int32_t kernel_class, double* total_ms, int64_t* launches);
+
+/* Kernels launched by this context so far (all classes); reset = 1 zeroes the
+ * counter after reading it. */
+pico_status pico_launch_count(pico_ctx* ctx, int64_t* count, int32_t reset);
+
+/* Wait for all work of the context; returns the first asynchronous error
+ * (PICO_E_CUDA) or PICO_E_BREAKDOWN if a CG system broke down since the last
+ * pico_sync. */
+pico_status pico_sync(pico_ctx* ctx);
+
+/* Text of the last error of this context ("" if none).  Owned by the context. */
+const char* pico_last_error(const pico_ctx* ctx);
+
+/* Release every device and host resource of the context (NULL is ignored). */
+void pico_destroy(pico_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PICO_H */

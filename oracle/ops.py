@@ -84,7 +84,13 @@ def cart_matrix(S: np.ndarray, mask: np.ndarray) -> np.ndarray:
     return np.concatenate(rows, axis=0)
 
 
-def cart_column_normal(S: np.ndarray, mask_1d: np.ndarray, col: int) -> np.ndarray:
+def pe_projector(mask_1d: np.ndarray) -> np.ndarray:
+    """``P = F_y^H diag(mask) F_y`` from the DFT definition (dense ``ny x ny``)."""
+    Fy = dft_matrix(len(mask_1d))
+    return Fy.conj().T @ (np.asarray(mask_1d, dtype=np.float64)[:, None] * Fy)
+
+
+def cart_column_normal(S: np.ndarray, mask_1d: np.ndarray, col: int, P: np.ndarray | None = None) -> np.ndarray:
     """Dense ``A^H A`` restricted to readout column ``col`` for a phase-encode mask.
 
     With a mask on ``ky`` only, ``F^H M F = (F_y^H M_y F_y) (x) I_x``, so
@@ -92,8 +98,8 @@ def cart_column_normal(S: np.ndarray, mask_1d: np.ndarray, col: int) -> np.ndarr
     ``sum_c diag(S_c[:, col])^H P diag(S_c[:, col])``, ``P = F_y^H M_y F_y``.
     """
     ny = S.shape[1]
-    Fy = dft_matrix(ny)
-    P = Fy.conj().T @ np.diag(np.asarray(mask_1d, dtype=np.float64)) @ Fy
+    if P is None:
+        P = pe_projector(mask_1d)
     M = np.zeros((ny, ny), dtype=np.complex128)
     for c in range(S.shape[0]):
         s = S[c, :, col]

@@ -67,8 +67,9 @@ def column_exact(op: ops.Operator, lam: float = 0.0):
     ny, nx = op.ny, op.nx
     diag = np.zeros((ny, nx))
     rowe = np.zeros((ny, nx))
+    P = ops.pe_projector(op.mask)
     for col in range(nx):
-        M = ops.cart_column_normal(op.S, op.mask, col)
+        M = ops.cart_column_normal(op.S, op.mask, col, P)
         Sig = dense_cov(M, lam)
         d = np.real(np.diag(Sig))
         diag[:, col] = d

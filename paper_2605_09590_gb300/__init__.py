@@ -1,0 +1,317 @@
+"""GB300-native PICO noise-map hot path: thin Python binding of ``libpico``.
+
+``libpico.so`` (built from ``csrc/`` for sm_103a, see ``build.py``) exposes the
+C ABI declared in ``include/pico.h``.  This module only marshals arguments:
+every step of the path -- probe draws, the SENSE normal operator, batched CG,
+accumulation, PMR noise and its adjoint -- runs in the library's CUDA
+kernels.  PyTorch supplies device memory and the CUDA stream.  There is no CPU
+fallback: if the library is missing the calls raise.
+
+The functions carry the ABI's names (``pico_init``, ``pico_apply_normal``,
+``pico_cg_batch``, ``pico_variance_map``, ``pico_pmr``, ...); ``Operator`` is a
+small owner object over one context.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libpico.so")
+
+PICO_OK, PICO_E_INVALID, PICO_E_OOM, PICO_E_CUDA, PICO_E_TIMEOUT, PICO_E_BREAKDOWN, PICO_E_UNSUPPORTED = range(7)
+PICO_CARTESIAN, PICO_SPIRAL = 0, 1
+PICO_PROBE_PHASE, PICO_PROBE_RADEMACHER, PICO_PROBE_GAUSS = 0, 1, 2
+STATUS_NAMES = ["PICO_OK", "PICO_E_INVALID", "PICO_E_OOM", "PICO_E_CUDA", "PICO_E_TIMEOUT",
+                "PICO_E_BREAKDOWN", "PICO_E_UNSUPPORTED"]
+
+
+class PicoError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        self.status = status
+        name = STATUS_NAMES[status] if 0 <= status < len(STATUS_NAMES) else str(status)
+        super().__init__(f"{name}: {msg}")
+
+
+class pico_operator_desc(ctypes.Structure):
+    _fields_ = [
+        ("kind", ctypes.c_int32), ("ny", ctypes.c_int32), ("nx", ctypes.c_int32), ("ncoils", ctypes.c_int32),
+        ("smaps", ctypes.c_void_p), ("noise_cov", ctypes.c_void_p), ("mask", ctypes.c_void_p),
+        ("mask_2d", ctypes.c_int32), ("traj", ctypes.c_void_p), ("nsamp", ctypes.c_int64),
+        ("oversamp", ctypes.c_float), ("kb_width", ctypes.c_int32), ("lambda_", ctypes.c_double),
+        ("power_iters", ctypes.c_int32), ("power_margin", ctypes.c_double), ("max_batch", ctypes.c_int32),
+        ("max_iter_cap", ctypes.c_int32),
+    ]
+
+
+class pico_info(ctypes.Structure):
+    _fields_ = [
+        ("lambda_max", ctypes.c_double), ("lambda_phys", ctypes.c_double), ("kind", ctypes.c_int32),
+        ("ny", ctypes.c_int32), ("nx", ctypes.c_int32), ("ncoils", ctypes.c_int32), ("max_batch", ctypes.c_int32),
+        ("max_iter_cap", ctypes.c_int32), ("nsamp", ctypes.c_int64), ("device_bytes", ctypes.c_uint64),
+    ]
+
+
+_lib: Optional[ctypes.CDLL] = None
+
+
+def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Load ``libpico.so`` (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"libpico is not built ({path} missing); run paper_2605_09590_gb300.build.build()")
+    lib = ctypes.CDLL(path)
+    vp, i32, i64, u64, f64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64, ctypes.c_double
+    sigs = {
+        "pico_init": ([ctypes.POINTER(pico_operator_desc), vp, ctypes.c_size_t, ctypes.POINTER(vp)], i32),
+        "pico_get_info": ([vp, ctypes.POINTER(pico_info)], i32),
+        "pico_apply_normal": ([vp, vp, vp, i32], i32),
+        "pico_cg_batch": ([vp, vp, vp, i32, i32, f64, vp, vp], i32),
+        "pico_variance_map": ([vp, u64, i64, i32, i32, i32, f64, vp, vp, i32], i32),
+        "pico_pmr": ([vp, u64, i64, i32, f64, i32, f64, vp, vp, i32], i32),
+        "pico_finalize": ([vp, vp, vp, i64, vp, vp], i32),
+        "pico_gfactor": ([vp, vp, vp, f64, vp], i32),
+        "pico_profile": ([vp, i32], i32),
+        "pico_profile_read": ([vp, i32, ctypes.POINTER(f64), ctypes.POINTER(i64)], i32),
+        "pico_launch_count": ([vp, ctypes.POINTER(i64), i32], i32),
+        "pico_sync": ([vp], i32),
+        "pico_last_error": ([vp], ctypes.c_char_p),
+        "pico_destroy": ([vp], None),
+    }
+    for name, (args, res) in sigs.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = res
+    _lib = lib
+    return lib
+
+
+def _check(ctx, st: int):
+    if st != PICO_OK:
+        msg = load_library().pico_last_error(ctx).decode() if ctx else ""
+        raise PicoError(st, msg)
+
+
+def _dev_ptr(t, dtype, what: str) -> int:
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{what} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{what} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{what} must be contiguous")
+    return t.data_ptr()
+
+
+# ----------------------------------------------------------------------------
+# functions with the ABI's names
+# ----------------------------------------------------------------------------
+def pico_init(smaps: np.ndarray, mask: Optional[np.ndarray] = None, noise_cov: Optional[np.ndarray] = None,
+              traj: Optional[np.ndarray] = None, lam: float = 0.0, power_iters: int = 15,
+              power_margin: float = 1.01, max_batch: int = 64, max_iter_cap: int = 128,
+              oversamp: float = 2.0, kb_width: int = 6, stream=None, hbm_budget: int = 0) -> int:
+    """Create a context (returns the opaque handle)."""
+    lib = load_library()
+    S = np.ascontiguousarray(smaps, dtype=np.complex64)
+    nc, ny, nx = S.shape
+    d = pico_operator_desc()
+    d.kind = PICO_SPIRAL if traj is not None else PICO_CARTESIAN
+    d.ny, d.nx, d.ncoils = ny, nx, nc
+    keep = [S]
+    d.smaps = S.ctypes.data
+    if noise_cov is not None:
+        C = np.ascontiguousarray(noise_cov, dtype=np.complex128)
+        keep.append(C)
+        d.noise_cov = C.ctypes.data
+    if mask is not None:
+        m = np.ascontiguousarray(mask, dtype=np.uint8)
+        keep.append(m)
+        d.mask = m.ctypes.data
+        d.mask_2d = 1 if m.ndim == 2 else 0
+    if traj is not None:
+        tr = np.ascontiguousarray(traj, dtype=np.float32)
+        keep.append(tr)
+        d.traj = tr.ctypes.data
+        d.nsamp = tr.shape[0]
+    d.oversamp, d.kb_width = oversamp, kb_width
+    d.lambda_ = lam
+    d.power_iters, d.power_margin = power_iters, power_margin
+    d.max_batch, d.max_iter_cap = max_batch, max_iter_cap
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream().cuda_stream
+    h = ctypes.c_void_p()
+    st = lib.pico_init(ctypes.byref(d), ctypes.c_void_p(stream), hbm_budget, ctypes.byref(h))
+    if st != PICO_OK:
+        msg = lib.pico_last_error(h).decode() if h.value else ""
+        if h.value:
+            lib.pico_destroy(h)
+        raise PicoError(st, msg)
+    return h.value
+
+
+def pico_get_info(ctx) -> dict:
+    info = pico_info()
+    _check(ctx, load_library().pico_get_info(ctx, ctypes.byref(info)))
+    return {f: getattr(info, f) for f, _ in pico_info._fields_}
+
+
+def pico_apply_normal(ctx, x, y) -> None:
+    import torch
+    _check(ctx, load_library().pico_apply_normal(ctx, _dev_ptr(x, torch.complex64, "x"),
+                                                 _dev_ptr(y, torch.complex64, "y"), x.shape[0]))
+
+
+def pico_cg_batch(ctx, rhs, x, max_iter: int, rtol: float = 0.0, stats: bool = False):
+    import torch
+    nb = rhs.shape[0]
+    it = np.zeros(nb, dtype=np.int32) if stats else None
+    rr = np.zeros(nb, dtype=np.float64) if stats else None
+    _check(ctx, load_library().pico_cg_batch(
+        ctx, _dev_ptr(rhs, torch.complex64, "rhs"), _dev_ptr(x, torch.complex64, "x"), nb, max_iter, rtol,
+        it.ctypes.data if stats else None, rr.ctypes.data if stats else None))
+    return (it, rr) if stats else None
+
+
+def pico_variance_map(ctx, seed: int, probe_begin: int, nprobes: int, probe_kind: int, max_iter: int,
+                      rtol: float, sum_, sumsq=None, accumulate: bool = False) -> None:
+    import torch
+    _check(ctx, load_library().pico_variance_map(
+        ctx, seed & (2 ** 64 - 1), probe_begin, nprobes, probe_kind, max_iter, rtol,
+        _dev_ptr(sum_, torch.float64, "sum"), None if sumsq is None else _dev_ptr(sumsq, torch.float64, "sumsq"),
+        1 if accumulate else 0))
+
+
+def pico_pmr(ctx, seed: int, rep_begin: int, nreps: int, sigma: float, max_iter: int, rtol: float, sum_,
+             sumsq=None, accumulate: bool = False) -> None:
+    import torch
+    _check(ctx, load_library().pico_pmr(
+        ctx, seed & (2 ** 64 - 1), rep_begin, nreps, sigma, max_iter, rtol, _dev_ptr(sum_, torch.float64, "sum"),
+        None if sumsq is None else _dev_ptr(sumsq, torch.float64, "sumsq"), 1 if accumulate else 0))
+
+
+def pico_finalize(ctx, sum_, sumsq, count: int, var=None, stderr=None) -> None:
+    import torch
+    _check(ctx, load_library().pico_finalize(
+        ctx, _dev_ptr(sum_, torch.float64, "sum"), None if sumsq is None else _dev_ptr(sumsq, torch.float64, "sumsq"),
+        count, None if var is None else _dev_ptr(var, torch.float32, "var"),
+        None if stderr is None else _dev_ptr(stderr, torch.float32, "stderr")))
+
+
+def pico_gfactor(ctx, var_acc, var_ref, R: float, g) -> None:
+    import torch
+    _check(ctx, load_library().pico_gfactor(ctx, _dev_ptr(var_acc, torch.float32, "var_acc"),
+                                            _dev_ptr(var_ref, torch.float32, "var_ref"), R,
+                                            _dev_ptr(g, torch.float32, "g")))
+
+
+def pico_profile(ctx, enable: bool) -> None:
+    _check(ctx, load_library().pico_profile(ctx, 1 if enable else 0))
+
+
+def pico_profile_read(ctx, kernel_class: int) -> tuple[float, int]:
+    ms, n = ctypes.c_double(), ctypes.c_int64()
+    _check(ctx, load_library().pico_profile_read(ctx, kernel_class, ctypes.byref(ms), ctypes.byref(n)))
+    return ms.value, n.value
+
+
+def pico_launch_count(ctx, reset: bool = False) -> int:
+    n = ctypes.c_int64()
+    _check(ctx, load_library().pico_launch_count(ctx, ctypes.byref(n), 1 if reset else 0))
+    return n.value
+
+
+def pico_sync(ctx) -> None:
+    _check(ctx, load_library().pico_sync(ctx))
+
+
+def pico_last_error(ctx) -> str:
+    return load_library().pico_last_error(ctx).decode()
+
+
+def pico_destroy(ctx) -> None:
+    if ctx:
+        load_library().pico_destroy(ctx)
+
+
+# ----------------------------------------------------------------------------
+# owner object
+# ----------------------------------------------------------------------------
+class Operator:
+    """One acquisition's whitened encoding operator and its GPU workspace."""
+
+    def __init__(self, smaps, mask=None, noise_cov=None, traj=None, **kw):
+        import torch
+        self.torch = torch
+        self.ctx = pico_init(smaps, mask=mask, noise_cov=noise_cov, traj=traj, **kw)
+        self.info = pico_get_info(self.ctx)
+        self.ny, self.nx = self.info["ny"], self.info["nx"]
+
+    def close(self):
+        if self.ctx:
+            pico_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _img(self, nb, dtype=None):
+        t = self.torch
+        return t.empty((nb, self.ny, self.nx), dtype=dtype or t.complex64, device="cuda")
+
+    def apply_normal(self, x):
+        y = self.torch.empty_like(x)
+        pico_apply_normal(self.ctx, x, y)
+        return y
+
+    def cg(self, rhs, max_iter, rtol=0.0, stats=False):
+        x = self.torch.empty_like(rhs)
+        st = pico_cg_batch(self.ctx, rhs, x, max_iter, rtol, stats)
+        return (x, *st) if stats else x
+
+    def variance_sums(self, seed, nprobes, max_iter, rtol=0.0, probe_begin=0, kind=PICO_PROBE_PHASE,
+                      sum_=None, sumsq=None):
+        t = self.torch
+        acc = sum_ is not None
+        if sum_ is None:
+            sum_ = t.empty((self.ny, self.nx), dtype=t.float64, device="cuda")
+            sumsq = t.empty_like(sum_)
+        pico_variance_map(self.ctx, seed, probe_begin, nprobes, kind, max_iter, rtol, sum_, sumsq, acc)
+        return sum_, sumsq
+
+    def pmr_sums(self, seed, nreps, sigma, max_iter, rtol=0.0, rep_begin=0, sum_=None, sumsq=None):
+        t = self.torch
+        acc = sum_ is not None
+        if sum_ is None:
+            sum_ = t.empty((self.ny, self.nx), dtype=t.float64, device="cuda")
+            sumsq = t.empty_like(sum_)
+        pico_pmr(self.ctx, seed, rep_begin, nreps, sigma, max_iter, rtol, sum_, sumsq, acc)
+        return sum_, sumsq
+
+    def finalize(self, sum_, sumsq, count):
+        t = self.torch
+        var = t.empty((self.ny, self.nx), dtype=t.float32, device="cuda")
+        se = t.empty_like(var)
+        pico_finalize(self.ctx, sum_, sumsq, count, var, se)
+        return var, se
+
+    def sync(self):
+        pico_sync(self.ctx)
+
+
+# ----------------------------------------------------------------------------
+# host-side sharding of probes across ranks (one process per GPU)
+# ----------------------------------------------------------------------------
+def shard_range(total: int, world: int, rank: int) -> tuple[int, int]:
+    """Contiguous probe range ``(begin, count)`` of ``rank`` out of ``world``."""
+    base, extra = divmod(total, world)
+    begin = rank * base + min(rank, extra)
+    return begin, base + (1 if rank < extra else 0)

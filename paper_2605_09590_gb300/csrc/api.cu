@@ -1,0 +1,517 @@
+// C-ABI layer of libpico: context management, operator set-up and the
+// stream-ordered drivers of the PICO / PMR / CG hot path.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <complex>
+#include <cstdio>
+#include <algorithm>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "pico.h"
+#include "common.cuh"
+#include "kernels.cuh"
+
+using cd = std::complex<double>;
+
+struct pico_ctx {
+  int kind = 0, ny = 0, nx = 0, nc = 0;
+  int64_t n = 0;
+  cudaStream_t stream = nullptr;
+  double lam_rel = 0, lam_phys = 0, lambda_max = 0, margin = 1.01;
+  int power_iters = 0, max_batch = 64, itmax = 128;
+  // device operator
+  float2* smaps = nullptr;
+  float* ymul = nullptr;
+  float2* tw = nullptr;
+  float2* twx = nullptr;
+  uint8_t* mask = nullptr;
+  // workspace
+  float2 *X = nullptr, *R = nullptr, *P = nullptr, *Q = nullptr;
+  double *rr_part = nullptr, *pq_part = nullptr;
+  int* status = nullptr;
+  int* d_iters = nullptr;
+  double* d_relres = nullptr;
+  double* d_norm = nullptr;
+  float2* G = nullptr;  // PMR hybrid buffer [max_batch][nc][ny][nx], allocated on first use
+  pico::CartOp cop{};
+  pico::CgArgs cg{};
+  size_t device_bytes = 0, budget = 0;
+  std::vector<void*> allocs;
+  std::string err;
+  // launch accounting and optional per-class event timing
+  int64_t launches = 0;
+  bool profiling = false;
+  struct Rec {
+    int cls;
+    cudaEvent_t a, b;
+  };
+  std::vector<Rec> recs;
+  std::vector<cudaEvent_t> event_pool;
+  double prof_ms[4] = {0, 0, 0, 0};
+  int64_t prof_n[4] = {0, 0, 0, 0};
+};
+
+namespace {
+
+pico_status fail(pico_ctx* c, pico_status st, const std::string& msg) {
+  if (c) c->err = msg;
+  return st;
+}
+
+pico_status cuda_check(pico_ctx* c, const char* where) {
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(c, PICO_E_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+  return PICO_OK;
+}
+
+template <typename T>
+pico_status dalloc(pico_ctx* c, T** p, size_t count) {
+  const size_t bytes = count * sizeof(T);
+  if (c->budget && c->device_bytes + bytes > c->budget)
+    return fail(c, PICO_E_OOM, "device footprint exceeds hbm_budget");
+  void* q = nullptr;
+  if (cudaMalloc(&q, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(c, PICO_E_OOM, "cudaMalloc of " + std::to_string(bytes) + " bytes failed");
+  }
+  c->allocs.push_back(q);
+  c->device_bytes += bytes;
+  *p = static_cast<T*>(q);
+  return PICO_OK;
+}
+
+// Cholesky of a Hermitian positive-definite matrix (lower), FP64.
+bool cholesky(std::vector<cd>& a, int n) {
+  for (int j = 0; j < n; ++j) {
+    double d = a[j * n + j].real();
+    for (int k = 0; k < j; ++k) d -= std::norm(a[j * n + k]);
+    if (!(d > 0.0)) return false;
+    d = std::sqrt(d);
+    a[j * n + j] = d;
+    for (int i = j + 1; i < n; ++i) {
+      cd s = a[i * n + j];
+      for (int k = 0; k < j; ++k) s -= a[i * n + k] * std::conj(a[j * n + k]);
+      a[i * n + j] = s / d;
+    }
+    for (int i = 0; i < j; ++i) a[i * n + j] = 0.0;
+  }
+  return true;
+}
+
+// inverse of a lower-triangular matrix by forward substitution
+std::vector<cd> tril_inverse(const std::vector<cd>& L, int n) {
+  std::vector<cd> inv(n * n, 0.0);
+  for (int col = 0; col < n; ++col) {
+    for (int i = 0; i < n; ++i) {
+      cd s = (i == col) ? cd(1.0) : cd(0.0);
+      for (int k = 0; k < i; ++k) s -= L[i * n + k] * inv[k * n + col];
+      inv[i * n + col] = s / L[i * n + i];
+    }
+  }
+  return inv;
+}
+
+std::vector<float2> twiddles(int N) {
+  std::vector<float2> t(N);
+  for (int e = 0; e < N; ++e) {
+    const double a = -2.0 * M_PI * (double)e / (double)N;
+    t[e] = make_float2((float)std::cos(a), (float)std::sin(a));
+  }
+  return t;
+}
+
+constexpr uint64_t kPowerSeed = 0x50574D;  // start vector of the power method
+
+cudaEvent_t take_event(pico_ctx* c) {
+  if (!c->event_pool.empty()) {
+    cudaEvent_t e = c->event_pool.back();
+    c->event_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+// Bracket one kernel launch: count it and, when profiling, time it with events.
+struct Launch {
+  pico_ctx* c;
+  int cls;
+  cudaEvent_t a = nullptr;
+  Launch(pico_ctx* c_, int cls_) : c(c_), cls(cls_) {
+    c->launches++;
+    if (c->profiling) {
+      a = take_event(c);
+      cudaEventRecord(a, c->stream);
+    }
+  }
+  ~Launch() {
+    if (a) {
+      cudaEvent_t b = take_event(c);
+      cudaEventRecord(b, c->stream);
+      c->recs.push_back({cls, a, b});
+    }
+  }
+};
+
+void prof_collect(pico_ctx* c) {
+  if (c->recs.empty()) return;
+  cudaStreamSynchronize(c->stream);
+  for (auto& r : c->recs) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) {
+      c->prof_ms[r.cls] += ms;
+      c->prof_n[r.cls] += 1;
+    }
+    c->event_pool.push_back(r.a);
+    c->event_pool.push_back(r.b);
+  }
+  c->recs.clear();
+}
+
+pico_status run_cg(pico_ctx* c, int nb, int max_iter, double rtol, float lam) {
+  c->cg.rtol2 = rtol * rtol;
+  { Launch L(c, 1); pico::launch_cg_init_rhs(c->cg, nb, c->stream); }
+  for (int it = 0; it < max_iter; ++it) {
+    { Launch L(c, 0); pico::launch_cart_cg_normal(c->cop, c->cg, nb, it, lam, c->stream); }
+    { Launch L(c, 1); pico::launch_cg_update(c->cg, nb, it, c->stream); }
+  }
+  return cuda_check(c, "cg");
+}
+
+pico_status run_cg_from_probe(pico_ctx* c, int nb, int max_iter, double rtol, float lam, uint64_t seed,
+                              int64_t begin, int kind) {
+  c->cg.rtol2 = rtol * rtol;
+  { Launch L(c, 1); pico::launch_cg_init_probe(c->cg, nb, seed, begin, kind, c->stream); }
+  for (int it = 0; it < max_iter; ++it) {
+    { Launch L(c, 0); pico::launch_cart_cg_normal(c->cop, c->cg, nb, it, lam, c->stream); }
+    { Launch L(c, 1); pico::launch_cg_update(c->cg, nb, it, c->stream); }
+  }
+  return cuda_check(c, "cg");
+}
+
+pico_status check_iter(pico_ctx* c, int max_iter, double rtol) {
+  if (max_iter < 0 || max_iter > c->itmax) return fail(c, PICO_E_INVALID, "max_iter outside [0, max_iter_cap]");
+  if (!(rtol >= 0.0)) return fail(c, PICO_E_INVALID, "rtol must be >= 0");
+  return PICO_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+pico_status pico_init(const pico_operator_desc* d, void* cuda_stream, size_t hbm_budget, pico_ctx** out) {
+  if (!out) return PICO_E_INVALID;
+  *out = nullptr;
+  if (!d || !d->smaps) return PICO_E_INVALID;
+  if (d->ny <= 0 || d->nx <= 0 || d->ncoils <= 0) return PICO_E_INVALID;
+  if (d->kind != PICO_CARTESIAN && d->kind != PICO_SPIRAL) return PICO_E_INVALID;
+  if (d->kind == PICO_SPIRAL) return PICO_E_UNSUPPORTED;
+  if (!d->mask) return PICO_E_INVALID;
+  if (d->mask_2d) return PICO_E_UNSUPPORTED;
+  if (d->lambda < 0.0 || d->power_iters < 0 || d->max_batch < 0 || d->max_iter_cap < 0) return PICO_E_INVALID;
+
+  auto* c = new pico_ctx();
+  c->kind = d->kind;
+  c->ny = d->ny;
+  c->nx = d->nx;
+  c->nc = d->ncoils;
+  c->n = (int64_t)d->ny * d->nx;
+  c->stream = (cudaStream_t)cuda_stream;
+  c->lam_rel = d->lambda;
+  c->power_iters = d->power_iters;
+  c->margin = d->power_margin > 0 ? d->power_margin : 1.01;
+  c->max_batch = d->max_batch > 0 ? d->max_batch : 64;
+  c->itmax = d->max_iter_cap > 0 ? d->max_iter_cap : 128;
+  c->budget = hbm_budget;
+
+  int N1, N2, M1, M2;
+  if (!pico::cart_supported(c->ny, c->nx, &N1, &N2, &M1, &M2)) {
+    pico_status st = fail(c, PICO_E_UNSUPPORTED, "ny has no FFT split in this build");
+    *out = c;
+    return st;
+  }
+
+  // footprint check before allocating anything
+  const int64_t n = c->n, B = c->max_batch;
+  const int PB = (int)((n + pico::kVecPerBlock - 1) / pico::kVecPerBlock);
+  const int PA = (c->nx + 15) / 16;
+  const size_t need = (size_t)c->nc * n * 8 + (size_t)4 * B * n * 8 + (size_t)B * (c->itmax + 1) * PB * 8 +
+                      (size_t)B * c->itmax * PA * 8 + (size_t)c->ny * 13 + (size_t)c->nx * 8 + (size_t)B * 16 +
+                      (size_t)PB * 8 + 64;
+  if (hbm_budget && need > hbm_budget) {
+    *out = c;
+    return fail(c, PICO_E_OOM, "operator and workspace need " + std::to_string(need) + " bytes > hbm_budget");
+  }
+
+  // whitening (Eq. 3): S' = L^-1 S with L L^H = Sigma_n
+  const int nc = c->nc;
+  std::vector<float2> S((size_t)nc * n);
+  std::memcpy(S.data(), d->smaps, S.size() * sizeof(float2));
+  if (d->noise_cov) {
+    std::vector<cd> L((size_t)nc * nc);
+    for (int i = 0; i < nc * nc; ++i) L[i] = cd(d->noise_cov[2 * i], d->noise_cov[2 * i + 1]);
+    if (!cholesky(L, nc)) {
+      *out = c;
+      return fail(c, PICO_E_INVALID, "noise_cov is not Hermitian positive definite");
+    }
+    const std::vector<cd> Li = tril_inverse(L, nc);
+    std::vector<float2> W((size_t)nc * n);
+    std::vector<cd> col(nc);
+    for (int64_t v = 0; v < n; ++v) {
+      for (int k = 0; k < nc; ++k) col[k] = cd(S[(size_t)k * n + v].x, S[(size_t)k * n + v].y);
+      for (int i = 0; i < nc; ++i) {
+        cd s = 0.0;
+        for (int k = 0; k <= i; ++k) s += Li[i * nc + k] * col[k];
+        W[(size_t)i * n + v] = make_float2((float)s.real(), (float)s.imag());
+      }
+    }
+    S.swap(W);
+  }
+
+  pico_status st = PICO_OK;
+#define TRY(x)              \
+  if ((st = (x)) != PICO_OK) { \
+    *out = c;               \
+    return st;              \
+  }
+  TRY(dalloc(c, &c->smaps, (size_t)nc * n));
+  TRY(dalloc(c, &c->ymul, (size_t)c->ny));
+  TRY(dalloc(c, &c->tw, (size_t)c->ny));
+  TRY(dalloc(c, &c->twx, (size_t)c->nx));
+  TRY(dalloc(c, &c->mask, (size_t)c->ny));
+  TRY(dalloc(c, &c->X, (size_t)B * n));
+  TRY(dalloc(c, &c->R, (size_t)B * n));
+  TRY(dalloc(c, &c->P, (size_t)B * n));
+  TRY(dalloc(c, &c->Q, (size_t)B * n));
+  TRY(dalloc(c, &c->rr_part, (size_t)B * (c->itmax + 1) * PB));
+  TRY(dalloc(c, &c->pq_part, (size_t)B * c->itmax * PA));
+  TRY(dalloc(c, &c->status, (size_t)B));
+  TRY(dalloc(c, &c->d_iters, (size_t)B));
+  TRY(dalloc(c, &c->d_relres, (size_t)B));
+  TRY(dalloc(c, &c->d_norm, (size_t)PB + 1));
+
+  std::vector<float> ym(c->ny);
+  for (int k = 0; k < c->ny; ++k) ym[k] = d->mask[k] ? (float)(1.0 / c->ny) : 0.f;
+  const std::vector<float2> twy = twiddles(c->ny), twxv = twiddles(c->nx);
+  cudaMemcpyAsync(c->smaps, S.data(), S.size() * sizeof(float2), cudaMemcpyHostToDevice, c->stream);
+  cudaMemcpyAsync(c->ymul, ym.data(), ym.size() * sizeof(float), cudaMemcpyHostToDevice, c->stream);
+  cudaMemcpyAsync(c->tw, twy.data(), twy.size() * sizeof(float2), cudaMemcpyHostToDevice, c->stream);
+  cudaMemcpyAsync(c->twx, twxv.data(), twxv.size() * sizeof(float2), cudaMemcpyHostToDevice, c->stream);
+  cudaMemcpyAsync(c->mask, d->mask, (size_t)c->ny, cudaMemcpyHostToDevice, c->stream);
+  cudaMemsetAsync(c->status, 0, (size_t)B * sizeof(int), c->stream);
+
+  c->cop = pico::CartOp{c->ny, c->nx, nc, N1, N2, c->smaps, c->ymul, c->tw, c->mask, M1, M2, c->twx};
+  c->cg = pico::CgArgs{n, c->X, c->R, c->P, c->Q, c->rr_part, c->pq_part, c->status, PB, PA, c->itmax, 0.0};
+
+  // power method (Sec. 3.3): lambda_max of A^H A from a hash-drawn start vector
+  c->lam_phys = c->lam_rel;
+  if (c->power_iters > 0) {
+    { Launch L(c, 3); pico::launch_fill_probe(c->X, n, kPowerSeed, 0, (float)(1.0 / std::sqrt((double)n)), c->stream); }
+    for (int i = 0; i < c->power_iters; ++i) {
+      { Launch L(c, 0); pico::launch_cart_apply(c->cop, c->X, c->R, 1, 0.f, c->stream); }
+      { Launch L(c, 3); pico::launch_norm2_part(c->R, n, c->d_norm + 1, c->stream); }
+      { Launch L(c, 3); pico::launch_scale_by_norm(c->R, c->X, n, c->d_norm + 1, PB, c->d_norm, c->stream); }
+    }
+    double lmax = 0.0;
+    cudaMemcpyAsync(&lmax, c->d_norm, sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess) {
+      *out = c;
+      return cuda_check(c, "pico_init power method");
+    }
+    c->lambda_max = lmax;
+    c->lam_phys = c->lam_rel * c->margin * lmax;
+  }
+  if (cudaStreamSynchronize(c->stream) != cudaSuccess || (st = cuda_check(c, "pico_init")) != PICO_OK) {
+    *out = c;
+    return st == PICO_OK ? PICO_E_CUDA : st;
+  }
+#undef TRY
+  *out = c;
+  return PICO_OK;
+}
+
+pico_status pico_get_info(const pico_ctx* c, pico_info* info) {
+  if (!c || !info) return PICO_E_INVALID;
+  info->lambda_max = c->lambda_max;
+  info->lambda_phys = c->lam_phys;
+  info->kind = c->kind;
+  info->ny = c->ny;
+  info->nx = c->nx;
+  info->ncoils = c->nc;
+  info->max_batch = c->max_batch;
+  info->max_iter_cap = c->itmax;
+  info->nsamp = 0;
+  info->device_bytes = c->device_bytes;
+  return PICO_OK;
+}
+
+pico_status pico_apply_normal(pico_ctx* c, const void* x, void* y, int32_t nbatch) {
+  if (!c || !c->smaps) return PICO_E_INVALID;
+  if (nbatch < 0 || (nbatch > 0 && (!x || !y))) return fail(c, PICO_E_INVALID, "bad batch or pointer");
+  for (int32_t b0 = 0; b0 < nbatch; b0 += 65535) {
+    const int nb = std::min(65535, nbatch - b0);
+    Launch L(c, 0);
+    pico::launch_cart_apply(c->cop, static_cast<const float2*>(x) + (size_t)b0 * c->n,
+                            static_cast<float2*>(y) + (size_t)b0 * c->n, nb, (float)c->lam_phys, c->stream);
+  }
+  return cuda_check(c, "pico_apply_normal");
+}
+
+pico_status pico_cg_batch(pico_ctx* c, const void* rhs, void* x, int32_t nbatch, int32_t max_iter, double rtol,
+                          int32_t* iters_out, double* relres_out) {
+  if (!c || !c->smaps) return PICO_E_INVALID;
+  if (nbatch < 0 || (nbatch > 0 && (!rhs || !x))) return fail(c, PICO_E_INVALID, "bad batch or pointer");
+  pico_status st = check_iter(c, max_iter, rtol);
+  if (st != PICO_OK) return st;
+  const size_t bytes_img = (size_t)c->n * sizeof(float2);
+  for (int32_t b0 = 0; b0 < nbatch; b0 += c->max_batch) {
+    const int nb = std::min(c->max_batch, nbatch - b0);
+    cudaMemcpyAsync(c->R, static_cast<const char*>(rhs) + (size_t)b0 * bytes_img, (size_t)nb * bytes_img,
+                    cudaMemcpyDeviceToDevice, c->stream);
+    if ((st = run_cg(c, nb, max_iter, rtol, (float)c->lam_phys)) != PICO_OK) return st;
+    cudaMemcpyAsync(static_cast<char*>(x) + (size_t)b0 * bytes_img, c->X, (size_t)nb * bytes_img,
+                    cudaMemcpyDeviceToDevice, c->stream);
+    if (iters_out || relres_out) {
+      { Launch L(c, 3); pico::launch_cg_report(c->cg, nb, max_iter, c->d_iters, c->d_relres, c->stream); }
+      std::vector<int> it(nb);
+      std::vector<double> rr(nb);
+      cudaMemcpyAsync(it.data(), c->d_iters, nb * sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+      cudaMemcpyAsync(rr.data(), c->d_relres, nb * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+      if (cudaStreamSynchronize(c->stream) != cudaSuccess) return cuda_check(c, "pico_cg_batch");
+      for (int i = 0; i < nb; ++i) {
+        if (iters_out) iters_out[b0 + i] = it[i];
+        if (relres_out) relres_out[b0 + i] = rr[i];
+      }
+    }
+  }
+  return cuda_check(c, "pico_cg_batch");
+}
+
+pico_status pico_variance_map(pico_ctx* c, uint64_t seed, int64_t probe_begin, int32_t nprobes, int32_t kind,
+                              int32_t max_iter, double rtol, double* sum, double* sumsq, int32_t accumulate) {
+  if (!c || !c->smaps) return PICO_E_INVALID;
+  if (!sum || nprobes < 0 || probe_begin < 0) return fail(c, PICO_E_INVALID, "bad sum pointer or probe range");
+  if (kind < 0 || kind > 2) return fail(c, PICO_E_INVALID, "unknown probe kind");
+  pico_status st = check_iter(c, max_iter, rtol);
+  if (st != PICO_OK) return st;
+  if (!accumulate) {
+    cudaMemsetAsync(sum, 0, (size_t)c->n * sizeof(double), c->stream);
+    if (sumsq) cudaMemsetAsync(sumsq, 0, (size_t)c->n * sizeof(double), c->stream);
+  }
+  const float lam = (float)c->lam_phys;
+  for (int32_t b0 = 0; b0 < nprobes; b0 += c->max_batch) {
+    const int nb = std::min(c->max_batch, nprobes - b0);
+    if ((st = run_cg_from_probe(c, nb, max_iter, rtol, lam, seed, probe_begin + b0, kind)) != PICO_OK) return st;
+    if (c->lam_phys != 0.0) {
+      // Sigma v = (M + lam)^-1 M (M + lam)^-1 v: apply M to the first solution, solve again
+      { Launch L(c, 0); pico::launch_cart_apply(c->cop, c->X, c->R, nb, 0.f, c->stream); }
+      if ((st = run_cg(c, nb, max_iter, rtol, lam)) != PICO_OK) return st;
+    }
+    { Launch L(c, 3); pico::launch_accum_pico(c->X, c->n, nb, seed, probe_begin + b0, kind, sum, sumsq, c->stream); }
+  }
+  return cuda_check(c, "pico_variance_map");
+}
+
+pico_status pico_pmr(pico_ctx* c, uint64_t seed, int64_t rep_begin, int32_t nreps, double sigma, int32_t max_iter,
+                     double rtol, double* sum, double* sumsq, int32_t accumulate) {
+  if (!c || !c->smaps) return PICO_E_INVALID;
+  if (!sum || nreps < 0 || rep_begin < 0) return fail(c, PICO_E_INVALID, "bad sum pointer or replica range");
+  if (!(sigma > 0.0)) return fail(c, PICO_E_INVALID, "sigma must be > 0");
+  if (c->cop.M1 == 0) return fail(c, PICO_E_UNSUPPORTED, "nx has no FFT split in this build (PMR adjoint)");
+  pico_status st = check_iter(c, max_iter, rtol);
+  if (st != PICO_OK) return st;
+  if (!c->G) {
+    if ((st = dalloc(c, &c->G, (size_t)c->max_batch * c->nc * c->n)) != PICO_OK) return st;
+  }
+  if (!accumulate) {
+    cudaMemsetAsync(sum, 0, (size_t)c->n * sizeof(double), c->stream);
+    if (sumsq) cudaMemsetAsync(sumsq, 0, (size_t)c->n * sizeof(double), c->stream);
+  }
+  const float lam = (float)c->lam_phys;
+  for (int32_t b0 = 0; b0 < nreps; b0 += c->max_batch) {
+    const int nb = std::min(c->max_batch, nreps - b0);
+    { Launch L(c, 2); pico::launch_cart_pmr_cols(c->cop, c->G, nb, seed, rep_begin + b0, (float)sigma, c->stream); }
+    { Launch L(c, 2); pico::launch_cart_rows_adjoint(c->cop, c->G, c->R, nb, c->stream); }
+    if ((st = run_cg(c, nb, max_iter, rtol, lam)) != PICO_OK) return st;
+    { Launch L(c, 3); pico::launch_accum_pmr(c->X, c->n, nb, (float)(1.0 / (sigma * sigma)), sum, sumsq, c->stream); }
+  }
+  return cuda_check(c, "pico_pmr");
+}
+
+pico_status pico_finalize(pico_ctx* c, const double* sum, const double* sumsq, int64_t count, float* var,
+                          float* se) {
+  if (!c || !sum || count <= 0) return c ? fail(c, PICO_E_INVALID, "bad finalize arguments") : PICO_E_INVALID;
+  if (se && !sumsq) return fail(c, PICO_E_INVALID, "stderr needs sumsq");
+  { Launch L(c, 3); pico::launch_finalize(sum, sumsq, c->n, count, var, se, c->stream); }
+  return cuda_check(c, "pico_finalize");
+}
+
+pico_status pico_gfactor(pico_ctx* c, const float* va, const float* vr, double R, float* g) {
+  if (!c || !va || !vr || !g || !(R > 0)) return c ? fail(c, PICO_E_INVALID, "bad gfactor arguments") : PICO_E_INVALID;
+  { Launch L(c, 3); pico::launch_gfactor(va, vr, c->n, R, g, c->stream); }
+  return cuda_check(c, "pico_gfactor");
+}
+
+pico_status pico_sync(pico_ctx* c) {
+  if (!c) return PICO_E_INVALID;
+  if (cudaStreamSynchronize(c->stream) != cudaSuccess) return cuda_check(c, "pico_sync");
+  if (c->status) {
+    std::vector<int> s(c->max_batch);
+    if (cudaMemcpy(s.data(), c->status, s.size() * sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+      return cuda_check(c, "pico_sync");
+    for (int v : s)
+      if (v) {
+        cudaMemset(c->status, 0, s.size() * sizeof(int));
+        return fail(c, PICO_E_BREAKDOWN, "CG breakdown (p^H M p <= 0) in at least one system");
+      }
+  }
+  return cuda_check(c, "pico_sync");
+}
+
+pico_status pico_profile(pico_ctx* c, int32_t enable) {
+  if (!c) return PICO_E_INVALID;
+  prof_collect(c);
+  if (enable) {
+    for (int k = 0; k < 4; ++k) {
+      c->prof_ms[k] = 0;
+      c->prof_n[k] = 0;
+    }
+  }
+  c->profiling = enable != 0;
+  return cuda_check(c, "pico_profile");
+}
+
+pico_status pico_profile_read(pico_ctx* c, int32_t cls, double* total_ms, int64_t* launches) {
+  if (!c || cls < 0 || cls > 3) return PICO_E_INVALID;
+  prof_collect(c);
+  if (total_ms) *total_ms = c->prof_ms[cls];
+  if (launches) *launches = c->prof_n[cls];
+  return cuda_check(c, "pico_profile_read");
+}
+
+pico_status pico_launch_count(pico_ctx* c, int64_t* count, int32_t reset) {
+  if (!c || !count) return PICO_E_INVALID;
+  *count = c->launches;
+  if (reset) c->launches = 0;
+  return PICO_OK;
+}
+
+const char* pico_last_error(const pico_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+void pico_destroy(pico_ctx* c) {
+  if (!c) return;
+  if (!c->allocs.empty()) cudaStreamSynchronize(c->stream);
+  for (auto& r : c->recs) {
+    cudaEventDestroy(r.a);
+    cudaEventDestroy(r.b);
+  }
+  for (cudaEvent_t e : c->event_pool) cudaEventDestroy(e);
+  for (void* p : c->allocs) cudaFree(p);
+  delete c;
+}
+
+}  // extern "C"

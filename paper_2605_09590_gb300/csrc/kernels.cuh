@@ -1,0 +1,73 @@
+// Kernel launch interface shared by the C-ABI layer (api.cu) and the kernel
+// translation units.  Host-side only declarations; no torch types anywhere.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace pico {
+
+// Threads and complex elements per block of the streaming vector kernels.
+constexpr int kVecThreads = 256;
+constexpr int kVecPerThread = 4;
+constexpr int kVecPerBlock = kVecThreads * kVecPerThread;
+
+// Batched CG state (Eq. 6 solved for many right-hand sides at once).
+// Scalars are kept per iteration so that every value is written once:
+// rr(b, it) = sum_j rr_part[(b*(itmax+1) + it)*PB + j]   (r^H r before update it)
+// pq(b, it) = sum_j pq_part[(b*itmax + it)*PA + j]        (p^H (M+lam) p of update it)
+struct CgArgs {
+  int64_t n;         // voxels per image
+  float2* X;         // [B][n] solution
+  float2* R;         // [B][n] residual (holds the right-hand side before init)
+  float2* P;         // [B][n] search direction
+  float2* Q;         // [B][n] (M + lam) P
+  double* rr_part;   // [B][itmax+1][PB]
+  double* pq_part;   // [B][itmax][PA]
+  int* status;       // [B] 0 ok, 5 breakdown
+  int PB, PA, itmax;
+  double rtol2;      // squared relative residual tolerance
+};
+
+// ---- cg.cu ----
+void launch_cg_init_probe(const CgArgs& a, int nb, uint64_t seed, int64_t probe_begin, int kind, cudaStream_t s);
+void launch_cg_init_rhs(const CgArgs& a, int nb, cudaStream_t s);
+void launch_cg_update(const CgArgs& a, int nb, int it, cudaStream_t s);
+void launch_cg_report(const CgArgs& a, int nb, int max_iter, int* iters, double* relres, cudaStream_t s);
+void launch_accum_pico(const float2* X, int64_t n, int nb, uint64_t seed, int64_t probe_begin, int kind,
+                       double* sum, double* sumsq, cudaStream_t s);
+void launch_accum_pmr(const float2* X, int64_t n, int nb, float inv_sigma2, double* sum, double* sumsq,
+                      cudaStream_t s);
+void launch_finalize(const double* sum, const double* sumsq, int64_t n, int64_t count, float* var,
+                     float* stderr_out, cudaStream_t s);
+void launch_gfactor(const float* var_acc, const float* var_ref, int64_t n, double R, float* g, cudaStream_t s);
+void launch_norm2_part(const float2* x, int64_t n, double* part, cudaStream_t s);
+void launch_scale_by_norm(const float2* y, float2* x, int64_t n, const double* part, int nparts,
+                          double* norm_out, cudaStream_t s);
+void launch_fill_probe(float2* x, int64_t n, uint64_t seed, int64_t index, float scale, cudaStream_t s);
+void launch_copy_scaled(const float2* in, float2* out, int64_t n, cudaStream_t s);
+
+// ---- cart.cu: Cartesian column-decoupled operators ----
+struct CartOp {
+  int ny, nx, nc;
+  int N1, N2;               // ny = N1 * N2 split of the column FFT
+  const float2* smaps;      // [nc][ny][nx] whitened sensitivities
+  const float* ymul;        // [ny] mask(ky) / ny
+  const float2* tw;         // [ny] exp(-2 pi i e / ny)
+  const uint8_t* mask;      // [ny]
+  // row transform for the PMR adjoint (length nx)
+  int M1, M2;               // nx = M1 * M2
+  const float2* twx;        // [nx] exp(-2 pi i e / nx)
+};
+bool cart_supported(int ny, int nx, int* N1, int* N2, int* M1, int* M2);
+int cart_col_tiles(const CartOp& op);
+// y = (A^H A + lam I) x for nb images
+void launch_cart_apply(const CartOp& op, const float2* x, float2* y, int nb, float lam, cudaStream_t s);
+// CG iteration `it`, normal-operator half: P = R + beta P; Q = (A^H A + lam) P; pq partials
+void launch_cart_cg_normal(const CartOp& op, const CgArgs& a, int nb, int it, float lam, cudaStream_t s);
+// PMR: G[b][c] = F^H_y (mask . n_{b,c}) (hybrid y, kx), scaled by 1/sqrt(ny nx)
+void launch_cart_pmr_cols(const CartOp& op, float2* G, int nb, uint64_t seed, int64_t rep_begin, float sigma,
+                          cudaStream_t s);
+// out[b] = sum_c conj(S_c) . F^H_x G[b][c]
+void launch_cart_rows_adjoint(const CartOp& op, const float2* G, float2* out, int nb, cudaStream_t s);
+
+}  // namespace pico
