@@ -149,6 +149,33 @@ pico_status pico_finalize(pico_ctx* ctx, const double* sum_dev, const double* su
 pico_status pico_gfactor(pico_ctx* ctx, const float* var_acc_dev, const float* var_ref_dev, double R,
                          float* g_dev);
 
+/* Batched CG-SENSE solve that allocates no device memory.  The paper has no
+ * counterpart: this is an interface for callers that cannot call cudaMalloc
+ * while they run -- code inside a host application that owns all device
+ * memory through its own fixed pool, or that must avoid the allocator's
+ * implicit synchronisation.  It runs the same kernels as pico_cg_batch for a
+ * Cartesian phase-encode mask but needs no context:
+ *   smaps_dev  caller's device complex64 [ncoils][ny][nx] sensitivities,
+ *              already pre-whitened (no noise covariance is applied here)
+ *   mask_dev   caller's device uint8 [ny] phase-encode mask (natural DFT order)
+ *   lam        physical Tikhonov weight added to A^H A
+ *   rhs_dev, x_dev, nbatch, max_iter (<= 128), rtol  as in pico_cg_batch
+ *              (no iteration report)
+ *   cuda_stream  stream the work is enqueued on (NULL = legacy default)
+ * Every temporary lives in one file-scope device array of
+ * pico_cg_batch_static_capacity() bytes (64 MiB) that each GPU loading the
+ * library keeps until the process exits.  A request whose temporaries do not
+ * fit returns PICO_E_INVALID; pico_static_last_error() then states the bytes
+ * needed.  The first call on a device looks the array's address up, so make
+ * one call before any stream capture.  All calls share the array and it keeps
+ * the previous call's contents: calls whose GPU work overlaps (other streams
+ * or threads) race and must be serialised by the caller. */
+pico_status pico_cg_batch_static(const void* smaps_dev, const uint8_t* mask_dev, int32_t ny, int32_t nx,
+                                 int32_t ncoils, double lam, const void* rhs_dev, void* x_dev, int32_t nbatch,
+                                 int32_t max_iter, double rtol, void* cuda_stream);
+size_t pico_cg_batch_static_capacity(void);
+const char* pico_static_last_error(void);
+
 /* Device timing of this context's kernels by class, from CUDA events recorded
  * on the context stream around every launch while profiling is enabled.
  * pico_profile(ctx, 1) clears the totals and starts recording, (ctx, 0) stops.
