@@ -41,8 +41,25 @@ def lambda_phys(op: ops.Operator, lam_rel: float, power_iters: int = 15,
 # Exact covariance (dense, tiny images) -- Eqs. 8-10
 # ----------------------------------------------------------------------------
 def dense_normal(op: ops.Operator) -> np.ndarray:
-    A = op.matrix()
-    return A.conj().T @ A
+    """Dense ``M = A^H A``.  Cartesian: from the explicit encoding matrix.
+    Spiral: ``M[r, r'] = sum_c conj(S_c[r]) S_c[r'] h(r - r')`` with the NUDFT
+    point-spread function ``h(d) = (1/n^2) sum_m exp(+2 pi i k_m . d / n)``
+    (the entries of ``E^H E`` written out), which avoids forming ``A``."""
+    if op.kind != "spiral":
+        A = op.matrix()
+        return A.conj().T @ A
+    n = op.ny
+    k = np.asarray(op.traj, dtype=np.float64)
+    d = np.arange(-(n - 1), n, dtype=np.float64)
+    ex = np.exp(2j * np.pi * np.outer(k[:, 0], d) / n)          # [M][dx]
+    ey = np.exp(2j * np.pi * np.outer(k[:, 1], d) / n)          # [M][dy]
+    h = (ey.T @ ex) / n ** 2                                     # h[dy + n-1, dx + n-1]
+    yy, xx = np.meshgrid(np.arange(n), np.arange(n), indexing="ij")
+    ry, rx = yy.reshape(-1), xx.reshape(-1)
+    H = h[(ry[:, None] - ry[None, :]) + n - 1, (rx[:, None] - rx[None, :]) + n - 1]
+    Sf = op.S.reshape(op.nc, -1)
+    G = np.einsum("cr,cs->rs", np.conj(Sf), Sf)
+    return G * H
 
 
 def dense_cov(M: np.ndarray, lam: float = 0.0) -> np.ndarray:

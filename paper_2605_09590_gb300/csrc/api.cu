@@ -35,8 +35,21 @@ struct pico_ctx {
   int* d_iters = nullptr;
   double* d_relres = nullptr;
   double* d_norm = nullptr;
-  float2* G = nullptr;  // PMR hybrid buffer [max_batch][nc][ny][nx], allocated on first use
+  float2* G = nullptr;  // PMR buffer, allocated on first use: Cartesian hybrid [B][nc][ny][nx],
+                        // spiral gridded noise [B][nc][2n][2n]
   pico::CartOp cop{};
+  // spiral operator
+  pico::SpiralOp sop{};
+  float* That = nullptr;
+  float* deapod = nullptr;
+  float2* tw2 = nullptr;
+  float2* u = nullptr;
+  float2* cphase = nullptr;
+  int* tile_ptr = nullptr;
+  int* tile_idx = nullptr;
+  float* traj = nullptr;
+  int64_t nsamp = 0;
+  float2* Gt = nullptr;  // Toeplitz intermediates [B][nc][n][2n]
   pico::CgArgs cg{};
   size_t device_bytes = 0, budget = 0;
   std::vector<void*> allocs;
@@ -141,8 +154,8 @@ struct Launch {
   pico_ctx* c;
   int cls;
   cudaEvent_t a = nullptr;
-  Launch(pico_ctx* c_, int cls_) : c(c_), cls(cls_) {
-    c->launches++;
+  Launch(pico_ctx* c_, int cls_, int kernels = 1) : c(c_), cls(cls_) {
+    c->launches += kernels;
     if (c->profiling) {
       a = take_event(c);
       cudaEventRecord(a, c->stream);
@@ -172,11 +185,33 @@ void prof_collect(pico_ctx* c) {
   c->recs.clear();
 }
 
+// (A^H A + lam) x for nb images (class 0)
+void op_apply(pico_ctx* c, const float2* x, float2* y, int nb, float lam) {
+  if (c->kind == PICO_CARTESIAN) {
+    Launch L(c, 0);
+    pico::launch_cart_apply(c->cop, x, y, nb, lam, c->stream);
+  } else {
+    Launch L(c, 0, 3);
+    pico::launch_toep_apply(c->sop, x, y, c->Gt, nb, lam, c->stream);
+  }
+}
+
+// CG iteration `it`, operator half (class 0)
+void op_cg_normal(pico_ctx* c, int nb, int it, float lam) {
+  if (c->kind == PICO_CARTESIAN) {
+    Launch L(c, 0);
+    pico::launch_cart_cg_normal(c->cop, c->cg, nb, it, lam, c->stream);
+  } else {
+    Launch L(c, 0, 3);
+    pico::launch_toep_cg_normal(c->sop, c->cg, c->Gt, nb, it, lam, c->stream);
+  }
+}
+
 pico_status run_cg(pico_ctx* c, int nb, int max_iter, double rtol, float lam) {
   c->cg.rtol2 = rtol * rtol;
   { Launch L(c, 1); pico::launch_cg_init_rhs(c->cg, nb, c->stream); }
   for (int it = 0; it < max_iter; ++it) {
-    { Launch L(c, 0); pico::launch_cart_cg_normal(c->cop, c->cg, nb, it, lam, c->stream); }
+    op_cg_normal(c, nb, it, lam);
     { Launch L(c, 1); pico::launch_cg_update(c->cg, nb, it, c->stream); }
   }
   return cuda_check(c, "cg");
@@ -187,7 +222,7 @@ pico_status run_cg_from_probe(pico_ctx* c, int nb, int max_iter, double rtol, fl
   c->cg.rtol2 = rtol * rtol;
   { Launch L(c, 1); pico::launch_cg_init_probe(c->cg, nb, seed, begin, kind, c->stream); }
   for (int it = 0; it < max_iter; ++it) {
-    { Launch L(c, 0); pico::launch_cart_cg_normal(c->cop, c->cg, nb, it, lam, c->stream); }
+    op_cg_normal(c, nb, it, lam);
     { Launch L(c, 1); pico::launch_cg_update(c->cg, nb, it, c->stream); }
   }
   return cuda_check(c, "cg");
@@ -197,6 +232,117 @@ pico_status check_iter(pico_ctx* c, int max_iter, double rtol) {
   if (max_iter < 0 || max_iter > c->itmax) return fail(c, PICO_E_INVALID, "max_iter outside [0, max_iter_cap]");
   if (!(rtol >= 0.0)) return fail(c, PICO_E_INVALID, "rtol must be >= 0");
   return PICO_OK;
+}
+
+
+// I0(x) by its power series sum_k (x^2/4)^k / (k!)^2 (FP64; x < 30 here)
+double bessel_i0(double x) {
+  const double q = 0.25 * x * x;
+  double term = 1.0, sum = 1.0;
+  for (int k = 1; k < 200; ++k) {
+    term *= q / ((double)k * (double)k);
+    sum += term;
+    if (term < 1e-17 * sum) break;
+  }
+  return sum;
+}
+
+// Spiral operator set-up: trajectory, gridding bins, deapodisation, twiddles,
+// and the Toeplitz kernel T^ = DFT_2N(h) / ((2N)^2 N^2) computed on the device.
+pico_status spiral_setup(pico_ctx* c, const pico_operator_desc* d, int img, int L, int P1, int P2, int kbw) {
+  const int64_t M = c->nsamp;
+  const int nc = c->nc;
+  pico_status st = PICO_OK;
+  if ((st = dalloc(c, &c->traj, (size_t)2 * M)) != PICO_OK) return st;
+  if ((st = dalloc(c, &c->u, (size_t)M)) != PICO_OK) return st;
+  if ((st = dalloc(c, &c->cphase, (size_t)M)) != PICO_OK) return st;
+  if ((st = dalloc(c, &c->That, (size_t)L * L)) != PICO_OK) return st;
+  if ((st = dalloc(c, &c->deapod, (size_t)img)) != PICO_OK) return st;
+  if ((st = dalloc(c, &c->tw2, (size_t)L)) != PICO_OK) return st;
+  // Toeplitz intermediates; also holds the (2N)^2 kernel during set-up
+  if ((st = dalloc(c, &c->Gt, std::max((size_t)c->max_batch * nc * img * L, (size_t)L * L))) != PICO_OK) return st;
+
+  // sample positions on the 2N grid (u = 2k), image-centre phase e^{i pi (kx + ky)}
+  const double hw = 0.5 * kbw;
+  const int tiles_x = L / 16, ntiles = tiles_x * tiles_x;
+  std::vector<float2> u(M), ph(M);
+  std::vector<int> cnt(ntiles + 1, 0);
+  std::vector<std::vector<int>> touch(M);
+  for (int64_t m = 0; m < M; ++m) {
+    const double kx = d->traj[2 * m], ky = d->traj[2 * m + 1];
+    if (!std::isfinite(kx) || !std::isfinite(ky)) return fail(c, PICO_E_INVALID, "non-finite trajectory sample");
+    u[m] = make_float2((float)(2.0 * kx), (float)(2.0 * ky));
+    const double a = M_PI * (kx + ky);
+    ph[m] = make_float2((float)std::cos(a), (float)std::sin(a));
+    // grid tiles within the kernel half-width (conservative by 1e-3 grid units)
+    const double ux = 2.0 * kx, uy = 2.0 * ky;
+    int tx[4], ty[4], ntx = 0, nty = 0;
+    for (int g = (int)std::floor(ux - hw - 1e-3); g <= (int)std::ceil(ux + hw + 1e-3); ++g) {
+      const int t = (((g % L) + L) % L) / 16;
+      bool seen = false;
+      for (int i = 0; i < ntx; ++i) seen |= tx[i] == t;
+      if (!seen && ntx < 4) tx[ntx++] = t;
+    }
+    for (int g = (int)std::floor(uy - hw - 1e-3); g <= (int)std::ceil(uy + hw + 1e-3); ++g) {
+      const int t = (((g % L) + L) % L) / 16;
+      bool seen = false;
+      for (int i = 0; i < nty; ++i) seen |= ty[i] == t;
+      if (!seen && nty < 4) ty[nty++] = t;
+    }
+    for (int i = 0; i < nty; ++i)
+      for (int j = 0; j < ntx; ++j) {
+        touch[m].push_back(ty[i] * tiles_x + tx[j]);
+        cnt[ty[i] * tiles_x + tx[j] + 1]++;
+      }
+  }
+  for (int t = 0; t < ntiles; ++t) cnt[t + 1] += cnt[t];
+  std::vector<int> idx(cnt[ntiles]);
+  std::vector<int> fillp(cnt.begin(), cnt.end() - 1);
+  for (int64_t m = 0; m < M; ++m)
+    for (int t : touch[m]) idx[fillp[t]++] = (int)m;  // increasing sample order inside each tile
+  if ((st = dalloc(c, &c->tile_ptr, (size_t)ntiles + 1)) != PICO_OK) return st;
+  if ((st = dalloc(c, &c->tile_idx, std::max<size_t>(1, idx.size()))) != PICO_OK) return st;
+
+  // Kaiser-Bessel kernel phi(t) = I0(beta sqrt(1 - (2t/W)^2)) / I0(beta) and its
+  // Fourier transform phi^(nu) = W sinh(z)/z / I0(beta), z = sqrt(beta^2 - (pi W nu)^2)
+  const double os = 2.0;
+  const double beta = M_PI * std::sqrt((kbw / os) * (kbw / os) * (os - 0.5) * (os - 0.5) - 0.8);
+  const double i0b = bessel_i0(beta);
+  std::vector<float> dap(img);
+  for (int x = 0; x < img; ++x) {
+    const double nu = (double)(x - img / 2) / (double)L;
+    const double z2 = beta * beta - (M_PI * kbw * nu) * (M_PI * kbw * nu);
+    double ft;
+    if (z2 > 0) {
+      const double z = std::sqrt(z2);
+      ft = kbw * std::sinh(z) / z;
+    } else {
+      const double z = std::sqrt(-z2);
+      ft = z > 0 ? kbw * std::sin(z) / z : (double)kbw;
+    }
+    dap[x] = (float)(1.0 / ((ft / i0b) * std::sqrt((double)img)));
+  }
+  const std::vector<float2> tw = twiddles(L);
+  cudaMemcpyAsync(c->traj, d->traj, (size_t)2 * M * sizeof(float), cudaMemcpyHostToDevice, c->stream);
+  cudaMemcpyAsync(c->u, u.data(), (size_t)M * sizeof(float2), cudaMemcpyHostToDevice, c->stream);
+  cudaMemcpyAsync(c->cphase, ph.data(), (size_t)M * sizeof(float2), cudaMemcpyHostToDevice, c->stream);
+  cudaMemcpyAsync(c->tile_ptr, cnt.data(), cnt.size() * sizeof(int), cudaMemcpyHostToDevice, c->stream);
+  if (!idx.empty())
+    cudaMemcpyAsync(c->tile_idx, idx.data(), idx.size() * sizeof(int), cudaMemcpyHostToDevice, c->stream);
+  cudaMemcpyAsync(c->deapod, dap.data(), dap.size() * sizeof(float), cudaMemcpyHostToDevice, c->stream);
+  cudaMemcpyAsync(c->tw2, tw.data(), tw.size() * sizeof(float2), cudaMemcpyHostToDevice, c->stream);
+
+  c->sop = pico::SpiralOp{img,      L,         nc,         P1,          P2,           c->smaps,
+                          c->tw2,   c->That,   c->deapod,  M,           c->u,         c->cphase,
+                          c->tile_ptr, c->tile_idx, (float)beta, (float)hw, (float)(1.0 / i0b)};
+  // Toeplitz kernel: h on the 2N grid (in the Toeplitz buffer), 2-D DFT, real part, scale
+  float2* cbuf = c->Gt;  // max_batch * nc * N * 2N >= (2N)^2 complex values
+  { Launch Lh(c, 3); pico::launch_toep_h(c->traj, M, img, cbuf, c->stream); }
+  { Launch Lf(c, 3, 2); pico::launch_toep_fft2(c->sop, cbuf, c->stream); }
+  const double scale = 1.0 / ((double)img * img * (double)L * L);
+  { Launch Lz(c, 3); pico::launch_toep_finalize(cbuf, L, (float)scale, c->That, c->stream); }
+  if (cudaStreamSynchronize(c->stream) != cudaSuccess) return cuda_check(c, "spiral set-up");
+  return cuda_check(c, "spiral set-up");
 }
 
 }  // namespace
@@ -209,12 +355,13 @@ pico_status pico_init(const pico_operator_desc* d, void* cuda_stream, size_t hbm
   if (!d || !d->smaps) return PICO_E_INVALID;
   if (d->ny <= 0 || d->nx <= 0 || d->ncoils <= 0) return PICO_E_INVALID;
   if (d->kind != PICO_CARTESIAN && d->kind != PICO_SPIRAL) return PICO_E_INVALID;
-  if (d->kind == PICO_SPIRAL) return PICO_E_UNSUPPORTED;
-  if (!d->mask) return PICO_E_INVALID;
-  if (d->mask_2d) return PICO_E_UNSUPPORTED;
+  if (d->kind == PICO_CARTESIAN && !d->mask) return PICO_E_INVALID;
+  if (d->kind == PICO_CARTESIAN && d->mask_2d) return PICO_E_UNSUPPORTED;
+  if (d->kind == PICO_SPIRAL && (!d->traj || d->nsamp <= 0 || d->nsamp > (int64_t)1 << 30)) return PICO_E_INVALID;
   if (d->lambda < 0.0 || d->power_iters < 0 || d->max_batch < 0 || d->max_iter_cap < 0) return PICO_E_INVALID;
 
   auto* c = new pico_ctx();
+  *out = c;
   c->kind = d->kind;
   c->ny = d->ny;
   c->nx = d->nx;
@@ -227,62 +374,65 @@ pico_status pico_init(const pico_operator_desc* d, void* cuda_stream, size_t hbm
   c->max_batch = d->max_batch > 0 ? d->max_batch : 64;
   c->itmax = d->max_iter_cap > 0 ? d->max_iter_cap : 128;
   c->budget = hbm_budget;
+  const int nc = c->nc;
+  const int64_t n = c->n, B = c->max_batch;
+  const int PB = (int)((n + pico::kVecPerBlock - 1) / pico::kVecPerBlock);
 
-  int N1, N2, M1, M2;
-  if (!pico::cart_supported(c->ny, c->nx, &N1, &N2, &M1, &M2)) {
-    pico_status st = fail(c, PICO_E_UNSUPPORTED, "ny has no FFT split in this build");
-    *out = c;
-    return st;
+  int N1 = 0, N2 = 0, M1 = 0, M2 = 0, P1 = 0, P2 = 0;
+  int PA = 0;
+  const int img = c->ny;  // spiral images are square
+  const int L = 2 * img;
+  const int kbw = d->kb_width > 0 ? d->kb_width : 6;
+  const double os = d->oversamp > 0 ? (double)d->oversamp : 2.0;
+  size_t extra = 0;
+  if (c->kind == PICO_CARTESIAN) {
+    if (!pico::cart_supported(c->ny, c->nx, &N1, &N2, &M1, &M2))
+      return fail(c, PICO_E_UNSUPPORTED, "ny has no FFT split in this build");
+    PA = (c->nx + 15) / 16;
+    extra = (size_t)c->ny * 13 + (size_t)c->nx * 8;
+  } else {
+    if (c->ny != c->nx) return fail(c, PICO_E_UNSUPPORTED, "spiral images must be square");
+    if (os != 2.0) return fail(c, PICO_E_UNSUPPORTED, "spiral gridding supports oversampling 2.0 only");
+    if (kbw < 2 || kbw > 8 || (kbw & 1)) return fail(c, PICO_E_UNSUPPORTED, "kb_width must be 2, 4, 6 or 8");
+    if (!pico::spiral_supported(img, &P1, &P2))
+      return fail(c, PICO_E_UNSUPPORTED, "spiral image size has no 2N grid split in this build");
+    PA = (img + 15) / 16;
+    c->nsamp = d->nsamp;
+    extra = std::max((size_t)B * nc * img * L, (size_t)L * L) * 8 + (size_t)L * L * 4 + (size_t)img * 4 + (size_t)L * 8 +
+            (size_t)c->nsamp * (8 + 8 + 8 + 16) + (size_t)(L / 16) * (L / 16) * 4 + 64;
   }
 
   // footprint check before allocating anything
-  const int64_t n = c->n, B = c->max_batch;
-  const int PB = (int)((n + pico::kVecPerBlock - 1) / pico::kVecPerBlock);
-  const int PA = (c->nx + 15) / 16;
-  const size_t need = (size_t)c->nc * n * 8 + (size_t)4 * B * n * 8 + (size_t)B * (c->itmax + 1) * PB * 8 +
-                      (size_t)B * c->itmax * PA * 8 + (size_t)c->ny * 13 + (size_t)c->nx * 8 + (size_t)B * 16 +
-                      (size_t)PB * 8 + 64;
-  if (hbm_budget && need > hbm_budget) {
-    *out = c;
+  const size_t need = (size_t)nc * n * 8 + (size_t)4 * B * n * 8 + (size_t)B * (c->itmax + 1) * PB * 8 +
+                      (size_t)B * c->itmax * PA * 8 + (size_t)B * 16 + (size_t)PB * 8 + 64 + extra;
+  if (hbm_budget && need > hbm_budget)
     return fail(c, PICO_E_OOM, "operator and workspace need " + std::to_string(need) + " bytes > hbm_budget");
-  }
 
   // whitening (Eq. 3): S' = L^-1 S with L L^H = Sigma_n
-  const int nc = c->nc;
   std::vector<float2> S((size_t)nc * n);
   std::memcpy(S.data(), d->smaps, S.size() * sizeof(float2));
   if (d->noise_cov) {
-    std::vector<cd> L((size_t)nc * nc);
-    for (int i = 0; i < nc * nc; ++i) L[i] = cd(d->noise_cov[2 * i], d->noise_cov[2 * i + 1]);
-    if (!cholesky(L, nc)) {
-      *out = c;
-      return fail(c, PICO_E_INVALID, "noise_cov is not Hermitian positive definite");
-    }
-    const std::vector<cd> Li = tril_inverse(L, nc);
+    std::vector<cd> Lc((size_t)nc * nc);
+    for (int i = 0; i < nc * nc; ++i) Lc[i] = cd(d->noise_cov[2 * i], d->noise_cov[2 * i + 1]);
+    if (!cholesky(Lc, nc)) return fail(c, PICO_E_INVALID, "noise_cov is not Hermitian positive definite");
+    const std::vector<cd> Li = tril_inverse(Lc, nc);
     std::vector<float2> W((size_t)nc * n);
     std::vector<cd> col(nc);
     for (int64_t v = 0; v < n; ++v) {
       for (int k = 0; k < nc; ++k) col[k] = cd(S[(size_t)k * n + v].x, S[(size_t)k * n + v].y);
       for (int i = 0; i < nc; ++i) {
-        cd s = 0.0;
-        for (int k = 0; k <= i; ++k) s += Li[i * nc + k] * col[k];
-        W[(size_t)i * n + v] = make_float2((float)s.real(), (float)s.imag());
+        cd acc = 0.0;
+        for (int k = 0; k <= i; ++k) acc += Li[i * nc + k] * col[k];
+        W[(size_t)i * n + v] = make_float2((float)acc.real(), (float)acc.imag());
       }
     }
     S.swap(W);
   }
 
   pico_status st = PICO_OK;
-#define TRY(x)              \
-  if ((st = (x)) != PICO_OK) { \
-    *out = c;               \
-    return st;              \
-  }
+#define TRY(x) \
+  if ((st = (x)) != PICO_OK) return st;
   TRY(dalloc(c, &c->smaps, (size_t)nc * n));
-  TRY(dalloc(c, &c->ymul, (size_t)c->ny));
-  TRY(dalloc(c, &c->tw, (size_t)c->ny));
-  TRY(dalloc(c, &c->twx, (size_t)c->nx));
-  TRY(dalloc(c, &c->mask, (size_t)c->ny));
   TRY(dalloc(c, &c->X, (size_t)B * n));
   TRY(dalloc(c, &c->R, (size_t)B * n));
   TRY(dalloc(c, &c->P, (size_t)B * n));
@@ -293,44 +443,47 @@ pico_status pico_init(const pico_operator_desc* d, void* cuda_stream, size_t hbm
   TRY(dalloc(c, &c->d_iters, (size_t)B));
   TRY(dalloc(c, &c->d_relres, (size_t)B));
   TRY(dalloc(c, &c->d_norm, (size_t)PB + 1));
-
-  std::vector<float> ym(c->ny);
-  for (int k = 0; k < c->ny; ++k) ym[k] = d->mask[k] ? (float)(1.0 / c->ny) : 0.f;
-  const std::vector<float2> twy = twiddles(c->ny), twxv = twiddles(c->nx);
   cudaMemcpyAsync(c->smaps, S.data(), S.size() * sizeof(float2), cudaMemcpyHostToDevice, c->stream);
-  cudaMemcpyAsync(c->ymul, ym.data(), ym.size() * sizeof(float), cudaMemcpyHostToDevice, c->stream);
-  cudaMemcpyAsync(c->tw, twy.data(), twy.size() * sizeof(float2), cudaMemcpyHostToDevice, c->stream);
-  cudaMemcpyAsync(c->twx, twxv.data(), twxv.size() * sizeof(float2), cudaMemcpyHostToDevice, c->stream);
-  cudaMemcpyAsync(c->mask, d->mask, (size_t)c->ny, cudaMemcpyHostToDevice, c->stream);
   cudaMemsetAsync(c->status, 0, (size_t)B * sizeof(int), c->stream);
-
-  c->cop = pico::CartOp{c->ny, c->nx, nc, N1, N2, c->smaps, c->ymul, c->tw, c->mask, M1, M2, c->twx};
   c->cg = pico::CgArgs{n, c->X, c->R, c->P, c->Q, c->rr_part, c->pq_part, c->status, PB, PA, c->itmax, 0.0};
+
+  if (c->kind == PICO_CARTESIAN) {
+    TRY(dalloc(c, &c->ymul, (size_t)c->ny));
+    TRY(dalloc(c, &c->tw, (size_t)c->ny));
+    TRY(dalloc(c, &c->twx, (size_t)c->nx));
+    TRY(dalloc(c, &c->mask, (size_t)c->ny));
+    std::vector<float> ym(c->ny);
+    for (int k = 0; k < c->ny; ++k) ym[k] = d->mask[k] ? (float)(1.0 / c->ny) : 0.f;
+    const std::vector<float2> twy = twiddles(c->ny), twxv = twiddles(c->nx);
+    cudaMemcpyAsync(c->ymul, ym.data(), ym.size() * sizeof(float), cudaMemcpyHostToDevice, c->stream);
+    cudaMemcpyAsync(c->tw, twy.data(), twy.size() * sizeof(float2), cudaMemcpyHostToDevice, c->stream);
+    cudaMemcpyAsync(c->twx, twxv.data(), twxv.size() * sizeof(float2), cudaMemcpyHostToDevice, c->stream);
+    cudaMemcpyAsync(c->mask, d->mask, (size_t)c->ny, cudaMemcpyHostToDevice, c->stream);
+    c->cop = pico::CartOp{c->ny, c->nx, nc, N1, N2, c->smaps, c->ymul, c->tw, c->mask, M1, M2, c->twx};
+    // the host vectors above must outlive the asynchronous copies
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess) return cuda_check(c, "pico_init upload");
+  } else {
+    TRY(spiral_setup(c, d, img, L, P1, P2, kbw));
+  }
 
   // power method (Sec. 3.3): lambda_max of A^H A from a hash-drawn start vector
   c->lam_phys = c->lam_rel;
   if (c->power_iters > 0) {
     { Launch L(c, 3); pico::launch_fill_probe(c->X, n, kPowerSeed, 0, (float)(1.0 / std::sqrt((double)n)), c->stream); }
     for (int i = 0; i < c->power_iters; ++i) {
-      { Launch L(c, 0); pico::launch_cart_apply(c->cop, c->X, c->R, 1, 0.f, c->stream); }
+      op_apply(c, c->X, c->R, 1, 0.f);
       { Launch L(c, 3); pico::launch_norm2_part(c->R, n, c->d_norm + 1, c->stream); }
       { Launch L(c, 3); pico::launch_scale_by_norm(c->R, c->X, n, c->d_norm + 1, PB, c->d_norm, c->stream); }
     }
     double lmax = 0.0;
     cudaMemcpyAsync(&lmax, c->d_norm, sizeof(double), cudaMemcpyDeviceToHost, c->stream);
-    if (cudaStreamSynchronize(c->stream) != cudaSuccess) {
-      *out = c;
-      return cuda_check(c, "pico_init power method");
-    }
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess) return cuda_check(c, "pico_init power method");
     c->lambda_max = lmax;
     c->lam_phys = c->lam_rel * c->margin * lmax;
   }
-  if (cudaStreamSynchronize(c->stream) != cudaSuccess || (st = cuda_check(c, "pico_init")) != PICO_OK) {
-    *out = c;
-    return st == PICO_OK ? PICO_E_CUDA : st;
-  }
+  if (cudaStreamSynchronize(c->stream) != cudaSuccess) return cuda_check(c, "pico_init");
+  if ((st = cuda_check(c, "pico_init")) != PICO_OK) return st;
 #undef TRY
-  *out = c;
   return PICO_OK;
 }
 
@@ -344,7 +497,7 @@ pico_status pico_get_info(const pico_ctx* c, pico_info* info) {
   info->ncoils = c->nc;
   info->max_batch = c->max_batch;
   info->max_iter_cap = c->itmax;
-  info->nsamp = 0;
+  info->nsamp = c->nsamp;
   info->device_bytes = c->device_bytes;
   return PICO_OK;
 }
@@ -352,11 +505,11 @@ pico_status pico_get_info(const pico_ctx* c, pico_info* info) {
 pico_status pico_apply_normal(pico_ctx* c, const void* x, void* y, int32_t nbatch) {
   if (!c || !c->smaps) return PICO_E_INVALID;
   if (nbatch < 0 || (nbatch > 0 && (!x || !y))) return fail(c, PICO_E_INVALID, "bad batch or pointer");
-  for (int32_t b0 = 0; b0 < nbatch; b0 += 65535) {
-    const int nb = std::min(65535, nbatch - b0);
-    Launch L(c, 0);
-    pico::launch_cart_apply(c->cop, static_cast<const float2*>(x) + (size_t)b0 * c->n,
-                            static_cast<float2*>(y) + (size_t)b0 * c->n, nb, (float)c->lam_phys, c->stream);
+  const int chunk = c->kind == PICO_CARTESIAN ? 65535 : c->max_batch;
+  for (int32_t b0 = 0; b0 < nbatch; b0 += chunk) {
+    const int nb = std::min(chunk, nbatch - b0);
+    op_apply(c, static_cast<const float2*>(x) + (size_t)b0 * c->n, static_cast<float2*>(y) + (size_t)b0 * c->n, nb,
+             (float)c->lam_phys);
   }
   return cuda_check(c, "pico_apply_normal");
 }
@@ -408,7 +561,7 @@ pico_status pico_variance_map(pico_ctx* c, uint64_t seed, int64_t probe_begin, i
     if ((st = run_cg_from_probe(c, nb, max_iter, rtol, lam, seed, probe_begin + b0, kind)) != PICO_OK) return st;
     if (c->lam_phys != 0.0) {
       // Sigma v = (M + lam)^-1 M (M + lam)^-1 v: apply M to the first solution, solve again
-      { Launch L(c, 0); pico::launch_cart_apply(c->cop, c->X, c->R, nb, 0.f, c->stream); }
+      op_apply(c, c->X, c->R, nb, 0.f);
       if ((st = run_cg(c, nb, max_iter, rtol, lam)) != PICO_OK) return st;
     }
     { Launch L(c, 3); pico::launch_accum_pico(c->X, c->n, nb, seed, probe_begin + b0, kind, sum, sumsq, c->stream); }
@@ -421,11 +574,13 @@ pico_status pico_pmr(pico_ctx* c, uint64_t seed, int64_t rep_begin, int32_t nrep
   if (!c || !c->smaps) return PICO_E_INVALID;
   if (!sum || nreps < 0 || rep_begin < 0) return fail(c, PICO_E_INVALID, "bad sum pointer or replica range");
   if (!(sigma > 0.0)) return fail(c, PICO_E_INVALID, "sigma must be > 0");
-  if (c->cop.M1 == 0) return fail(c, PICO_E_UNSUPPORTED, "nx has no FFT split in this build (PMR adjoint)");
+  if (c->kind == PICO_CARTESIAN && c->cop.M1 == 0)
+    return fail(c, PICO_E_UNSUPPORTED, "nx has no FFT split in this build (PMR adjoint)");
   pico_status st = check_iter(c, max_iter, rtol);
   if (st != PICO_OK) return st;
   if (!c->G) {
-    if ((st = dalloc(c, &c->G, (size_t)c->max_batch * c->nc * c->n)) != PICO_OK) return st;
+    const size_t per = c->kind == PICO_CARTESIAN ? (size_t)c->n : (size_t)4 * c->n;
+    if ((st = dalloc(c, &c->G, (size_t)c->max_batch * c->nc * per)) != PICO_OK) return st;
   }
   if (!accumulate) {
     cudaMemsetAsync(sum, 0, (size_t)c->n * sizeof(double), c->stream);
@@ -434,8 +589,13 @@ pico_status pico_pmr(pico_ctx* c, uint64_t seed, int64_t rep_begin, int32_t nrep
   const float lam = (float)c->lam_phys;
   for (int32_t b0 = 0; b0 < nreps; b0 += c->max_batch) {
     const int nb = std::min(c->max_batch, nreps - b0);
-    { Launch L(c, 2); pico::launch_cart_pmr_cols(c->cop, c->G, nb, seed, rep_begin + b0, (float)sigma, c->stream); }
-    { Launch L(c, 2); pico::launch_cart_rows_adjoint(c->cop, c->G, c->R, nb, c->stream); }
+    if (c->kind == PICO_CARTESIAN) {
+      { Launch L(c, 2); pico::launch_cart_pmr_cols(c->cop, c->G, nb, seed, rep_begin + b0, (float)sigma, c->stream); }
+      { Launch L(c, 2); pico::launch_cart_rows_adjoint(c->cop, c->G, c->R, nb, c->stream); }
+    } else {
+      { Launch L(c, 2); pico::launch_grid_pmr(c->sop, c->G, nb, seed, rep_begin + b0, (float)sigma, c->stream); }
+      { Launch L(c, 2, 2); pico::launch_grid_adjoint_rest(c->sop, c->G, c->R, nb, c->stream); }
+    }
     if ((st = run_cg(c, nb, max_iter, rtol, lam)) != PICO_OK) return st;
     { Launch L(c, 3); pico::launch_accum_pmr(c->X, c->n, nb, (float)(1.0 / (sigma * sigma)), sum, sumsq, c->stream); }
   }

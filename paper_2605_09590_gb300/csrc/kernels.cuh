@@ -70,4 +70,33 @@ void launch_cart_pmr_cols(const CartOp& op, float2* G, int nb, uint64_t seed, in
 // out[b] = sum_c conj(S_c) . F^H_x G[b][c]
 void launch_cart_rows_adjoint(const CartOp& op, const float2* G, float2* out, int nb, cudaStream_t s);
 
+// ---- spiral.cu: non-Cartesian (Toeplitz normal operator, KB gridding) ----
+struct SpiralOp {
+  int n;                    // image is n x n
+  int L;                    // grid 2n
+  int nc;
+  int P1, P2;               // L = P1 * P2 split
+  const float2* smaps;      // [nc][n][n] whitened
+  const float2* tw2;        // [L] exp(-2 pi i e / L)
+  const float* That;        // [L][L] real Toeplitz kernel, includes 1/L^2
+  const float* deapod;      // [n] 1 / (phi^((x - n/2)/L) sqrt(n))
+  // gridding
+  int64_t M;                // samples
+  const float2* u;          // [M] sample positions in grid units (2 k)
+  const float2* cphase;     // [M] e^{i pi (kx + ky)} (image-centre shift)
+  const int* tile_ptr;      // [ntiles + 1] CSR over 16x16 grid tiles
+  const int* tile_idx;      // samples touching each tile (with the kernel half-width)
+  float beta, halfw, inv_i0beta;
+};
+bool spiral_supported(int n, int* P1, int* P2);
+void launch_toep_h(const float* traj, int64_t M, int n, float2* c, cudaStream_t s);
+void launch_toep_fft2(const SpiralOp& op, float2* c, cudaStream_t s);  // c <- DFT_2D(c)
+void launch_toep_finalize(const float2* c, int L, float scale, float* That, cudaStream_t s);
+void launch_toep_apply(const SpiralOp& op, const float2* x, float2* y, float2* G, int nb, float lam, cudaStream_t s);
+void launch_toep_cg_normal(const SpiralOp& op, const CgArgs& a, float2* G, int nb, int it, float lam,
+                           cudaStream_t s);
+void launch_grid_pmr(const SpiralOp& op, float2* Qgrid, int nb, uint64_t seed, int64_t rep_begin, float sigma,
+                     cudaStream_t s);
+void launch_grid_adjoint_rest(const SpiralOp& op, float2* Qgrid, float2* out, int nb, cudaStream_t s);
+
 }  // namespace pico

@@ -1,0 +1,435 @@
+// Non-Cartesian (spiral) operators on the GPU (kernel templates).
+//
+// Normal operator by Toeplitz embedding (Sec. 3.2.2 / Sec. 3.3, Fessler 2005):
+// for an N x N image and the exact NUDFT A_c = E diag(S_c),
+//     A^H A x = sum_c conj(S_c) . crop_N IDFT_2N( T^ . DFT_2N( pad_2N(S_c . x) ) )
+// where T^ = DFT_2N of the point-spread kernel h(d) = (1/N^2) sum_m e^{+2 pi i k_m.d/N},
+// d in (-N, N)^2, placed circularly on the 2N grid (its DFT is real because h
+// is Hermitian).  Three passes per normal operator, all on the 2N grid:
+//   rows_fwd : per image row and coil, S_c . p zero-padded to 2N, row FFT  -> G[b][c][N][2N]
+//   cols     : per grid column and coil, column FFT (rows >= N are zero), x T^,
+//              inverse column FFT, rows < N written back in place
+//   rows_inv : per image row, inverse row FFT of every coil, first N samples,
+//              conj(S_c) coil combine, + lam p, p^H q partial
+// The CG direction update p = r + beta p is fused into rows_fwd.
+//
+// PMR adjoint A^H n (Sec. 1; Kaiser-Bessel gridding, width W, oversampling 2):
+//   grid     : gather-form gridding of CN(0, sigma^2) k-space noise drawn per
+//              (replica, coil, sample) onto the 2N grid, no atomics
+//   fft rows : inverse row FFT of the grid
+//   cols_adj : inverse column FFT, centred crop, deapodisation, conj(S_c)
+//              coil combine
+#pragma once
+#include "common.cuh"
+#include "fft_blocks.cuh"
+#include "kernels.cuh"
+
+namespace pico {
+
+__device__ __forceinline__ const double* sp_rr(const CgArgs& a, int b, int it) {
+  return a.rr_part + ((size_t)b * (a.itmax + 1) + it) * a.PB;
+}
+__device__ __forceinline__ double* sp_pq(const CgArgs& a, int b, int it) {
+  return a.pq_part + ((size_t)b * a.itmax + it) * a.PA;
+}
+
+// CG scalars of iteration it (computed by warp 0): returns done flag and beta
+__device__ __forceinline__ void cg_scalars(const CgArgs& a, int b, int it, int* sh_done, float* sh_beta) {
+  if (threadIdx.x < 32) {
+    const double rr = warp_sum_parts(sp_rr(a, b, it), a.PB);
+    const double rr0 = warp_sum_parts(sp_rr(a, b, 0), a.PB);
+    const double rrp = it > 0 ? warp_sum_parts(sp_rr(a, b, it - 1), a.PB) : 1.0;
+    if (threadIdx.x == 0) {
+      *sh_done = !(rr > a.rtol2 * rr0);
+      *sh_beta = it > 0 ? (float)(rr / rrp) : 0.f;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Pass 1: rows of the image, forward transform of S_c . p padded to L = 2N
+// ---------------------------------------------------------------------------
+template <int P1, int P2, bool CG>
+__global__ void __launch_bounds__(Split<P1, P2>::NT, 1)
+    k_toep_rows_fwd(SpiralOp op, const float2* __restrict__ xin, float2* __restrict__ G, CgArgs a, int it) {
+  constexpr int L = P1 * P2;
+  constexpr int NT = Split<P1, P2>::NT;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  float2* buf = reinterpret_cast<float2*>(smraw);
+  float2* tws = buf + kLines * P2 * Split<P1, P2>::LD;
+  __shared__ float sh_beta;
+  __shared__ int sh_done;
+  const int t = threadIdx.x, b = blockIdx.y, N = op.n;
+  for (int i = t; i < L; i += NT) tws[i] = op.tw2[i];
+  if (CG) cg_scalars(a, b, it, &sh_done, &sh_beta);
+  __syncthreads();
+  if (CG && sh_done) return;
+
+  const int ra = t / P1, n1 = t % P1;
+  const bool ajob = t < kLines * P1;
+  const int ya = blockIdx.x * kLines + ra;
+  const bool aval = ajob && ya < N;
+  const int rb = t / P2, k2 = t % P2;
+  const bool bjob = t < kLines * P2;
+  const int yb = blockIdx.x * kLines + rb;
+  const bool bval = bjob && yb < N;
+  const size_t img = (size_t)b * N * N;
+
+  float2 p[P2];
+  if (ajob) {
+    const float beta = CG ? sh_beta : 0.f;
+#pragma unroll
+    for (int n2 = 0; n2 < P2; ++n2) {
+      const int x = n1 + P1 * n2;
+      float2 v = make_float2(0.f, 0.f);
+      if (aval && x < N) {
+        const size_t idx = img + (size_t)ya * N + x;
+        if (CG) {
+          const float2 r = a.R[idx];
+          if (it > 0) {
+            const float2 po = a.P[idx];
+            v = make_float2(fmaf(beta, po.x, r.x), fmaf(beta, po.y, r.y));
+          } else {
+            v = r;
+          }
+          a.P[idx] = v;
+        } else {
+          v = xin[idx];
+        }
+      }
+      p[n2] = v;
+    }
+  }
+  for (int c = 0; c < op.nc; ++c) {
+    if (ajob) {
+      float2 z[P2];
+      const float2* __restrict__ S = op.smaps + ((size_t)c * N + (aval ? ya : 0)) * N;
+#pragma unroll
+      for (int n2 = 0; n2 < P2; ++n2) {
+        const int x = n1 + P1 * n2;
+        z[n2] = (aval && x < N) ? cmul(__ldg(S + x), p[n2]) : make_float2(0.f, 0.f);
+      }
+      rowa_store<P1, P2, -1>(z, n1, ra, buf, tws);
+    }
+    __syncthreads();
+    if (bval) {
+      float2 y[P1];
+      rowb_load<P1, P2, -1>(y, k2, rb, buf);
+      float2* __restrict__ g = G + (((size_t)b * op.nc + c) * N + yb) * L;
+#pragma unroll
+      for (int k1 = 0; k1 < P1; ++k1) g[k2 + P2 * k1] = y[k1];
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Pass 2: columns of the grid: FFT (rows >= N zero), x T^, inverse FFT, rows < N
+// ---------------------------------------------------------------------------
+template <int P1, int P2>
+__global__ void __launch_bounds__(Split<P1, P2>::NT, 1) k_toep_cols(SpiralOp op, float2* __restrict__ G) {
+  constexpr int L = P1 * P2;
+  constexpr int NT = Split<P1, P2>::NT;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  float2* buf = reinterpret_cast<float2*>(smraw);
+  float2* tws = buf + L * kLines;
+  const int t = threadIdx.x, N = op.n;
+  for (int i = t; i < L; i += NT) tws[i] = op.tw2[i];
+  __syncthreads();
+  const int ln = t % kLines, job = t / kLines;
+  const int kx = blockIdx.x * kLines + ln;  // grid column (always < L: L is a multiple of 16)
+  float2* __restrict__ g = G + (size_t)blockIdx.y * N * L;  // (b, c) plane [N][L]
+  const int n1 = job, k2 = job;
+  if (job < P1) {
+    float2 z[P2];
+#pragma unroll
+    for (int n2 = 0; n2 < P2; ++n2) {
+      const int y = n1 + P1 * n2;
+      z[n2] = y < N ? g[(size_t)y * L + kx] : make_float2(0.f, 0.f);
+    }
+    cola_store<P1, P2, -1>(z, n1, ln, buf, tws);
+  }
+  __syncthreads();
+  if (job < P2) {
+    float2 y[P1];
+    colb_load<P1, P2>(y, k2, ln, buf);
+    DFT<P1, -1>::run(y);
+#pragma unroll
+    for (int k1 = 0; k1 < P1; ++k1) y[k1] = cscale(y[k1], __ldg(op.That + (size_t)(k2 + P2 * k1) * L + kx));
+    colb_inv_store<P1, P2>(y, k2, ln, buf, tws);
+  }
+  __syncthreads();
+  if (job < P1) {
+    float2 z[P2];
+    cola_load<P1, P2, 1>(z, n1, ln, buf);
+#pragma unroll
+    for (int n2 = 0; n2 < P2; ++n2) {
+      const int y = n1 + P1 * n2;
+      if (y < N) g[(size_t)y * L + kx] = z[n2];
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Pass 3: rows: inverse FFT per coil, first N samples, conj(S) combine, + lam p
+// ---------------------------------------------------------------------------
+template <int P1, int P2, bool CG>
+__global__ void __launch_bounds__(Split<P1, P2>::NT, 1)
+    k_toep_rows_inv(SpiralOp op, const float2* __restrict__ G, const float2* __restrict__ xin,
+                    float2* __restrict__ yout, float lam, CgArgs a, int it) {
+  constexpr int L = P1 * P2;
+  constexpr int NT = Split<P1, P2>::NT;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  float2* buf = reinterpret_cast<float2*>(smraw);
+  float2* tws = buf + kLines * P2 * Split<P1, P2>::LD;
+  __shared__ double red[(NT + 31) / 32];
+  __shared__ float sh_beta;
+  __shared__ int sh_done;
+  const int t = threadIdx.x, b = blockIdx.y, N = op.n;
+  for (int i = t; i < L; i += NT) tws[i] = op.tw2[i];
+  if (CG) cg_scalars(a, b, it, &sh_done, &sh_beta);
+  __syncthreads();
+  if (CG && sh_done) return;
+
+  const int ra = t / P1, n1 = t % P1;
+  const bool ajob = t < kLines * P1;
+  const int ya = blockIdx.x * kLines + ra;
+  const bool aval = ajob && ya < N;
+  const int rb = t / P2, k2 = t % P2;
+  const bool bjob = t < kLines * P2;
+  const int yb = blockIdx.x * kLines + rb;
+  const bool bval = bjob && yb < N;
+  const size_t img = (size_t)b * N * N;
+
+  float2 acc[P2];
+#pragma unroll
+  for (int n2 = 0; n2 < P2; ++n2) acc[n2] = make_float2(0.f, 0.f);
+  for (int c = 0; c < op.nc; ++c) {
+    if (bjob) {
+      float2 y[P1];
+      const float2* __restrict__ g = G + (((size_t)b * op.nc + c) * N + (bval ? yb : 0)) * L;
+#pragma unroll
+      for (int k1 = 0; k1 < P1; ++k1) y[k1] = bval ? g[k2 + P2 * k1] : make_float2(0.f, 0.f);
+      rowb_inv_store<P1, P2>(y, k2, rb, buf, tws);
+    }
+    __syncthreads();
+    if (ajob) {
+      float2 z[P2];
+      rowa_inv_load<P1, P2>(z, n1, ra, buf);
+      if (aval) {
+        const float2* __restrict__ S = op.smaps + ((size_t)c * N + ya) * N;
+#pragma unroll
+        for (int n2 = 0; n2 < P2; ++n2) {
+          const int x = n1 + P1 * n2;
+          if (x < N) acc[n2] = cfma_c(acc[n2], __ldg(S + x), z[n2]);
+        }
+      }
+    }
+    __syncthreads();
+  }
+  float pq = 0.f;
+  if (aval) {
+    const float2* __restrict__ pin = CG ? a.P : xin;
+    float2* __restrict__ out = CG ? a.Q : yout;
+#pragma unroll
+    for (int n2 = 0; n2 < P2; ++n2) {
+      const int x = n1 + P1 * n2;
+      if (x < N) {
+        const size_t idx = img + (size_t)ya * N + x;
+        const float2 pv = pin[idx];
+        const float2 q = make_float2(fmaf(lam, pv.x, acc[n2].x), fmaf(lam, pv.y, acc[n2].y));
+        out[idx] = q;
+        pq += cdot_re(pv, q);
+      }
+    }
+  }
+  if (CG) {
+    const double tot = block_sum_d((double)pq, red);
+    if (t == 0) sp_pq(a, b, it)[blockIdx.x] = tot;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Generic in-place FFTs of all rows / all columns of [planes][L][L] grids
+// ---------------------------------------------------------------------------
+template <int P1, int P2, int SIGN>
+__global__ void __launch_bounds__(Split<P1, P2>::NT, 1) k_fft_rows(float2* __restrict__ data, const float2* tw2) {
+  constexpr int L = P1 * P2;
+  constexpr int NT = Split<P1, P2>::NT;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  float2* buf = reinterpret_cast<float2*>(smraw);
+  float2* tws = buf + kLines * P2 * Split<P1, P2>::LD;
+  const int t = threadIdx.x;
+  for (int i = t; i < L; i += NT) tws[i] = tw2[i];
+  __syncthreads();
+  float2* __restrict__ plane = data + (size_t)blockIdx.y * L * L;
+  const int ra = t / P1, n1 = t % P1;
+  const int rb = t / P2, k2 = t % P2;
+  if (t < kLines * P1) {
+    float2 z[P2];
+    const float2* row = plane + (size_t)(blockIdx.x * kLines + ra) * L;
+#pragma unroll
+    for (int n2 = 0; n2 < P2; ++n2) z[n2] = row[n1 + P1 * n2];
+    rowa_store<P1, P2, SIGN>(z, n1, ra, buf, tws);
+  }
+  __syncthreads();
+  if (t < kLines * P2) {
+    float2 y[P1];
+    rowb_load<P1, P2, SIGN>(y, k2, rb, buf);
+    float2* row = plane + (size_t)(blockIdx.x * kLines + rb) * L;
+#pragma unroll
+    for (int k1 = 0; k1 < P1; ++k1) row[k2 + P2 * k1] = y[k1];
+  }
+}
+
+template <int P1, int P2, int SIGN>
+__global__ void __launch_bounds__(Split<P1, P2>::NT, 1) k_fft_cols(float2* __restrict__ data, const float2* tw2) {
+  constexpr int L = P1 * P2;
+  constexpr int NT = Split<P1, P2>::NT;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  float2* buf = reinterpret_cast<float2*>(smraw);
+  float2* tws = buf + L * kLines;
+  const int t = threadIdx.x;
+  for (int i = t; i < L; i += NT) tws[i] = tw2[i];
+  __syncthreads();
+  float2* __restrict__ plane = data + (size_t)blockIdx.y * L * L;
+  const int ln = t % kLines, job = t / kLines;
+  const int kx = blockIdx.x * kLines + ln;
+  if (job < P1) {
+    float2 z[P2];
+#pragma unroll
+    for (int n2 = 0; n2 < P2; ++n2) z[n2] = plane[(size_t)(job + P1 * n2) * L + kx];
+    cola_store<P1, P2, SIGN>(z, job, ln, buf, tws);
+  }
+  __syncthreads();
+  if (job < P2) {
+    float2 y[P1];
+    colb_load<P1, P2>(y, job, ln, buf);
+    DFT<P1, SIGN>::run(y);
+#pragma unroll
+    for (int k1 = 0; k1 < P1; ++k1) plane[(size_t)(job + P2 * k1) * L + kx] = y[k1];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// PMR adjoint, last pass: inverse column FFT of the (row-transformed) grid,
+// centred crop to the N x N image, deapodisation and conj(S_c) coil combine.
+// Image column x reads grid column (x - N/2) mod L; image row y is grid row
+// (y - N/2) mod L.  One CTA: 16 image columns of one replica, all coils.
+// ---------------------------------------------------------------------------
+template <int P1, int P2>
+__global__ void __launch_bounds__(Split<P1, P2>::NT, 1)
+    k_grid_cols_adjoint(SpiralOp op, const float2* __restrict__ Q, float2* __restrict__ out) {
+  constexpr int L = P1 * P2;
+  constexpr int NT = Split<P1, P2>::NT;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  float2* buf = reinterpret_cast<float2*>(smraw);
+  float2* tws = buf + L * kLines;
+  const int t = threadIdx.x, N = op.n, b = blockIdx.y;
+  for (int i = t; i < L; i += NT) tws[i] = op.tw2[i];
+  __syncthreads();
+  const int ln = t % kLines, job = t / kLines;
+  const int x = blockIdx.x * kLines + ln;  // image column
+  const bool xval = x < N;
+  const int gx = ((x - N / 2) % L + L) % L;
+  const float dax = xval ? op.deapod[x] : 0.f;
+  float2 acc[P1];
+#pragma unroll
+  for (int k1 = 0; k1 < P1; ++k1) acc[k1] = make_float2(0.f, 0.f);
+  for (int c = 0; c < op.nc; ++c) {
+    const float2* __restrict__ q = Q + ((size_t)b * op.nc + c) * L * L;
+    if (job < P1) {
+      float2 z[P2];
+#pragma unroll
+      for (int n2 = 0; n2 < P2; ++n2) z[n2] = xval ? q[(size_t)(job + P1 * n2) * L + gx] : make_float2(0.f, 0.f);
+      cola_store<P1, P2, 1>(z, job, ln, buf, tws);
+    }
+    __syncthreads();
+    if (job < P2 && xval) {
+      float2 y[P1];
+      colb_load<P1, P2>(y, job, ln, buf);
+      DFT<P1, 1>::run(y);
+#pragma unroll
+      for (int k1 = 0; k1 < P1; ++k1) {
+        const int gy = job + P2 * k1;
+        const int yy = (gy + N / 2) % L;  // image row of grid row gy
+        if (yy < N) {
+          const float2 s = __ldg(op.smaps + ((size_t)c * N + yy) * N + x);
+          acc[k1] = cfma_c(acc[k1], s, cscale(y[k1], dax * op.deapod[yy]));
+        }
+      }
+    }
+    __syncthreads();
+  }
+  if (job < P2 && xval) {
+#pragma unroll
+    for (int k1 = 0; k1 < P1; ++k1) {
+      const int gy = job + P2 * k1;
+      const int yy = (gy + N / 2) % L;
+      if (yy < N) out[((size_t)b * N + yy) * N + x] = acc[k1];
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------
+template <int P1, int P2>
+void launch_toep_normal_t(const SpiralOp& op, const float2* x, float2* y, float2* G, int nb, float lam,
+                          const CgArgs* a, int it, cudaStream_t s) {
+  using Sp = Split<P1, P2>;
+  constexpr int L = P1 * P2;
+  const size_t smr = Sp::row_buf + L * sizeof(float2), smc = Sp::col_buf + L * sizeof(float2);
+  const dim3 grow((op.n + kLines - 1) / kLines, nb);
+  CgArgs dummy{};
+  if (a) {
+    auto k1 = k_toep_rows_fwd<P1, P2, true>;
+    cudaFuncSetAttribute(k1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smr);
+    k1<<<grow, Sp::NT, smr, s>>>(op, nullptr, G, *a, it);
+  } else {
+    auto k1 = k_toep_rows_fwd<P1, P2, false>;
+    cudaFuncSetAttribute(k1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smr);
+    k1<<<grow, Sp::NT, smr, s>>>(op, x, G, dummy, 0);
+  }
+  auto k2 = k_toep_cols<P1, P2>;
+  cudaFuncSetAttribute(k2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smc);
+  k2<<<dim3(L / kLines, nb * op.nc), Sp::NT, smc, s>>>(op, G);
+  if (a) {
+    auto k3 = k_toep_rows_inv<P1, P2, true>;
+    cudaFuncSetAttribute(k3, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smr);
+    k3<<<grow, Sp::NT, smr, s>>>(op, G, nullptr, nullptr, lam, *a, it);
+  } else {
+    auto k3 = k_toep_rows_inv<P1, P2, false>;
+    cudaFuncSetAttribute(k3, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smr);
+    k3<<<grow, Sp::NT, smr, s>>>(op, G, x, y, lam, dummy, 0);
+  }
+}
+
+template <int P1, int P2>
+void launch_fft2_t(float2* data, const float2* tw2, int planes, int sign, bool rows, cudaStream_t s) {
+  using Sp = Split<P1, P2>;
+  constexpr int L = P1 * P2;
+  if (rows) {
+    const size_t sm = Sp::row_buf + L * sizeof(float2);
+    auto k = sign < 0 ? k_fft_rows<P1, P2, -1> : k_fft_rows<P1, P2, 1>;
+    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k<<<dim3(L / kLines, planes), Sp::NT, sm, s>>>(data, tw2);
+  } else {
+    const size_t sm = Sp::col_buf + L * sizeof(float2);
+    auto k = sign < 0 ? k_fft_cols<P1, P2, -1> : k_fft_cols<P1, P2, 1>;
+    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k<<<dim3(L / kLines, planes), Sp::NT, sm, s>>>(data, tw2);
+  }
+}
+
+template <int P1, int P2>
+void launch_grid_cols_adjoint_t(const SpiralOp& op, const float2* Q, float2* out, int nb, cudaStream_t s) {
+  using Sp = Split<P1, P2>;
+  constexpr int L = P1 * P2;
+  const size_t sm = Sp::col_buf + L * sizeof(float2);
+  auto k = k_grid_cols_adjoint<P1, P2>;
+  cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  k<<<dim3((op.n + kLines - 1) / kLines, nb), Sp::NT, sm, s>>>(op, Q, out);
+}
+
+}  // namespace pico

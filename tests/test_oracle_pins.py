@@ -127,6 +127,15 @@ def test_grid_aligned_nudft_equals_fft():
     assert abs(np.vdot(E.forward(z), w) - np.vdot(z, E.adjoint(w))) < 1e-10
 
 
+def test_spiral_dense_normal_from_psf_matches_explicit_matrix():
+    n, nc = 8, 3
+    S = synth.coil_maps(n, n, nc, 5)
+    traj = synth.spiral_traj(n, n_interleaves=4, nsamp=50, R=1)
+    op = ops.Operator(S, synth.noise_cov(nc, 5), traj=traj)
+    A = op.matrix()
+    assert np.allclose(pico.dense_normal(op), A.conj().T @ A, atol=1e-12)
+
+
 def test_spiral_operator_matches_explicit_matrix():
     n, nc = 8, 3
     S = synth.coil_maps(n, n, nc, 4)
