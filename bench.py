@@ -43,6 +43,7 @@ def parse():
     ap.add_argument("--workload", default="knee320_r2")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-t1pct", action="store_true")
     return ap.parse_args()
 
 
@@ -53,18 +54,35 @@ def workload(name):
 
 
 def flops_per_probe(w):
-    """Algorithmic FLOPs of one normal-operator application to one image:
-    per coil and readout column an FFT and an inverse FFT of length ny
-    (5 N log2 N each) and the sensitivity multiply / conjugate combine-add
-    (6 + 8 flops per sample) plus the mask (2 per sample)."""
-    N = w.ny
-    return w.nc * w.nx * (2 * 5 * N * math.log2(N) + 16 * N)
+    """Algorithmic FLOPs of one normal-operator application to one image.
+
+    Cartesian (column-decoupled): per coil and readout column an FFT and an
+    inverse FFT of length ny (5 N log2 N each) plus the sensitivity multiply,
+    conjugate combine-add and mask (16 flops per sample).
+    Spiral (Toeplitz, grid L = 2n): per coil n row FFTs, L column FFT pairs and
+    n row IFFTs of length L (5 L log2 L each), plus 16 flops per image sample
+    and 2 per grid sample for the kernel multiply."""
+    if w.kind == "cartesian":
+        N = w.ny
+        return w.nc * w.nx * (2 * 5 * N * math.log2(N) + 16 * N)
+    n, L = w.ny, 2 * w.ny
+    fft = 5 * L * math.log2(L)
+    return w.nc * ((2 * n + 2 * L) * fft + 16 * n * n + 2 * L * L)
 
 
 def bytes_per_probe_normal(w):
-    """HBM bytes of one fused CG normal-operator launch per image: reads r and
-    p_old, writes p and q (complex64)."""
-    return 4 * w.ny * w.nx * 8
+    """HBM bytes of one normal-operator application per image in the CG loop.
+    Cartesian: reads r and p_old, writes p and q.  Spiral: the same four images
+    plus the coil grids written and read twice (4 x nc x n x 2n complex64)."""
+    if w.kind == "cartesian":
+        return 4 * w.ny * w.nx * 8
+    return 4 * w.ny * w.nx * 8 + 4 * w.nc * w.ny * 2 * w.ny * 8
+
+
+def normal_ops_per_probe(w):
+    """Normal-operator applications per probe: one CG solve (lam = 0) or two
+    solves and one A^H A (lam > 0)."""
+    return w.max_iter if w.lam == 0 else 2 * w.max_iter + 1
 
 
 def cores_in_use():
@@ -78,14 +96,28 @@ def cores_in_use():
 # CPU oracle (reference arm and cpu_baseline leg)
 # ---------------------------------------------------------------------------
 def oracle_sample(w, inp, nprobe=1, nrep=1):
+    """Time the oracle on a bounded sample; returns (probe-solves/s, seconds, description)."""
+    import numpy as np
     from oracle import ops as O
     from oracle import pico as OP
-    op = O.Operator(inp["smaps"], inp["noise_cov"], mask=inp["mask"])
+    if w.kind == "cartesian":
+        op = O.Operator(inp["smaps"], inp["noise_cov"], mask=inp["mask"])
+        t0 = time.perf_counter()
+        OP.pico(op, SEED_PICO, 0, nprobe, 0.0, w.max_iter, 0.0)
+        OP.pmr(op, SEED_PMR, 0, nrep, w.sigma, 0.0, w.max_iter, 0.0)
+        dt = time.perf_counter() - t0
+        return (nprobe + nrep) / dt, dt, (f"{nprobe} PICO probe + {nrep} PMR replica of the same workload "
+                                          f"({w.max_iter} CG iterations each)")
+    # spiral: one exact-NUDFT normal operator application, scaled to whole probes/replicas
+    op = O.Operator(inp["smaps"], inp["noise_cov"], traj=inp["traj"])
+    x = np.ones((w.ny, w.nx), dtype=np.complex128)
     t0 = time.perf_counter()
-    OP.pico(op, SEED_PICO, 0, nprobe, 0.0, w.max_iter, 0.0)
-    OP.pmr(op, SEED_PMR, 0, nrep, w.sigma, 0.0, w.max_iter, 0.0)
+    op.normal(x, 0.1)
     dt = time.perf_counter() - t0
-    return (nprobe + nrep) / dt, dt
+    per_probe = normal_ops_per_probe(w) * dt
+    per_rep = w.max_iter * dt
+    return 2.0 / (per_probe + per_rep), dt, (f"one exact-NUDFT A^H A application ({dt:.1f} s), scaled to "
+                                             f"{normal_ops_per_probe(w)} per probe and {w.max_iter} per replica")
 
 
 def run_reference(args):
@@ -95,13 +127,14 @@ def run_reference(args):
     w, inp = workload(args.workload)
     for _ in range(args.warmup):
         oracle_sample(w, inp)
-    times = []
+    times, vals = [], []
     for _ in range(args.steps):
-        _, dt = oracle_sample(w, inp)
+        v, dt, sample = oracle_sample(w, inp)
         times.append(dt)
+        vals.append(v)
     total = sum(times)
-    value = 2 * args.steps / total
-    sample = f"1 PICO probe + 1 PMR replica per step ({w.max_iter} CG iterations each), FP64 NumPy"
+    value = len(vals) / sum(1.0 / v for v in vals)
+    sample = sample + ", FP64 NumPy, per step"
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
@@ -167,6 +200,64 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------------------
+# time to a 1 %-error noise map (Sec. 3.2.2 protocol: N in steps of 10)
+# ---------------------------------------------------------------------------
+def exact_variance_cartesian(op, w, torch):
+    """Exact diag(Sigma) of a phase-encode Cartesian operator on the GPU.
+
+    A^H A is block diagonal over readout columns, so the probe e_y (x) 1 (row y
+    set to one) returns column y of every column block at once: ny converged
+    solves give the whole diagonal."""
+    ny, nx = w.ny, w.nx
+    diag = torch.empty((ny, nx), dtype=torch.float64, device="cuda")
+    B = 64
+    for y0 in range(0, ny, B):
+        nb = min(B, ny - y0)
+        rhs = torch.zeros((nb, ny, nx), dtype=torch.complex64, device="cuda")
+        rhs[torch.arange(nb), torch.arange(y0, y0 + nb)] = 1.0
+        x = op.cg(rhs, 100, 1e-6)
+        diag[y0:y0 + nb] = x[torch.arange(nb), torch.arange(y0, y0 + nb)].real.double()
+    return diag
+
+
+def measure_time_to_1pct(op, w, torch, pico, max_n=20000, step=10):
+    ref = exact_variance_cartesian(op, w, torch)
+    ref_std = ref.clamp_min(0).sqrt()
+    nref = torch.linalg.vector_norm(ref_std)
+    out = {"reference": f"exact diag(Sigma) from {w.ny} structured converged CG solves", "step": step,
+           "threshold": 0.01, "nrmse_on": "std maps",
+           "reference_range": [float(ref.min()), float(ref.max())]}
+    for name in ("pico", "pmr"):
+        s = torch.zeros((w.ny, w.nx), dtype=torch.float64, device="cuda")
+        ss = torch.zeros_like(s)
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        elapsed, n, hit = 0.0, 0, None
+        curve = []
+        while n < max_n:
+            ev0.record()
+            if name == "pico":
+                pico.pico_variance_map(op.ctx, SEED_PICO + 1, n, step, pico.PICO_PROBE_PHASE, w.max_iter, 0.0,
+                                       s, ss, True)
+            else:
+                pico.pico_pmr(op.ctx, SEED_PMR + 1, n, step, w.sigma, w.max_iter, 0.0, s, ss, True)
+            ev1.record()
+            torch.cuda.synchronize()
+            elapsed += ev0.elapsed_time(ev1) / 1e3
+            n += step
+            err = float(torch.linalg.vector_norm((s / n).clamp_min(0).sqrt() - ref_std) / nref)
+            if n == step:
+                out[name + "_first_map_range"] = [float((s / n).min()), float((s / n).max())]
+            if n in (10, 50, 100, 200, 500, 1000, 2000, 5000, 10000):
+                curve.append((n, round(err, 5)))
+            if err <= 0.01:
+                hit = (n, elapsed, err)
+                break
+        out[name] = ({"N": hit[0], "seconds_in_steps_of_10": hit[1], "nrmse": hit[2], "curve": curve}
+                     if hit else {"N": None, "nrmse_at_max": err, "max_n": max_n, "curve": curve})
+    return out
+
+
+# ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
 def main():
@@ -199,8 +290,8 @@ def main():
     n = w.ny * w.nx
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream()
-    op = pico.Operator(inp["smaps"], mask=inp["mask"], noise_cov=inp["noise_cov"], max_batch=K,
-                       power_iters=15, stream=stream.cuda_stream)
+    op = pico.Operator(inp["smaps"], mask=inp.get("mask"), traj=inp.get("traj"), noise_cov=inp["noise_cov"],
+                       lam=w.lam, max_batch=K, power_iters=15, stream=stream.cuda_stream)
     s = torch.zeros((w.ny, w.nx), dtype=torch.float64, device=dev)
     ss, ps, pss = torch.zeros_like(s), torch.zeros_like(s), torch.zeros_like(s)
     red = torch.zeros((2, w.ny, w.nx), dtype=torch.float64, device=dev)
@@ -253,11 +344,13 @@ def main():
 
     # roofline of the dominant kernel (the fused CG normal operator)
     avg_norm_s = norm_ms / max(norm_n, 1) / 1e3
-    flops_launch = K * flops_per_probe(w)
+    flops_launch = K * flops_per_probe(w)   # one class-0 launch (group) = one normal op on K images
     achieved = flops_launch / avg_norm_s / 1e12
     peak = N_SM * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
     roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-            "traffic": None, "kernel": "k_col_normal<20,16,CG>",
+            "traffic": None,
+            "kernel": "k_col_normal (fused CG prologue)" if w.kind == "cartesian" else
+                      "k_toep_rows_fwd + k_toep_cols + k_toep_rows_inv (one normal operator)",
             "avg_launch_ms": avg_norm_s * 1e3, "launches": norm_n,
             "hbm_GBps_algorithmic": K * bytes_per_probe_normal(w) / avg_norm_s / 1e9,
             "peak_note": "FP32 FMA peak 152 SM x 128 lanes x 2 x 2070 MHz (nominal max clock)"}
@@ -268,7 +361,8 @@ def main():
         "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "c64", "data": "synthetic",
         "config": {"workload": args.workload, "ny": w.ny, "nx": w.nx, "coils": w.nc, "R": w.R, "acs": w.acs,
-                   "noise_cov": "15x15 correlated", "cg_iters": w.max_iter, "probes_per_step": K,
+                   "noise_cov": "correlated" if w.noise_corr else "white", "lambda_rel": w.lam,
+                   "cg_iters": w.max_iter, "probes_per_step": K,
                    "replicas_per_step": K, "l2": f"working set {4 * K * n * 8 / 1e9:.2f} GB of CG vectors > 129 MB L2",
                    "parallelism": f"probe shards x{world}"},
         "roofline": roof, "kernel_ms_in_timed_region": share,
@@ -281,14 +375,16 @@ def main():
     # end to end through the C ABI from host buffers
     if not args.no_e2e:
         S_h = np.ascontiguousarray(inp["smaps"])
-        m_h, C_h = inp["mask"], inp["noise_cov"]
+        m_h = inp["mask"] if w.kind == "cartesian" else inp["traj"]
+        C_h = inp["noise_cov"]
         out_h = np.empty((2, w.ny, w.nx), dtype=np.float64)
         e2e_steps = max(2, min(args.steps, 3))
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for i in range(e2e_steps):
-            op2 = pico.Operator(S_h, mask=m_h, noise_cov=C_h, max_batch=K, power_iters=15,
-                                stream=stream.cuda_stream)
+            kw = {"mask": m_h} if w.kind == "cartesian" else {"traj": m_h}
+            op2 = pico.Operator(S_h, noise_cov=C_h, lam=w.lam, max_batch=K, power_iters=15,
+                                stream=stream.cuda_stream, **kw)
             a, _ = op2.variance_sums(SEED_PICO, K, w.max_iter, 0.0, probe_begin=(i * world + rank) * K)
             b, _ = op2.pmr_sums(SEED_PMR, K, w.sigma, w.max_iter, 0.0, rep_begin=(i * world + rank) * K)
             out_h[0] = a.cpu().numpy()
@@ -305,11 +401,19 @@ def main():
                        "d2h_bytes_per_step": int(out_h.nbytes), "steps": e2e_steps,
                        "includes": "pico_init (upload, whitening, power method, workspace) + maps + read-back"}
 
+    if rank == 0 and world == 1 and not args.no_t1pct and w.kind == "cartesian":
+        t1 = measure_time_to_1pct(op, w, torch, pico)
+        for name in ("pico", "pmr"):
+            if t1[name].get("N"):
+                per = total_ms / 1e3 / (2 * K * args.steps)      # device seconds per solve in the batched step
+                t1[name]["seconds_at_batched_rate"] = t1[name]["N"] * per
+        line["time_to_1pct"] = t1
+
     if rank == 0 and world == 1 and not args.no_cpu:
-        v, dt = oracle_sample(w, inp)
+        v, dt, desc = oracle_sample(w, inp)
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-                                "sample": f"1 PICO probe + 1 PMR replica of the same workload, {dt:.1f} s, "
-                                          f"NumPy FP64 (single-threaded pocketfft; {cores_in_use()} cores visible)"}
+                                "sample": f"{desc}, {dt:.1f} s, NumPy FP64 (single-threaded pocketfft; "
+                                          f"{cores_in_use()} cores visible)"}
     if rank == 0:
         print(json.dumps(line), flush=True)
     op.close()

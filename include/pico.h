@@ -105,6 +105,19 @@ pico_status pico_get_info(const pico_ctx* ctx, pico_info* info);
  * x_dev, y_dev: device complex64 [nbatch][ny][nx]; must not overlap. */
 pico_status pico_apply_normal(pico_ctx* ctx, const void* x_dev, void* y_dev, int32_t nbatch);
 
+/* Forward encoding operator y = A x (Sec. 2.1.1, Eq. 1, pre-whitened as in
+ * Eq. 3: A = L^-1 A~, so y is whitened k-space).  x_dev: device complex64
+ * [nbatch][ny][nx].  y_dev: device complex64, Cartesian [nbatch][ncoils][ny][nx]
+ * (orthonormal 2-D DFT, zero off the mask); spiral [nbatch][ncoils][nsamp]
+ * (NUDFT e^{-2 pi i k.r/n}/n with r = (x, y) from 0, evaluated by a
+ * Kaiser-Bessel NUFFT of width kb_width on the 2n grid). */
+pico_status pico_forward(pico_ctx* ctx, const void* x_dev, void* y_dev, int32_t nbatch);
+
+/* Adjoint y -> A^H y (layouts as pico_forward; Cartesian entries off the mask
+ * are ignored).  With whitened data b_w, A^H b_w is the right-hand side of the
+ * CG-SENSE normal equations (Eq. 6). */
+pico_status pico_adjoint(pico_ctx* ctx, const void* y_dev, void* x_dev, int32_t nbatch);
+
 /* Solve (A^H A + lam_phys I) x = rhs by CG from x0 = 0 for nbatch right-hand
  * sides (Eq. 6, CG-SENSE).  Each system stops after max_iter updates or once
  * ||r|| <= rtol ||rhs|| (rtol = 0: exactly max_iter updates).  Inner products
@@ -127,6 +140,19 @@ pico_status pico_cg_batch(pico_ctx* ctx, const void* rhs_dev, void* x_dev, int32
 pico_status pico_variance_map(pico_ctx* ctx, uint64_t seed, int64_t probe_begin, int32_t nprobes,
                               int32_t probe_kind, int32_t max_iter, double rtol, double* sum_dev,
                               double* sumsq_dev, int32_t accumulate);
+
+/* Adaptive PICO (Sec. 4, stopping from the estimator's own variance): runs
+ * probes 0, 1, ... under seed in chunks of `chunk` (>= 2) and stops once the
+ * relative standard error of the running mean map,
+ *   ||stderr||_2 / ||sum / N||_2  with  stderr = sqrt((sumsq/N - (sum/N)^2)/(N-1)),
+ * is <= target, or after max_probes.  sum_dev and sumsq_dev (required,
+ * device float64 [ny][nx]) are overwritten with the running sums;
+ * probes_used (host) receives N, rel_stderr (host, nullable) the final
+ * statistic.  Synchronises once per chunk. */
+pico_status pico_variance_map_adaptive(pico_ctx* ctx, uint64_t seed, int32_t probe_kind, int32_t chunk,
+                                       int64_t max_probes, int32_t max_iter, double rtol, double target,
+                                       double* sum_dev, double* sumsq_dev, int64_t* probes_used,
+                                       double* rel_stderr);
 
 /* PMR running sums (Sec. 1; Sec. 3.2.2): replica i draws whitened k-space
  * noise n_i ~ CN(0, sigma^2 I) on the sampled positions, solves

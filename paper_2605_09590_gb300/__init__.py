@@ -72,8 +72,12 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "pico_get_info": ([vp, ctypes.POINTER(pico_info)], i32),
         "pico_apply_normal": ([vp, vp, vp, i32], i32),
         "pico_cg_batch": ([vp, vp, vp, i32, i32, f64, vp, vp], i32),
+        "pico_forward": ([vp, vp, vp, i32], i32),
+        "pico_adjoint": ([vp, vp, vp, i32], i32),
         "pico_variance_map": ([vp, u64, i64, i32, i32, i32, f64, vp, vp, i32], i32),
         "pico_pmr": ([vp, u64, i64, i32, f64, i32, f64, vp, vp, i32], i32),
+        "pico_variance_map_adaptive": ([vp, u64, i32, i32, i64, i32, f64, f64, vp, vp,
+                                        ctypes.POINTER(i64), ctypes.POINTER(f64)], i32),
         "pico_finalize": ([vp, vp, vp, i64, vp, vp], i32),
         "pico_gfactor": ([vp, vp, vp, f64, vp], i32),
         "pico_profile": ([vp, i32], i32),
@@ -167,6 +171,18 @@ def pico_apply_normal(ctx, x, y) -> None:
                                                  _dev_ptr(y, torch.complex64, "y"), x.shape[0]))
 
 
+def pico_forward(ctx, x, y) -> None:
+    import torch
+    _check(ctx, load_library().pico_forward(ctx, _dev_ptr(x, torch.complex64, "x"),
+                                            _dev_ptr(y, torch.complex64, "y"), x.shape[0]))
+
+
+def pico_adjoint(ctx, y, x) -> None:
+    import torch
+    _check(ctx, load_library().pico_adjoint(ctx, _dev_ptr(y, torch.complex64, "y"),
+                                            _dev_ptr(x, torch.complex64, "x"), x.shape[0]))
+
+
 def pico_cg_batch(ctx, rhs, x, max_iter: int, rtol: float = 0.0, stats: bool = False):
     import torch
     nb = rhs.shape[0]
@@ -185,6 +201,17 @@ def pico_variance_map(ctx, seed: int, probe_begin: int, nprobes: int, probe_kind
         ctx, seed & (2 ** 64 - 1), probe_begin, nprobes, probe_kind, max_iter, rtol,
         _dev_ptr(sum_, torch.float64, "sum"), None if sumsq is None else _dev_ptr(sumsq, torch.float64, "sumsq"),
         1 if accumulate else 0))
+
+
+def pico_variance_map_adaptive(ctx, seed: int, probe_kind: int, chunk: int, max_probes: int, max_iter: int,
+                               rtol: float, target: float, sum_, sumsq) -> tuple[int, float]:
+    import torch
+    used, rel = ctypes.c_int64(), ctypes.c_double()
+    _check(ctx, load_library().pico_variance_map_adaptive(
+        ctx, seed & (2 ** 64 - 1), probe_kind, chunk, max_probes, max_iter, rtol, target,
+        _dev_ptr(sum_, torch.float64, "sum"), _dev_ptr(sumsq, torch.float64, "sumsq"),
+        ctypes.byref(used), ctypes.byref(rel)))
+    return used.value, rel.value
 
 
 def pico_pmr(ctx, seed: int, rep_begin: int, nreps: int, sigma: float, max_iter: int, rtol: float, sum_,
@@ -271,6 +298,22 @@ class Operator:
         y = self.torch.empty_like(x)
         pico_apply_normal(self.ctx, x, y)
         return y
+
+    def kspace_shape(self, nb):
+        nc = self.info["ncoils"]
+        if self.info["kind"] == PICO_CARTESIAN:
+            return (nb, nc, self.ny, self.nx)
+        return (nb, nc, self.info["nsamp"])
+
+    def forward(self, x):
+        y = self.torch.empty(self.kspace_shape(x.shape[0]), dtype=self.torch.complex64, device=x.device)
+        pico_forward(self.ctx, x, y)
+        return y
+
+    def adjoint(self, y):
+        x = self.torch.empty((y.shape[0], self.ny, self.nx), dtype=self.torch.complex64, device=y.device)
+        pico_adjoint(self.ctx, y, x)
+        return x
 
     def cg(self, rhs, max_iter, rtol=0.0, stats=False):
         x = self.torch.empty_like(rhs)

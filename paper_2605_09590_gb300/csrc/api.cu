@@ -4,6 +4,9 @@
 
 #include <cmath>
 #include <complex>
+#include <map>
+#include <set>
+#include <tuple>
 #include <cstdio>
 #include <algorithm>
 #include <cstring>
@@ -35,6 +38,7 @@ struct pico_ctx {
   int* d_iters = nullptr;
   double* d_relres = nullptr;
   double* d_norm = nullptr;
+  double* d_adapt = nullptr;
   float2* G = nullptr;  // PMR buffer, allocated on first use: Cartesian hybrid [B][nc][ny][nx],
                         // spiral gridded noise [B][nc][2n][2n]
   pico::CartOp cop{};
@@ -65,6 +69,11 @@ struct pico_ctx {
   std::vector<cudaEvent_t> event_pool;
   double prof_ms[4] = {0, 0, 0, 0};
   int64_t prof_n[4] = {0, 0, 0, 0};
+  // CUDA graphs of the CG iteration loop, keyed by (nb, max_iter, rtol, lam)
+  cudaStream_t cap = nullptr;
+  bool use_graphs = true;
+  std::map<std::tuple<int, int, double, float>, std::pair<cudaGraphExec_t, int64_t>> graphs;
+  std::set<std::tuple<int, int, double, float>> seen;
 };
 
 namespace {
@@ -207,13 +216,52 @@ void op_cg_normal(pico_ctx* c, int nb, int it, float lam) {
   }
 }
 
+// The CG iterations of one batch: 2 * max_iter kernels (normal operator + update).
+// Replayed from a CUDA graph (captured on a private stream the second time a
+// (nb, max_iter, rtol, lam) combination is used) unless profiling is on.
+void cg_iterations(pico_ctx* c, int nb, int max_iter, double rtol, float lam) {
+  c->cg.rtol2 = rtol * rtol;
+  auto direct = [&]() {
+    for (int it = 0; it < max_iter; ++it) {
+      op_cg_normal(c, nb, it, lam);
+      { Launch L(c, 1); pico::launch_cg_update(c->cg, nb, it, c->stream); }
+    }
+  };
+  if (c->profiling || !c->use_graphs || max_iter == 0) return direct();
+  const auto key = std::make_tuple(nb, max_iter, rtol, lam);
+  auto itg = c->graphs.find(key);
+  if (itg == c->graphs.end()) {
+    if (c->seen.insert(key).second) return direct();  // first use: plain launches (sets kernel attributes)
+    cudaStream_t user = c->stream;
+    c->stream = c->cap;
+    const int64_t before = c->launches;
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t ex = nullptr;
+    bool ok = cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+    if (ok) {
+      direct();
+      ok = cudaStreamEndCapture(c->cap, &g) == cudaSuccess && g;
+    }
+    if (ok) ok = cudaGraphInstantiate(&ex, g, 0) == cudaSuccess;
+    if (g) cudaGraphDestroy(g);
+    c->stream = user;
+    const int64_t kernels = c->launches - before;
+    c->launches = before;
+    if (!ok) {
+      cudaGetLastError();
+      c->use_graphs = false;
+      return direct();
+    }
+    itg = c->graphs.emplace(key, std::make_pair(ex, kernels)).first;
+  }
+  cudaGraphLaunch(itg->second.first, c->stream);
+  c->launches += itg->second.second;
+}
+
 pico_status run_cg(pico_ctx* c, int nb, int max_iter, double rtol, float lam) {
   c->cg.rtol2 = rtol * rtol;
   { Launch L(c, 1); pico::launch_cg_init_rhs(c->cg, nb, c->stream); }
-  for (int it = 0; it < max_iter; ++it) {
-    op_cg_normal(c, nb, it, lam);
-    { Launch L(c, 1); pico::launch_cg_update(c->cg, nb, it, c->stream); }
-  }
+  cg_iterations(c, nb, max_iter, rtol, lam);
   return cuda_check(c, "cg");
 }
 
@@ -221,11 +269,16 @@ pico_status run_cg_from_probe(pico_ctx* c, int nb, int max_iter, double rtol, fl
                               int64_t begin, int kind) {
   c->cg.rtol2 = rtol * rtol;
   { Launch L(c, 1); pico::launch_cg_init_probe(c->cg, nb, seed, begin, kind, c->stream); }
-  for (int it = 0; it < max_iter; ++it) {
-    op_cg_normal(c, nb, it, lam);
-    { Launch L(c, 1); pico::launch_cg_update(c->cg, nb, it, c->stream); }
-  }
+  cg_iterations(c, nb, max_iter, rtol, lam);
   return cuda_check(c, "cg");
+}
+
+// k-space / grid work buffer shared by PMR, the forward and the adjoint operator:
+// Cartesian [B][nc][ny][nx], spiral [B][nc][2n][2n]; allocated on first use
+pico_status ensure_kbuf(pico_ctx* c) {
+  if (c->G) return PICO_OK;
+  const size_t per = c->kind == PICO_CARTESIAN ? (size_t)c->n : (size_t)4 * c->n;
+  return dalloc(c, &c->G, (size_t)c->max_batch * c->nc * per);
 }
 
 pico_status check_iter(pico_ctx* c, int max_iter, double rtol) {
@@ -374,6 +427,11 @@ pico_status pico_init(const pico_operator_desc* d, void* cuda_stream, size_t hbm
   c->max_batch = d->max_batch > 0 ? d->max_batch : 64;
   c->itmax = d->max_iter_cap > 0 ? d->max_iter_cap : 128;
   c->budget = hbm_budget;
+  if (cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking) != cudaSuccess) {
+    c->cap = nullptr;
+    c->use_graphs = false;
+    cudaGetLastError();
+  }
   const int nc = c->nc;
   const int64_t n = c->n, B = c->max_batch;
   const int PB = (int)((n + pico::kVecPerBlock - 1) / pico::kVecPerBlock);
@@ -388,7 +446,7 @@ pico_status pico_init(const pico_operator_desc* d, void* cuda_stream, size_t hbm
   if (c->kind == PICO_CARTESIAN) {
     if (!pico::cart_supported(c->ny, c->nx, &N1, &N2, &M1, &M2))
       return fail(c, PICO_E_UNSUPPORTED, "ny has no FFT split in this build");
-    PA = (c->nx + 15) / 16;
+    PA = pico::cart_normal_tiles(c->nx);
     extra = (size_t)c->ny * 13 + (size_t)c->nx * 8;
   } else {
     if (c->ny != c->nx) return fail(c, PICO_E_UNSUPPORTED, "spiral images must be square");
@@ -569,6 +627,44 @@ pico_status pico_variance_map(pico_ctx* c, uint64_t seed, int64_t probe_begin, i
   return cuda_check(c, "pico_variance_map");
 }
 
+pico_status pico_variance_map_adaptive(pico_ctx* c, uint64_t seed, int32_t probe_kind, int32_t chunk,
+                                       int64_t max_probes, int32_t max_iter, double rtol, double target,
+                                       double* sum, double* sumsq, int64_t* probes_used, double* rel_stderr) {
+  if (!c || !c->smaps) return PICO_E_INVALID;
+  if (!sum || !sumsq || !probes_used || chunk < 2 || max_probes < 2 || !(target > 0.0))
+    return fail(c, PICO_E_INVALID, "adaptive map needs sum, sumsq, probes_used, chunk >= 2, target > 0");
+  constexpr int kParts = 64;
+  double* part = c->d_norm;  // PB + 1 >= 1 doubles; use a dedicated area below when too small
+  pico_status st = PICO_OK;
+  if (c->cg.PB + 1 < 2 * kParts) {
+    if (!c->d_adapt && (st = dalloc(c, &c->d_adapt, (size_t)2 * kParts)) != PICO_OK) return st;
+    part = c->d_adapt;
+  }
+  int64_t done = 0;
+  double rel = INFINITY;
+  std::vector<double> h(2 * kParts);
+  while (done < max_probes) {
+    const int32_t nb = (int32_t)std::min<int64_t>(chunk, max_probes - done);
+    if ((st = pico_variance_map(c, seed, done, nb, probe_kind, max_iter, rtol, sum, sumsq, done > 0)) != PICO_OK)
+      return st;
+    done += nb;
+    if (done < 2) continue;
+    { Launch L(c, 3); pico::launch_stderr_parts(sum, sumsq, c->n, done, part, kParts, c->stream); }
+    cudaMemcpyAsync(h.data(), part, h.size() * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess) return cuda_check(c, "pico_variance_map_adaptive");
+    double a = 0.0, b = 0.0;
+    for (int k = 0; k < kParts; ++k) {
+      a += h[2 * k];
+      b += h[2 * k + 1];
+    }
+    rel = a > 0.0 ? std::sqrt(b / a) : INFINITY;
+    if (rel <= target) break;
+  }
+  *probes_used = done;
+  if (rel_stderr) *rel_stderr = rel;
+  return cuda_check(c, "pico_variance_map_adaptive");
+}
+
 pico_status pico_pmr(pico_ctx* c, uint64_t seed, int64_t rep_begin, int32_t nreps, double sigma, int32_t max_iter,
                      double rtol, double* sum, double* sumsq, int32_t accumulate) {
   if (!c || !c->smaps) return PICO_E_INVALID;
@@ -578,10 +674,7 @@ pico_status pico_pmr(pico_ctx* c, uint64_t seed, int64_t rep_begin, int32_t nrep
     return fail(c, PICO_E_UNSUPPORTED, "nx has no FFT split in this build (PMR adjoint)");
   pico_status st = check_iter(c, max_iter, rtol);
   if (st != PICO_OK) return st;
-  if (!c->G) {
-    const size_t per = c->kind == PICO_CARTESIAN ? (size_t)c->n : (size_t)4 * c->n;
-    if ((st = dalloc(c, &c->G, (size_t)c->max_batch * c->nc * per)) != PICO_OK) return st;
-  }
+  if ((st = ensure_kbuf(c)) != PICO_OK) return st;
   if (!accumulate) {
     cudaMemsetAsync(sum, 0, (size_t)c->n * sizeof(double), c->stream);
     if (sumsq) cudaMemsetAsync(sumsq, 0, (size_t)c->n * sizeof(double), c->stream);
@@ -600,6 +693,63 @@ pico_status pico_pmr(pico_ctx* c, uint64_t seed, int64_t rep_begin, int32_t nrep
     { Launch L(c, 3); pico::launch_accum_pmr(c->X, c->n, nb, (float)(1.0 / (sigma * sigma)), sum, sumsq, c->stream); }
   }
   return cuda_check(c, "pico_pmr");
+}
+
+pico_status pico_forward(pico_ctx* c, const void* x, void* y, int32_t nbatch) {
+  if (!c || !c->smaps) return PICO_E_INVALID;
+  if (nbatch < 0 || (nbatch > 0 && (!x || !y))) return fail(c, PICO_E_INVALID, "bad batch or pointer");
+  const float2* xi = static_cast<const float2*>(x);
+  float2* yo = static_cast<float2*>(y);
+  pico_status st = PICO_OK;
+  if (c->kind == PICO_CARTESIAN) {
+    if (!pico::fft_length_supported(c->nx) || !pico::fft_length_supported(c->ny))
+      return fail(c, PICO_E_UNSUPPORTED, "nx or ny has no FFT split in this build (forward operator)");
+    const int chunk = std::max(1, 65535 / c->nc);
+    const float scale = (float)(1.0 / std::sqrt((double)c->n));
+    for (int32_t b0 = 0; b0 < nbatch; b0 += chunk) {
+      const int nb = std::min(chunk, nbatch - b0);
+      float2* yb = yo + (size_t)b0 * c->nc * c->n;
+      { Launch L(c, 3); pico::launch_cart_smul(xi + (size_t)b0 * c->n, c->smaps, yb, nb, c->nc, c->n, c->stream); }
+      { Launch L(c, 3); pico::launch_fft_rows(c->nx, yb, c->twx, c->ny, nb * c->nc, c->n, -1, c->stream); }
+      { Launch L(c, 3); pico::launch_fft_cols(c->ny, yb, c->tw, c->nx, nb * c->nc, c->n, -1, c->stream); }
+      { Launch L(c, 3); pico::launch_cart_mask_scale(yb, c->mask, nb * c->nc, c->ny, c->nx, scale, c->stream); }
+    }
+  } else {
+    if ((st = ensure_kbuf(c)) != PICO_OK) return st;
+    const int L = c->sop.L;
+    for (int32_t b0 = 0; b0 < nbatch; b0 += c->max_batch) {
+      const int nb = std::min(c->max_batch, nbatch - b0);
+      { Launch Lk(c, 3); pico::launch_spiral_pad(c->sop, xi + (size_t)b0 * c->n, c->G, nb, c->stream); }
+      { Launch Lk(c, 3); pico::launch_fft_rows(L, c->G, c->tw2, L, nb * c->nc, (int64_t)L * L, -1, c->stream); }
+      { Launch Lk(c, 3); pico::launch_fft_cols(L, c->G, c->tw2, L, nb * c->nc, (int64_t)L * L, -1, c->stream); }
+      { Launch Lk(c, 3); pico::launch_nufft_interp(c->sop, c->G, yo + (size_t)b0 * c->nc * c->nsamp, nb, c->stream); }
+    }
+  }
+  return cuda_check(c, "pico_forward");
+}
+
+pico_status pico_adjoint(pico_ctx* c, const void* y, void* x, int32_t nbatch) {
+  if (!c || !c->smaps) return PICO_E_INVALID;
+  if (nbatch < 0 || (nbatch > 0 && (!x || !y))) return fail(c, PICO_E_INVALID, "bad batch or pointer");
+  if (c->kind == PICO_CARTESIAN && c->cop.M1 == 0)
+    return fail(c, PICO_E_UNSUPPORTED, "nx has no FFT split in this build (adjoint operator)");
+  pico_status st = ensure_kbuf(c);
+  if (st != PICO_OK) return st;
+  const float2* yi = static_cast<const float2*>(y);
+  float2* xo = static_cast<float2*>(x);
+  const int64_t kper = c->kind == PICO_CARTESIAN ? c->n : c->nsamp;
+  for (int32_t b0 = 0; b0 < nbatch; b0 += c->max_batch) {
+    const int nb = std::min(c->max_batch, nbatch - b0);
+    const float2* yb = yi + (size_t)b0 * c->nc * kper;
+    if (c->kind == PICO_CARTESIAN) {
+      { Launch L(c, 3); pico::launch_cart_pmr_cols(c->cop, c->G, nb, 0, 0, 0.f, c->stream, yb); }
+      { Launch L(c, 3); pico::launch_cart_rows_adjoint(c->cop, c->G, xo + (size_t)b0 * c->n, nb, c->stream); }
+    } else {
+      { Launch L(c, 3); pico::launch_grid_pmr(c->sop, c->G, nb, 0, 0, 0.f, c->stream, yb); }
+      { Launch L(c, 3, 2); pico::launch_grid_adjoint_rest(c->sop, c->G, xo + (size_t)b0 * c->n, nb, c->stream); }
+    }
+  }
+  return cuda_check(c, "pico_adjoint");
 }
 
 pico_status pico_finalize(pico_ctx* c, const double* sum, const double* sumsq, int64_t count, float* var,
@@ -670,6 +820,8 @@ void pico_destroy(pico_ctx* c) {
     cudaEventDestroy(r.b);
   }
   for (cudaEvent_t e : c->event_pool) cudaEventDestroy(e);
+  for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second.first);
+  if (c->cap) cudaStreamDestroy(c->cap);
   for (void* p : c->allocs) cudaFree(p);
   delete c;
 }

@@ -7,7 +7,7 @@ namespace pico {
 template <int N1, int N2>
 void launch_col_normal_t(const CartOp&, const float2*, float2*, int, float, const CgArgs*, int, cudaStream_t);
 template <int N1, int N2>
-void launch_col_pmr_t(const CartOp&, float2*, int, uint64_t, int64_t, float, cudaStream_t);
+void launch_col_pmr_t(const CartOp&, float2*, int, uint64_t, int64_t, float, cudaStream_t, const float2*);
 template <int M1, int M2>
 void launch_row_adjoint_t(const CartOp&, const float2*, float2*, int, cudaStream_t);
 
@@ -30,7 +30,6 @@ bool cart_supported(int ny, int nx, int* N1, int* N2, int* M1, int* M2) {
   return split_of(ny, N1, N2);
 }
 
-int cart_col_tiles(const CartOp& op) { return (op.nx + 15) / 16; }
 
 void launch_cart_apply(const CartOp& op, const float2* x, float2* y, int nb, float lam, cudaStream_t s) {
 #define PICO_CASE(N, A, B) \
@@ -47,9 +46,9 @@ void launch_cart_cg_normal(const CartOp& op, const CgArgs& a, int nb, int it, fl
 }
 
 void launch_cart_pmr_cols(const CartOp& op, float2* G, int nb, uint64_t seed, int64_t rep_begin, float sigma,
-                          cudaStream_t s) {
+                          cudaStream_t s, const float2* data) {
 #define PICO_CASE(N, A, B) \
-  if (op.N1 == A && op.N2 == B) return launch_col_pmr_t<A, B>(op, G, nb, seed, rep_begin, sigma, s);
+  if (op.N1 == A && op.N2 == B) return launch_col_pmr_t<A, B>(op, G, nb, seed, rep_begin, sigma, s, data);
   PICO_SIZES(PICO_CASE)
 #undef PICO_CASE
 }

@@ -22,7 +22,7 @@
 
 namespace pico {
 
-constexpr int kColTile = 16;  // columns per CTA
+constexpr int kColTile = 16;  // columns per CTA of the PMR column kernel
 constexpr int kRowTile = 16;  // rows per CTA of the row transforms
 
 template <int N1, int N2>
@@ -49,34 +49,110 @@ __device__ __forceinline__ double* cg_pq(const CgArgs& a, int b, int it) {
 }
 
 // ---------------------------------------------------------------------------
-// Normal operator q = (A^H A + lam) p on column tiles.
+// Normal operator q = (A^H A + lam) p on column tiles of kNormTile columns.
 // CG = true fuses the CG direction update p = r + beta p (beta from the
 // per-iteration r^H r partials) and emits the p^H q partial of this tile.
+//
+// The coil sensitivities of the tile are staged through shared memory with
+// cp.async, one coil ahead of the FFTs (double buffer), so their L2 latency is
+// hidden; the search direction and the accumulator stay in registers.  Small
+// tiles (8 columns, 8 * max(N1, N2) threads) let three CTAs share an SM so
+// that one CTA's barriers overlap another's arithmetic.
 // ---------------------------------------------------------------------------
+template <int N1, int N2>
+struct NormShape {
+  static constexpr int N = N1 * N2;
+  static constexpr int NC = kNormTile;
+  static constexpr int NT = (NC * (N1 > N2 ? N1 : N2) + 31) / 32 * 32;
+  // Frequency jobs are ordered even k2 first, then odd k2 (see k2_of), so the
+  // two groups of a half-warp differ by 2; a k2 stride of 4 (mod 16) float2
+  // then puts them on different bank halves (conflict-free), and the four
+  // groups of a warp share a parity -- for uniform R = 2 masks also a mask class.
+  static constexpr int KST = N1 * NC + ((N1 * NC) % 16 == 0 ? 4 : 12);
+  static constexpr size_t buf = (size_t)N2 * KST * sizeof(float2);
+  static constexpr size_t stile = (size_t)N * NC * sizeof(float2);
+  static constexpr size_t smem = buf + 2 * stile + (size_t)N * sizeof(float2) + (size_t)N * sizeof(float) + 64;
+};
+
+__device__ __forceinline__ void cp_async8(void* smem_dst, const void* gmem_src, bool valid) {
+  const unsigned dst = (unsigned)__cvta_generic_to_shared(smem_dst);
+  const int bytes = valid ? 8 : 0;  // 0: zero-fill without reading global memory
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(dst), "l"(gmem_src), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gmem_src, bool valid) {
+  const unsigned dst = (unsigned)__cvta_generic_to_shared(smem_dst);
+  const int bytes = valid ? 16 : 0;
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(dst), "l"(gmem_src), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
 template <int N1, int N2, bool CG>
-__global__ void __launch_bounds__(ColShape<N1, N2>::NT, 1)
+__global__ void __launch_bounds__(NormShape<N1, N2>::NT, 3)
     k_col_normal(CartOp op, const float2* __restrict__ xin, float2* __restrict__ yout, float lam, CgArgs a,
                  int it) {
+  using Sh = NormShape<N1, N2>;
   constexpr int N = N1 * N2;
-  constexpr int NT = ColShape<N1, N2>::NT;
+  constexpr int NT = Sh::NT;
+  constexpr int NC = Sh::NC;
+  constexpr int KST = Sh::KST;
   extern __shared__ __align__(16) unsigned char smraw[];
-  float2* buf = reinterpret_cast<float2*>(smraw);  // [N2][N1][kColTile]
-  float2* tws = buf + N * kColTile;                 // [N]
-  float* ym = reinterpret_cast<float*>(tws + N);    // [N]
+  float2* buf = reinterpret_cast<float2*>(smraw);                            // [N2][KST]
+  float2* stile = reinterpret_cast<float2*>(smraw + Sh::buf);                // [2][N][NC]
+  float2* tws = reinterpret_cast<float2*>(smraw + Sh::buf + 2 * Sh::stile);  // [N]
+  float* ym = reinterpret_cast<float*>(tws + N);                             // [N]
+  unsigned char* knz = reinterpret_cast<unsigned char*>(ym + N);             // [N2] frequency-group class
   __shared__ double red[(NT + 31) / 32];
   __shared__ float sh_beta;
   __shared__ int sh_done;
 
   const int t = threadIdx.x;
-  const int col = t % kColTile, job = t / kColTile;
+  const int col = t % NC, job = t / NC;
   const int b = blockIdx.y;
-  const int nx = op.nx;
-  const int colg = blockIdx.x * kColTile + col;
+  const int nx = op.nx, ny = op.ny;
+  const int col0 = blockIdx.x * NC;
+  const int colg = col0 + col;
   const bool cval = colg < nx;
+
+  // stage the first coil's sensitivities while the CG scalars are summed;
+  // 16-byte copies (two columns) when rows are 16-byte aligned (nx even)
+  const bool even = (nx & 1) == 0;
+  auto stage = [&](int c, int slot) {
+    const float2* __restrict__ S = op.smaps + (size_t)c * ny * nx;
+    float2* dst = stile + (size_t)slot * N * NC;
+    if (even) {
+      for (int e = t; e < N * NC / 2; e += NT) {
+        const int row = e / (NC / 2), cc = 2 * (e % (NC / 2));
+        const bool v = col0 + cc < nx;
+        cp_async16(dst + 2 * e, v ? (const void*)(S + (size_t)row * nx + col0 + cc) : (const void*)S, v);
+      }
+    } else {
+      for (int e = t; e < N * NC; e += NT) {
+        const int row = e / NC, cc = e % NC;
+        const bool v = col0 + cc < nx;
+        cp_async8(dst + e, v ? (const void*)(S + (size_t)row * nx + col0 + cc) : (const void*)S, v);
+      }
+    }
+    cp_async_commit();
+  };
+  stage(0, 0);
 
   for (int i = t; i < N; i += NT) {
     tws[i] = op.tw[i];
     ym[i] = op.ymul[i];
+  }
+  // class of each frequency group k2 under the mask: 0 none of its N1
+  // frequencies sampled (spectrum zero), 1 all sampled with one weight (the
+  // DFT_N1 / inverse DFT_N1 pair is N1 x identity), 2 anything else
+  if (t < N2) {
+    const float w0 = op.ymul[t];
+    bool any = false, uniform = true;
+    for (int k1 = 0; k1 < N1; ++k1) {
+      const float w = op.ymul[t + N2 * k1];
+      any |= w != 0.f;
+      uniform &= w == w0;
+    }
+    knz[t] = !any ? 0 : (uniform ? 1 : 2);
   }
   if (CG) {
     if (t < 32) {
@@ -90,12 +166,17 @@ __global__ void __launch_bounds__(ColShape<N1, N2>::NT, 1)
     }
   }
   __syncthreads();
-  if (CG && sh_done) return;
+  if (CG && sh_done) {
+    cp_async_wait_all();  // leave no copy in flight
+    return;
+  }
 
-  const size_t img = (size_t)b * op.ny * nx;
+  const size_t img = (size_t)b * ny * nx;
   const bool rowjob = job < N1;
   const bool freqjob = job < N2;
-  const int n1 = job, k2 = job;
+  const int n1 = job;
+  // frequency group of this frequency job: even groups first, then odd ones
+  const int k2 = (N2 % 2 == 0) ? (job < N2 / 2 ? 2 * job : 2 * (job - N2 / 2) + 1) : job;
 
   float2 p[N2], acc[N2];
   if (rowjob) {
@@ -122,41 +203,61 @@ __global__ void __launch_bounds__(ColShape<N1, N2>::NT, 1)
       acc[n2] = make_float2(0.f, 0.f);
     }
   }
+  const int fcls = freqjob ? knz[k2] : 0;
+  const float fw = freqjob ? (float)N1 * ym[k2] : 0.f;
 
+  // Two barriers per coil: (A) after the forward row-job pass, (B) after the
+  // frequency pass.  Coil c+1's sensitivities are copied during the frequency
+  // pass of coil c (its slot was last read in the inverse pass of coil c-1,
+  // which every thread finished before barrier A of coil c) and waited for
+  // before barrier B, so the inverse pass of coil c and the forward pass of
+  // coil c+1 run back to back without a barrier between them.
+  cp_async_wait_all();
+  __syncthreads();  // coil 0 staged
   for (int c = 0; c < op.nc; ++c) {
-    const float2* __restrict__ S = op.smaps + (size_t)c * op.ny * nx;
-    float2 s[N2];
+    const float2* __restrict__ Ss = stile + (size_t)(c & 1) * N * NC;
     if (rowjob) {
       float2 z[N2];
 #pragma unroll
-      for (int n2 = 0; n2 < N2; ++n2) {
-        s[n2] = cval ? __ldg(S + (size_t)(n1 + N1 * n2) * nx + colg) : make_float2(0.f, 0.f);
-        z[n2] = cmul(s[n2], p[n2]);
-      }
+      for (int n2 = 0; n2 < N2; ++n2) z[n2] = cmul(Ss[(n1 + N1 * n2) * NC + col], p[n2]);
       DFT<N2, -1>::run(z);
 #pragma unroll
-      for (int k = 0; k < N2; ++k) buf[(k * N1 + n1) * kColTile + col] = k == 0 ? z[0] : cmul(z[k], tws[n1 * k]);
+      for (int k = 0; k < N2; ++k) buf[k * KST + n1 * NC + col] = k == 0 ? z[0] : cmul(z[k], tws[n1 * k]);
     }
-    __syncthreads();
-    if (freqjob) {
+    __syncthreads();  // (A)
+    if (c + 1 < op.nc) stage(c + 1, (c + 1) & 1);
+    if (fcls == 2) {
       float2 y[N1];
 #pragma unroll
-      for (int m = 0; m < N1; ++m) y[m] = buf[(k2 * N1 + m) * kColTile + col];
+      for (int m = 0; m < N1; ++m) y[m] = buf[k2 * KST + m * NC + col];
       DFT<N1, -1>::run(y);
 #pragma unroll
       for (int k1 = 0; k1 < N1; ++k1) y[k1] = cscale(y[k1], ym[k2 + N2 * k1]);
       DFT<N1, 1>::run(y);
 #pragma unroll
-      for (int m = 0; m < N1; ++m) buf[(k2 * N1 + m) * kColTile + col] = m == 0 ? y[0] : cmul_cb(y[m], tws[m * k2]);
+      for (int m = 0; m < N1; ++m) buf[k2 * KST + m * NC + col] = m == 0 ? y[0] : cmul_cb(y[m], tws[m * k2]);
+    } else if (fcls == 1) {
+      // every frequency of the group sampled with weight ym: forward and inverse
+      // DFT_N1 cancel to N1 x identity; only the conjugate twiddle remains
+#pragma unroll
+      for (int m = 0; m < N1; ++m) {
+        const float2 v = cscale(buf[k2 * KST + m * NC + col], fw);
+        buf[k2 * KST + m * NC + col] = m == 0 ? v : cmul_cb(v, tws[m * k2]);
+      }
+    } else if (freqjob) {
+      // no sampled frequency in this group: the masked spectrum is zero
+#pragma unroll
+      for (int m = 0; m < N1; ++m) buf[k2 * KST + m * NC + col] = make_float2(0.f, 0.f);
     }
-    __syncthreads();
+    cp_async_wait_all();
+    __syncthreads();  // (B): frequency pass done, coil c+1 staged
     if (rowjob) {
       float2 z[N2];
 #pragma unroll
-      for (int k = 0; k < N2; ++k) z[k] = buf[(k * N1 + n1) * kColTile + col];
+      for (int k = 0; k < N2; ++k) z[k] = buf[k * KST + n1 * NC + col];
       DFT<N2, 1>::run(z);
 #pragma unroll
-      for (int n2 = 0; n2 < N2; ++n2) acc[n2] = cfma_c(acc[n2], s[n2], z[n2]);
+      for (int n2 = 0; n2 < N2; ++n2) acc[n2] = cfma_c(acc[n2], Ss[(n1 + N1 * n2) * NC + col], z[n2]);
     }
   }
 
@@ -185,7 +286,8 @@ __global__ void __launch_bounds__(ColShape<N1, N2>::NT, 1)
 // ---------------------------------------------------------------------------
 template <int N1, int N2>
 __global__ void __launch_bounds__(ColShape<N1, N2>::NT, 1)
-    k_col_pmr(CartOp op, float2* __restrict__ G, uint64_t seed, int64_t rep_begin, float sigma, float scale) {
+    k_col_pmr(CartOp op, float2* __restrict__ G, uint64_t seed, int64_t rep_begin, float sigma, float scale,
+              const float2* __restrict__ data) {
   constexpr int N = N1 * N2;
   constexpr int NT = ColShape<N1, N2>::NT;
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -211,7 +313,7 @@ __global__ void __launch_bounds__(ColShape<N1, N2>::NT, 1)
       float2 v = make_float2(0.f, 0.f);
       if (cval && op.mask[ky]) {
         const uint64_t e = ((uint64_t)c * ny + ky) * (uint64_t)nx + colg;
-        v = draw_cnoise(key, e, sigma);
+        v = data ? data[((size_t)b * op.nc * ny) * nx + e] : draw_cnoise(key, e, sigma);
       }
       y[k1] = v;
     }
@@ -305,8 +407,8 @@ __global__ void __launch_bounds__(RowShape<M1, M2>::NT, 1)
 template <int N1, int N2>
 void launch_col_normal_t(const CartOp& op, const float2* x, float2* y, int nb, float lam, const CgArgs* a, int it,
                          cudaStream_t s) {
-  using Sh = ColShape<N1, N2>;
-  const dim3 grid((op.nx + kColTile - 1) / kColTile, nb);
+  using Sh = NormShape<N1, N2>;
+  const dim3 grid(cart_normal_tiles(op.nx), nb);
   if (a) {
     auto k = k_col_normal<N1, N2, true>;
     cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Sh::smem);
@@ -321,13 +423,13 @@ void launch_col_normal_t(const CartOp& op, const float2* x, float2* y, int nb, f
 
 template <int N1, int N2>
 void launch_col_pmr_t(const CartOp& op, float2* G, int nb, uint64_t seed, int64_t rep_begin, float sigma,
-                      cudaStream_t s) {
+                      cudaStream_t s, const float2* data) {
   using Sh = ColShape<N1, N2>;
   const dim3 grid((op.nx + kColTile - 1) / kColTile, nb * op.nc);
   auto k = k_col_pmr<N1, N2>;
   cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Sh::smem);
   const float scale = (float)(1.0 / sqrt((double)op.ny * (double)op.nx));
-  k<<<grid, Sh::NT, Sh::smem, s>>>(op, G, seed, rep_begin, sigma, scale);
+  k<<<grid, Sh::NT, Sh::smem, s>>>(op, G, seed, rep_begin, sigma, scale, data);
 }
 
 template <int M1, int M2>

@@ -83,7 +83,12 @@ __global__ void __launch_bounds__(kVecThreads) k_cg_update(CgArgs a, int it) {
     }
   }
   __syncthreads();
-  if (sh_state == 1) return;
+  if (sh_state == 1) {
+    // converged (or stopped): carry this block's r^H r partial forward so that
+    // every later iteration of this system sees the same, converged value
+    if (threadIdx.x == 0) rr_at_w(a, b, it + 1)[blockIdx.x] = rr_at(a, b, it)[blockIdx.x];
+    return;
+  }
   if (sh_state == 2) {
     // CG breakdown: record it and make the probe look converged from here on.
     if (threadIdx.x == 0) {
@@ -187,6 +192,25 @@ __global__ void k_finalize(const double* sum, const double* sumsq, int64_t n, in
   }
 }
 
+// partial sums over voxels of (s/N)^2 and the squared standard error of the mean
+__global__ void __launch_bounds__(256) k_stderr_parts(const double* sum, const double* sumsq, int64_t n,
+                                                      int64_t count, double* part) {
+  __shared__ double scratch[8];
+  double a = 0.0, b = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x; i < n; i += (int64_t)gridDim.x * 256) {
+    const double m = sum[i] / (double)count;
+    const double v = fmax(sumsq[i] / (double)count - m * m, 0.0) / (double)(count - 1);
+    a += m * m;
+    b += v;
+  }
+  const double ta = block_sum_d(a, scratch);
+  const double tb = block_sum_d(b, scratch);
+  if (threadIdx.x == 0) {
+    part[2 * blockIdx.x] = ta;
+    part[2 * blockIdx.x + 1] = tb;
+  }
+}
+
 __global__ void k_gfactor(const float* va, const float* vr, int64_t n, double R, float* g) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
@@ -261,6 +285,10 @@ void launch_accum_pmr(const float2* X, int64_t n, int nb, float inv_sigma2, doub
 void launch_finalize(const double* sum, const double* sumsq, int64_t n, int64_t count, float* var, float* se,
                      cudaStream_t s) {
   k_finalize<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(sum, sumsq, n, count, var, se);
+}
+void launch_stderr_parts(const double* sum, const double* sumsq, int64_t n, int64_t count, double* part, int nblk,
+                         cudaStream_t s) {
+  k_stderr_parts<<<nblk, 256, 0, s>>>(sum, sumsq, n, count, part);
 }
 void launch_gfactor(const float* va, const float* vr, int64_t n, double R, float* g, cudaStream_t s) {
   k_gfactor<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(va, vr, n, R, g);

@@ -31,9 +31,11 @@ struct Split {
 };
 
 // ---- column layout ----
-template <int P1, int P2, int SIGN>
+template <int P, int SIGN, int NZ>
+__device__ __forceinline__ void dft_nz(float2 (&z)[P]);
+template <int P1, int P2, int SIGN, int NZ = P2>
 __device__ __forceinline__ void cola_store(float2 (&z)[P2], int n1, int ln, float2* buf, const float2* tws) {
-  DFT<P2, SIGN>::run(z);
+  dft_nz<P2, SIGN, NZ>(z);
 #pragma unroll
   for (int k = 0; k < P2; ++k) {
     const float2 w = tws[n1 * k];
@@ -64,11 +66,21 @@ __device__ __forceinline__ void cola_load(float2 (&z)[P2], int n1, int ln, const
   DFT<P2, SIGN>::run(z);
 }
 
+// DFT_P of which only the first NZ inputs can be non-zero (zero-padded lines)
+template <int P, int SIGN, int NZ>
+__device__ __forceinline__ void dft_nz(float2 (&z)[P]) {
+  if constexpr (NZ == P) {
+    DFT<P, SIGN>::run(z);
+  } else {
+    DFTZ<P, SIGN, NZ>::run(z);
+  }
+}
+
 // ---- row layout ----
-template <int P1, int P2, int SIGN>
+template <int P1, int P2, int SIGN, int NZ = P2>
 __device__ __forceinline__ void rowa_store(float2 (&z)[P2], int n1, int ln, float2* buf, const float2* tws) {
   constexpr int LD = Split<P1, P2>::LD;
-  DFT<P2, SIGN>::run(z);
+  dft_nz<P2, SIGN, NZ>(z);
 #pragma unroll
   for (int k = 0; k < P2; ++k) {
     const float2 w = tws[n1 * k];

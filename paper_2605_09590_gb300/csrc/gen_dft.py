@@ -21,17 +21,21 @@ from types import SimpleNamespace
 import numpy as np
 
 SIZES = [2, 3, 4, 5, 6, 8, 10, 12, 15, 16, 20, 24, 30, 32]
+ZERO_TAIL = [(8, 4), (16, 8)]   # (N, non-zero leading inputs) for zero-padded transforms
 
 
 def flit(v: float) -> str:
     return repr(float(v)) + "f"
 
 
+ZERO = "ZERO"   # an input known to be zero; ops on it are folded away
+
+
 class Gen:
     def __init__(self, rng):
         self.lines: list[str] = []
         self.n = 0
-        self.val: dict[str, complex] = {}
+        self.val: dict[str, complex] = {ZERO: 0j}
         self.flops = 0
 
     def fresh(self, value: complex) -> str:
@@ -42,18 +46,28 @@ class Gen:
 
     # ---- primitive ops (each emits one CUDA statement and tracks the value) ----
     def add(self, a, b):
+        if a == ZERO:
+            return b
+        if b == ZERO:
+            return a
         r = self.fresh(self.val[a] + self.val[b])
         self.lines.append(f"const float2 {r} = make_float2({a}.x + {b}.x, {a}.y + {b}.y);")
         self.flops += 2
         return r
 
     def sub(self, a, b):
+        if b == ZERO:
+            return a
+        if a == ZERO:
+            return self.neg(b)
         r = self.fresh(self.val[a] - self.val[b])
         self.lines.append(f"const float2 {r} = make_float2({a}.x - {b}.x, {a}.y - {b}.y);")
         self.flops += 2
         return r
 
     def scale(self, a, c):
+        if a == ZERO:
+            return ZERO
         r = self.fresh(self.val[a] * c)
         self.lines.append(f"const float2 {r} = make_float2({flit(c)} * {a}.x, {flit(c)} * {a}.y);")
         self.flops += 2
@@ -61,6 +75,8 @@ class Gen:
 
     def mulj(self, a, s):
         """``a * (s * i)`` with ``s = +-1`` (no arithmetic, a swap and a negation)."""
+        if a == ZERO:
+            return ZERO
         r = self.fresh(self.val[a] * 1j * s)
         if s > 0:
             self.lines.append(f"const float2 {r} = make_float2(-{a}.y, {a}.x);")
@@ -69,12 +85,18 @@ class Gen:
         return r
 
     def neg(self, a):
+        if a == ZERO:
+            return ZERO
         r = self.fresh(-self.val[a])
         self.lines.append(f"const float2 {r} = make_float2(-{a}.x, -{a}.y);")
         return r
 
     def fma_add(self, a, b, c):
         """``a + c * b`` for a real constant ``c``."""
+        if b == ZERO:
+            return a
+        if a == ZERO:
+            return self.scale(b, c)
         r = self.fresh(self.val[a] + c * self.val[b])
         self.lines.append(
             f"const float2 {r} = make_float2(fmaf({flit(c)}, {b}.x, {a}.x), fmaf({flit(c)}, {b}.y, {a}.y));")
@@ -83,6 +105,8 @@ class Gen:
 
     def twiddle(self, a, e: int, N: int, sign: int):
         """``a * exp(sign * 2 pi i e / N)``."""
+        if a == ZERO:
+            return ZERO
         e %= N
         if e == 0:
             return a
@@ -166,13 +190,17 @@ class Gen:
         return X
 
 
-def codelet(N: int, sign: int, rng) -> tuple[str, int]:
+def codelet(N: int, sign: int, rng, nz: int | None = None) -> tuple[str, int]:
+    """DFT of N inputs of which only the first ``nz`` may be non-zero."""
+    nz = N if nz is None else nz
     g = Gen(rng)
     vals = rng.standard_normal(N) + 1j * rng.standard_normal(N)
+    vals[nz:] = 0
     ins = []
     for i in range(N):
-        name = f"i{i}"
-        g.val[name] = vals[i]
+        name = f"i{i}" if i < nz else ZERO
+        if i < nz:
+            g.val[name] = vals[i]
         ins.append(name)
     outs = g.dft(ins, sign)
     n = np.arange(N)
@@ -181,8 +209,9 @@ def codelet(N: int, sign: int, rng) -> tuple[str, int]:
     if not np.allclose(got, want, rtol=1e-12, atol=1e-12):
         raise AssertionError(f"codelet N={N} sign={sign} is wrong")
     # execute the emitted statements themselves (not the tracked values)
-    env = {"make_float2": lambda a, b: SimpleNamespace(x=a, y=b), "fmaf": lambda a, b, c: a * b + c}
-    for i in range(N):
+    env = {"make_float2": lambda a, b: SimpleNamespace(x=a, y=b), "fmaf": lambda a, b, c: a * b + c,
+           ZERO: SimpleNamespace(x=0.0, y=0.0)}
+    for i in range(nz):
         env[f"i{i}"] = SimpleNamespace(x=vals[i].real, y=vals[i].imag)
     for line in g.lines:
         m = re.fullmatch(r"const float2 (t\d+) = (.*);", line)
@@ -191,9 +220,9 @@ def codelet(N: int, sign: int, rng) -> tuple[str, int]:
     got2 = np.array([env[o].x + 1j * env[o].y for o in outs])
     if not np.allclose(got2, want, rtol=1e-12, atol=1e-12):
         raise AssertionError(f"emitted code for N={N} sign={sign} is wrong")
-    body = [f"    const float2 i{i} = v[{i}];" for i in range(N)]
+    body = [f"    const float2 i{i} = v[{i}];" for i in range(nz)]
     body += ["    " + l for l in g.lines]
-    body += [f"    v[{k}] = {outs[k]};" for k in range(N)]
+    body += [f"    v[{k}] = {'make_float2(0.f, 0.f)' if outs[k] == ZERO else outs[k]};" for k in range(N)]
     return "\n".join(body), g.flops
 
 
@@ -218,6 +247,17 @@ def main(out_path: str):
             parts.append(f"  static constexpr int flops = {flops};")
             parts.append("};")
             table.append((N, sign, flops))
+    # zero-tail variants: DFTZ<N, SIGN, NZ> treats inputs NZ..N-1 as zero
+    parts.append("template <int N, int SIGN, int NZ> struct DFTZ;")
+    for N, nz in ZERO_TAIL:
+        for sign in (-1, 1):
+            body, flops = codelet(N, sign, rng, nz)
+            parts.append(f"template <> struct DFTZ<{N}, {sign}, {nz}> {{")
+            parts.append("  static __device__ __forceinline__ void run(float2* v) {")
+            parts.append(body)
+            parts.append("  }")
+            parts.append(f"  static constexpr int flops = {flops};")
+            parts.append("};")
     parts.append("}  // namespace pico")
     with open(out_path, "w") as f:
         f.write("\n".join(parts) + "\n")

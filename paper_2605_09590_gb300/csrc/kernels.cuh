@@ -40,6 +40,9 @@ void launch_accum_pmr(const float2* X, int64_t n, int nb, float inv_sigma2, doub
 void launch_finalize(const double* sum, const double* sumsq, int64_t n, int64_t count, float* var,
                      float* stderr_out, cudaStream_t s);
 void launch_gfactor(const float* var_acc, const float* var_ref, int64_t n, double R, float* g, cudaStream_t s);
+// per-block partials (sum of mean^2, sum of stderr^2) of running PICO sums over `count` probes
+void launch_stderr_parts(const double* sum, const double* sumsq, int64_t n, int64_t count, double* part, int nblk,
+                         cudaStream_t s);
 void launch_norm2_part(const float2* x, int64_t n, double* part, cudaStream_t s);
 void launch_scale_by_norm(const float2* y, float2* x, int64_t n, const double* part, int nparts,
                           double* norm_out, cudaStream_t s);
@@ -59,14 +62,18 @@ struct CartOp {
   const float2* twx;        // [nx] exp(-2 pi i e / nx)
 };
 bool cart_supported(int ny, int nx, int* N1, int* N2, int* M1, int* M2);
-int cart_col_tiles(const CartOp& op);
+// Columns per CTA of the normal operator; the number of column tiles is also
+// the number of p^H q partials per image and iteration.
+constexpr int kNormTile = 8;
+inline int cart_normal_tiles(int nx) { return (nx + kNormTile - 1) / kNormTile; }
 // y = (A^H A + lam I) x for nb images
 void launch_cart_apply(const CartOp& op, const float2* x, float2* y, int nb, float lam, cudaStream_t s);
 // CG iteration `it`, normal-operator half: P = R + beta P; Q = (A^H A + lam) P; pq partials
 void launch_cart_cg_normal(const CartOp& op, const CgArgs& a, int nb, int it, float lam, cudaStream_t s);
-// PMR: G[b][c] = F^H_y (mask . n_{b,c}) (hybrid y, kx), scaled by 1/sqrt(ny nx)
+// PMR: G[b][c] = F^H_y (mask . n_{b,c}) (hybrid y, kx), scaled by 1/sqrt(ny nx);
+// with data != nullptr the k-space values come from data [nb][nc][ny][nx] instead of the noise draw
 void launch_cart_pmr_cols(const CartOp& op, float2* G, int nb, uint64_t seed, int64_t rep_begin, float sigma,
-                          cudaStream_t s);
+                          cudaStream_t s, const float2* data = nullptr);
 // out[b] = sum_c conj(S_c) . F^H_x G[b][c]
 void launch_cart_rows_adjoint(const CartOp& op, const float2* G, float2* out, int nb, cudaStream_t s);
 
@@ -96,7 +103,20 @@ void launch_toep_apply(const SpiralOp& op, const float2* x, float2* y, float2* G
 void launch_toep_cg_normal(const SpiralOp& op, const CgArgs& a, float2* G, int nb, int it, float lam,
                            cudaStream_t s);
 void launch_grid_pmr(const SpiralOp& op, float2* Qgrid, int nb, uint64_t seed, int64_t rep_begin, float sigma,
-                     cudaStream_t s);
+                     cudaStream_t s, const float2* data = nullptr);
 void launch_grid_adjoint_rest(const SpiralOp& op, float2* Qgrid, float2* out, int nb, cudaStream_t s);
+
+// ---- fft_generic.cu: batched 1-D FFTs along rows / columns of row-major planes ----
+bool fft_length_supported(int L);
+bool launch_fft_rows(int L, float2* data, const float2* tw, int nrows, int planes, int64_t plane_stride, int sign,
+                     cudaStream_t s);
+bool launch_fft_cols(int L, float2* data, const float2* tw, int ncols, int planes, int64_t plane_stride, int sign,
+                     cudaStream_t s);
+
+// ---- encode.cu: forward encoding operator pieces ----
+void launch_cart_smul(const float2* x, const float2* S, float2* G, int nb, int nc, int64_t n, cudaStream_t s);
+void launch_cart_mask_scale(float2* G, const uint8_t* mask, int planes, int ny, int nx, float scale, cudaStream_t s);
+void launch_spiral_pad(const SpiralOp& op, const float2* x, float2* G, int nb, cudaStream_t s);
+void launch_nufft_interp(const SpiralOp& op, const float2* G, float2* y, int nb, cudaStream_t s);
 
 }  // namespace pico

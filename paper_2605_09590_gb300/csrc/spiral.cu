@@ -92,7 +92,7 @@ __global__ void k_toep_finalize(const float2* c, int64_t count, float scale, flo
 // CTA: one 16x16 grid tile, one replica, kCoilGroup coils; thread = grid point.
 constexpr int kCoilGroup = 4;
 __global__ void __launch_bounds__(256) k_grid_pmr(SpiralOp op, float2* __restrict__ Q, uint64_t seed,
-                                                  int64_t rep_begin, float sigma) {
+                                                  int64_t rep_begin, float sigma, const float2* __restrict__ data) {
   __shared__ float2 s_u[kChunk];
   __shared__ float2 s_w[kChunk][kCoilGroup];
   const int L = op.L;
@@ -119,7 +119,10 @@ __global__ void __launch_bounds__(256) k_grid_pmr(SpiralOp op, float2* __restric
       for (int g = 0; g < kCoilGroup; ++g) {
         const int c = c0 + g;
         float2 v = make_float2(0.f, 0.f);
-        if (c < op.nc) v = cmul(draw_cnoise(key, (uint64_t)c * (uint64_t)op.M + (uint64_t)m, sigma), ph);
+        if (c < op.nc) {
+          const uint64_t e = (uint64_t)c * (uint64_t)op.M + (uint64_t)m;
+          v = cmul(data ? data[(size_t)b * op.nc * op.M + e] : draw_cnoise(key, e, sigma), ph);
+        }
         s_w[threadIdx.x][g] = v;
       }
     }
@@ -200,10 +203,10 @@ void launch_toep_cg_normal(const SpiralOp& op, const CgArgs& a, float2* G, int n
 }
 
 void launch_grid_pmr(const SpiralOp& op, float2* Q, int nb, uint64_t seed, int64_t rep_begin, float sigma,
-                     cudaStream_t s) {
+                     cudaStream_t s, const float2* data) {
   const int tiles = (op.L / 16) * (op.L / 16);
   const dim3 grid(tiles, nb, (op.nc + kCoilGroup - 1) / kCoilGroup);
-  k_grid_pmr<<<grid, 256, 0, s>>>(op, Q, seed, rep_begin, sigma);
+  k_grid_pmr<<<grid, 256, 0, s>>>(op, Q, seed, rep_begin, sigma, data);
 }
 
 void launch_grid_adjoint_rest(const SpiralOp& op, float2* Q, float2* out, int nb, cudaStream_t s) {

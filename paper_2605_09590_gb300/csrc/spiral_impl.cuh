@@ -82,7 +82,7 @@ __global__ void __launch_bounds__(Split<P1, P2>::NT, 1)
     for (int n2 = 0; n2 < P2; ++n2) {
       const int x = n1 + P1 * n2;
       float2 v = make_float2(0.f, 0.f);
-      if (aval && x < N) {
+      if (aval && n2 < P2 / 2) {
         const size_t idx = img + (size_t)ya * N + x;
         if (CG) {
           const float2 r = a.R[idx];
@@ -104,12 +104,13 @@ __global__ void __launch_bounds__(Split<P1, P2>::NT, 1)
     if (ajob) {
       float2 z[P2];
       const float2* __restrict__ S = op.smaps + ((size_t)c * N + (aval ? ya : 0)) * N;
+      // the grid is 2N wide: sample n1 + P1 n2 lies in the image iff n2 < P2/2
 #pragma unroll
       for (int n2 = 0; n2 < P2; ++n2) {
         const int x = n1 + P1 * n2;
-        z[n2] = (aval && x < N) ? cmul(__ldg(S + x), p[n2]) : make_float2(0.f, 0.f);
+        z[n2] = (aval && n2 < P2 / 2) ? cmul(__ldg(S + x), p[n2]) : make_float2(0.f, 0.f);
       }
-      rowa_store<P1, P2, -1>(z, n1, ra, buf, tws);
+      rowa_store<P1, P2, -1, P2 / 2>(z, n1, ra, buf, tws);
     }
     __syncthreads();
     if (bval) {
@@ -144,10 +145,10 @@ __global__ void __launch_bounds__(Split<P1, P2>::NT, 1) k_toep_cols(SpiralOp op,
     float2 z[P2];
 #pragma unroll
     for (int n2 = 0; n2 < P2; ++n2) {
-      const int y = n1 + P1 * n2;
-      z[n2] = y < N ? g[(size_t)y * L + kx] : make_float2(0.f, 0.f);
+      const int y = n1 + P1 * n2;  // rows >= N (n2 >= P2/2) are the zero padding
+      z[n2] = n2 < P2 / 2 ? g[(size_t)y * L + kx] : make_float2(0.f, 0.f);
     }
-    cola_store<P1, P2, -1>(z, n1, ln, buf, tws);
+    cola_store<P1, P2, -1, P2 / 2>(z, n1, ln, buf, tws);
   }
   __syncthreads();
   if (job < P2) {
@@ -163,10 +164,7 @@ __global__ void __launch_bounds__(Split<P1, P2>::NT, 1) k_toep_cols(SpiralOp op,
     float2 z[P2];
     cola_load<P1, P2, 1>(z, n1, ln, buf);
 #pragma unroll
-    for (int n2 = 0; n2 < P2; ++n2) {
-      const int y = n1 + P1 * n2;
-      if (y < N) g[(size_t)y * L + kx] = z[n2];
-    }
+    for (int n2 = 0; n2 < P2 / 2; ++n2) g[(size_t)(n1 + P1 * n2) * L + kx] = z[n2];  // rows < N only
   }
 }
 
@@ -201,9 +199,9 @@ __global__ void __launch_bounds__(Split<P1, P2>::NT, 1)
   const bool bval = bjob && yb < N;
   const size_t img = (size_t)b * N * N;
 
-  float2 acc[P2];
+  float2 acc[P2 / 2];
 #pragma unroll
-  for (int n2 = 0; n2 < P2; ++n2) acc[n2] = make_float2(0.f, 0.f);
+  for (int n2 = 0; n2 < P2 / 2; ++n2) acc[n2] = make_float2(0.f, 0.f);
   for (int c = 0; c < op.nc; ++c) {
     if (bjob) {
       float2 y[P1];
@@ -219,10 +217,7 @@ __global__ void __launch_bounds__(Split<P1, P2>::NT, 1)
       if (aval) {
         const float2* __restrict__ S = op.smaps + ((size_t)c * N + ya) * N;
 #pragma unroll
-        for (int n2 = 0; n2 < P2; ++n2) {
-          const int x = n1 + P1 * n2;
-          if (x < N) acc[n2] = cfma_c(acc[n2], __ldg(S + x), z[n2]);
-        }
+        for (int n2 = 0; n2 < P2 / 2; ++n2) acc[n2] = cfma_c(acc[n2], __ldg(S + n1 + P1 * n2), z[n2]);
       }
     }
     __syncthreads();
@@ -232,9 +227,9 @@ __global__ void __launch_bounds__(Split<P1, P2>::NT, 1)
     const float2* __restrict__ pin = CG ? a.P : xin;
     float2* __restrict__ out = CG ? a.Q : yout;
 #pragma unroll
-    for (int n2 = 0; n2 < P2; ++n2) {
+    for (int n2 = 0; n2 < P2 / 2; ++n2) {
       const int x = n1 + P1 * n2;
-      if (x < N) {
+      {
         const size_t idx = img + (size_t)ya * N + x;
         const float2 pv = pin[idx];
         const float2 q = make_float2(fmaf(lam, pv.x, acc[n2].x), fmaf(lam, pv.y, acc[n2].y));

@@ -97,7 +97,7 @@ pico_status pico_cg_batch_static(const void* smaps_dev, const uint8_t* mask_dev,
 
   const int64_t n = (int64_t)ny * nx;
   const int PB = (int)((n + pico::kVecPerBlock - 1) / pico::kVecPerBlock);
-  const int PA = (nx + 15) / 16;
+  const int PA = pico::cart_normal_tiles(nx);
   // layout of the scratch array for this call
   const size_t vec = align256((size_t)nbatch * n * sizeof(float2));
   const size_t off_R = 0, off_P = vec, off_Q = 2 * vec;

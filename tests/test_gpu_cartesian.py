@@ -105,6 +105,24 @@ def test_cg_stopping_rule_matches_oracle():
         assert relres[b] <= 1e-3
 
 
+def test_cg_stopping_rule_after_other_solves_on_the_same_context():
+    # earlier fixed-iteration solves leave large r^H r partials in the context's
+    # per-iteration tables; a later tolerance-stopped solve must not read them
+    S, cov, mask = case(64, 48, 6, acs=4, corr=True, seed=10)
+    op = pico.Operator(S, mask=mask, noise_cov=cov, power_iters=0, max_batch=8)
+    oop = O.Operator(S, cov, mask=mask)
+    op.cg(to_dev(rand_imgs(8, 64, 48, 1) * 1e3), 60, 0.0)
+    rhs = np.zeros((3, 64, 48), dtype=np.complex64)
+    for b in range(3):
+        rhs[b, 5 + 7 * b, :] = 1.0                      # structured right-hand sides, converge fast
+    x, iters, relres = op.cg(to_dev(rhs), 100, 1e-6, stats=True)
+    x = x.cpu().numpy()
+    for b in range(3):
+        want, it, _ = OS.cg(lambda z: oop.normal(z), rhs[b].astype(np.complex128), 100, 1e-6)
+        assert np.linalg.norm(x[b] - want) / np.linalg.norm(want) < 1e-4
+        assert abs(int(iters[b]) - it) <= 1 and relres[b] <= 1e-6
+
+
 def _pico_sums(op, seed, K, it, kind=pico.PICO_PROBE_PHASE, begin=0):
     s, ss = op.variance_sums(seed, K, it, 0.0, probe_begin=begin, kind=kind)
     return s.cpu().numpy(), ss.cpu().numpy()
@@ -254,3 +272,25 @@ def test_full_size_variance_map_band(knee):
     # 30 CG iterations are not fully converged; allow the truncation bias on top of the band
     assert np.mean(np.abs(z) > 4) < 0.01, np.mean(np.abs(z) > 4)
     assert np.abs(s.cpu().numpy() / K - d).max() / d.max() < 0.2
+
+
+def test_adaptive_stopping_matches_plain_run():
+    S, cov, mask = case(64, 64, 8, R=2, acs=4, corr=True, seed=12)
+    op = pico.Operator(S, mask=mask, noise_cov=cov, power_iters=0, max_batch=16)
+    s = torch.empty((64, 64), dtype=torch.float64, device="cuda")
+    ss = torch.empty_like(s)
+    used, rel = pico.pico_variance_map_adaptive(op.ctx, 9, pico.PICO_PROBE_PHASE, 8, 400, 30, 0.0, 0.02, s, ss)
+    assert 8 <= used <= 400 and used % 8 == 0 and rel <= 0.02
+    s2, ss2 = op.variance_sums(9, used, 30, 0.0)
+    assert torch.equal(s, s2) and torch.equal(ss, ss2)       # same probes, same order, same bits
+    sn, ssn = s2.cpu().numpy(), ss2.cpu().numpy()
+    m = sn / used
+    se = np.sqrt(np.maximum(ssn / used - m * m, 0) / (used - 1))
+    assert abs(np.linalg.norm(se) / np.linalg.norm(m) - rel) < 1e-9
+    # one chunk fewer would not have met the target
+    if used > 8:
+        s3, ss3 = op.variance_sums(9, used - 8, 30, 0.0)
+        n3 = used - 8
+        m3 = s3.cpu().numpy() / n3
+        se3 = np.sqrt(np.maximum(ss3.cpu().numpy() / n3 - m3 * m3, 0) / (n3 - 1))
+        assert np.linalg.norm(se3) / np.linalg.norm(m3) > 0.02
