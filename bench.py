@@ -44,6 +44,9 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-t1pct", action="store_true")
+    ap.add_argument("--serving", type=int, default=0, help="also run the serving mix with this many requests")
+    ap.add_argument("--t1pct-spiral", action="store_true",
+                    help="time to 1%% on the spiral workload (exact reference by unit-vector probing, minutes)")
     return ap.parse_args()
 
 
@@ -220,11 +223,35 @@ def exact_variance_cartesian(op, w, torch):
     return diag
 
 
+def exact_variance_unit_probes(op, w, torch, batch=256):
+    """Exact diag(Sigma) of any operator by unit-vector probing on the GPU:
+    Sigma_kk = x_k^H M x_k with x_k = (M + lam)^-1 e_k (one converged solve and
+    one normal-operator application per voxel, batched)."""
+    n = w.ny * w.nx
+    lam = op.info["lambda_phys"]
+    diag = torch.empty(n, dtype=torch.float64, device="cuda")
+    for k0 in range(0, n, batch):
+        nb = min(batch, n - k0)
+        rhs = torch.zeros((nb, n), dtype=torch.complex64, device="cuda")
+        rhs[torch.arange(nb), torch.arange(k0, k0 + nb)] = 1.0
+        x = op.cg(rhs.view(nb, w.ny, w.nx), 100, 1e-6)
+        y = op.apply_normal(x)                       # (M + lam) x
+        xy = (x.conj() * y).real.double().flatten(1).sum(1)
+        xx = (x.abs() ** 2).double().flatten(1).sum(1)
+        diag[k0:k0 + nb] = xy - lam * xx
+    return diag.view(w.ny, w.nx)
+
+
 def measure_time_to_1pct(op, w, torch, pico, max_n=20000, step=10):
-    ref = exact_variance_cartesian(op, w, torch)
+    if w.kind == "cartesian":
+        ref = exact_variance_cartesian(op, w, torch)
+        how = f"exact diag(Sigma) from {w.ny} structured converged CG solves"
+    else:
+        ref = exact_variance_unit_probes(op, w, torch)
+        how = f"exact diag(Sigma) by unit-vector probing ({w.ny * w.nx} converged solves)"
     ref_std = ref.clamp_min(0).sqrt()
     nref = torch.linalg.vector_norm(ref_std)
-    out = {"reference": f"exact diag(Sigma) from {w.ny} structured converged CG solves", "step": step,
+    out = {"reference": how, "step": step,
            "threshold": 0.01, "nrmse_on": "std maps",
            "reference_range": [float(ref.min()), float(ref.max())]}
     for name in ("pico", "pmr"):
@@ -254,6 +281,69 @@ def measure_time_to_1pct(op, w, torch, pico, max_n=20000, step=10):
                 break
         out[name] = ({"N": hit[0], "seconds_in_steps_of_10": hit[1], "nrmse": hit[2], "curve": curve}
                      if hit else {"N": None, "nrmse_at_max": err, "max_n": max_n, "curve": curve})
+    return out
+
+
+# ---------------------------------------------------------------------------
+# serving mix: Poisson arrivals of uneven requests (p50 / p99 latency, maps/s)
+# ---------------------------------------------------------------------------
+def serving_mix(nreq, seed=0):
+    import numpy as np
+    import synth
+    rng = np.random.default_rng(seed)
+    reqs = []
+    for i in range(nreq):
+        u = rng.random()
+        K = int(rng.choice([32, 64, 128, 256]))
+        if u < 0.5:      # Cartesian, 5-smooth even matrix in [192, 384], 8-32 coils
+            n = int(rng.choice([192, 240, 256, 320, 384]))
+            nc = int(rng.choice([8, 16, 24, 32]))
+            # correlation 0.1 at 15 coils, scaled down for more coils to stay well conditioned
+            rho = 0.1 * min(1.0, (15.0 / nc) ** 0.5)
+            reqs.append(dict(smaps=synth.coil_maps(n, n, nc, i), mask=synth.mask_pe(n, 2, 24),
+                             noise_cov=synth.noise_cov(nc, i, rho=rho), seed=i, nprobes=K, max_iter=30,
+                             kind=f"cart{n}x{nc}"))
+        elif u < 0.8:    # spiral 240^2, 20 coils, R in {2, 3, 4}
+            R = int(rng.choice([2, 3, 4]))
+            reqs.append(dict(smaps=synth.coil_maps(240, 240, 20, i), traj=synth.spiral_traj(240, 16, 4096, R),
+                             lam=0.1, seed=i, nprobes=K, max_iter=30, kind=f"spiral_r{R}"))
+        else:            # 320^2, 15 coils (the knee-shaped operator)
+            reqs.append(dict(smaps=synth.coil_maps(320, 320, 15, i), mask=synth.mask_pe(320, 2, 24),
+                             noise_cov=synth.noise_cov(15, i), seed=i, nprobes=K, max_iter=30, kind="knee320"))
+    return reqs
+
+
+def run_serving(pico, nreq=24, loads=(0.5, 0.8, 0.95), max_active=4):
+    import numpy as np
+    reqs = serving_mix(nreq)
+    strip = lambda r: {k: v for k, v in r.items() if k != "kind"}
+    # closed loop: everything submitted at once -> capacity
+    sv = pico.Server(max_active=max_active, chunk=64)
+    t0 = time.perf_counter()
+    ids = [sv.submit(**strip(r)) for r in reqs]
+    for i in ids:
+        sv.wait(i)
+    cap = nreq / (time.perf_counter() - t0)
+    sv.close()
+    out = {"requests": nreq, "mix": "50% Cartesian 192-384 / 8-32 coils, 30% spiral 240 R=2-4, "
+                                   "20% 320x320 15 coils; K in {32,64,128,256}; 30 CG iterations",
+           "capacity_maps_per_s": cap, "max_active": max_active, "loads": []}
+    rng = np.random.default_rng(1)
+    for rho in loads:
+        rate = rho * cap
+        gaps = rng.exponential(1.0 / rate, size=nreq)
+        sv = pico.Server(max_active=max_active, chunk=64)
+        t0 = time.perf_counter()
+        ids = []
+        for r, g in zip(reqs, gaps):
+            time.sleep(g)
+            ids.append(sv.submit(**strip(r)))
+        infos = [sv.wait(i)[2] for i in ids]
+        wall = time.perf_counter() - t0
+        sv.close()
+        lat = np.array([i["t_done"] - i["t_arrival"] for i in infos])
+        out["loads"].append({"offered": rho, "p50_s": float(np.percentile(lat, 50)),
+                             "p99_s": float(np.percentile(lat, 99)), "maps_per_s": nreq / wall})
     return out
 
 
@@ -401,13 +491,16 @@ def main():
                        "d2h_bytes_per_step": int(out_h.nbytes), "steps": e2e_steps,
                        "includes": "pico_init (upload, whitening, power method, workspace) + maps + read-back"}
 
-    if rank == 0 and world == 1 and not args.no_t1pct and w.kind == "cartesian":
-        t1 = measure_time_to_1pct(op, w, torch, pico)
+    if rank == 0 and world == 1 and not args.no_t1pct and (w.kind == "cartesian" or args.t1pct_spiral):
+        t1 = measure_time_to_1pct(op, w, torch, pico, step=10 if w.kind == "cartesian" else 50)
         for name in ("pico", "pmr"):
             if t1[name].get("N"):
                 per = total_ms / 1e3 / (2 * K * args.steps)      # device seconds per solve in the batched step
                 t1[name]["seconds_at_batched_rate"] = t1[name]["N"] * per
         line["time_to_1pct"] = t1
+
+    if rank == 0 and world == 1 and args.serving > 0:
+        line["serving"] = run_serving(pico, args.serving)
 
     if rank == 0 and world == 1 and not args.no_cpu:
         v, dt, desc = oracle_sample(w, inp)

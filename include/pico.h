@@ -202,6 +202,52 @@ pico_status pico_cg_batch_static(const void* smaps_dev, const uint8_t* mask_dev,
 size_t pico_cg_batch_static_capacity(void);
 const char* pico_static_last_error(void);
 
+/* Device bytes a context for `desc` holds (what pico_init allocates, plus the
+ * k-space / grid buffer of pico_pmr, pico_forward and pico_adjoint when
+ * with_kspace != 0).  Host-only; for admission control. */
+pico_status pico_footprint(const pico_operator_desc* desc, int32_t with_kspace, size_t* bytes);
+
+/* ---- Serving runtime ------------------------------------------------------
+ * A request asks for one PICO variance map (and optionally a PMR map) of one
+ * acquisition.  Requests of different sizes, coil counts and trajectories may
+ * be submitted at any time from any thread; a scheduler thread admits them in
+ * arrival order while a slot is free (max_active) and their footprint fits
+ * hbm_budget (0 = unlimited), builds each request's operator on its own CUDA
+ * stream with stream-ordered allocation, enqueues its probes in batches of
+ * `chunk`, and retires it when its work completes.  Work of admitted requests
+ * overlaps on the GPU.  A request's result depends only on its own inputs and
+ * seed: it is bit-identical alone or in any mix.  The server uses the device
+ * current at pico_server_create. */
+typedef struct pico_server pico_server;
+
+typedef struct {
+  pico_operator_desc op;    /* acquisition; its host arrays are copied at submit            */
+  uint64_t seed;            /* probes 0..nprobes-1 and replicas 0..pmr_reps-1 of this seed */
+  int32_t nprobes;          /* PICO probes (0 = no PICO map)                               */
+  int32_t probe_kind;       /* pico_probe                                                  */
+  int32_t max_iter;         /* CG iterations per solve                                     */
+  double rtol;              /* CG relative-residual stop (0 = max_iter exactly)            */
+  int32_t pmr_reps;         /* PMR replicas (0 = no PMR map)                               */
+  double pmr_sigma;         /* PMR noise standard deviation                                */
+} pico_request;
+
+typedef struct {
+  int64_t id;
+  int32_t status;           /* pico_status of the request                                  */
+  double t_arrival, t_admit, t_done;  /* seconds on the server's clock                     */
+  int64_t footprint_bytes;
+} pico_request_info;
+
+pico_status pico_server_create(size_t hbm_budget, int32_t max_active, int32_t chunk, pico_server** out);
+/* Queue a request; returns at once with its id (PICO_E_OOM if it can never fit). */
+pico_status pico_server_submit(pico_server* server, const pico_request* request, int64_t* id);
+/* Block until request `id` is done; copy its maps (host float64 [ny][nx]: the
+ * variance map sum/N and the PMR map, each nullable) and timing; forget it. */
+pico_status pico_server_wait(pico_server* server, int64_t id, double* var_out, double* pmr_out,
+                             pico_request_info* info);
+/* Finish all queued work, stop the scheduler, free the server. */
+pico_status pico_server_destroy(pico_server* server);
+
 /* Device timing of this context's kernels by class, from CUDA events recorded
  * on the context stream around every launch while profiling is enabled.
  * pico_profile(ctx, 1) clears the totals and starts recording, (ctx, 0) stops.

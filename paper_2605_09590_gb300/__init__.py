@@ -55,6 +55,21 @@ class pico_info(ctypes.Structure):
     ]
 
 
+class pico_request(ctypes.Structure):
+    _fields_ = [
+        ("op", pico_operator_desc), ("seed", ctypes.c_uint64), ("nprobes", ctypes.c_int32),
+        ("probe_kind", ctypes.c_int32), ("max_iter", ctypes.c_int32), ("rtol", ctypes.c_double),
+        ("pmr_reps", ctypes.c_int32), ("pmr_sigma", ctypes.c_double),
+    ]
+
+
+class pico_request_info(ctypes.Structure):
+    _fields_ = [
+        ("id", ctypes.c_int64), ("status", ctypes.c_int32), ("t_arrival", ctypes.c_double),
+        ("t_admit", ctypes.c_double), ("t_done", ctypes.c_double), ("footprint_bytes", ctypes.c_int64),
+    ]
+
+
 _lib: Optional[ctypes.CDLL] = None
 
 
@@ -83,6 +98,11 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "pico_profile": ([vp, i32], i32),
         "pico_profile_read": ([vp, i32, ctypes.POINTER(f64), ctypes.POINTER(i64)], i32),
         "pico_launch_count": ([vp, ctypes.POINTER(i64), i32], i32),
+        "pico_footprint": ([ctypes.POINTER(pico_operator_desc), i32, ctypes.POINTER(ctypes.c_size_t)], i32),
+        "pico_server_create": ([ctypes.c_size_t, i32, i32, ctypes.POINTER(vp)], i32),
+        "pico_server_submit": ([vp, ctypes.POINTER(pico_request), ctypes.POINTER(i64)], i32),
+        "pico_server_wait": ([vp, i64, vp, vp, ctypes.POINTER(pico_request_info)], i32),
+        "pico_server_destroy": ([vp], i32),
         "pico_sync": ([vp], i32),
         "pico_last_error": ([vp], ctypes.c_char_p),
         "pico_destroy": ([vp], None),
@@ -121,6 +141,24 @@ def pico_init(smaps: np.ndarray, mask: Optional[np.ndarray] = None, noise_cov: O
               oversamp: float = 2.0, kb_width: int = 6, stream=None, hbm_budget: int = 0) -> int:
     """Create a context (returns the opaque handle)."""
     lib = load_library()
+    d, keep = make_desc(smaps, mask, noise_cov, traj, lam, power_iters, power_margin, max_batch, max_iter_cap,
+                        oversamp, kb_width)
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream().cuda_stream
+    h = ctypes.c_void_p()
+    st = lib.pico_init(ctypes.byref(d), ctypes.c_void_p(stream), hbm_budget, ctypes.byref(h))
+    if st != PICO_OK:
+        msg = lib.pico_last_error(h).decode() if h.value else ""
+        if h.value:
+            lib.pico_destroy(h)
+        raise PicoError(st, msg)
+    return h.value
+
+
+def make_desc(smaps, mask=None, noise_cov=None, traj=None, lam=0.0, power_iters=15, power_margin=1.01,
+              max_batch=64, max_iter_cap=128, oversamp=2.0, kb_width=6):
+    """``pico_operator_desc`` plus the arrays it points to (keep them alive)."""
     S = np.ascontiguousarray(smaps, dtype=np.complex64)
     nc, ny, nx = S.shape
     d = pico_operator_desc()
@@ -146,17 +184,7 @@ def pico_init(smaps: np.ndarray, mask: Optional[np.ndarray] = None, noise_cov: O
     d.lambda_ = lam
     d.power_iters, d.power_margin = power_iters, power_margin
     d.max_batch, d.max_iter_cap = max_batch, max_iter_cap
-    if stream is None:
-        import torch
-        stream = torch.cuda.current_stream().cuda_stream
-    h = ctypes.c_void_p()
-    st = lib.pico_init(ctypes.byref(d), ctypes.c_void_p(stream), hbm_budget, ctypes.byref(h))
-    if st != PICO_OK:
-        msg = lib.pico_last_error(h).decode() if h.value else ""
-        if h.value:
-            lib.pico_destroy(h)
-        raise PicoError(st, msg)
-    return h.value
+    return d, keep
 
 
 def pico_get_info(ctx) -> dict:
@@ -348,6 +376,66 @@ class Operator:
 
     def sync(self):
         pico_sync(self.ctx)
+
+
+# ----------------------------------------------------------------------------
+# serving runtime
+# ----------------------------------------------------------------------------
+class Server:
+    """Noise-map request server (``pico_server_*``): submit from any thread, wait for results."""
+
+    def __init__(self, hbm_budget: int = 0, max_active: int = 4, chunk: int = 64):
+        self.lib = load_library()
+        h = ctypes.c_void_p()
+        st = self.lib.pico_server_create(hbm_budget, max_active, chunk, ctypes.byref(h))
+        if st != PICO_OK:
+            raise PicoError(st, "pico_server_create")
+        self.h = h.value
+        self.shapes = {}
+
+    def submit(self, smaps, mask=None, traj=None, noise_cov=None, lam=0.0, seed=0, nprobes=32,
+               probe_kind=PICO_PROBE_PHASE, max_iter=30, rtol=0.0, pmr_reps=0, pmr_sigma=1.0,
+               power_iters=15, max_batch=64) -> int:
+        d, keep = make_desc(smaps, mask, noise_cov, traj, lam, power_iters, 1.01, max_batch, 128)
+        r = pico_request()
+        r.op = d
+        r.seed, r.nprobes, r.probe_kind, r.max_iter, r.rtol = seed & (2 ** 64 - 1), nprobes, probe_kind, max_iter, rtol
+        r.pmr_reps, r.pmr_sigma = pmr_reps, pmr_sigma
+        rid = ctypes.c_int64()
+        st = self.lib.pico_server_submit(self.h, ctypes.byref(r), ctypes.byref(rid))
+        if st != PICO_OK:
+            raise PicoError(st, "pico_server_submit")
+        self.shapes[rid.value] = (d.ny, d.nx, pmr_reps > 0)
+        return rid.value
+
+    def wait(self, rid: int):
+        ny, nx, has_pmr = self.shapes.pop(rid)
+        var = np.zeros((ny, nx), dtype=np.float64)
+        pmr = np.zeros((ny, nx), dtype=np.float64) if has_pmr else None
+        info = pico_request_info()
+        st = self.lib.pico_server_wait(self.h, rid, var.ctypes.data, None if pmr is None else pmr.ctypes.data,
+                                       ctypes.byref(info))
+        if st != PICO_OK:
+            raise PicoError(st, f"request {rid}")
+        return var, pmr, {f: getattr(info, f) for f, _ in pico_request_info._fields_}
+
+    def close(self):
+        if self.h:
+            self.lib.pico_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def pico_footprint(smaps, mask=None, traj=None, with_kspace=False, **kw) -> int:
+    d, keep = make_desc(smaps, mask, kw.pop("noise_cov", None), traj, **kw)
+    out = ctypes.c_size_t()
+    _check(None, load_library().pico_footprint(ctypes.byref(d), 1 if with_kspace else 0, ctypes.byref(out)))
+    return out.value
 
 
 # ----------------------------------------------------------------------------

@@ -56,6 +56,7 @@ struct pico_ctx {
   float2* Gt = nullptr;  // Toeplitz intermediates [B][nc][n][2n]
   pico::CgArgs cg{};
   size_t device_bytes = 0, budget = 0;
+  bool async_alloc = false;  // stream-ordered cudaMallocAsync / cudaFreeAsync (serving contexts)
   std::vector<void*> allocs;
   std::string err;
   // launch accounting and optional per-class event timing
@@ -95,7 +96,8 @@ pico_status dalloc(pico_ctx* c, T** p, size_t count) {
   if (c->budget && c->device_bytes + bytes > c->budget)
     return fail(c, PICO_E_OOM, "device footprint exceeds hbm_budget");
   void* q = nullptr;
-  if (cudaMalloc(&q, bytes) != cudaSuccess) {
+  const cudaError_t e = c->async_alloc ? cudaMallocAsync(&q, bytes, c->stream) : cudaMalloc(&q, bytes);
+  if (e != cudaSuccess) {
     cudaGetLastError();
     return fail(c, PICO_E_OOM, "cudaMalloc of " + std::to_string(bytes) + " bytes failed");
   }
@@ -402,7 +404,12 @@ pico_status spiral_setup(pico_ctx* c, const pico_operator_desc* d, int img, int 
 
 extern "C" {
 
-pico_status pico_init(const pico_operator_desc* d, void* cuda_stream, size_t hbm_budget, pico_ctx** out) {
+}  // extern "C"
+
+namespace pico {
+
+pico_status init_impl(const pico_operator_desc* d, void* cuda_stream, size_t hbm_budget, bool async_alloc,
+                      pico_ctx** out) {
   if (!out) return PICO_E_INVALID;
   *out = nullptr;
   if (!d || !d->smaps) return PICO_E_INVALID;
@@ -415,6 +422,7 @@ pico_status pico_init(const pico_operator_desc* d, void* cuda_stream, size_t hbm
 
   auto* c = new pico_ctx();
   *out = c;
+  c->async_alloc = async_alloc;
   c->kind = d->kind;
   c->ny = d->ny;
   c->nx = d->nx;
@@ -543,6 +551,38 @@ pico_status pico_init(const pico_operator_desc* d, void* cuda_stream, size_t hbm
   if ((st = cuda_check(c, "pico_init")) != PICO_OK) return st;
 #undef TRY
   return PICO_OK;
+}
+
+// Device bytes a context for `d` holds (the same sizes pico_init allocates);
+// with_kbuf adds the k-space / grid buffer of PMR and the forward/adjoint calls.
+size_t footprint_bytes(const pico_operator_desc* d, bool with_kbuf) {
+  const int64_t B = d->max_batch > 0 ? d->max_batch : 64;
+  const int64_t itmax = d->max_iter_cap > 0 ? d->max_iter_cap : 128;
+  const int64_t nc = d->ncoils, n = (int64_t)d->ny * d->nx;
+  const int64_t PB = (n + kVecPerBlock - 1) / kVecPerBlock;
+  int64_t PA, extra, kbuf;
+  if (d->kind == PICO_CARTESIAN) {
+    PA = cart_normal_tiles(d->nx);
+    extra = (int64_t)d->ny * 13 + (int64_t)d->nx * 8;
+    kbuf = B * nc * n * 8;
+  } else {
+    const int64_t img = d->ny, L = 2 * img;
+    PA = (img + 15) / 16;
+    extra = std::max(B * nc * img * L, L * L) * 8 + L * L * 4 + img * 4 + L * 8 + d->nsamp * 56 +
+            (L / 16) * (L / 16) * 4 + 64;
+    kbuf = B * nc * 4 * n * 8;
+  }
+  const int64_t need = nc * n * 8 + 4 * B * n * 8 + B * (itmax + 1) * PB * 8 + B * itmax * PA * 8 + B * 16 +
+                       PB * 8 + 64 + extra + (with_kbuf ? kbuf : 0);
+  return (size_t)need;
+}
+
+}  // namespace pico
+
+extern "C" {
+
+pico_status pico_init(const pico_operator_desc* d, void* cuda_stream, size_t hbm_budget, pico_ctx** out) {
+  return pico::init_impl(d, cuda_stream, hbm_budget, false, out);
 }
 
 pico_status pico_get_info(const pico_ctx* c, pico_info* info) {
@@ -822,7 +862,12 @@ void pico_destroy(pico_ctx* c) {
   for (cudaEvent_t e : c->event_pool) cudaEventDestroy(e);
   for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second.first);
   if (c->cap) cudaStreamDestroy(c->cap);
-  for (void* p : c->allocs) cudaFree(p);
+  for (void* p : c->allocs) {
+    if (c->async_alloc)
+      cudaFreeAsync(p, c->stream);
+    else
+      cudaFree(p);
+  }
   delete c;
 }
 
