@@ -15,9 +15,11 @@ ops      encoding operators: pre-whitening (Sec. 2.1.2), Cartesian SENSE and
 solvers  conjugate gradients (Eq. 6) and the power method (Sec. 3.3)
 pico     PICO estimator (Alg. 1), PMR (Sec. 1), exact covariance diagonals
          (Eqs. 8-10), closed-form SENSE g-factor, per-sample variances (Eq. A1)
+cs       L1-wavelet FISTA reconstruction, its Jacobian (JVP / VJP) and the
+         Jacobian PICO estimator for nonlinear reconstructions (Sec. 2.2.5)
 
 Every function states the passage it follows.  Pins that hold the oracle to
 the mathematics (closed forms, brute force, invariants) live in
 ``tests/test_oracle_pins.py``.
 """
-from . import rng, ops, solvers, pico  # noqa: F401
+from . import rng, ops, solvers, pico, cs  # noqa: F401

@@ -32,6 +32,8 @@ __all__ = [
     "noise_cov",
     "mask_pe",
     "spiral_traj",
+    "poisson_disc_mask",
+    "phantom",
     "Workload",
     "WORKLOADS",
 ]
@@ -175,3 +177,84 @@ WORKLOADS = {
     "spiral240_r4": Workload("spiral240_r4", "spiral", 240, 240, 20, 4, probes=256,
                              max_iter=30, lam=0.1, sigma=1e-2, reps=500),
 }
+
+
+def poisson_disc_mask(ny: int, nx: int, R: float, calib: int = 24, seed: int = 0,
+                      density_power: float = 1.0) -> np.ndarray:
+    """Variable-density Poisson-disc sampling mask, uint8 ``[ny][nx]`` in natural DFT order.
+
+    Dart throwing in the centred ``(ky, kx)`` plane: a candidate is accepted if no
+    accepted point lies within ``r(k) = r0 (1 + density_power * |k| / k_max)``
+    of it (Bridson-style rejection with a growing radius), the central
+    ``calib x calib`` block is fully sampled, and ``r0`` is bisected until the
+    acceleration ``ny nx / #samples`` is within 2 % of ``R``.
+    """
+    rng = np.random.default_rng(np.random.SeedSequence([0x9D15C, seed, ny, nx]))
+    ky = np.arange(ny) - ny // 2
+    kx = np.arange(nx) - nx // 2
+    KY, KX = np.meshgrid(ky, kx, indexing="ij")
+    kn = np.sqrt((KY / (ny / 2)) ** 2 + (KX / (nx / 2)) ** 2) / math.sqrt(2)
+    order = rng.permutation(ny * nx)
+    calib_blk = (KY >= -(calib // 2)) & (KY < calib - calib // 2) & (KX >= -(calib // 2)) & (KX < calib - calib // 2)
+
+    def draw(r0):
+        m = calib_blk.copy()
+        cell = max(r0, 0.5)
+        grid = {}
+        for idx in order:
+            y, x = divmod(int(idx), nx)
+            if m[y, x]:
+                continue
+            r = r0 * (1.0 + density_power * kn[y, x])
+            gy, gx = int(y // cell), int(x // cell)
+            reach = int(math.ceil(r * (1.0 + density_power) / cell)) + 1
+            ok = True
+            for dy in range(-reach, reach + 1):
+                for dx in range(-reach, reach + 1):
+                    for (py, px) in grid.get((gy + dy, gx + dx), ()):
+                        rr = r0 * (1.0 + density_power * 0.5 * (kn[y, x] + kn[py, px]))
+                        if (py - y) ** 2 + (px - x) ** 2 < rr * rr:
+                            ok = False
+                            break
+                    if not ok:
+                        break
+                if not ok:
+                    break
+            if ok:
+                m[y, x] = True
+                grid.setdefault((gy, gx), []).append((y, x))
+        return m
+
+    lo, hi = 0.5, 4.0
+    best = None
+    for _ in range(20):
+        r0 = 0.5 * (lo + hi)
+        m = draw(r0)
+        acc = ny * nx / m.sum()
+        best = m
+        if abs(acc - R) / R < 0.02:
+            break
+        if acc < R:
+            lo = r0
+        else:
+            hi = r0
+    # centred -> natural DFT order
+    return np.fft.ifftshift(best).astype(np.uint8)
+
+
+def phantom(n: int, seed: int = 0, n_ellipses: int = 10) -> np.ndarray:
+    """Seeded piecewise-constant ellipse phantom, complex64 ``[n][n]`` (smooth phase)."""
+    rng = np.random.default_rng(np.random.SeedSequence([0xE111, seed, n]))
+    yy = (np.arange(n) - n / 2) / (n / 2)
+    Y, X = np.meshgrid(yy, yy, indexing="ij")
+    img = np.zeros((n, n))
+    img[(X / 0.75) ** 2 + (Y / 0.9) ** 2 <= 1] = 1.0
+    for _ in range(n_ellipses - 1):
+        cx, cy = rng.uniform(-0.5, 0.5, 2)
+        ax, ay = rng.uniform(0.05, 0.3, 2)
+        th = rng.uniform(0, math.pi)
+        Xr = (X - cx) * math.cos(th) + (Y - cy) * math.sin(th)
+        Yr = -(X - cx) * math.sin(th) + (Y - cy) * math.cos(th)
+        img[(Xr / ax) ** 2 + (Yr / ay) ** 2 <= 1] += rng.uniform(-0.4, 0.4)
+    phase = np.exp(1j * math.pi * 0.3 * (X + 0.5 * Y))
+    return (img * phase).astype(np.complex64)
