@@ -65,8 +65,9 @@ typedef struct {
                                covariance Sigma_n (Eq. 2), or NULL for white noise; folded
                                into the sensitivities as L^-1 S with L L^H = Sigma_n (Eq. 3) */
   const uint8_t* mask;      /* Cartesian: host [ny] phase-encode mask, natural DFT order
-                               (index ky, 0 = DC); every kx of a kept line is sampled        */
-  int32_t mask_2d;          /* must be 0 (2-D Cartesian masks: PICO_E_UNSUPPORTED)            */
+                               (index ky, 0 = DC); every kx of a kept line is sampled;
+                               with mask_2d: host [ny][nx] mask (ky, kx), square images      */
+  int32_t mask_2d;          /* 0: phase-encode mask; 1: 2-D mask (e.g. Poisson disc)          */
   const float* traj;        /* spiral: host [nsamp][2] (kx, ky) in cycles/FOV                 */
   int64_t nsamp;            /* spiral samples                                                 */
   float oversamp;           /* spiral gridding oversampling (2.0)                             */
@@ -161,6 +162,37 @@ pico_status pico_variance_map_adaptive(pico_ctx* ctx, uint64_t seed, int32_t pro
  * Arguments as for pico_variance_map. */
 pico_status pico_pmr(pico_ctx* ctx, uint64_t seed, int64_t rep_begin, int32_t nreps, double sigma,
                      int32_t max_iter, double rtol, double* sum_dev, double* sumsq_dev, int32_t accumulate);
+
+/* ---- Nonlinear compressed sensing (Sec. 2.2.5) -----------------------------
+ * Reconstruction f: b -> x by L1-wavelet FISTA (Beck & Teboulle; the paper's
+ * FISTA of Sec. 3.2.3 with a db4 wavelet penalty):
+ *   min_x 1/2 ||A x - b||^2 + lambda_l1 ||W x||_1,
+ * W the periodised orthonormal 2-D Daubechies-4 DWT with `levels` levels, x0 = 0,
+ * step 1/Lc with Lc = power_margin * lambda_max (Sec. 3.3; needs power_iters > 0),
+ * standard momentum, complex soft threshold, `iters` iterations.  b_dev is
+ * whitened k-space (layout of pico_forward, one acquisition), x_dev the image
+ * [ny][nx].  The iterates are kept on the device for the Jacobian calls below;
+ * the image must be square with ny divisible by 2^levels. */
+pico_status pico_cs_recon(pico_ctx* ctx, const void* b_dev, double lambda_l1, int32_t iters, int32_t levels,
+                          void* x_dev);
+
+/* Jacobian-vector product dx = J db of the last pico_cs_recon (tangent of the
+ * unrolled iterations; the soft threshold's derivative is R-linear:
+ * dS[dc] = (1 - tau/|c|) dc + (tau/|c|) u Re(conj(u) dc), u = c/|c|, for
+ * |c| > tau, else 0).  db_dev: k-space [nbatch][...] as pico_forward;
+ * dx_dev: [nbatch][ny][nx]. */
+pico_status pico_cs_jvp(pico_ctx* ctx, const void* db_dev, void* dx_dev, int32_t nbatch);
+
+/* Vector-Jacobian product bbar = J^T xbar, the adjoint of pico_cs_jvp for the
+ * real inner product Re<a, b> (reverse sweep over the stored iterates).
+ * xbar_dev [nbatch][ny][nx] -> bbar_dev k-space [nbatch][...]. */
+pico_status pico_cs_vjp(pico_ctx* ctx, const void* xbar_dev, void* bbar_dev, int32_t nbatch);
+
+/* Jacobian PICO (Sec. 2.2.5 with Alg. 1): running sums of Re(conj(v) . J J^T v)
+ * over probes probe_begin.. of seed; arguments as pico_variance_map (the CG
+ * settings do not apply).  Needs a prior pico_cs_recon. */
+pico_status pico_cs_variance_map(pico_ctx* ctx, uint64_t seed, int64_t probe_begin, int32_t nprobes,
+                                 int32_t probe_kind, double* sum_dev, double* sumsq_dev, int32_t accumulate);
 
 /* Finalise running sums over `count` samples (Alg. 1 output; Sec. 4
  * "per-voxel standard error of the running mean"):

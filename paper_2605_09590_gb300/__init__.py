@@ -94,6 +94,10 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "pico_variance_map_adaptive": ([vp, u64, i32, i32, i64, i32, f64, f64, vp, vp,
                                         ctypes.POINTER(i64), ctypes.POINTER(f64)], i32),
         "pico_finalize": ([vp, vp, vp, i64, vp, vp], i32),
+        "pico_cs_recon": ([vp, vp, f64, i32, i32, vp], i32),
+        "pico_cs_jvp": ([vp, vp, vp, i32], i32),
+        "pico_cs_vjp": ([vp, vp, vp, i32], i32),
+        "pico_cs_variance_map": ([vp, u64, i64, i32, i32, vp, vp, i32], i32),
         "pico_gfactor": ([vp, vp, vp, f64, vp], i32),
         "pico_profile": ([vp, i32], i32),
         "pico_profile_read": ([vp, i32, ctypes.POINTER(f64), ctypes.POINTER(i64)], i32),
@@ -250,6 +254,32 @@ def pico_pmr(ctx, seed: int, rep_begin: int, nreps: int, sigma: float, max_iter:
         None if sumsq is None else _dev_ptr(sumsq, torch.float64, "sumsq"), 1 if accumulate else 0))
 
 
+def pico_cs_recon(ctx, b, lambda_l1: float, iters: int, levels: int, x) -> None:
+    import torch
+    _check(ctx, load_library().pico_cs_recon(ctx, _dev_ptr(b, torch.complex64, "b"), lambda_l1, iters, levels,
+                                             _dev_ptr(x, torch.complex64, "x")))
+
+
+def pico_cs_jvp(ctx, db, dx) -> None:
+    import torch
+    _check(ctx, load_library().pico_cs_jvp(ctx, _dev_ptr(db, torch.complex64, "db"),
+                                           _dev_ptr(dx, torch.complex64, "dx"), dx.shape[0]))
+
+
+def pico_cs_vjp(ctx, xbar, bbar) -> None:
+    import torch
+    _check(ctx, load_library().pico_cs_vjp(ctx, _dev_ptr(xbar, torch.complex64, "xbar"),
+                                           _dev_ptr(bbar, torch.complex64, "bbar"), xbar.shape[0]))
+
+
+def pico_cs_variance_map(ctx, seed: int, probe_begin: int, nprobes: int, probe_kind: int, sum_, sumsq=None,
+                         accumulate: bool = False) -> None:
+    import torch
+    _check(ctx, load_library().pico_cs_variance_map(
+        ctx, seed & (2 ** 64 - 1), probe_begin, nprobes, probe_kind, _dev_ptr(sum_, torch.float64, "sum"),
+        None if sumsq is None else _dev_ptr(sumsq, torch.float64, "sumsq"), 1 if accumulate else 0))
+
+
 def pico_finalize(ctx, sum_, sumsq, count: int, var=None, stderr=None) -> None:
     import torch
     _check(ctx, load_library().pico_finalize(
@@ -376,6 +406,46 @@ class Operator:
 
     def sync(self):
         pico_sync(self.ctx)
+
+
+# ----------------------------------------------------------------------------
+# nonlinear CS reconstruction as a differentiable function
+# ----------------------------------------------------------------------------
+def cs_function():
+    """``torch.autograd.Function`` of the L1-wavelet FISTA reconstruction ``x = f(b)``.
+
+    ``apply(op, b, lambda_l1, iters, levels)`` reconstructs one acquisition
+    (``b``: whitened k-space of ``op``'s layout).  Backward returns
+    ``J^T grad_x`` (``pico_cs_vjp``; the real-inner-product adjoint, which is
+    PyTorch's convention for complex gradients), forward-mode AD ``J db``
+    (``pico_cs_jvp``); both at the point of the last forward call.
+    """
+    import torch
+
+    class CSRecon(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, op, b, lambda_l1, iters, levels):
+            x = torch.empty((op.ny, op.nx), dtype=torch.complex64, device=b.device)
+            pico_cs_recon(op.ctx, b.detach().contiguous(), lambda_l1, iters, levels, x)
+            ctx.op = op
+            ctx.kshape = tuple(b.shape)
+            return x
+
+        @staticmethod
+        def backward(ctx, grad_x):
+            op = ctx.op
+            bbar = torch.empty((1,) + ctx.kshape, dtype=torch.complex64, device=grad_x.device)
+            pico_cs_vjp(op.ctx, grad_x.contiguous().reshape(1, op.ny, op.nx), bbar)
+            return None, bbar.reshape(ctx.kshape), None, None, None
+
+        @staticmethod
+        def jvp(ctx, _op, db, *_):
+            op = ctx.op
+            dx = torch.empty((1, op.ny, op.nx), dtype=torch.complex64, device=db.device)
+            pico_cs_jvp(op.ctx, db.contiguous().reshape((1,) + ctx.kshape), dx)
+            return dx.reshape(op.ny, op.nx)
+
+    return CSRecon
 
 
 # ----------------------------------------------------------------------------

@@ -53,7 +53,16 @@ struct pico_ctx {
   int* tile_idx = nullptr;
   float* traj = nullptr;
   int64_t nsamp = 0;
-  float2* Gt = nullptr;  // Toeplitz intermediates [B][nc][n][2n]
+  float2* Gt = nullptr;  // Toeplitz / 2-D intermediates [B][nc][n][L]
+  bool mask2d = false;   // Cartesian with a 2-D sampling mask (normal operator by the 2-D passes, L = n)
+  // nonlinear CS state (pico_cs_*)
+  bool cs_ready = false;
+  int cs_iters = 0, cs_levels = 0;
+  double cs_lc = 0, cs_tau = 0;
+  std::vector<float> cs_c;     // momentum coefficients c_k
+  float2* cs_traj = nullptr;   // [iters][n] wavelet coefficients W y_k of the reconstruction
+  float2* cs_buf = nullptr;    // [6][B][n] work images
+  pico::Wavelet wav{};
   pico::CgArgs cg{};
   size_t device_bytes = 0, budget = 0;
   bool async_alloc = false;  // stream-ordered cudaMallocAsync / cudaFreeAsync (serving contexts)
@@ -198,7 +207,7 @@ void prof_collect(pico_ctx* c) {
 
 // (A^H A + lam) x for nb images (class 0)
 void op_apply(pico_ctx* c, const float2* x, float2* y, int nb, float lam) {
-  if (c->kind == PICO_CARTESIAN) {
+  if (c->kind == PICO_CARTESIAN && !c->mask2d) {
     Launch L(c, 0);
     pico::launch_cart_apply(c->cop, x, y, nb, lam, c->stream);
   } else {
@@ -209,7 +218,7 @@ void op_apply(pico_ctx* c, const float2* x, float2* y, int nb, float lam) {
 
 // CG iteration `it`, operator half (class 0)
 void op_cg_normal(pico_ctx* c, int nb, int it, float lam) {
-  if (c->kind == PICO_CARTESIAN) {
+  if (c->kind == PICO_CARTESIAN && !c->mask2d) {
     Launch L(c, 0);
     pico::launch_cart_cg_normal(c->cop, c->cg, nb, it, lam, c->stream);
   } else {
@@ -283,12 +292,51 @@ pico_status ensure_kbuf(pico_ctx* c) {
   return dalloc(c, &c->G, (size_t)c->max_batch * c->nc * per);
 }
 
+// 2-D mask adjoint of k-space planes already in c->G (masked, scaled): inverse
+// column and row FFTs in place, then the conj(S) coil combine into out [nb][n]
+void adjoint2d_from_kbuf(pico_ctx* c, float2* out, int nb) {
+  const int n1 = c->ny;
+  { Launch L(c, 2); pico::launch_fft_cols(n1, c->G, c->tw2, c->nx, nb * c->nc, c->n, 1, c->stream); }
+  { Launch L(c, 2); pico::launch_fft_rows(c->nx, c->G, c->tw2, c->ny, nb * c->nc, c->n, 1, c->stream); }
+  { Launch L(c, 2); pico::launch_coil_combine(c->G, c->smaps, c->nc, out, c->n, nb, c->stream); }
+}
+
 pico_status check_iter(pico_ctx* c, int max_iter, double rtol) {
   if (max_iter < 0 || max_iter > c->itmax) return fail(c, PICO_E_INVALID, "max_iter outside [0, max_iter_cap]");
   if (!(rtol >= 0.0)) return fail(c, PICO_E_INVALID, "rtol must be >= 0");
   return PICO_OK;
 }
 
+
+// 2-D Cartesian mask: the normal operator runs the unpadded 2-D passes with the
+// real multiplier mask(ky, kx) / n^2 (orthonormal DFT pair), L = n.
+pico_status cart2d_setup(pico_ctx* c, const pico_operator_desc* d, int img, int P1, int P2) {
+  const int64_t n = c->n;
+  pico_status st = PICO_OK;
+  if ((st = dalloc(c, &c->That, (size_t)n)) != PICO_OK) return st;
+  if ((st = dalloc(c, &c->tw2, (size_t)img)) != PICO_OK) return st;
+  if ((st = dalloc(c, &c->mask, (size_t)n)) != PICO_OK) return st;
+  if ((st = dalloc(c, &c->Gt, std::max((size_t)c->max_batch * c->nc * n, (size_t)n))) != PICO_OK) return st;
+  std::vector<float> T(n);
+  for (int64_t i = 0; i < n; ++i) T[i] = d->mask[i] ? (float)(1.0 / (double)n) : 0.f;
+  const std::vector<float2> tw = twiddles(img);
+  cudaMemcpyAsync(c->That, T.data(), T.size() * sizeof(float), cudaMemcpyHostToDevice, c->stream);
+  cudaMemcpyAsync(c->tw2, tw.data(), tw.size() * sizeof(float2), cudaMemcpyHostToDevice, c->stream);
+  cudaMemcpyAsync(c->mask, d->mask, (size_t)n, cudaMemcpyHostToDevice, c->stream);
+  c->sop = pico::SpiralOp{};
+  c->sop.n = img;
+  c->sop.L = img;
+  c->sop.nc = c->nc;
+  c->sop.P1 = P1;
+  c->sop.P2 = P2;
+  c->sop.smaps = c->smaps;
+  c->sop.tw2 = c->tw2;
+  c->sop.That = c->That;
+  c->twx = c->tw2;
+  c->tw = c->tw2;
+  if (cudaStreamSynchronize(c->stream) != cudaSuccess) return cuda_check(c, "2-D mask set-up");
+  return PICO_OK;
+}
 
 // I0(x) by its power series sum_k (x^2/4)^k / (k!)^2 (FP64; x < 30 here)
 double bessel_i0(double x) {
@@ -400,6 +448,72 @@ pico_status spiral_setup(pico_ctx* c, const pico_operator_desc* d, int img, int 
   return cuda_check(c, "spiral set-up");
 }
 
+
+// ---------------------------------------------------------------------------
+// nonlinear CS: L1-wavelet FISTA and its Jacobian (Sec. 2.2.5)
+// ---------------------------------------------------------------------------
+// Daubechies' orthonormal scaling filter with 4 vanishing moments (8 taps), as
+// tabulated by Daubechies (Comm. Pure Appl. Math. 41, 1988, Table 1).
+constexpr double kDb4[8] = {0.2303778133088964,  0.7148465705529154, 0.6308807679298587, -0.0279837694168599,
+                            -0.1870348117190931, 0.0308413818355607, 0.0328830116668852, -0.0105974017850690};
+
+pico_status cs_buffers(pico_ctx* c) {
+  if (c->cs_buf) return PICO_OK;
+  return dalloc(c, &c->cs_buf, (size_t)6 * c->max_batch * c->n);
+}
+float2* cs_e(pico_ctx* c, int k) { return c->cs_buf + (size_t)k * c->max_batch * c->n; }
+
+void cs_W(pico_ctx* c, const float2* x, float2* coef, float2* tmp, int nb) {
+  Launch L(c, 3, pico::dwt_kernels(c->cs_levels));
+  pico::launch_dwt(x, coef, tmp, c->ny, c->cs_levels, nb, c->wav, c->stream);
+}
+void cs_WH(pico_ctx* c, const float2* coef, float2* x, float2* tmp, int nb) {
+  Launch L(c, 3, pico::dwt_kernels(c->cs_levels));
+  pico::launch_idwt(coef, x, tmp, c->ny, c->cs_levels, nb, c->wav, c->stream);
+}
+
+// dx (E0) = J applied to the image-domain tangent A^H db given in `ahdb` [nb][n]
+void cs_jvp_core(pico_ctx* c, const float2* ahdb, int nb) {
+  float2 *dx = cs_e(c, 0), *dz = cs_e(c, 1), *t2 = cs_e(c, 2), *t3 = cs_e(c, 3), *t4 = cs_e(c, 4);
+  const int64_t n = c->n;
+  const float inv_lc = (float)(1.0 / c->cs_lc), tau = (float)c->cs_tau;
+  cudaMemsetAsync(dx, 0, (size_t)nb * n * sizeof(float2), c->stream);
+  cudaMemsetAsync(dz, 0, (size_t)nb * n * sizeof(float2), c->stream);
+  for (int k = 0; k < c->cs_iters; ++k) {
+    op_apply(c, dz, t2, nb, 0.f);
+    { Launch L(c, 3); pico::launch_cs_gradstep(dz, t2, ahdb, n, inv_lc, t3, n, nb, c->stream); }
+    cs_W(c, t3, t4, t2, nb);
+    { Launch L(c, 3); pico::launch_cs_soft_tan(c->cs_traj + (size_t)k * n, t4, tau, n, nb, c->stream); }
+    cs_WH(c, t4, t3, t2, nb);
+    { Launch L(c, 3); pico::launch_cs_momentum(t3, dx, dz, c->cs_c[k], n, nb, c->stream); }
+  }
+}
+
+// E0 = (sum_k ybar_k) / Lc for the output cotangent `xbar` [nb][n] (reverse sweep)
+void cs_vjp_core(pico_ctx* c, const float2* xbar, int nb) {
+  float2 *ys = cs_e(c, 0), *zb = cs_e(c, 1), *t2 = cs_e(c, 2), *t3 = cs_e(c, 3), *t4 = cs_e(c, 4),
+         *xbn = cs_e(c, 5);
+  const int64_t n = c->n;
+  const float inv_lc = (float)(1.0 / c->cs_lc), tau = (float)c->cs_tau;
+  cudaMemsetAsync(ys, 0, (size_t)nb * n * sizeof(float2), c->stream);
+  cudaMemsetAsync(zb, 0, (size_t)nb * n * sizeof(float2), c->stream);
+  cudaMemcpyAsync(xbn, xbar, (size_t)nb * n * sizeof(float2), cudaMemcpyDeviceToDevice, c->stream);
+  for (int k = c->cs_iters - 1; k >= 0; --k) {
+    { Launch L(c, 3); pico::launch_vjp_a(xbn, zb, t3, c->cs_c[k], n, nb, c->stream); }
+    cs_W(c, t3, t4, t2, nb);
+    { Launch L(c, 3); pico::launch_cs_soft_tan(c->cs_traj + (size_t)k * n, t4, tau, n, nb, c->stream); }
+    cs_WH(c, t4, t3, t2, nb);
+    op_apply(c, t3, t2, nb, 0.f);
+    { Launch L(c, 3); pico::launch_vjp_b(t3, t2, inv_lc, zb, ys, n, nb, c->stream); }
+  }
+  { Launch L(c, 3); pico::launch_scale(ys, inv_lc, n, nb, c->stream); }
+}
+
+pico_status cs_check(pico_ctx* c) {
+  if (!c || !c->smaps) return PICO_E_INVALID;
+  if (!c->cs_ready) return fail(c, PICO_E_INVALID, "run pico_cs_recon first");
+  return PICO_OK;
+}
 }  // namespace
 
 extern "C" {
@@ -416,7 +530,6 @@ pico_status init_impl(const pico_operator_desc* d, void* cuda_stream, size_t hbm
   if (d->ny <= 0 || d->nx <= 0 || d->ncoils <= 0) return PICO_E_INVALID;
   if (d->kind != PICO_CARTESIAN && d->kind != PICO_SPIRAL) return PICO_E_INVALID;
   if (d->kind == PICO_CARTESIAN && !d->mask) return PICO_E_INVALID;
-  if (d->kind == PICO_CARTESIAN && d->mask_2d) return PICO_E_UNSUPPORTED;
   if (d->kind == PICO_SPIRAL && (!d->traj || d->nsamp <= 0 || d->nsamp > (int64_t)1 << 30)) return PICO_E_INVALID;
   if (d->lambda < 0.0 || d->power_iters < 0 || d->max_batch < 0 || d->max_iter_cap < 0) return PICO_E_INVALID;
 
@@ -451,7 +564,14 @@ pico_status init_impl(const pico_operator_desc* d, void* cuda_stream, size_t hbm
   const int kbw = d->kb_width > 0 ? d->kb_width : 6;
   const double os = d->oversamp > 0 ? (double)d->oversamp : 2.0;
   size_t extra = 0;
-  if (c->kind == PICO_CARTESIAN) {
+  c->mask2d = c->kind == PICO_CARTESIAN && d->mask_2d != 0;
+  if (c->mask2d) {
+    if (c->ny != c->nx) return fail(c, PICO_E_UNSUPPORTED, "2-D masks need square images");
+    if (!pico::grid_split(img, &P1, &P2) || !pico::fft_length_supported(img))
+      return fail(c, PICO_E_UNSUPPORTED, "image size has no 2-D FFT split in this build");
+    PA = (img + 15) / 16;
+    extra = std::max((size_t)B * nc * n, (size_t)n) * 8 + (size_t)n * 5 + (size_t)img * 8;
+  } else if (c->kind == PICO_CARTESIAN) {
     if (!pico::cart_supported(c->ny, c->nx, &N1, &N2, &M1, &M2))
       return fail(c, PICO_E_UNSUPPORTED, "ny has no FFT split in this build");
     PA = pico::cart_normal_tiles(c->nx);
@@ -513,7 +633,9 @@ pico_status init_impl(const pico_operator_desc* d, void* cuda_stream, size_t hbm
   cudaMemsetAsync(c->status, 0, (size_t)B * sizeof(int), c->stream);
   c->cg = pico::CgArgs{n, c->X, c->R, c->P, c->Q, c->rr_part, c->pq_part, c->status, PB, PA, c->itmax, 0.0};
 
-  if (c->kind == PICO_CARTESIAN) {
+  if (c->mask2d) {
+    TRY(cart2d_setup(c, d, img, P1, P2));
+  } else if (c->kind == PICO_CARTESIAN) {
     TRY(dalloc(c, &c->ymul, (size_t)c->ny));
     TRY(dalloc(c, &c->tw, (size_t)c->ny));
     TRY(dalloc(c, &c->twx, (size_t)c->nx));
@@ -710,7 +832,7 @@ pico_status pico_pmr(pico_ctx* c, uint64_t seed, int64_t rep_begin, int32_t nrep
   if (!c || !c->smaps) return PICO_E_INVALID;
   if (!sum || nreps < 0 || rep_begin < 0) return fail(c, PICO_E_INVALID, "bad sum pointer or replica range");
   if (!(sigma > 0.0)) return fail(c, PICO_E_INVALID, "sigma must be > 0");
-  if (c->kind == PICO_CARTESIAN && c->cop.M1 == 0)
+  if (c->kind == PICO_CARTESIAN && !c->mask2d && c->cop.M1 == 0)
     return fail(c, PICO_E_UNSUPPORTED, "nx has no FFT split in this build (PMR adjoint)");
   pico_status st = check_iter(c, max_iter, rtol);
   if (st != PICO_OK) return st;
@@ -722,7 +844,11 @@ pico_status pico_pmr(pico_ctx* c, uint64_t seed, int64_t rep_begin, int32_t nrep
   const float lam = (float)c->lam_phys;
   for (int32_t b0 = 0; b0 < nreps; b0 += c->max_batch) {
     const int nb = std::min(c->max_batch, nreps - b0);
-    if (c->kind == PICO_CARTESIAN) {
+    if (c->mask2d) {
+      { Launch L(c, 2); pico::launch_noise_kspace2d(c->G, c->mask, c->nc, c->n, nb, seed, rep_begin + b0,
+                                                    (float)(sigma / std::sqrt((double)c->n)), c->stream); }
+      adjoint2d_from_kbuf(c, c->R, nb);
+    } else if (c->kind == PICO_CARTESIAN) {
       { Launch L(c, 2); pico::launch_cart_pmr_cols(c->cop, c->G, nb, seed, rep_begin + b0, (float)sigma, c->stream); }
       { Launch L(c, 2); pico::launch_cart_rows_adjoint(c->cop, c->G, c->R, nb, c->stream); }
     } else {
@@ -752,7 +878,13 @@ pico_status pico_forward(pico_ctx* c, const void* x, void* y, int32_t nbatch) {
       { Launch L(c, 3); pico::launch_cart_smul(xi + (size_t)b0 * c->n, c->smaps, yb, nb, c->nc, c->n, c->stream); }
       { Launch L(c, 3); pico::launch_fft_rows(c->nx, yb, c->twx, c->ny, nb * c->nc, c->n, -1, c->stream); }
       { Launch L(c, 3); pico::launch_fft_cols(c->ny, yb, c->tw, c->nx, nb * c->nc, c->n, -1, c->stream); }
-      { Launch L(c, 3); pico::launch_cart_mask_scale(yb, c->mask, nb * c->nc, c->ny, c->nx, scale, c->stream); }
+      if (c->mask2d) {
+        Launch L(c, 3);
+        pico::launch_mask2d(yb, yb, c->mask, scale, c->n, nb * c->nc, c->stream);
+      } else {
+        Launch L(c, 3);
+        pico::launch_cart_mask_scale(yb, c->mask, nb * c->nc, c->ny, c->nx, scale, c->stream);
+      }
     }
   } else {
     if ((st = ensure_kbuf(c)) != PICO_OK) return st;
@@ -771,7 +903,7 @@ pico_status pico_forward(pico_ctx* c, const void* x, void* y, int32_t nbatch) {
 pico_status pico_adjoint(pico_ctx* c, const void* y, void* x, int32_t nbatch) {
   if (!c || !c->smaps) return PICO_E_INVALID;
   if (nbatch < 0 || (nbatch > 0 && (!x || !y))) return fail(c, PICO_E_INVALID, "bad batch or pointer");
-  if (c->kind == PICO_CARTESIAN && c->cop.M1 == 0)
+  if (c->kind == PICO_CARTESIAN && !c->mask2d && c->cop.M1 == 0)
     return fail(c, PICO_E_UNSUPPORTED, "nx has no FFT split in this build (adjoint operator)");
   pico_status st = ensure_kbuf(c);
   if (st != PICO_OK) return st;
@@ -781,7 +913,11 @@ pico_status pico_adjoint(pico_ctx* c, const void* y, void* x, int32_t nbatch) {
   for (int32_t b0 = 0; b0 < nbatch; b0 += c->max_batch) {
     const int nb = std::min(c->max_batch, nbatch - b0);
     const float2* yb = yi + (size_t)b0 * c->nc * kper;
-    if (c->kind == PICO_CARTESIAN) {
+    if (c->mask2d) {
+      { Launch L(c, 3); pico::launch_mask2d(yb, c->G, c->mask, (float)(1.0 / std::sqrt((double)c->n)), c->n,
+                                            nb * c->nc, c->stream); }
+      adjoint2d_from_kbuf(c, xo + (size_t)b0 * c->n, nb);
+    } else if (c->kind == PICO_CARTESIAN) {
       { Launch L(c, 3); pico::launch_cart_pmr_cols(c->cop, c->G, nb, 0, 0, 0.f, c->stream, yb); }
       { Launch L(c, 3); pico::launch_cart_rows_adjoint(c->cop, c->G, xo + (size_t)b0 * c->n, nb, c->stream); }
     } else {
@@ -790,6 +926,106 @@ pico_status pico_adjoint(pico_ctx* c, const void* y, void* x, int32_t nbatch) {
     }
   }
   return cuda_check(c, "pico_adjoint");
+}
+
+pico_status pico_cs_recon(pico_ctx* c, const void* b_dev, double lambda_l1, int32_t iters, int32_t levels,
+                          void* x_dev) {
+  if (!c || !c->smaps) return PICO_E_INVALID;
+  if (!b_dev || !x_dev || iters < 1 || levels < 1 || !(lambda_l1 >= 0.0))
+    return fail(c, PICO_E_INVALID, "bad CS reconstruction arguments");
+  if (c->ny != c->nx || (c->ny % (1 << levels)) != 0)
+    return fail(c, PICO_E_UNSUPPORTED, "the wavelet transform needs a square image divisible by 2^levels");
+  if (!(c->lambda_max > 0.0)) return fail(c, PICO_E_INVALID, "CS needs the power-method lambda_max (power_iters > 0)");
+  pico_status st = cs_buffers(c);
+  if (st != PICO_OK) return st;
+  if (!c->cs_traj || c->cs_iters < iters) {
+    if ((st = dalloc(c, &c->cs_traj, (size_t)iters * c->n)) != PICO_OK) return st;
+  }
+  for (int m = 0; m < 8; ++m) {
+    c->wav.h[m] = (float)kDb4[m];
+    c->wav.g[m] = (float)((m % 2 ? -1.0 : 1.0) * kDb4[7 - m]);
+  }
+  c->wav.L = 8;
+  c->cs_iters = iters;
+  c->cs_levels = levels;
+  c->cs_lc = c->margin * c->lambda_max;
+  c->cs_tau = lambda_l1 / c->cs_lc;
+  c->cs_c.assign(iters, 0.f);
+  double t = 1.0;
+  for (int k = 0; k < iters; ++k) {
+    const double tn = 0.5 * (1.0 + std::sqrt(1.0 + 4.0 * t * t));
+    c->cs_c[k] = (float)((t - 1.0) / tn);
+    t = tn;
+  }
+  const int64_t n = c->n;
+  float2 *x = cs_e(c, 0), *z = cs_e(c, 1), *t2 = cs_e(c, 2), *t3 = cs_e(c, 3), *t4 = cs_e(c, 4), *ahb = cs_e(c, 5);
+  if ((st = pico_adjoint(c, b_dev, ahb, 1)) != PICO_OK) return st;
+  cudaMemsetAsync(x, 0, (size_t)n * sizeof(float2), c->stream);
+  cudaMemsetAsync(z, 0, (size_t)n * sizeof(float2), c->stream);
+  const float inv_lc = (float)(1.0 / c->cs_lc), tau = (float)c->cs_tau;
+  for (int k = 0; k < iters; ++k) {
+    op_apply(c, z, t2, 1, 0.f);
+    { Launch L(c, 3); pico::launch_cs_gradstep(z, t2, ahb, 0, inv_lc, t3, n, 1, c->stream); }
+    cs_W(c, t3, t4, t2, 1);
+    { Launch L(c, 3); pico::launch_cs_soft(t4, c->cs_traj + (size_t)k * n, t4, tau, n, c->stream); }
+    cs_WH(c, t4, t3, t2, 1);
+    { Launch L(c, 3); pico::launch_cs_momentum(t3, x, z, c->cs_c[k], n, 1, c->stream); }
+  }
+  cudaMemcpyAsync(x_dev, x, (size_t)n * sizeof(float2), cudaMemcpyDeviceToDevice, c->stream);
+  c->cs_ready = true;
+  return cuda_check(c, "pico_cs_recon");
+}
+
+pico_status pico_cs_jvp(pico_ctx* c, const void* db_dev, void* dx_dev, int32_t nbatch) {
+  pico_status st = cs_check(c);
+  if (st != PICO_OK) return st;
+  if (nbatch < 0 || (nbatch > 0 && (!db_dev || !dx_dev))) return fail(c, PICO_E_INVALID, "bad batch or pointer");
+  const int64_t kper = c->kind == PICO_CARTESIAN ? (int64_t)c->nc * c->n : (int64_t)c->nc * c->nsamp;
+  for (int32_t b0 = 0; b0 < nbatch; b0 += c->max_batch) {
+    const int nb = std::min(c->max_batch, nbatch - b0);
+    if ((st = pico_adjoint(c, static_cast<const float2*>(db_dev) + (size_t)b0 * kper, c->Q, nb)) != PICO_OK)
+      return st;
+    cs_jvp_core(c, c->Q, nb);
+    cudaMemcpyAsync(static_cast<float2*>(dx_dev) + (size_t)b0 * c->n, cs_e(c, 0), (size_t)nb * c->n * sizeof(float2),
+                    cudaMemcpyDeviceToDevice, c->stream);
+  }
+  return cuda_check(c, "pico_cs_jvp");
+}
+
+pico_status pico_cs_vjp(pico_ctx* c, const void* xbar_dev, void* bbar_dev, int32_t nbatch) {
+  pico_status st = cs_check(c);
+  if (st != PICO_OK) return st;
+  if (nbatch < 0 || (nbatch > 0 && (!xbar_dev || !bbar_dev))) return fail(c, PICO_E_INVALID, "bad batch or pointer");
+  const int64_t kper = c->kind == PICO_CARTESIAN ? (int64_t)c->nc * c->n : (int64_t)c->nc * c->nsamp;
+  for (int32_t b0 = 0; b0 < nbatch; b0 += c->max_batch) {
+    const int nb = std::min(c->max_batch, nbatch - b0);
+    cs_vjp_core(c, static_cast<const float2*>(xbar_dev) + (size_t)b0 * c->n, nb);
+    if ((st = pico_forward(c, cs_e(c, 0), static_cast<float2*>(bbar_dev) + (size_t)b0 * kper, nb)) != PICO_OK)
+      return st;
+  }
+  return cuda_check(c, "pico_cs_vjp");
+}
+
+pico_status pico_cs_variance_map(pico_ctx* c, uint64_t seed, int64_t probe_begin, int32_t nprobes, int32_t kind,
+                                 double* sum, double* sumsq, int32_t accumulate) {
+  pico_status st = cs_check(c);
+  if (st != PICO_OK) return st;
+  if (!sum || nprobes < 0 || probe_begin < 0 || kind < 0 || kind > 2)
+    return fail(c, PICO_E_INVALID, "bad sum pointer, probe range or kind");
+  if (!accumulate) {
+    cudaMemsetAsync(sum, 0, (size_t)c->n * sizeof(double), c->stream);
+    if (sumsq) cudaMemsetAsync(sumsq, 0, (size_t)c->n * sizeof(double), c->stream);
+  }
+  for (int32_t b0 = 0; b0 < nprobes; b0 += c->max_batch) {
+    const int nb = std::min(c->max_batch, nprobes - b0);
+    { Launch L(c, 1); pico::launch_cg_init_probe(c->cg, nb, seed, probe_begin + b0, kind, c->stream); }
+    cs_vjp_core(c, c->R, nb);                   // E0 = J^T v  (as the image-domain A^H-side vector / Lc sum)
+    op_apply(c, cs_e(c, 0), c->Q, nb, 0.f);     // A^H (A g) = M g: the tangent J needs, without k-space
+    cs_jvp_core(c, c->Q, nb);                   // E0 = J J^T v
+    { Launch L(c, 3); pico::launch_accum_pico(cs_e(c, 0), c->n, nb, seed, probe_begin + b0, kind, sum, sumsq,
+                                              c->stream); }
+  }
+  return cuda_check(c, "pico_cs_variance_map");
 }
 
 pico_status pico_finalize(pico_ctx* c, const double* sum, const double* sumsq, int64_t count, float* var,

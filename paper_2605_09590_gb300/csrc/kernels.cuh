@@ -96,6 +96,7 @@ struct SpiralOp {
   float beta, halfw, inv_i0beta;
 };
 bool spiral_supported(int n, int* P1, int* P2);
+bool grid_split(int L, int* P1, int* P2);  // split of a 2-D pass length (Toeplitz or 2-D Cartesian)
 void launch_toep_h(const float* traj, int64_t M, int n, float2* c, cudaStream_t s);
 void launch_toep_fft2(const SpiralOp& op, float2* c, cudaStream_t s);  // c <- DFT_2D(c)
 void launch_toep_finalize(const float2* c, int L, float scale, float* That, cudaStream_t s);
@@ -105,6 +106,32 @@ void launch_toep_cg_normal(const SpiralOp& op, const CgArgs& a, float2* G, int n
 void launch_grid_pmr(const SpiralOp& op, float2* Qgrid, int nb, uint64_t seed, int64_t rep_begin, float sigma,
                      cudaStream_t s, const float2* data = nullptr);
 void launch_grid_adjoint_rest(const SpiralOp& op, float2* Qgrid, float2* out, int nb, cudaStream_t s);
+
+// ---- cs.cu: nonlinear CS (L1-wavelet FISTA) and its Jacobian ----
+struct Wavelet {
+  float h[8], g[8];  // scaling / wavelet filters, g[m] = (-1)^m h[L-1-m]
+  int L;
+};
+// coef = W x (levels, periodised, in place layout), tmp: scratch of the same size
+void launch_dwt(const float2* x, float2* coef, float2* tmp, int n, int levels, int nb, const Wavelet& w,
+                cudaStream_t s);
+void launch_idwt(const float2* coef, float2* x, float2* tmp, int n, int levels, int nb, const Wavelet& w,
+                 cudaStream_t s);
+int dwt_kernels(int levels);
+void launch_cs_gradstep(const float2* z, const float2* Mz, const float2* rhs, int64_t rhs_stride, float inv_lc,
+                        float2* y, int64_t n, int nb, cudaStream_t s);
+void launch_cs_soft(const float2* c, float2* keep, float2* out, float tau, int64_t n, cudaStream_t s);
+void launch_cs_soft_tan(const float2* at, float2* dc, float tau, int64_t n, int nb, cudaStream_t s);
+void launch_cs_momentum(const float2* xn, float2* x, float2* z, float c, int64_t n, int nb, cudaStream_t s);
+void launch_vjp_a(float2* xbn, const float2* zb, float2* xk1, float c, int64_t n, int nb, cudaStream_t s);
+void launch_vjp_b(const float2* yb, const float2* Myb, float inv_lc, float2* zb, float2* ysum, int64_t n, int nb,
+                  cudaStream_t s);
+void launch_scale(float2* x, float sc, int64_t n, int nb, cudaStream_t s);
+void launch_mask2d(const float2* in, float2* out, const uint8_t* mask, float scale, int64_t n, int planes,
+                   cudaStream_t s);
+void launch_coil_combine(const float2* G, const float2* S, int nc, float2* x, int64_t n, int nb, cudaStream_t s);
+void launch_noise_kspace2d(float2* G, const uint8_t* mask, int nc, int64_t n, int nb, uint64_t seed,
+                           int64_t rep_begin, float sigma, cudaStream_t s);
 
 // ---- fft_generic.cu: batched 1-D FFTs along rows / columns of row-major planes ----
 bool fft_length_supported(int L);

@@ -166,6 +166,18 @@ bool spiral_supported(int n, int* P1, int* P2) {
   return false;
 }
 
+bool grid_split(int L, int* P1, int* P2) {
+#define PICO_SPLIT(LL, A, B) \
+  if (L == LL) {             \
+    *P1 = A;                 \
+    *P2 = B;                 \
+    return true;             \
+  }
+  PICO_GRID_SIZES(PICO_SPLIT)
+#undef PICO_SPLIT
+  return false;
+}
+
 void launch_toep_h(const float* traj, int64_t M, int n, float2* c, cudaStream_t s) {
   const int64_t threads = (int64_t)(2 * n) * (2 * n / kStrip);
   k_toep_h<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(traj, M, n, c);

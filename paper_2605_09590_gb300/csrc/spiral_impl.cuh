@@ -49,9 +49,12 @@ __device__ __forceinline__ void cg_scalars(const CgArgs& a, int b, int it, int* 
 // ---------------------------------------------------------------------------
 // Pass 1: rows of the image, forward transform of S_c . p padded to L = 2N
 // ---------------------------------------------------------------------------
-template <int P1, int P2, bool CG>
+// PAD: the grid is 2N (Toeplitz embedding, image in the first half of each
+// line); otherwise L = N (2-D Cartesian masks: plain 2-D DFT, no padding).
+template <int P1, int P2, bool CG, bool PAD>
 __global__ void __launch_bounds__(Split<P1, P2>::NT, 1)
     k_toep_rows_fwd(SpiralOp op, const float2* __restrict__ xin, float2* __restrict__ G, CgArgs a, int it) {
+  constexpr int NIN = PAD ? P2 / 2 : P2;  // samples n1 + P1 n2 inside the image: n2 < NIN
   constexpr int L = P1 * P2;
   constexpr int NT = Split<P1, P2>::NT;
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -82,7 +85,7 @@ __global__ void __launch_bounds__(Split<P1, P2>::NT, 1)
     for (int n2 = 0; n2 < P2; ++n2) {
       const int x = n1 + P1 * n2;
       float2 v = make_float2(0.f, 0.f);
-      if (aval && n2 < P2 / 2) {
+      if (aval && n2 < NIN) {
         const size_t idx = img + (size_t)ya * N + x;
         if (CG) {
           const float2 r = a.R[idx];
@@ -104,13 +107,12 @@ __global__ void __launch_bounds__(Split<P1, P2>::NT, 1)
     if (ajob) {
       float2 z[P2];
       const float2* __restrict__ S = op.smaps + ((size_t)c * N + (aval ? ya : 0)) * N;
-      // the grid is 2N wide: sample n1 + P1 n2 lies in the image iff n2 < P2/2
 #pragma unroll
       for (int n2 = 0; n2 < P2; ++n2) {
         const int x = n1 + P1 * n2;
-        z[n2] = (aval && n2 < P2 / 2) ? cmul(__ldg(S + x), p[n2]) : make_float2(0.f, 0.f);
+        z[n2] = (aval && n2 < NIN) ? cmul(__ldg(S + x), p[n2]) : make_float2(0.f, 0.f);
       }
-      rowa_store<P1, P2, -1, P2 / 2>(z, n1, ra, buf, tws);
+      rowa_store<P1, P2, -1, NIN>(z, n1, ra, buf, tws);
     }
     __syncthreads();
     if (bval) {
@@ -127,8 +129,9 @@ __global__ void __launch_bounds__(Split<P1, P2>::NT, 1)
 // ---------------------------------------------------------------------------
 // Pass 2: columns of the grid: FFT (rows >= N zero), x T^, inverse FFT, rows < N
 // ---------------------------------------------------------------------------
-template <int P1, int P2>
+template <int P1, int P2, bool PAD>
 __global__ void __launch_bounds__(Split<P1, P2>::NT, 1) k_toep_cols(SpiralOp op, float2* __restrict__ G) {
+  constexpr int NIN = PAD ? P2 / 2 : P2;
   constexpr int L = P1 * P2;
   constexpr int NT = Split<P1, P2>::NT;
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -145,10 +148,10 @@ __global__ void __launch_bounds__(Split<P1, P2>::NT, 1) k_toep_cols(SpiralOp op,
     float2 z[P2];
 #pragma unroll
     for (int n2 = 0; n2 < P2; ++n2) {
-      const int y = n1 + P1 * n2;  // rows >= N (n2 >= P2/2) are the zero padding
-      z[n2] = n2 < P2 / 2 ? g[(size_t)y * L + kx] : make_float2(0.f, 0.f);
+      const int y = n1 + P1 * n2;  // rows >= N (n2 >= NIN) are the zero padding
+      z[n2] = n2 < NIN ? g[(size_t)y * L + kx] : make_float2(0.f, 0.f);
     }
-    cola_store<P1, P2, -1, P2 / 2>(z, n1, ln, buf, tws);
+    cola_store<P1, P2, -1, NIN>(z, n1, ln, buf, tws);
   }
   __syncthreads();
   if (job < P2) {
@@ -164,17 +167,18 @@ __global__ void __launch_bounds__(Split<P1, P2>::NT, 1) k_toep_cols(SpiralOp op,
     float2 z[P2];
     cola_load<P1, P2, 1>(z, n1, ln, buf);
 #pragma unroll
-    for (int n2 = 0; n2 < P2 / 2; ++n2) g[(size_t)(n1 + P1 * n2) * L + kx] = z[n2];  // rows < N only
+    for (int n2 = 0; n2 < NIN; ++n2) g[(size_t)(n1 + P1 * n2) * L + kx] = z[n2];  // rows < N only
   }
 }
 
 // ---------------------------------------------------------------------------
 // Pass 3: rows: inverse FFT per coil, first N samples, conj(S) combine, + lam p
 // ---------------------------------------------------------------------------
-template <int P1, int P2, bool CG>
+template <int P1, int P2, bool CG, bool PAD>
 __global__ void __launch_bounds__(Split<P1, P2>::NT, 1)
     k_toep_rows_inv(SpiralOp op, const float2* __restrict__ G, const float2* __restrict__ xin,
                     float2* __restrict__ yout, float lam, CgArgs a, int it) {
+  constexpr int NIN = PAD ? P2 / 2 : P2;
   constexpr int L = P1 * P2;
   constexpr int NT = Split<P1, P2>::NT;
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -199,9 +203,9 @@ __global__ void __launch_bounds__(Split<P1, P2>::NT, 1)
   const bool bval = bjob && yb < N;
   const size_t img = (size_t)b * N * N;
 
-  float2 acc[P2 / 2];
+  float2 acc[NIN];
 #pragma unroll
-  for (int n2 = 0; n2 < P2 / 2; ++n2) acc[n2] = make_float2(0.f, 0.f);
+  for (int n2 = 0; n2 < NIN; ++n2) acc[n2] = make_float2(0.f, 0.f);
   for (int c = 0; c < op.nc; ++c) {
     if (bjob) {
       float2 y[P1];
@@ -217,7 +221,7 @@ __global__ void __launch_bounds__(Split<P1, P2>::NT, 1)
       if (aval) {
         const float2* __restrict__ S = op.smaps + ((size_t)c * N + ya) * N;
 #pragma unroll
-        for (int n2 = 0; n2 < P2 / 2; ++n2) acc[n2] = cfma_c(acc[n2], __ldg(S + n1 + P1 * n2), z[n2]);
+        for (int n2 = 0; n2 < NIN; ++n2) acc[n2] = cfma_c(acc[n2], __ldg(S + n1 + P1 * n2), z[n2]);
       }
     }
     __syncthreads();
@@ -227,7 +231,7 @@ __global__ void __launch_bounds__(Split<P1, P2>::NT, 1)
     const float2* __restrict__ pin = CG ? a.P : xin;
     float2* __restrict__ out = CG ? a.Q : yout;
 #pragma unroll
-    for (int n2 = 0; n2 < P2 / 2; ++n2) {
+    for (int n2 = 0; n2 < NIN; ++n2) {
       const int x = n1 + P1 * n2;
       {
         const size_t idx = img + (size_t)ya * N + x;
@@ -369,35 +373,44 @@ __global__ void __launch_bounds__(Split<P1, P2>::NT, 1)
 // ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
-template <int P1, int P2>
-void launch_toep_normal_t(const SpiralOp& op, const float2* x, float2* y, float2* G, int nb, float lam,
-                          const CgArgs* a, int it, cudaStream_t s) {
+template <int P1, int P2, bool PAD>
+void toep_normal_impl(const SpiralOp& op, const float2* x, float2* y, float2* G, int nb, float lam, const CgArgs* a,
+                      int it, cudaStream_t s) {
   using Sp = Split<P1, P2>;
   constexpr int L = P1 * P2;
   const size_t smr = Sp::row_buf + L * sizeof(float2), smc = Sp::col_buf + L * sizeof(float2);
   const dim3 grow((op.n + kLines - 1) / kLines, nb);
   CgArgs dummy{};
   if (a) {
-    auto k1 = k_toep_rows_fwd<P1, P2, true>;
+    auto k1 = k_toep_rows_fwd<P1, P2, true, PAD>;
     cudaFuncSetAttribute(k1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smr);
     k1<<<grow, Sp::NT, smr, s>>>(op, nullptr, G, *a, it);
   } else {
-    auto k1 = k_toep_rows_fwd<P1, P2, false>;
+    auto k1 = k_toep_rows_fwd<P1, P2, false, PAD>;
     cudaFuncSetAttribute(k1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smr);
     k1<<<grow, Sp::NT, smr, s>>>(op, x, G, dummy, 0);
   }
-  auto k2 = k_toep_cols<P1, P2>;
+  auto k2 = k_toep_cols<P1, P2, PAD>;
   cudaFuncSetAttribute(k2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smc);
   k2<<<dim3(L / kLines, nb * op.nc), Sp::NT, smc, s>>>(op, G);
   if (a) {
-    auto k3 = k_toep_rows_inv<P1, P2, true>;
+    auto k3 = k_toep_rows_inv<P1, P2, true, PAD>;
     cudaFuncSetAttribute(k3, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smr);
     k3<<<grow, Sp::NT, smr, s>>>(op, G, nullptr, nullptr, lam, *a, it);
   } else {
-    auto k3 = k_toep_rows_inv<P1, P2, false>;
+    auto k3 = k_toep_rows_inv<P1, P2, false, PAD>;
     cudaFuncSetAttribute(k3, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smr);
     k3<<<grow, Sp::NT, smr, s>>>(op, G, x, y, lam, dummy, 0);
   }
+}
+
+template <int P1, int P2>
+void launch_toep_normal_t(const SpiralOp& op, const float2* x, float2* y, float2* G, int nb, float lam,
+                          const CgArgs* a, int it, cudaStream_t s) {
+  if (op.L == 2 * op.n)
+    toep_normal_impl<P1, P2, true>(op, x, y, G, nb, lam, a, it, s);
+  else
+    toep_normal_impl<P1, P2, false>(op, x, y, G, nb, lam, a, it, s);
 }
 
 template <int P1, int P2>

@@ -7,5 +7,5 @@ namespace pico {
                                            const CgArgs*, int, cudaStream_t);                                \
   template void launch_fft2_t<A, B>(float2*, const float2*, int, int, bool, cudaStream_t);                   \
   template void launch_grid_cols_adjoint_t<A, B>(const SpiralOp&, const float2*, float2*, int, cudaStream_t);
-PICO_GRID_SIZES(PICO_INST)
+PICO_GRID_SIZES_B(PICO_INST)
 }  // namespace pico
