@@ -32,7 +32,7 @@ import math
 
 import numpy as np
 
-from . import ops, rng, solvers
+from . import ops, pico, rng, solvers
 
 
 # ----------------------------------------------------------------------------
@@ -175,18 +175,25 @@ class Fista:
     def WH(self, c):
         return idwt2(c, self.levels, self.h, self.g)
 
-    def _run(self):
+    def _run(self, Ahb=None, keep=True):
+        """The FISTA iterations for the data term ``A^H b`` (the stored one by default)."""
         op = self.op
+        Ahb = self.Ahb if Ahb is None else Ahb
         x = np.zeros((op.ny, op.nx), dtype=complex)
         z = x.copy()
         for k in range(self.iters):
-            y = z - (op.normal(z) - self.Ahb) / self.Lc
+            y = z - (op.normal(z) - Ahb) / self.Lc
             wy = self.W(y)
-            self.Wy.append(wy)
+            if keep:
+                self.Wy.append(wy)
             xn = self.WH(soft(wy, self.tau))
             z = xn + self.c[k] * (xn - x)
             x = xn
         return x
+
+    def recon(self, b: np.ndarray) -> np.ndarray:
+        """``f(b)`` with this reconstruction's weight, step and iteration count."""
+        return self._run(self.op.adjoint(np.asarray(b, dtype=complex)), keep=False)
 
     def jvp(self, db: np.ndarray) -> np.ndarray:
         """``J db``: tangent of the reconstruction for a k-space tangent ``db``."""
@@ -230,3 +237,36 @@ def pico_cs(fista: Fista, seed: int, probe_begin: int, nprobes: int, kind: int =
         s += d
         ss += d * d
     return s, ss
+
+
+def pmr_cs(fista: Fista, seed: int, rep_begin: int, nreps: int, sigma: float):
+    """PMR for the nonlinear reconstruction (Sec. 3.2.3): running sums of
+    ``d_i = |f(b + n_i) - f(b)|^2 / sigma^2`` with ``n_i`` the whitened k-space
+    noise of replica ``i`` (the same draw as the linear PMR), ``f(b)`` the
+    stored reconstruction."""
+    ny, nx = fista.op.ny, fista.op.nx
+    s = np.zeros((ny, nx))
+    ss = np.zeros((ny, nx))
+    for i in range(rep_begin, rep_begin + nreps):
+        n = pico.pmr_noise(fista.op, seed, i, sigma)
+        d = np.abs(fista.recon(fista.b + n) - fista.x) ** 2 / sigma ** 2
+        s += d
+        ss += d * d
+    return s, ss
+
+
+def jacobian_diag(fista: Fista) -> np.ndarray:
+    """Exact target of Jacobian PICO and of small-noise PMR (Sec. 2.2.5):
+    ``E|J n|_k^2`` for ``n ~ CN(0, I)``, which for the R-linear ``J`` is
+    ``1/2 (||J^T e_k||^2 + ||J^T (i e_k)||^2)`` with ``J^T`` the adjoint for
+    ``Re<.,.>``; one VJP per real and per imaginary unit image."""
+    ny, nx = fista.op.ny, fista.op.nx
+    out = np.zeros(ny * nx)
+    for k in range(ny * nx):
+        e = np.zeros(ny * nx, dtype=complex)
+        e[k] = 1.0
+        r = fista.vjp(e.reshape(ny, nx))
+        e[k] = 1j
+        i = fista.vjp(e.reshape(ny, nx))
+        out[k] = 0.5 * (np.vdot(r, r).real + np.vdot(i, i).real)
+    return out.reshape(ny, nx)

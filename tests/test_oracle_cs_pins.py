@@ -123,3 +123,53 @@ def test_linear_case_jacobian_is_the_reconstruction_and_sigma():
     v = rng.probe(5, 0, 256).reshape(16, 16)
     u, w = f.jvp(f.vjp(v)).reshape(-1), Sig @ v.reshape(-1)
     assert np.linalg.norm(u - w) <= 1e-10 * np.linalg.norm(w)
+
+
+def _linear_case(n=16, iters=300):
+    S = synth.coil_maps(n, n, 8, 7)
+    op = ops.Operator(S, None, mask=synth.mask_pe(n, 2, n // 4))
+    b = op.forward(synth.phantom(n, 7).astype(np.complex128))
+    return op, b, cs.Fista(op, b, 0.0, iters, levels=2)
+
+
+def test_jacobian_diag_is_the_covariance_diagonal_in_the_linear_case():
+    # lam = 0, converged: J = M^-1 A^H is C-linear, E|J n|^2 = diag(M^-1) (Eqs. 8-10)
+    op, b, f = _linear_case(n=8, iters=200)
+    want = np.real(np.diag(pico.dense_cov(pico.dense_normal(op)))).reshape(op.ny, op.nx)
+    assert np.allclose(cs.jacobian_diag(f), want, rtol=1e-7)
+
+
+def test_cs_pmr_linear_case_is_the_reconstruction_of_the_noise():
+    # lam = 0: f(b + n) - f(b) = f(n) = J n exactly, so each sample is |J n_i|^2 / sigma^2
+    op, b, f = _linear_case(iters=60)
+    sigma = 0.3
+    s, ss = cs.pmr_cs(f, 11, 2, 3, sigma)
+    ws, wss = np.zeros_like(s), np.zeros_like(s)
+    for i in range(2, 5):
+        d = np.abs(f.jvp(pico.pmr_noise(op, 11, i, sigma))) ** 2 / sigma ** 2
+        ws += d
+        wss += d * d
+    assert np.allclose(s, ws, rtol=1e-9) and np.allclose(ss, wss, rtol=1e-9)
+
+
+def test_cs_pmr_small_noise_limit_is_the_tangent():
+    # nonlinear f: (f(b + sigma n) - f(b)) / sigma -> J n as sigma -> 0 (first order in sigma)
+    op, b, f = _cs_case(n=16, nc=4, iters=20)
+    n1 = pico.pmr_noise(op, 5, 0, 1.0)
+    jn = f.jvp(n1)
+    for sigma, bound in [(1e-4, 1e-3), (1e-6, 1e-5)]:
+        s, _ = cs.pmr_cs(f, 5, 0, 1, sigma)
+        assert np.linalg.norm(np.sqrt(s) - np.abs(jn)) <= bound * np.linalg.norm(jn)
+
+
+def test_jacobian_pico_and_cs_pmr_are_unbiased_for_the_jacobian_diagonal():
+    # Sec. 2.2.5: both estimate E|J n|^2; band from each estimator's own sample variance
+    op, b, f = _cs_case(n=16, nc=4, iters=12)
+    exact = cs.jacobian_diag(f)
+    K = 300
+    for s, ss in (cs.pico_cs(f, 21, 0, K), cs.pmr_cs(f, 22, 0, K, 1e-6)):
+        mean = s / K
+        var = (ss / K - mean ** 2) * K / (K - 1)
+        z = (mean - exact) / np.sqrt(var / K)
+        assert np.abs(z).max() <= 6.0
+        assert np.mean(np.abs(z) > 3.0) <= 0.02
