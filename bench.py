@@ -82,6 +82,15 @@ def bytes_per_probe_normal(w):
     return 4 * w.ny * w.nx * 8 + 4 * w.nc * w.ny * 2 * w.ny * 8
 
 
+def flops_2d_normal(w):
+    """Algorithmic FLOPs of one 2-D-mask Cartesian normal operator on one image:
+    per coil a 2-D FFT and inverse 2-D FFT of n x n (4 n line FFTs of length n,
+    5 n log2 n each) plus 16 flops per image sample (S multiply, conj(S)
+    combine-add) and 2 per k-space sample (mask)."""
+    n = w.ny
+    return w.nc * (4 * n * 5 * n * math.log2(n) + 18 * n * n)
+
+
 def normal_ops_per_probe(w):
     """Normal-operator applications per probe: one CG solve (lam = 0) or two
     solves and one A^H A (lam > 0)."""
@@ -111,6 +120,24 @@ def oracle_sample(w, inp, nprobe=1, nrep=1):
         dt = time.perf_counter() - t0
         return (nprobe + nrep) / dt, dt, (f"{nprobe} PICO probe + {nrep} PMR replica of the same workload "
                                           f"({w.max_iter} CG iterations each)")
+    if w.kind == "cs":
+        from oracle import cs as OCS
+        op = O.Operator(inp["smaps"], inp["noise_cov"], mask=inp["mask"])
+        b = op.forward(inp["phantom"].astype(np.complex128))
+        h, g = OCS.wavelet_filters(4)
+        lam = w.extra["lam_l1_rel"] * np.abs(OCS.dwt2(op.adjoint(b), w.extra["levels"], h, g)).max()
+        t0 = time.perf_counter()
+        f = OCS.Fista(op, b, lam, w.max_iter, levels=w.extra["levels"])
+        t1 = time.perf_counter()
+        OCS.pico_cs(f, SEED_PICO, 0, nprobe)
+        sigma = cs_sigma(w, np.sqrt(np.mean(np.abs(b[:, inp["mask"].astype(bool)]) ** 2)))
+        OCS.pmr_cs(f, SEED_PMR, 0, nrep, sigma)
+        t2 = time.perf_counter()
+        # a step = one reconstruction + K probes + K replicas; the sample runs one of each
+        per_pair = (t2 - t1)
+        value = 2.0 * w.probes / ((t1 - t0) + w.probes * per_pair)
+        return value, t2 - t0, (f"FISTA reconstruction ({t1 - t0:.1f} s) + {nprobe} Jacobian probe + {nrep} "
+                                f"PMR replica ({per_pair:.1f} s), scaled to a step of {w.probes} + {w.probes}")
     # spiral: one exact-NUDFT normal operator application, scaled to whole probes/replicas
     op = O.Operator(inp["smaps"], inp["noise_cov"], traj=inp["traj"])
     x = np.ones((w.ny, w.nx), dtype=np.complex128)
@@ -121,6 +148,11 @@ def oracle_sample(w, inp, nprobe=1, nrep=1):
     per_rep = w.max_iter * dt
     return 2.0 / (per_probe + per_rep), dt, (f"one exact-NUDFT A^H A application ({dt:.1f} s), scaled to "
                                              f"{normal_ops_per_probe(w)} per probe and {w.max_iter} per replica")
+
+
+def cs_sigma(w, data_rms):
+    """PMR noise level of the CS workload: ``pmr_snr_db`` below the data rms."""
+    return float(data_rms) * 10.0 ** (-w.extra["pmr_snr_db"] / 20.0)
 
 
 def run_reference(args):
@@ -143,7 +175,8 @@ def run_reference(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128", "data": "synthetic",
         "config": {"workload": args.workload, "ny": w.ny, "nx": w.nx, "coils": w.nc, "R": w.R, "acs": w.acs,
-                   "cg_iters": w.max_iter, "probes_per_step": 1, "replicas_per_step": 1},
+                   "iters": w.max_iter, "probes_per_step": w.probes if w.kind == "cs" else 1,
+                   "replicas_per_step": w.probes if w.kind == "cs" else 1},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -254,7 +287,10 @@ def measure_time_to_1pct(op, w, torch, pico, max_n=20000, step=10):
     out = {"reference": how, "step": step,
            "threshold": 0.01, "nrmse_on": "std maps",
            "reference_range": [float(ref.min()), float(ref.max())]}
-    for name in ("pico", "pmr"):
+    # the three probe families of the ablation (Sec. 3.2.2; Eqs. 18-20) and PMR
+    arms = (("pico", pico.PICO_PROBE_PHASE), ("pico_rademacher", pico.PICO_PROBE_RADEMACHER),
+            ("pico_gauss", pico.PICO_PROBE_GAUSS), ("pmr", None))
+    for name, kind in arms:
         s = torch.zeros((w.ny, w.nx), dtype=torch.float64, device="cuda")
         ss = torch.zeros_like(s)
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -262,9 +298,8 @@ def measure_time_to_1pct(op, w, torch, pico, max_n=20000, step=10):
         curve = []
         while n < max_n:
             ev0.record()
-            if name == "pico":
-                pico.pico_variance_map(op.ctx, SEED_PICO + 1, n, step, pico.PICO_PROBE_PHASE, w.max_iter, 0.0,
-                                       s, ss, True)
+            if kind is not None:
+                pico.pico_variance_map(op.ctx, SEED_PICO + 1, n, step, kind, w.max_iter, 0.0, s, ss, True)
             else:
                 pico.pico_pmr(op.ctx, SEED_PMR + 1, n, step, w.sigma, w.max_iter, 0.0, s, ss, True)
             ev1.record()
@@ -376,6 +411,8 @@ def main():
     pico.load_library()
 
     w, inp = workload(args.workload)
+    if w.kind == "cs":
+        return main_cs(args, w, inp, torch, dist, pico, world, rank, local)
     K = w.probes
     n = w.ny * w.nx
     dev = torch.device("cuda", local)
@@ -493,15 +530,169 @@ def main():
 
     if rank == 0 and world == 1 and not args.no_t1pct and (w.kind == "cartesian" or args.t1pct_spiral):
         t1 = measure_time_to_1pct(op, w, torch, pico, step=10 if w.kind == "cartesian" else 50)
+        # device seconds per probe and per replica at the bench's batch size, timed separately
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        s.zero_()
+        ps.zero_()
+        e0.record(stream)
+        pico.pico_variance_map(op.ctx, SEED_PICO, 0, K, pico.PICO_PROBE_PHASE, w.max_iter, 0.0, s, ss, True)
+        e1.record(stream)
+        pico.pico_pmr(op.ctx, SEED_PMR, 0, K, w.sigma, w.max_iter, 0.0, ps, pss, True)
+        e2.record(stream)
+        torch.cuda.synchronize()
+        per = {"pico": e0.elapsed_time(e1) / 1e3 / K, "pmr": e1.elapsed_time(e2) / 1e3 / K}
         for name in ("pico", "pmr"):
+            t1[name]["seconds_per_sample_batched"] = per[name]
             if t1[name].get("N"):
-                per = total_ms / 1e3 / (2 * K * args.steps)      # device seconds per solve in the batched step
-                t1[name]["seconds_at_batched_rate"] = t1[name]["N"] * per
+                t1[name]["seconds_at_batched_rate"] = t1[name]["N"] * per[name]
         line["time_to_1pct"] = t1
 
     if rank == 0 and world == 1 and args.serving > 0:
         line["serving"] = run_serving(pico, args.serving)
 
+    if rank == 0 and world == 1 and not args.no_cpu:
+        v, dt, desc = oracle_sample(w, inp)
+        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                "sample": f"{desc}, {dt:.1f} s, NumPy FP64 (single-threaded pocketfft; "
+                                          f"{cores_in_use()} cores visible)"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    op.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main_cs(args, w, inp, torch, dist, pico, world, rank, local):
+    """Nonlinear CS workload: one step = the L1-wavelet FISTA reconstruction
+    (the linearisation point), K Jacobian-probe products J(J^T v) accumulated
+    into the PICO map (Sec. 2.2.5) and K PMR replicas (FISTA reruns on b + n_i,
+    Sec. 3.2.3).  ``value`` counts probes + replicas per second."""
+    import numpy as np
+    K = w.probes
+    levels, iters = w.extra["levels"], w.max_iter
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    op = pico.Operator(inp["smaps"], mask=inp["mask"], noise_cov=inp["noise_cov"], max_batch=K, power_iters=15,
+                       stream=stream.cuda_stream)
+    # data b = A x0 (whitened), weight and PMR noise level (set-up, outside the timed region)
+    x0 = torch.from_numpy(np.ascontiguousarray(inp["phantom"], dtype=np.complex64)).to(dev)
+    b = op.forward(x0.reshape(1, w.ny, w.nx))[0].contiguous()
+    ahb = op.adjoint(b.reshape((1,) + tuple(b.shape)))
+    coef = torch.empty_like(ahb)
+    pico.pico_wavelet(op.ctx, ahb, coef, levels)
+    lam = w.extra["lam_l1_rel"] * float(coef.abs().max())
+    m = torch.from_numpy(inp["mask"].astype(bool)).to(dev)
+    sigma = cs_sigma(w, float((b.abs() ** 2)[:, m].mean().sqrt()))
+    x = torch.empty((w.ny, w.nx), dtype=torch.complex64, device=dev)
+    s = torch.zeros((w.ny, w.nx), dtype=torch.float64, device=dev)
+    ss, ps, pss = torch.zeros_like(s), torch.zeros_like(s), torch.zeros_like(s)
+    red = torch.zeros((2, w.ny, w.nx), dtype=torch.float64, device=dev)
+
+    def step(i):
+        begin = (i * world + rank) * K
+        pico.pico_cs_recon(op.ctx, b, lam, iters, levels, x)
+        pico.pico_cs_variance_map(op.ctx, SEED_PICO, begin, K, pico.PICO_PROBE_PHASE, s, ss, True)
+        pico.pico_cs_pmr(op.ctx, SEED_PMR, begin, K, sigma, ps, pss, True)
+        if world > 1:
+            red[0].copy_(s)
+            red[1].copy_(ps)
+            dist.all_reduce(red)
+
+    for i in range(args.warmup):
+        step(i)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    pico.pico_launch_count(op.ctx, reset=True)
+    pico.pico_profile(op.ctx, True)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    ev[0].record(stream)
+    for i in range(args.steps):
+        step(args.warmup + i)
+        ev[i + 1].record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    per_step = [ev[i].elapsed_time(ev[i + 1]) for i in range(args.steps)]
+    total_ms = ev[0].elapsed_time(ev[-1])
+    launches = pico.pico_launch_count(op.ctx)
+    prof = [pico.pico_profile_read(op.ctx, k) for k in range(4)]
+    pico.pico_profile(op.ctx, False)
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = 2 * K * args.steps * world / (total_ms / 1e3)
+
+    norm_ms, norm_n = prof[0]
+    avg_norm_s = norm_ms / max(norm_n, 1) / 1e3
+    # the normal-operator launch groups of the timed region: nearly all run on K images
+    achieved = K * flops_2d_normal(w) / avg_norm_s / 1e12
+    peak = N_SM * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    img = w.ny * w.nx * 8
+    roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            "traffic": None,
+            "kernel": "k_toep_rows_fwd + k_toep_cols + k_toep_rows_inv (2-D-mask normal operator, no padding)",
+            "avg_launch_ms": avg_norm_s * 1e3, "launches": norm_n,
+            "hbm_GBps_incl_coil_grids": K * (2 * img + 4 * w.nc * img) / avg_norm_s / 1e9,
+            "peak_note": "FP32 FMA peak 152 SM x 128 lanes x 2 x 2070 MHz (nominal max clock)"}
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "c64", "data": "synthetic",
+        "config": {"workload": args.workload, "ny": w.ny, "nx": w.nx, "coils": w.nc, "R": w.R,
+                   "mask": f"Poisson-disc, {w.acs}x{w.acs} calibration", "noise_cov": "correlated",
+                   "recon": f"L1-wavelet FISTA (db4, {levels} levels), {iters} iterations, "
+                            f"lambda = {w.extra['lam_l1_rel']} max|W A^H b| = {lam:.4g}",
+                   "probes_per_step": K, "replicas_per_step": K, "pmr_sigma": sigma,
+                   "unit_note": "one solve = one Jacobian-probe product J(J^T v) or one FISTA replica",
+                   "l2": f"working set {6 * K * w.ny * w.nx * 8 / 1e9:.2f} GB of images + "
+                         f"{iters * img / 1e6:.0f} MB trajectory > 129 MB L2",
+                   "parallelism": f"probe shards x{world}"},
+        "roofline": roof,
+        "kernel_ms_in_timed_region": {"normal_op_ms": norm_ms, "cg_vector_ms": prof[1][0],
+                                      "noise_adjoint_ms": prof[2][0], "elementwise_and_dwt_ms": prof[3][0]},
+        "gpu_launches": launches, "clocks": clk,
+        "latency_ms": {"p50": statistics.median(per_step), "p99": max(per_step)},
+    }
+    if not args.no_e2e:
+        S_h, m_h, C_h = np.ascontiguousarray(inp["smaps"]), inp["mask"], inp["noise_cov"]
+        b_h = b.cpu().pin_memory()
+        out_h = np.empty((2, w.ny, w.nx), dtype=np.float64)
+        e2e_steps = max(2, min(args.steps, 3))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for i in range(e2e_steps):
+            op2 = pico.Operator(S_h, mask=m_h, noise_cov=C_h, max_batch=K, power_iters=15, stream=stream.cuda_stream)
+            bd = b_h.to(dev, non_blocking=True)
+            xd = torch.empty((w.ny, w.nx), dtype=torch.complex64, device=dev)
+            a = torch.empty((w.ny, w.nx), dtype=torch.float64, device=dev)
+            c = torch.empty_like(a)
+            begin = (i * world + rank) * K
+            pico.pico_cs_recon(op2.ctx, bd, lam, iters, levels, xd)
+            pico.pico_cs_variance_map(op2.ctx, SEED_PICO, begin, K, pico.PICO_PROBE_PHASE, a)
+            pico.pico_cs_pmr(op2.ctx, SEED_PMR, begin, K, sigma, c)
+            out_h[0] = a.cpu().numpy()
+            out_h[1] = c.cpu().numpy()
+            op2.close()
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        if world > 1:
+            t = torch.tensor([dt], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            dt = float(t.item())
+        line["e2e"] = {"value": 2 * K * e2e_steps * world / dt, "unit": UNIT,
+                       "h2d_bytes_per_step": int(S_h.nbytes + m_h.nbytes + C_h.nbytes + b_h.numel() * 8),
+                       "d2h_bytes_per_step": int(out_h.nbytes), "steps": e2e_steps,
+                       "includes": "pico_init (upload, whitening, power method) + data upload + reconstruction "
+                                   "+ both maps + read-back"}
     if rank == 0 and world == 1 and not args.no_cpu:
         v, dt, desc = oracle_sample(w, inp)
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",

@@ -194,6 +194,26 @@ pico_status pico_cs_vjp(pico_ctx* ctx, const void* xbar_dev, void* bbar_dev, int
 pico_status pico_cs_variance_map(pico_ctx* ctx, uint64_t seed, int64_t probe_begin, int32_t nprobes,
                                  int32_t probe_kind, double* sum_dev, double* sumsq_dev, int32_t accumulate);
 
+/* PMR for the nonlinear reconstruction (Sec. 3.2.3): for replicas
+ * rep_begin .. rep_begin + nreps - 1 of `seed`, draw whitened k-space noise n_i
+ * (the draw of pico_pmr), rerun the last pico_cs_recon's FISTA on b + n_i with
+ * the same lambda_l1, step, levels and iteration count, and accumulate
+ *   sum_dev[k] (+)= |f(b + n_i)[k] - f(b)[k]|^2 / sigma^2,   sumsq_dev[k] (+)= (.)^2
+ * (float64 [ny][nx], caller-owned; sumsq_dev nullable).  Needs a prior
+ * pico_cs_recon.  For small sigma the mean tends to the same E|J n|^2 that
+ * pico_cs_variance_map estimates. */
+pico_status pico_cs_pmr(pico_ctx* ctx, uint64_t seed, int64_t rep_begin, int32_t nreps, double sigma,
+                        double* sum_dev, double* sumsq_dev, int32_t accumulate);
+
+/* The sparsifying transform W of the CS reconstruction as an operator: the
+ * periodised orthonormal 2-D Daubechies-4 DWT with `levels` levels (inverse = 0)
+ * or its inverse W^H (inverse = 1), coefficients in the in-place layout (the
+ * approximation band top-left).  in_dev / out_dev: device complex64
+ * [nbatch][ny][nx], caller-owned, may be equal.  Needs a square image divisible
+ * by 2^levels (PICO_E_UNSUPPORTED otherwise). */
+pico_status pico_wavelet(pico_ctx* ctx, const void* in_dev, void* out_dev, int32_t nbatch, int32_t levels,
+                         int32_t inverse);
+
 /* Finalise running sums over `count` samples (Alg. 1 output; Sec. 4
  * "per-voxel standard error of the running mean"):
  *   var_dev[k] = sum[k] / count                                   (float32, nullable)

@@ -98,6 +98,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "pico_cs_jvp": ([vp, vp, vp, i32], i32),
         "pico_cs_vjp": ([vp, vp, vp, i32], i32),
         "pico_cs_variance_map": ([vp, u64, i64, i32, i32, vp, vp, i32], i32),
+        "pico_cs_pmr": ([vp, u64, i64, i32, f64, vp, vp, i32], i32),
+        "pico_wavelet": ([vp, vp, vp, i32, i32, i32], i32),
         "pico_gfactor": ([vp, vp, vp, f64, vp], i32),
         "pico_profile": ([vp, i32], i32),
         "pico_profile_read": ([vp, i32, ctypes.POINTER(f64), ctypes.POINTER(i64)], i32),
@@ -278,6 +280,21 @@ def pico_cs_variance_map(ctx, seed: int, probe_begin: int, nprobes: int, probe_k
     _check(ctx, load_library().pico_cs_variance_map(
         ctx, seed & (2 ** 64 - 1), probe_begin, nprobes, probe_kind, _dev_ptr(sum_, torch.float64, "sum"),
         None if sumsq is None else _dev_ptr(sumsq, torch.float64, "sumsq"), 1 if accumulate else 0))
+
+
+def pico_cs_pmr(ctx, seed: int, rep_begin: int, nreps: int, sigma: float, sum_, sumsq=None,
+                accumulate: bool = False) -> None:
+    import torch
+    _check(ctx, load_library().pico_cs_pmr(
+        ctx, seed & (2 ** 64 - 1), rep_begin, nreps, sigma, _dev_ptr(sum_, torch.float64, "sum"),
+        None if sumsq is None else _dev_ptr(sumsq, torch.float64, "sumsq"), 1 if accumulate else 0))
+
+
+def pico_wavelet(ctx, x, out, levels: int, inverse: bool = False) -> None:
+    import torch
+    _check(ctx, load_library().pico_wavelet(ctx, _dev_ptr(x, torch.complex64, "x"),
+                                            _dev_ptr(out, torch.complex64, "out"), x.shape[0], levels,
+                                            1 if inverse else 0))
 
 
 def pico_finalize(ctx, sum_, sumsq, count: int, var=None, stderr=None) -> None:

@@ -61,7 +61,11 @@ struct pico_ctx {
   double cs_lc = 0, cs_tau = 0;
   std::vector<float> cs_c;     // momentum coefficients c_k
   float2* cs_traj = nullptr;   // [iters][n] wavelet coefficients W y_k of the reconstruction
+  int cs_traj_cap = 0;         // iterations cs_traj has room for
   float2* cs_buf = nullptr;    // [6][B][n] work images
+  float2* cs_ahb = nullptr;    // A^H b of the reconstruction's data [n]
+  float2* cs_x0 = nullptr;     // the reconstruction f(b) [n]
+  double cs_lam = 0;           // lambda_l1 of the reconstruction
   pico::Wavelet wav{};
   pico::CgArgs cg{};
   size_t device_bytes = 0, budget = 0;
@@ -459,22 +463,50 @@ constexpr double kDb4[8] = {0.2303778133088964,  0.7148465705529154, 0.630880767
 
 pico_status cs_buffers(pico_ctx* c) {
   if (c->cs_buf) return PICO_OK;
-  return dalloc(c, &c->cs_buf, (size_t)6 * c->max_batch * c->n);
+  pico_status st = dalloc(c, &c->cs_buf, (size_t)6 * c->max_batch * c->n);
+  if (st == PICO_OK) st = dalloc(c, &c->cs_ahb, (size_t)c->n);
+  if (st == PICO_OK) st = dalloc(c, &c->cs_x0, (size_t)c->n);
+  for (int m = 0; m < 8; ++m) {
+    c->wav.h[m] = (float)kDb4[m];
+    c->wav.g[m] = (float)((m % 2 ? -1.0 : 1.0) * kDb4[7 - m]);
+  }
+  c->wav.L = 8;
+  return st;
 }
 float2* cs_e(pico_ctx* c, int k) { return c->cs_buf + (size_t)k * c->max_batch * c->n; }
 
-void cs_W(pico_ctx* c, const float2* x, float2* coef, float2* tmp, int nb) {
-  Launch L(c, 3, pico::dwt_kernels(c->cs_levels));
-  pico::launch_dwt(x, coef, tmp, c->ny, c->cs_levels, nb, c->wav, c->stream);
+void cs_W(pico_ctx* c, const float2* x, float2* coef, float2* tmp, int nb, int levels) {
+  Launch L(c, 3, pico::dwt_kernels(levels));
+  pico::launch_dwt(x, coef, tmp, c->ny, levels, nb, c->wav, c->stream);
 }
-void cs_WH(pico_ctx* c, const float2* coef, float2* x, float2* tmp, int nb) {
-  Launch L(c, 3, pico::dwt_kernels(c->cs_levels));
-  pico::launch_idwt(coef, x, tmp, c->ny, c->cs_levels, nb, c->wav, c->stream);
+void cs_WH(pico_ctx* c, const float2* coef, float2* x, float2* tmp, int nb, int levels) {
+  Launch L(c, 3, pico::idwt_kernels(levels, coef == x));
+  pico::launch_idwt(coef, x, tmp, c->ny, levels, nb, c->wav, c->stream);
+}
+
+// FISTA iterations on nb data terms A^H b_i (rhs, stride rhs_stride; 0 = one broadcast term).
+// Result x in E0 (E1..E3 work).  With `keep`, nb == 1 and W y_k is stored as the
+// linearisation point of the Jacobian.
+void cs_fista(pico_ctx* c, const float2* rhs, int64_t rhs_stride, int nb, bool keep) {
+  float2 *x = cs_e(c, 0), *z = cs_e(c, 1), *t2 = cs_e(c, 2), *t3 = cs_e(c, 3);
+  const int64_t n = c->n;
+  const float inv_lc = (float)(1.0 / c->cs_lc), tau = (float)c->cs_tau;
+  cudaMemsetAsync(x, 0, (size_t)nb * n * sizeof(float2), c->stream);
+  cudaMemsetAsync(z, 0, (size_t)nb * n * sizeof(float2), c->stream);
+  for (int k = 0; k < c->cs_iters; ++k) {
+    op_apply(c, z, t2, nb, 0.f);
+    { Launch L(c, 3); pico::launch_cs_gradstep(z, t2, rhs, rhs_stride, inv_lc, t3, n, nb, c->stream); }
+    cs_W(c, t3, t3, t2, nb, c->cs_levels);
+    { Launch L(c, 3); pico::launch_cs_soft(t3, keep ? c->cs_traj + (size_t)k * n : nullptr, t3, tau, n, nb,
+                                           c->stream); }
+    cs_WH(c, t3, t3, t2, nb, c->cs_levels);
+    { Launch L(c, 3); pico::launch_cs_momentum(t3, x, z, c->cs_c[k], n, nb, c->stream); }
+  }
 }
 
 // dx (E0) = J applied to the image-domain tangent A^H db given in `ahdb` [nb][n]
 void cs_jvp_core(pico_ctx* c, const float2* ahdb, int nb) {
-  float2 *dx = cs_e(c, 0), *dz = cs_e(c, 1), *t2 = cs_e(c, 2), *t3 = cs_e(c, 3), *t4 = cs_e(c, 4);
+  float2 *dx = cs_e(c, 0), *dz = cs_e(c, 1), *t2 = cs_e(c, 2), *t3 = cs_e(c, 3);
   const int64_t n = c->n;
   const float inv_lc = (float)(1.0 / c->cs_lc), tau = (float)c->cs_tau;
   cudaMemsetAsync(dx, 0, (size_t)nb * n * sizeof(float2), c->stream);
@@ -482,17 +514,16 @@ void cs_jvp_core(pico_ctx* c, const float2* ahdb, int nb) {
   for (int k = 0; k < c->cs_iters; ++k) {
     op_apply(c, dz, t2, nb, 0.f);
     { Launch L(c, 3); pico::launch_cs_gradstep(dz, t2, ahdb, n, inv_lc, t3, n, nb, c->stream); }
-    cs_W(c, t3, t4, t2, nb);
-    { Launch L(c, 3); pico::launch_cs_soft_tan(c->cs_traj + (size_t)k * n, t4, tau, n, nb, c->stream); }
-    cs_WH(c, t4, t3, t2, nb);
+    cs_W(c, t3, t3, t2, nb, c->cs_levels);
+    { Launch L(c, 3); pico::launch_cs_soft_tan(c->cs_traj + (size_t)k * n, t3, tau, n, nb, c->stream); }
+    cs_WH(c, t3, t3, t2, nb, c->cs_levels);
     { Launch L(c, 3); pico::launch_cs_momentum(t3, dx, dz, c->cs_c[k], n, nb, c->stream); }
   }
 }
 
 // E0 = (sum_k ybar_k) / Lc for the output cotangent `xbar` [nb][n] (reverse sweep)
 void cs_vjp_core(pico_ctx* c, const float2* xbar, int nb) {
-  float2 *ys = cs_e(c, 0), *zb = cs_e(c, 1), *t2 = cs_e(c, 2), *t3 = cs_e(c, 3), *t4 = cs_e(c, 4),
-         *xbn = cs_e(c, 5);
+  float2 *ys = cs_e(c, 0), *zb = cs_e(c, 1), *t2 = cs_e(c, 2), *t3 = cs_e(c, 3), *xbn = cs_e(c, 5);
   const int64_t n = c->n;
   const float inv_lc = (float)(1.0 / c->cs_lc), tau = (float)c->cs_tau;
   cudaMemsetAsync(ys, 0, (size_t)nb * n * sizeof(float2), c->stream);
@@ -500,13 +531,34 @@ void cs_vjp_core(pico_ctx* c, const float2* xbar, int nb) {
   cudaMemcpyAsync(xbn, xbar, (size_t)nb * n * sizeof(float2), cudaMemcpyDeviceToDevice, c->stream);
   for (int k = c->cs_iters - 1; k >= 0; --k) {
     { Launch L(c, 3); pico::launch_vjp_a(xbn, zb, t3, c->cs_c[k], n, nb, c->stream); }
-    cs_W(c, t3, t4, t2, nb);
-    { Launch L(c, 3); pico::launch_cs_soft_tan(c->cs_traj + (size_t)k * n, t4, tau, n, nb, c->stream); }
-    cs_WH(c, t4, t3, t2, nb);
+    cs_W(c, t3, t3, t2, nb, c->cs_levels);
+    { Launch L(c, 3); pico::launch_cs_soft_tan(c->cs_traj + (size_t)k * n, t3, tau, n, nb, c->stream); }
+    cs_WH(c, t3, t3, t2, nb, c->cs_levels);
     op_apply(c, t3, t2, nb, 0.f);
     { Launch L(c, 3); pico::launch_vjp_b(t3, t2, inv_lc, zb, ys, n, nb, c->stream); }
   }
   { Launch L(c, 3); pico::launch_scale(ys, inv_lc, n, nb, c->stream); }
+}
+
+// out[b] = A^H n_b for the whitened k-space noise of replicas rep_begin.. (PMR, Sec. 1); needs ensure_kbuf
+void noise_adjoint(pico_ctx* c, float2* out, int nb, uint64_t seed, int64_t rep_begin, double sigma) {
+  if (c->mask2d) {
+    { Launch L(c, 2); pico::launch_noise_kspace2d(c->G, c->mask, c->nc, c->n, nb, seed, rep_begin,
+                                                  (float)(sigma / std::sqrt((double)c->n)), c->stream); }
+    adjoint2d_from_kbuf(c, out, nb);
+  } else if (c->kind == PICO_CARTESIAN) {
+    { Launch L(c, 2); pico::launch_cart_pmr_cols(c->cop, c->G, nb, seed, rep_begin, (float)sigma, c->stream); }
+    { Launch L(c, 2); pico::launch_cart_rows_adjoint(c->cop, c->G, out, nb, c->stream); }
+  } else {
+    { Launch L(c, 2); pico::launch_grid_pmr(c->sop, c->G, nb, seed, rep_begin, (float)sigma, c->stream); }
+    { Launch L(c, 2, 2); pico::launch_grid_adjoint_rest(c->sop, c->G, out, nb, c->stream); }
+  }
+}
+
+pico_status wavelet_check(pico_ctx* c, int levels) {
+  if (c->ny != c->nx || levels > 30 || (c->ny % (1 << levels)) != 0 || (c->ny >> levels) < 1)
+    return fail(c, PICO_E_UNSUPPORTED, "the wavelet transform needs a square image divisible by 2^levels");
+  return PICO_OK;
 }
 
 pico_status cs_check(pico_ctx* c) {
@@ -844,17 +896,7 @@ pico_status pico_pmr(pico_ctx* c, uint64_t seed, int64_t rep_begin, int32_t nrep
   const float lam = (float)c->lam_phys;
   for (int32_t b0 = 0; b0 < nreps; b0 += c->max_batch) {
     const int nb = std::min(c->max_batch, nreps - b0);
-    if (c->mask2d) {
-      { Launch L(c, 2); pico::launch_noise_kspace2d(c->G, c->mask, c->nc, c->n, nb, seed, rep_begin + b0,
-                                                    (float)(sigma / std::sqrt((double)c->n)), c->stream); }
-      adjoint2d_from_kbuf(c, c->R, nb);
-    } else if (c->kind == PICO_CARTESIAN) {
-      { Launch L(c, 2); pico::launch_cart_pmr_cols(c->cop, c->G, nb, seed, rep_begin + b0, (float)sigma, c->stream); }
-      { Launch L(c, 2); pico::launch_cart_rows_adjoint(c->cop, c->G, c->R, nb, c->stream); }
-    } else {
-      { Launch L(c, 2); pico::launch_grid_pmr(c->sop, c->G, nb, seed, rep_begin + b0, (float)sigma, c->stream); }
-      { Launch L(c, 2, 2); pico::launch_grid_adjoint_rest(c->sop, c->G, c->R, nb, c->stream); }
-    }
+    noise_adjoint(c, c->R, nb, seed, rep_begin + b0, sigma);
     if ((st = run_cg(c, nb, max_iter, rtol, lam)) != PICO_OK) return st;
     { Launch L(c, 3); pico::launch_accum_pmr(c->X, c->n, nb, (float)(1.0 / (sigma * sigma)), sum, sumsq, c->stream); }
   }
@@ -933,21 +975,17 @@ pico_status pico_cs_recon(pico_ctx* c, const void* b_dev, double lambda_l1, int3
   if (!c || !c->smaps) return PICO_E_INVALID;
   if (!b_dev || !x_dev || iters < 1 || levels < 1 || !(lambda_l1 >= 0.0))
     return fail(c, PICO_E_INVALID, "bad CS reconstruction arguments");
-  if (c->ny != c->nx || (c->ny % (1 << levels)) != 0)
-    return fail(c, PICO_E_UNSUPPORTED, "the wavelet transform needs a square image divisible by 2^levels");
-  if (!(c->lambda_max > 0.0)) return fail(c, PICO_E_INVALID, "CS needs the power-method lambda_max (power_iters > 0)");
-  pico_status st = cs_buffers(c);
+  pico_status st = wavelet_check(c, levels);
   if (st != PICO_OK) return st;
-  if (!c->cs_traj || c->cs_iters < iters) {
+  if (!(c->lambda_max > 0.0)) return fail(c, PICO_E_INVALID, "CS needs the power-method lambda_max (power_iters > 0)");
+  if ((st = cs_buffers(c)) != PICO_OK) return st;
+  if (c->cs_traj_cap < iters) {
     if ((st = dalloc(c, &c->cs_traj, (size_t)iters * c->n)) != PICO_OK) return st;
+    c->cs_traj_cap = iters;
   }
-  for (int m = 0; m < 8; ++m) {
-    c->wav.h[m] = (float)kDb4[m];
-    c->wav.g[m] = (float)((m % 2 ? -1.0 : 1.0) * kDb4[7 - m]);
-  }
-  c->wav.L = 8;
   c->cs_iters = iters;
   c->cs_levels = levels;
+  c->cs_lam = lambda_l1;
   c->cs_lc = c->margin * c->lambda_max;
   c->cs_tau = lambda_l1 / c->cs_lc;
   c->cs_c.assign(iters, 0.f);
@@ -957,23 +995,56 @@ pico_status pico_cs_recon(pico_ctx* c, const void* b_dev, double lambda_l1, int3
     c->cs_c[k] = (float)((t - 1.0) / tn);
     t = tn;
   }
-  const int64_t n = c->n;
-  float2 *x = cs_e(c, 0), *z = cs_e(c, 1), *t2 = cs_e(c, 2), *t3 = cs_e(c, 3), *t4 = cs_e(c, 4), *ahb = cs_e(c, 5);
-  if ((st = pico_adjoint(c, b_dev, ahb, 1)) != PICO_OK) return st;
-  cudaMemsetAsync(x, 0, (size_t)n * sizeof(float2), c->stream);
-  cudaMemsetAsync(z, 0, (size_t)n * sizeof(float2), c->stream);
-  const float inv_lc = (float)(1.0 / c->cs_lc), tau = (float)c->cs_tau;
-  for (int k = 0; k < iters; ++k) {
-    op_apply(c, z, t2, 1, 0.f);
-    { Launch L(c, 3); pico::launch_cs_gradstep(z, t2, ahb, 0, inv_lc, t3, n, 1, c->stream); }
-    cs_W(c, t3, t4, t2, 1);
-    { Launch L(c, 3); pico::launch_cs_soft(t4, c->cs_traj + (size_t)k * n, t4, tau, n, c->stream); }
-    cs_WH(c, t4, t3, t2, 1);
-    { Launch L(c, 3); pico::launch_cs_momentum(t3, x, z, c->cs_c[k], n, 1, c->stream); }
-  }
-  cudaMemcpyAsync(x_dev, x, (size_t)n * sizeof(float2), cudaMemcpyDeviceToDevice, c->stream);
+  if ((st = pico_adjoint(c, b_dev, c->cs_ahb, 1)) != PICO_OK) return st;
+  cs_fista(c, c->cs_ahb, 0, 1, true);
+  cudaMemcpyAsync(c->cs_x0, cs_e(c, 0), (size_t)c->n * sizeof(float2), cudaMemcpyDeviceToDevice, c->stream);
+  cudaMemcpyAsync(x_dev, cs_e(c, 0), (size_t)c->n * sizeof(float2), cudaMemcpyDeviceToDevice, c->stream);
   c->cs_ready = true;
   return cuda_check(c, "pico_cs_recon");
+}
+
+pico_status pico_cs_pmr(pico_ctx* c, uint64_t seed, int64_t rep_begin, int32_t nreps, double sigma, double* sum,
+                        double* sumsq, int32_t accumulate) {
+  pico_status st = cs_check(c);
+  if (st != PICO_OK) return st;
+  if (!sum || nreps < 0 || rep_begin < 0) return fail(c, PICO_E_INVALID, "bad sum pointer or replica range");
+  if (!(sigma > 0.0)) return fail(c, PICO_E_INVALID, "sigma must be > 0");
+  if (c->kind == PICO_CARTESIAN && !c->mask2d && c->cop.M1 == 0)
+    return fail(c, PICO_E_UNSUPPORTED, "nx has no FFT split in this build (PMR adjoint)");
+  if ((st = ensure_kbuf(c)) != PICO_OK) return st;
+  if (!accumulate) {
+    cudaMemsetAsync(sum, 0, (size_t)c->n * sizeof(double), c->stream);
+    if (sumsq) cudaMemsetAsync(sumsq, 0, (size_t)c->n * sizeof(double), c->stream);
+  }
+  for (int32_t b0 = 0; b0 < nreps; b0 += c->max_batch) {
+    const int nb = std::min(c->max_batch, nreps - b0);
+    noise_adjoint(c, c->R, nb, seed, rep_begin + b0, sigma);                           // A^H n_i
+    { Launch L(c, 3); pico::launch_axpy_bcast(c->R, c->cs_ahb, 1.f, c->n, nb, c->stream); }  // A^H (b + n_i)
+    cs_fista(c, c->R, c->n, nb, false);                                               // f(b + n_i)
+    { Launch L(c, 3); pico::launch_axpy_bcast(cs_e(c, 0), c->cs_x0, -1.f, c->n, nb, c->stream); }
+    { Launch L(c, 3); pico::launch_accum_pmr(cs_e(c, 0), c->n, nb, (float)(1.0 / (sigma * sigma)), sum, sumsq,
+                                             c->stream); }
+  }
+  return cuda_check(c, "pico_cs_pmr");
+}
+
+pico_status pico_wavelet(pico_ctx* c, const void* in_dev, void* out_dev, int32_t nbatch, int32_t levels,
+                         int32_t inverse) {
+  if (!c || !c->smaps) return PICO_E_INVALID;
+  if (nbatch < 0 || (nbatch > 0 && (!in_dev || !out_dev)) || levels < 1)
+    return fail(c, PICO_E_INVALID, "bad batch, pointer or level count");
+  pico_status st = wavelet_check(c, levels);
+  if (st != PICO_OK) return st;
+  if ((st = cs_buffers(c)) != PICO_OK) return st;
+  const float2* in = static_cast<const float2*>(in_dev);
+  float2* out = static_cast<float2*>(out_dev);
+  for (int32_t b0 = 0; b0 < nbatch; b0 += c->max_batch) {
+    const int nb = std::min(c->max_batch, nbatch - b0);
+    const size_t off = (size_t)b0 * c->n;
+    if (inverse) cs_WH(c, in + off, out + off, cs_e(c, 2), nb, levels);
+    else cs_W(c, in + off, out + off, cs_e(c, 2), nb, levels);
+  }
+  return cuda_check(c, "pico_wavelet");
 }
 
 pico_status pico_cs_jvp(pico_ctx* c, const void* db_dev, void* dx_dev, int32_t nbatch) {

@@ -134,14 +134,24 @@ __global__ void k_cs_gradstep(const float2* __restrict__ z, const float2* __rest
   y[o] = make_float2(fmaf(-inv_lc, mz.x - r.x, zz.x), fmaf(-inv_lc, mz.y - r.y, zz.y));
 }
 
-// primal: keep the coefficients (trajectory) and threshold them
-__global__ void k_cs_soft(const float2* __restrict__ c, float2* __restrict__ keep, float2* __restrict__ out, float tau,
-                          int64_t n) {
+// primal: threshold the coefficients (batch b = blockIdx.y); `keep` (one image) stores them
+// as the linearisation point of the Jacobian
+__global__ void k_cs_soft(const float2* c, float2* __restrict__ keep, float2* out, float tau, int64_t n) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  const float2 v = c[i];
+  const size_t o = (size_t)blockIdx.y * n + i;
+  const float2 v = c[o];
   if (keep) keep[i] = v;
-  out[i] = soft1(v, tau);
+  out[o] = soft1(v, tau);
+}
+
+// x[b] += alpha y (y one image, broadcast over the batch)
+__global__ void k_axpy_bcast(float2* __restrict__ x, const float2* __restrict__ y, float alpha, int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const size_t o = (size_t)blockIdx.y * n + i;
+  const float2 a = x[o], b = y[i];
+  x[o] = make_float2(fmaf(alpha, b.x, a.x), fmaf(alpha, b.y, a.y));
 }
 
 // tangent of the soft threshold at the stored coefficients (broadcast over the batch), in place
@@ -229,21 +239,22 @@ __global__ void k_noise_kspace2d(float2* __restrict__ G, const uint8_t* __restri
 
 }  // namespace
 
+// The first analysis level covers the whole image, so it reads x directly (x may equal coef).
 void launch_dwt(const float2* x, float2* coef, float2* tmp, int n, int levels, int nb, const Wavelet& w,
                 cudaStream_t s) {
   const int64_t img = (int64_t)n * n;
-  k_copy_region<<<dim3(blocks(img), nb), 256, 0, s>>>(x, coef, n, n, n, img);
   for (int l = 0; l < levels; ++l) {
     const int m = n >> l;
-    k_dwt_rows_fwd<<<dim3(blocks((int64_t)m * (m / 2)), nb), 256, 0, s>>>(coef, tmp, n, m, m, img, w);
+    k_dwt_rows_fwd<<<dim3(blocks((int64_t)m * (m / 2)), nb), 256, 0, s>>>(l == 0 ? x : coef, tmp, n, m, m, img, w);
     k_dwt_cols_fwd<<<dim3(blocks((int64_t)(m / 2) * m), nb), 256, 0, s>>>(tmp, coef, n, m, m, img, w);
   }
 }
 
+// Synthesis runs in place on x; with x == coef no copy is needed.
 void launch_idwt(const float2* coef, float2* x, float2* tmp, int n, int levels, int nb, const Wavelet& w,
                  cudaStream_t s) {
   const int64_t img = (int64_t)n * n;
-  k_copy_region<<<dim3(blocks(img), nb), 256, 0, s>>>(coef, x, n, n, n, img);
+  if (coef != x) k_copy_region<<<dim3(blocks(img), nb), 256, 0, s>>>(coef, x, n, n, n, img);
   for (int l = levels - 1; l >= 0; --l) {
     const int m = n >> l;
     k_dwt_cols_inv<<<dim3(blocks((int64_t)m * m), nb), 256, 0, s>>>(x, tmp, n, m, m, img, w);
@@ -251,14 +262,18 @@ void launch_idwt(const float2* coef, float2* x, float2* tmp, int n, int levels, 
   }
 }
 
-int dwt_kernels(int levels) { return 1 + 2 * levels; }
+int dwt_kernels(int levels) { return 2 * levels; }
+int idwt_kernels(int levels, bool in_place) { return 2 * levels + (in_place ? 0 : 1); }
 
 void launch_cs_gradstep(const float2* z, const float2* Mz, const float2* rhs, int64_t rhs_stride, float inv_lc,
                         float2* y, int64_t n, int nb, cudaStream_t s) {
   k_cs_gradstep<<<dim3(blocks(n), nb), 256, 0, s>>>(z, Mz, rhs, rhs_stride, inv_lc, y, n);
 }
-void launch_cs_soft(const float2* c, float2* keep, float2* out, float tau, int64_t n, cudaStream_t s) {
-  k_cs_soft<<<blocks(n), 256, 0, s>>>(c, keep, out, tau, n);
+void launch_cs_soft(const float2* c, float2* keep, float2* out, float tau, int64_t n, int nb, cudaStream_t s) {
+  k_cs_soft<<<dim3(blocks(n), nb), 256, 0, s>>>(c, keep, out, tau, n);
+}
+void launch_axpy_bcast(float2* x, const float2* y, float alpha, int64_t n, int nb, cudaStream_t s) {
+  k_axpy_bcast<<<dim3(blocks(n), nb), 256, 0, s>>>(x, y, alpha, n);
 }
 void launch_cs_soft_tan(const float2* at, float2* dc, float tau, int64_t n, int nb, cudaStream_t s) {
   k_cs_soft_tan<<<dim3(blocks(n), nb), 256, 0, s>>>(at, dc, tau, n);

@@ -118,9 +118,11 @@ void launch_dwt(const float2* x, float2* coef, float2* tmp, int n, int levels, i
 void launch_idwt(const float2* coef, float2* x, float2* tmp, int n, int levels, int nb, const Wavelet& w,
                  cudaStream_t s);
 int dwt_kernels(int levels);
+int idwt_kernels(int levels, bool in_place);
 void launch_cs_gradstep(const float2* z, const float2* Mz, const float2* rhs, int64_t rhs_stride, float inv_lc,
                         float2* y, int64_t n, int nb, cudaStream_t s);
-void launch_cs_soft(const float2* c, float2* keep, float2* out, float tau, int64_t n, cudaStream_t s);
+void launch_cs_soft(const float2* c, float2* keep, float2* out, float tau, int64_t n, int nb, cudaStream_t s);
+void launch_axpy_bcast(float2* x, const float2* y, float alpha, int64_t n, int nb, cudaStream_t s);
 void launch_cs_soft_tan(const float2* at, float2* dc, float tau, int64_t n, int nb, cudaStream_t s);
 void launch_cs_momentum(const float2* xn, float2* x, float2* z, float c, int64_t n, int nb, cudaStream_t s);
 void launch_vjp_a(float2* xbn, const float2* zb, float2* xk1, float c, int64_t n, int nb, cudaStream_t s);

@@ -134,7 +134,7 @@ def spiral_traj(n: int, n_interleaves: int = 16, nsamp: int = 4096, R: int = 1,
 class Workload:
     """A named synthetic workload (sizes follow the paper's experiments)."""
     name: str
-    kind: str            # "cartesian" or "spiral"
+    kind: str            # "cartesian", "spiral" or "cs" (2-D Poisson-disc mask, L1-wavelet FISTA)
     ny: int
     nx: int
     nc: int
@@ -157,6 +157,9 @@ class Workload:
         out["noise_cov"] = noise_cov(self.nc, s) if self.noise_corr else None
         if self.kind == "cartesian":
             out["mask"] = mask_pe(self.ny, self.R, self.acs)
+        elif self.kind == "cs":
+            out["mask"] = poisson_disc_mask(self.ny, self.nx, float(self.R), self.acs, s)
+            out["phantom"] = phantom(self.ny, s)
         else:
             out["traj"] = spiral_traj(self.ny, self.n_interleaves, self.nsamp, self.R)
         return out
@@ -176,6 +179,12 @@ WORKLOADS = {
                              max_iter=30, lam=0.1, sigma=1e-2, reps=500),
     "spiral240_r4": Workload("spiral240_r4", "spiral", 240, 240, 20, 4, probes=256,
                              max_iter=30, lam=0.1, sigma=1e-2, reps=500),
+    # 320x320, 15 correlated coils, variable-density Poisson-disc R=2 with a 24x24
+    # calibration block; L1-wavelet (db4, 4 levels) FISTA, 100 iterations, weight
+    # 1e-2 max|W A^H b|; K=64 Jacobian probes; PMR noise 45 dB below the data rms.
+    "cs320_r2": Workload("cs320_r2", "cs", 320, 320, 15, 2, acs=24, noise_corr=True,
+                         probes=64, max_iter=100,
+                         extra={"levels": 4, "lam_l1_rel": 1e-2, "pmr_snr_db": 45.0}),
 }
 
 

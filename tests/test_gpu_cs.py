@@ -128,3 +128,38 @@ def test_autograd_function_backward_is_the_vjp(case64):
     bb = torch.empty((1, nc, n, n), dtype=torch.complex64, device="cuda")
     pico.pico_cs_vjp(op.ctx, g.reshape(1, n, n), bb)
     assert torch.allclose(gb, bb[0], rtol=1e-5, atol=1e-6)
+
+
+@pytest.mark.parametrize("levels", [1, 4])
+def test_wavelet_operator_matches_oracle(case64, levels):
+    n, nc, S, mask, op, oop, b, lam = case64
+    h, g = OCS.wavelet_filters(4)
+    r = np.random.default_rng(5)
+    x = (r.standard_normal((3, n, n)) + 1j * r.standard_normal((3, n, n))).astype(np.complex64)
+    c = torch.empty((3, n, n), dtype=torch.complex64, device="cuda")
+    pico.pico_wavelet(op.ctx, dev(x), c, levels)
+    xi = dev(x)
+    pico.pico_wavelet(op.ctx, xi, xi, levels, inverse=True)          # in place
+    for i in range(3):
+        assert rel(c[i].cpu().numpy(), OCS.dwt2(x[i].astype(np.complex128), levels, h, g)) < 2e-6
+        assert rel(xi[i].cpu().numpy(), OCS.idwt2(x[i].astype(np.complex128), levels, h, g)) < 2e-6
+
+
+def test_cs_pmr_same_seed_matches_oracle(case64):
+    n, nc, S, mask, op, oop, b, lam = case64
+    f = OCS.Fista(oop, b, lam, 30, levels=4)
+    x = torch.empty((n, n), dtype=torch.complex64, device="cuda")
+    pico.pico_cs_recon(op.ctx, dev(b), lam, 30, 4, x)
+    sigma = 0.1 * float(np.sqrt(np.mean(np.abs(b[:, mask.astype(bool)]) ** 2)))
+    K = 5                                               # max_batch 8: one chunk; then 3 more accumulated
+    s = torch.empty((n, n), dtype=torch.float64, device="cuda")
+    ss = torch.empty_like(s)
+    pico.pico_cs_pmr(op.ctx, 23, 0, K, sigma, s, ss)
+    pico.pico_cs_pmr(op.ctx, 23, K, 3, sigma, s, ss, accumulate=True)
+    so, sso = OCS.pmr_cs(f, 23, 0, K + 3, sigma)
+    assert rel(s.cpu().numpy(), so) < 2e-3
+    assert rel(ss.cpu().numpy(), sso) < 4e-3
+    # the reconstruction itself is unchanged by the replica runs
+    xs = x.clone()
+    pico.pico_cs_recon(op.ctx, dev(b), lam, 30, 4, x)
+    assert torch.equal(x, xs)
