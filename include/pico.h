@@ -87,6 +87,10 @@ typedef struct {
   int32_t kind, ny, nx, ncoils, max_batch, max_iter_cap;
   int64_t nsamp;
   uint64_t device_bytes;    /* device memory held by the context                              */
+  int32_t normal_op;        /* how (A^H A + lam I) is applied inside CG: 0 column FFTs,
+                               1 dense per-column Gram matrices on the tensor cores
+                               (phase-encode masks, ny % 16 == 0, ny >= 128; environment
+                               PICO_NORMAL_OP=fft selects 0), 2 Toeplitz 2-D FFT passes   */
 } pico_info;
 
 /* Create a context: validates the descriptor, whitens the sensitivities,

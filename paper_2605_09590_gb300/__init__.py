@@ -52,6 +52,7 @@ class pico_info(ctypes.Structure):
         ("lambda_max", ctypes.c_double), ("lambda_phys", ctypes.c_double), ("kind", ctypes.c_int32),
         ("ny", ctypes.c_int32), ("nx", ctypes.c_int32), ("ncoils", ctypes.c_int32), ("max_batch", ctypes.c_int32),
         ("max_iter_cap", ctypes.c_int32), ("nsamp", ctypes.c_int64), ("device_bytes", ctypes.c_uint64),
+        ("normal_op", ctypes.c_int32),
     ]
 
 

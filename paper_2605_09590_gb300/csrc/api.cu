@@ -67,6 +67,16 @@ struct pico_ctx {
   float2* cs_x0 = nullptr;     // the reconstruction f(b) [n]
   double cs_lam = 0;           // lambda_l1 of the reconstruction
   pico::Wavelet wav{};
+  // dense per-column normal operator on the tensor cores (Cartesian phase-encode
+  // masks): CG vectors in the column-planar layout, two direction buffers
+  bool gram = false;
+  pico::GramOp gop{};
+  CUtensorMap mR{}, mX{}, mP0{}, mP1{};
+  float* P2 = nullptr;
+  float* g_beta = nullptr;
+  int* g_done = nullptr;
+  int* g_err = nullptr;
+  double2* g_pbuf = nullptr;
   pico::CgArgs cg{};
   size_t device_bytes = 0, budget = 0;
   bool async_alloc = false;  // stream-ordered cudaMallocAsync / cudaFreeAsync (serving contexts)
@@ -209,8 +219,33 @@ void prof_collect(pico_ctx* c) {
   c->recs.clear();
 }
 
-// (A^H A + lam) x for nb images (class 0)
+float* cpf(float2* p) { return reinterpret_cast<float*>(p); }
+// Gram mode: the direction written by CG iteration `it` (two buffers alternate,
+// because the operator reads the previous direction while writing the new one)
+float* gram_pbuf(pico_ctx* c, int it) { return (it & 1) ? c->P2 : cpf(c->P); }
+const CUtensorMap& gram_pmap(pico_ctx* c, int it) { return (it & 1) ? c->mP1 : c->mP0; }
+pico::CgArgs gram_cg(pico_ctx* c, int it) {
+  pico::CgArgs a = c->cg;
+  a.P = reinterpret_cast<float2*>(gram_pbuf(c, it));
+  return a;
+}
+
+// (A^H A + lam) x for nb images (class 0).  Gram mode: x is one of the
+// context's column-planar buffers X or R.
 void op_apply(pico_ctx* c, const float2* x, float2* y, int nb, float lam) {
+  if (c->gram) {
+    const CUtensorMap& m = x == c->X ? c->mX : c->mR;
+    pico::GramArgs g{};
+    g.in = reinterpret_cast<const float*>(x);
+    g.q = cpf(y);
+    g.nb = nb;
+    g.lam = lam;
+    g.itmax = c->itmax;
+    g.err = c->g_err;
+    Launch L(c, 0);
+    pico::launch_gram_normal(c->gop, m, m, g, c->stream);
+    return;
+  }
   if (c->kind == PICO_CARTESIAN && !c->mask2d) {
     Launch L(c, 0);
     pico::launch_cart_apply(c->cop, x, y, nb, lam, c->stream);
@@ -222,6 +257,27 @@ void op_apply(pico_ctx* c, const float2* x, float2* y, int nb, float lam) {
 
 // CG iteration `it`, operator half (class 0)
 void op_cg_normal(pico_ctx* c, int nb, int it, float lam) {
+  if (c->gram) {
+    { Launch L(c, 1); pico::launch_gram_scalars(c->cg, nb, it, c->g_beta, c->g_done, c->stream); }
+    pico::GramArgs g{};
+    g.in = cpf(c->R);
+    g.pold = gram_pbuf(c, it + 1);
+    g.pnew = gram_pbuf(c, it);
+    g.q = cpf(c->Q);
+    g.beta = c->g_beta;
+    g.done = c->g_done;
+    g.pq = c->cg.pq_part;
+    g.itmax = c->itmax;
+    g.PA = c->cg.PA;
+    g.it = it;
+    g.nb = nb;
+    g.cg = 1;
+    g.lam = lam;
+    g.err = c->g_err;
+    Launch L(c, 0);
+    pico::launch_gram_normal(c->gop, c->mR, gram_pmap(c, it + 1), g, c->stream);
+    return;
+  }
   if (c->kind == PICO_CARTESIAN && !c->mask2d) {
     Launch L(c, 0);
     pico::launch_cart_cg_normal(c->cop, c->cg, nb, it, lam, c->stream);
@@ -239,7 +295,7 @@ void cg_iterations(pico_ctx* c, int nb, int max_iter, double rtol, float lam) {
   auto direct = [&]() {
     for (int it = 0; it < max_iter; ++it) {
       op_cg_normal(c, nb, it, lam);
-      { Launch L(c, 1); pico::launch_cg_update(c->cg, nb, it, c->stream); }
+      { Launch L(c, 1); pico::launch_cg_update(c->gram ? gram_cg(c, it) : c->cg, nb, it, c->stream); }
     }
   };
   if (c->profiling || !c->use_graphs || max_iter == 0) return direct();
@@ -283,7 +339,16 @@ pico_status run_cg(pico_ctx* c, int nb, int max_iter, double rtol, float lam) {
 pico_status run_cg_from_probe(pico_ctx* c, int nb, int max_iter, double rtol, float lam, uint64_t seed,
                               int64_t begin, int kind) {
   c->cg.rtol2 = rtol * rtol;
-  { Launch L(c, 1); pico::launch_cg_init_probe(c->cg, nb, seed, begin, kind, c->stream); }
+  if (c->gram) {
+    // probes drawn in the natural layout into Q, then rearranged into R
+    pico::CgArgs a = c->cg;
+    a.R = c->Q;
+    { Launch L(c, 1); pico::launch_cg_init_probe(a, nb, seed, begin, kind, c->stream); }
+    { Launch L(c, 1); pico::launch_to_cp(c->Q, cpf(c->R), c->ny, c->nx, nb, c->stream); }
+  } else {
+    Launch L(c, 1);
+    pico::launch_cg_init_probe(c->cg, nb, seed, begin, kind, c->stream);
+  }
   cg_iterations(c, nb, max_iter, rtol, lam);
   return cuda_check(c, "cg");
 }
@@ -555,6 +620,49 @@ void noise_adjoint(pico_ctx* c, float2* out, int nb, uint64_t seed, int64_t rep_
   }
 }
 
+// The dense Gram operator serves Cartesian phase-encode masks with ny a multiple
+// of 16 and at least 128 (smaller images stay on the column-FFT kernel, which is
+// latency-bound there anyway); PICO_NORMAL_OP=fft in the environment opts out.
+bool want_gram(const pico_operator_desc* d) {
+  if (d->kind != PICO_CARTESIAN || d->mask_2d) return false;
+  const char* e = std::getenv("PICO_NORMAL_OP");
+  if (e && std::string(e) == "fft") return false;
+  return d->ny >= 128 && pico::gram_supported(d->ny, d->nx);
+}
+
+// G planes, second direction buffer and per-image scalars of the Gram mode
+size_t gram_extra_bytes(const pico_operator_desc* d, int64_t B) {
+  return pico::gram_bytes(d->ny, d->nx) + (size_t)B * d->ny * d->nx * 8 + (size_t)B * 8 + (size_t)d->ny * 16 + 16;
+}
+
+pico_status gram_setup(pico_ctx* c, const pico_operator_desc* d) {
+  pico_status st = PICO_OK;
+  const size_t half = pico::gram_bytes(c->ny, c->nx) / 2 / sizeof(float);
+  if ((st = dalloc(c, &c->gop.Ghi, half)) != PICO_OK) return st;
+  if ((st = dalloc(c, &c->gop.Glo, half)) != PICO_OK) return st;
+  if ((st = dalloc(c, &c->P2, (size_t)2 * c->max_batch * c->n)) != PICO_OK) return st;
+  if ((st = dalloc(c, &c->g_beta, (size_t)c->max_batch)) != PICO_OK) return st;
+  if ((st = dalloc(c, &c->g_done, (size_t)c->max_batch)) != PICO_OK) return st;
+  if ((st = dalloc(c, &c->g_err, (size_t)4)) != PICO_OK) return st;
+  if ((st = dalloc(c, &c->g_pbuf, (size_t)c->ny)) != PICO_OK) return st;
+  cudaMemsetAsync(c->g_err, 0, 4 * sizeof(int), c->stream);
+  c->gop.ny = c->ny;
+  c->gop.nx = c->nx;
+  c->gop.nt = pico::gram_tile(c->ny);
+  pico::launch_gram_build(c->smaps, d->mask, c->nc, c->ny, c->nx, c->gop.Ghi, c->gop.Glo, c->g_pbuf, c->stream);
+  const int B = c->max_batch;
+  const bool ok = pico::gram_encode_g(&c->gop.mGhi, c->gop.Ghi, c->ny, c->nx) &&
+                  pico::gram_encode_g(&c->gop.mGlo, c->gop.Glo, c->ny, c->nx) &&
+                  pico::gram_encode_x(&c->mR, cpf(c->R), c->ny, c->nx, B) &&
+                  pico::gram_encode_x(&c->mX, cpf(c->X), c->ny, c->nx, B) &&
+                  pico::gram_encode_x(&c->mP0, cpf(c->P), c->ny, c->nx, B) &&
+                  pico::gram_encode_x(&c->mP1, c->P2, c->ny, c->nx, B);
+  if (!ok) return fail(c, PICO_E_CUDA, "tensor map encoding for the Gram operator failed");
+  if (cudaStreamSynchronize(c->stream) != cudaSuccess) return cuda_check(c, "Gram operator set-up");
+  c->gram = true;
+  return cuda_check(c, "Gram operator set-up");
+}
+
 pico_status wavelet_check(pico_ctx* c, int levels) {
   if (c->ny != c->nx || levels > 30 || (c->ny % (1 << levels)) != 0 || (c->ny >> levels) < 1)
     return fail(c, PICO_E_UNSUPPORTED, "the wavelet transform needs a square image divisible by 2^levels");
@@ -628,6 +736,10 @@ pico_status init_impl(const pico_operator_desc* d, void* cuda_stream, size_t hbm
       return fail(c, PICO_E_UNSUPPORTED, "ny has no FFT split in this build");
     PA = pico::cart_normal_tiles(c->nx);
     extra = (size_t)c->ny * 13 + (size_t)c->nx * 8;
+    if (want_gram(d)) {
+      PA = std::max(PA, pico::gram_pa(c->ny, c->nx));
+      extra += gram_extra_bytes(d, B);
+    }
   } else {
     if (c->ny != c->nx) return fail(c, PICO_E_UNSUPPORTED, "spiral images must be square");
     if (os != 2.0) return fail(c, PICO_E_UNSUPPORTED, "spiral gridding supports oversampling 2.0 only");
@@ -721,6 +833,8 @@ pico_status init_impl(const pico_operator_desc* d, void* cuda_stream, size_t hbm
     c->lambda_max = lmax;
     c->lam_phys = c->lam_rel * c->margin * lmax;
   }
+  // the dense Gram operator takes over the CG normal operator once lambda_max is known
+  if (!c->mask2d && c->kind == PICO_CARTESIAN && want_gram(d)) TRY(gram_setup(c, d));
   if (cudaStreamSynchronize(c->stream) != cudaSuccess) return cuda_check(c, "pico_init");
   if ((st = cuda_check(c, "pico_init")) != PICO_OK) return st;
 #undef TRY
@@ -739,6 +853,10 @@ size_t footprint_bytes(const pico_operator_desc* d, bool with_kbuf) {
     PA = cart_normal_tiles(d->nx);
     extra = (int64_t)d->ny * 13 + (int64_t)d->nx * 8;
     kbuf = B * nc * n * 8;
+    if (want_gram(d)) {
+      PA = std::max<int64_t>(PA, gram_pa(d->ny, d->nx));
+      extra += (int64_t)gram_extra_bytes(d, B);
+    }
   } else {
     const int64_t img = d->ny, L = 2 * img;
     PA = (img + 15) / 16;
@@ -771,17 +889,25 @@ pico_status pico_get_info(const pico_ctx* c, pico_info* info) {
   info->max_iter_cap = c->itmax;
   info->nsamp = c->nsamp;
   info->device_bytes = c->device_bytes;
+  info->normal_op = c->gram ? 1 : (c->kind == PICO_CARTESIAN && !c->mask2d) ? 0 : 2;
   return PICO_OK;
 }
 
 pico_status pico_apply_normal(pico_ctx* c, const void* x, void* y, int32_t nbatch) {
   if (!c || !c->smaps) return PICO_E_INVALID;
   if (nbatch < 0 || (nbatch > 0 && (!x || !y))) return fail(c, PICO_E_INVALID, "bad batch or pointer");
-  const int chunk = c->kind == PICO_CARTESIAN ? 65535 : c->max_batch;
+  const int chunk = c->kind == PICO_CARTESIAN && !c->gram ? 65535 : c->max_batch;
   for (int32_t b0 = 0; b0 < nbatch; b0 += chunk) {
     const int nb = std::min(chunk, nbatch - b0);
-    op_apply(c, static_cast<const float2*>(x) + (size_t)b0 * c->n, static_cast<float2*>(y) + (size_t)b0 * c->n, nb,
-             (float)c->lam_phys);
+    const float2* xi = static_cast<const float2*>(x) + (size_t)b0 * c->n;
+    float2* yo = static_cast<float2*>(y) + (size_t)b0 * c->n;
+    if (c->gram) {
+      { Launch L(c, 3); pico::launch_to_cp(xi, cpf(c->R), c->ny, c->nx, nb, c->stream); }
+      op_apply(c, c->R, c->Q, nb, (float)c->lam_phys);
+      { Launch L(c, 3); pico::launch_from_cp(cpf(c->Q), yo, c->ny, c->nx, nb, c->stream); }
+    } else {
+      op_apply(c, xi, yo, nb, (float)c->lam_phys);
+    }
   }
   return cuda_check(c, "pico_apply_normal");
 }
@@ -795,11 +921,21 @@ pico_status pico_cg_batch(pico_ctx* c, const void* rhs, void* x, int32_t nbatch,
   const size_t bytes_img = (size_t)c->n * sizeof(float2);
   for (int32_t b0 = 0; b0 < nbatch; b0 += c->max_batch) {
     const int nb = std::min(c->max_batch, nbatch - b0);
-    cudaMemcpyAsync(c->R, static_cast<const char*>(rhs) + (size_t)b0 * bytes_img, (size_t)nb * bytes_img,
-                    cudaMemcpyDeviceToDevice, c->stream);
+    const float2* rb = reinterpret_cast<const float2*>(static_cast<const char*>(rhs) + (size_t)b0 * bytes_img);
+    float2* xb = reinterpret_cast<float2*>(static_cast<char*>(x) + (size_t)b0 * bytes_img);
+    if (c->gram) {
+      Launch L(c, 3);
+      pico::launch_to_cp(rb, cpf(c->R), c->ny, c->nx, nb, c->stream);
+    } else {
+      cudaMemcpyAsync(c->R, rb, (size_t)nb * bytes_img, cudaMemcpyDeviceToDevice, c->stream);
+    }
     if ((st = run_cg(c, nb, max_iter, rtol, (float)c->lam_phys)) != PICO_OK) return st;
-    cudaMemcpyAsync(static_cast<char*>(x) + (size_t)b0 * bytes_img, c->X, (size_t)nb * bytes_img,
-                    cudaMemcpyDeviceToDevice, c->stream);
+    if (c->gram) {
+      Launch L(c, 3);
+      pico::launch_from_cp(cpf(c->X), xb, c->ny, c->nx, nb, c->stream);
+    } else {
+      cudaMemcpyAsync(xb, c->X, (size_t)nb * bytes_img, cudaMemcpyDeviceToDevice, c->stream);
+    }
     if (iters_out || relres_out) {
       { Launch L(c, 3); pico::launch_cg_report(c->cg, nb, max_iter, c->d_iters, c->d_relres, c->stream); }
       std::vector<int> it(nb);
@@ -836,7 +972,12 @@ pico_status pico_variance_map(pico_ctx* c, uint64_t seed, int64_t probe_begin, i
       op_apply(c, c->X, c->R, nb, 0.f);
       if ((st = run_cg(c, nb, max_iter, rtol, lam)) != PICO_OK) return st;
     }
-    { Launch L(c, 3); pico::launch_accum_pico(c->X, c->n, nb, seed, probe_begin + b0, kind, sum, sumsq, c->stream); }
+    const float2* xs = c->X;
+    if (c->gram) {  // back to the natural layout for the probe-indexed accumulation
+      { Launch L(c, 3); pico::launch_from_cp(cpf(c->X), c->Q, c->ny, c->nx, nb, c->stream); }
+      xs = c->Q;
+    }
+    { Launch L(c, 3); pico::launch_accum_pico(xs, c->n, nb, seed, probe_begin + b0, kind, sum, sumsq, c->stream); }
   }
   return cuda_check(c, "pico_variance_map");
 }
@@ -896,9 +1037,19 @@ pico_status pico_pmr(pico_ctx* c, uint64_t seed, int64_t rep_begin, int32_t nrep
   const float lam = (float)c->lam_phys;
   for (int32_t b0 = 0; b0 < nreps; b0 += c->max_batch) {
     const int nb = std::min(c->max_batch, nreps - b0);
-    noise_adjoint(c, c->R, nb, seed, rep_begin + b0, sigma);
+    if (c->gram) {
+      noise_adjoint(c, c->Q, nb, seed, rep_begin + b0, sigma);
+      { Launch L(c, 2); pico::launch_to_cp(c->Q, cpf(c->R), c->ny, c->nx, nb, c->stream); }
+    } else {
+      noise_adjoint(c, c->R, nb, seed, rep_begin + b0, sigma);
+    }
     if ((st = run_cg(c, nb, max_iter, rtol, lam)) != PICO_OK) return st;
-    { Launch L(c, 3); pico::launch_accum_pmr(c->X, c->n, nb, (float)(1.0 / (sigma * sigma)), sum, sumsq, c->stream); }
+    const float2* xs = c->X;
+    if (c->gram) {
+      { Launch L(c, 3); pico::launch_from_cp(cpf(c->X), c->Q, c->ny, c->nx, nb, c->stream); }
+      xs = c->Q;
+    }
+    { Launch L(c, 3); pico::launch_accum_pmr(xs, c->n, nb, (float)(1.0 / (sigma * sigma)), sum, sumsq, c->stream); }
   }
   return cuda_check(c, "pico_pmr");
 }
@@ -1116,6 +1267,14 @@ pico_status pico_gfactor(pico_ctx* c, const float* va, const float* vr, double R
 pico_status pico_sync(pico_ctx* c) {
   if (!c) return PICO_E_INVALID;
   if (cudaStreamSynchronize(c->stream) != cudaSuccess) return cuda_check(c, "pico_sync");
+  if (c->g_err) {
+    int e = 0;
+    if (cudaMemcpy(&e, c->g_err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return cuda_check(c, "pico_sync");
+    if (e) {
+      cudaMemset(c->g_err, 0, sizeof(int));
+      return fail(c, PICO_E_TIMEOUT, "Gram operator pipeline wait timed out (stage " + std::to_string(e) + ")");
+    }
+  }
   if (c->status) {
     std::vector<int> s(c->max_batch);
     if (cudaMemcpy(s.data(), c->status, s.size() * sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)

@@ -1,0 +1,486 @@
+// Dense per-column SENSE normal operator on the tensor cores (Cartesian
+// phase-encode masks).
+//
+// With a mask on the phase-encode axis only, A^H A acts on every readout
+// column j independently (the x-FFT cancels, Sec. 2.1.3 with M = M_y (x) I):
+//   (A^H A p)[y, j] = sum_y' G_j[y, y'] p[y', j],
+//   G_j[y, y'] = P[y - y'] sum_c conj(S_c[y, j]) S_c[y', j],
+//   P[d] = (1/ny) sum_k m_k exp(2 pi i k d / ny)   (F_y^H M_y F_y, a circulant).
+// G_j is Hermitian, ny x ny, and the same for every probe, so one normal
+// operator over a batch of K images is nx dense complex products
+// Q_j (K x ny) = P_j (K x ny) G_j^T -- a contraction with reuse K that runs
+// on tcgen05 tensor cores.  FP32 accuracy comes from the 3-term TF32 split
+// a b ~ a_hi b_hi + a_hi b_lo + a_lo b_hi (G split once at set-up, the
+// direction p split on the fly), accumulated in FP32 in tensor memory.
+//
+// CG vectors of a Gram-mode context live in a column-planar layout
+// [image][x][re|im][y] (so that the contraction index y is contiguous); the
+// kernels here convert to and from the natural [image][y][x] complex layout.
+#include <vector>
+
+#include "common.cuh"
+#include "kernels.cuh"
+#include "tc_util.cuh"
+
+namespace pico {
+
+namespace {
+
+using namespace tc;
+
+constexpr int kGramRows = 128;   // images per CTA (MMA M)
+constexpr int kGramKC = 16;      // contraction chunk (64 B rows, 64-byte swizzle)
+constexpr int kGramThreads = 192;
+constexpr uint32_t kATile = kGramRows * kGramKC * 4;  // 8 KB
+
+__device__ __forceinline__ void set_err(int* err, int code) {
+  if (err) atomicCAS(err, 0, code);
+}
+
+// ---------------------------------------------------------------------------
+// set-up: G_j split into TF32 head and remainder, layout [j][re|im][y][y']
+// ---------------------------------------------------------------------------
+__global__ void k_gram_build(const float2* __restrict__ S, const double2* __restrict__ P, int nc, int ny, int nx,
+                             float* __restrict__ Ghi, float* __restrict__ Glo) {
+  const int j = blockIdx.y;
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (int64_t)ny * ny) return;
+  const int y = (int)(t / ny), yp = (int)(t % ny);
+  const int64_t n = (int64_t)ny * nx;
+  double re = 0.0, im = 0.0;
+  for (int c = 0; c < nc; ++c) {
+    const float2 a = S[c * n + (int64_t)y * nx + j], b = S[c * n + (int64_t)yp * nx + j];
+    // conj(a) b
+    re += (double)a.x * b.x + (double)a.y * b.y;
+    im += (double)a.x * b.y - (double)a.y * b.x;
+  }
+  int d = y - yp;
+  if (d < 0) d += ny;
+  const double2 p = P[d];
+  const double gr = p.x * re - p.y * im, gi = p.x * im + p.y * re;
+  const size_t plane = (size_t)ny * ny;
+  const size_t o = (size_t)j * 2 * plane + (size_t)y * ny + yp;
+  float hr, lr, hi_, li;
+  split_tf32((float)gr, hr, lr);
+  split_tf32((float)gi, hi_, li);
+  Ghi[o] = hr;
+  Ghi[o + plane] = hi_;
+  Glo[o] = (float)(gr - (double)hr);
+  Glo[o + plane] = (float)(gi - (double)hi_);
+}
+
+// per-image CG scalars of iteration it: beta = rr(it) / rr(it-1) (0 at it = 0), done flag
+__global__ void k_gram_scalars(CgArgs a, int it, float* beta, int* done) {
+  const int b = blockIdx.x;
+  const double* base = a.rr_part + (size_t)b * (a.itmax + 1) * a.PB;
+  const double rr = warp_sum_parts(base + (size_t)it * a.PB, a.PB);
+  const double rr0 = warp_sum_parts(base, a.PB);
+  const double rrp = it > 0 ? warp_sum_parts(base + (size_t)(it - 1) * a.PB, a.PB) : 1.0;
+  if (threadIdx.x == 0) {
+    done[b] = !(rr > a.rtol2 * rr0);
+    beta[b] = it > 0 ? (float)(rr / rrp) : 0.f;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// layout conversion: natural [b][y][x] complex <-> column-planar [b][x][re|im][y]
+// ---------------------------------------------------------------------------
+__global__ void k_to_cp(const float2* __restrict__ in, float* __restrict__ out, int ny, int nx) {
+  __shared__ float2 tile[32][33];
+  const int b = blockIdx.z, x0 = blockIdx.x * 32, y0 = blockIdx.y * 32;
+  const int64_t n = (int64_t)ny * nx;
+  const float2* src = in + (size_t)b * n;
+  for (int r = threadIdx.y; r < 32; r += 8) {
+    const int y = y0 + r, x = x0 + threadIdx.x;
+    if (y < ny && x < nx) tile[r][threadIdx.x] = src[(int64_t)y * nx + x];
+  }
+  __syncthreads();
+  float* dst = out + (size_t)b * 2 * n;
+  for (int r = threadIdx.y; r < 32; r += 8) {
+    const int x = x0 + r, y = y0 + threadIdx.x;
+    if (y < ny && x < nx) {
+      const float2 v = tile[threadIdx.x][r];
+      dst[(int64_t)x * 2 * ny + y] = v.x;
+      dst[(int64_t)x * 2 * ny + ny + y] = v.y;
+    }
+  }
+}
+
+__global__ void k_from_cp(const float* __restrict__ in, float2* __restrict__ out, int ny, int nx) {
+  __shared__ float2 tile[32][33];
+  const int b = blockIdx.z, x0 = blockIdx.x * 32, y0 = blockIdx.y * 32;
+  const int64_t n = (int64_t)ny * nx;
+  const float* src = in + (size_t)b * 2 * n;
+  for (int r = threadIdx.y; r < 32; r += 8) {
+    const int x = x0 + r, y = y0 + threadIdx.x;
+    if (y < ny && x < nx)
+      tile[threadIdx.x][r] = make_float2(src[(int64_t)x * 2 * ny + y], src[(int64_t)x * 2 * ny + ny + y]);
+  }
+  __syncthreads();
+  float2* dst = out + (size_t)b * n;
+  for (int r = threadIdx.y; r < 32; r += 8) {
+    const int y = y0 + r, x = x0 + threadIdx.x;
+    if (y < ny && x < nx) dst[(int64_t)y * nx + x] = tile[r][threadIdx.x];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// the tensor-core normal operator
+// ---------------------------------------------------------------------------
+// CTA (y tile, image tile, column j).  Warp 0: TMA producer.  Warp 1: TMEM
+// owner and MMA issuer.  Warps 2-5: split the direction into TF32 head and
+// remainder in shared memory during the main loop, then run the epilogue
+// (tensor memory -> q = G p + lam p, the new direction p, the p^H q partial).
+// Pipeline per contraction chunk (16 values of y'): stage s holds
+//   A: [r_re | r_im | pold_re | pold_im] 128 x 16 fp32 each, rewritten in place
+//      as [p_re hi | p_im hi | p_re lo | p_im lo]
+//   B: [G_re hi | G_im hi | G_re lo | G_im lo] NT x 16 fp32 each
+// and D_re (columns 0..NT-1), D_im (NT..2NT-1) accumulate in tensor memory:
+//   D_re += p_re G_re^T - p_im G_im^T,  D_im += p_re G_im^T + p_im G_re^T.
+__global__ void __launch_bounds__(kGramThreads, 1)
+    k_gram_normal(const __grid_constant__ CUtensorMap mIn, const __grid_constant__ CUtensorMap mPold,
+                  const __grid_constant__ CUtensorMap mGhi, const __grid_constant__ CUtensorMap mGlo, GramArgs g) {
+  extern __shared__ uint8_t smraw[];
+  uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smraw) + 1023) & ~(uintptr_t)1023);
+  const int NT = g.nt, S = g.stages;
+  const uint32_t btile = (uint32_t)NT * kGramKC * 4;
+  const uint32_t stage_bytes = 4 * kATile + 4 * btile;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sm + (size_t)S * stage_bytes);
+  uint64_t* full = bars;
+  uint64_t* conv = bars + S;
+  uint64_t* empty = bars + 2 * S;
+  uint64_t* accf = bars + 3 * S;
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + 3 * S + 1);
+  float* beta_s = reinterpret_cast<float*>(tslot + 4);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int ytile = blockIdx.x % g.nyt, itile = blockIdx.x / g.nyt, j = blockIdx.y;
+  const int n0 = ytile * NT, m0 = itile * kGramRows;
+  const int nkc = g.ny / kGramKC;
+  const bool use_pold = g.cg && g.it > 0;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < S; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&conv[s], 128);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(accf, 1);
+    fence_mbar_init();
+  }
+  if (warp >= 2) {
+    const int r = threadIdx.x - 64;
+    const int k = m0 + r;
+    beta_s[r] = (use_pold && k < g.nb) ? g.beta[k] : 0.f;
+  }
+  if (warp == 1) tmem_alloc(tslot, g.tmem_cols);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tbase = *tslot;
+
+  auto slotA = [&](int s, int q) { return sm + (size_t)s * stage_bytes + (size_t)q * kATile; };
+  auto slotB = [&](int s, int q) { return sm + (size_t)s * stage_bytes + 4 * kATile + (size_t)q * btile; };
+
+  if (warp == 0) {
+    if (lane == 0) {
+      tma_prefetch_desc(&mIn);
+      tma_prefetch_desc(&mGhi);
+      tma_prefetch_desc(&mGlo);
+      if (use_pold) tma_prefetch_desc(&mPold);
+      const uint32_t bytes = (use_pold ? 4u : 2u) * kATile + 4u * btile;
+      bool ok = true;
+      for (int kc = 0; kc < nkc && ok; ++kc) {
+        const int s = kc % S;
+        if (kc >= S && !mbar_wait(&empty[s], ((kc / S) - 1) & 1)) {
+          set_err(g.err, 1);
+          ok = false;
+          break;
+        }
+        mbar_expect_tx(&full[s], bytes);
+        const int y0 = kc * kGramKC;
+        tma_load_4d(slotA(s, 0), &mIn, &full[s], y0, 0, j, m0);
+        tma_load_4d(slotA(s, 1), &mIn, &full[s], y0, 1, j, m0);
+        if (use_pold) {
+          tma_load_4d(slotA(s, 2), &mPold, &full[s], y0, 0, j, m0);
+          tma_load_4d(slotA(s, 3), &mPold, &full[s], y0, 1, j, m0);
+        }
+        tma_load_4d(slotB(s, 0), &mGhi, &full[s], y0, n0, 0, j);
+        tma_load_4d(slotB(s, 1), &mGhi, &full[s], y0, n0, 1, j);
+        tma_load_4d(slotB(s, 2), &mGlo, &full[s], y0, n0, 0, j);
+        tma_load_4d(slotB(s, 3), &mGlo, &full[s], y0, n0, 1, j);
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      const uint32_t id = idesc_tf32(kGramRows, NT, false), idn = idesc_tf32(kGramRows, NT, true);
+      const uint32_t dre = tbase, dim = tbase + (uint32_t)NT;
+      for (int kc = 0; kc < nkc; ++kc) {
+        const int s = kc % S;
+        if (!mbar_wait(&conv[s], (kc / S) & 1)) {
+          set_err(g.err, 2);
+          break;
+        }
+        tc_fence_after();
+        const uint32_t ahr = smem_u32(slotA(s, 0)), ahi = smem_u32(slotA(s, 1));
+        const uint32_t alr = smem_u32(slotA(s, 2)), ali = smem_u32(slotA(s, 3));
+        const uint32_t bhr = smem_u32(slotB(s, 0)), bhi = smem_u32(slotB(s, 1));
+        const uint32_t blr = smem_u32(slotB(s, 2)), bli = smem_u32(slotB(s, 3));
+#pragma unroll
+        for (int kk = 0; kk < kGramKC / 8; ++kk) {
+          const uint32_t o = 32u * kk;
+          const uint32_t acc0 = (kc == 0 && kk == 0) ? 0u : 1u;
+          const uint64_t Ahr = desc_k_sw64(ahr + o), Ahi = desc_k_sw64(ahi + o);
+          const uint64_t Alr = desc_k_sw64(alr + o), Ali = desc_k_sw64(ali + o);
+          const uint64_t Bhr = desc_k_sw64(bhr + o), Bhi = desc_k_sw64(bhi + o);
+          const uint64_t Blr = desc_k_sw64(blr + o), Bli = desc_k_sw64(bli + o);
+          // D_re += p_re G_re^T - p_im G_im^T
+          mma_tf32(dre, Ahr, Bhr, id, acc0);
+          mma_tf32(dre, Ahr, Blr, id, 1);
+          mma_tf32(dre, Alr, Bhr, id, 1);
+          mma_tf32(dre, Ahi, Bhi, idn, 1);
+          mma_tf32(dre, Ahi, Bli, idn, 1);
+          mma_tf32(dre, Ali, Bhi, idn, 1);
+          // D_im += p_re G_im^T + p_im G_re^T
+          mma_tf32(dim, Ahr, Bhi, id, acc0);
+          mma_tf32(dim, Ahr, Bli, id, 1);
+          mma_tf32(dim, Alr, Bhi, id, 1);
+          mma_tf32(dim, Ahi, Bhr, id, 1);
+          mma_tf32(dim, Ahi, Blr, id, 1);
+          mma_tf32(dim, Ali, Bhr, id, 1);
+        }
+        mma_commit(&empty[s]);
+      }
+      mma_commit(accf);
+    }
+  } else {
+    // ---- split p = r + beta p_old into TF32 head / remainder, in place ----
+    const int e = threadIdx.x - 64;  // 0..127
+    bool ok = true;
+    for (int kc = 0; kc < nkc; ++kc) {
+      const int s = kc % S;
+      if (ok && !mbar_wait(&full[s], (kc / S) & 1)) {
+        set_err(g.err, 3);
+        ok = false;
+      }
+      if (ok) {
+        float4* r_re = reinterpret_cast<float4*>(slotA(s, 0));
+        float4* r_im = reinterpret_cast<float4*>(slotA(s, 1));
+        float4* p_re = reinterpret_cast<float4*>(slotA(s, 2));
+        float4* p_im = reinterpret_cast<float4*>(slotA(s, 3));
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const int q = e + 128 * i;  // float4 index in the 128 x 16 tile; row = q / 4
+          const float b = beta_s[q >> 2];
+          float4 vr = r_re[q], vi = r_im[q];
+          if (use_pold) {
+            const float4 wr = p_re[q], wi = p_im[q];
+            vr.x = fmaf(b, wr.x, vr.x); vr.y = fmaf(b, wr.y, vr.y);
+            vr.z = fmaf(b, wr.z, vr.z); vr.w = fmaf(b, wr.w, vr.w);
+            vi.x = fmaf(b, wi.x, vi.x); vi.y = fmaf(b, wi.y, vi.y);
+            vi.z = fmaf(b, wi.z, vi.z); vi.w = fmaf(b, wi.w, vi.w);
+          }
+          float4 hr, lr, hi4, li;
+          split_tf32(vr.x, hr.x, lr.x); split_tf32(vr.y, hr.y, lr.y);
+          split_tf32(vr.z, hr.z, lr.z); split_tf32(vr.w, hr.w, lr.w);
+          split_tf32(vi.x, hi4.x, li.x); split_tf32(vi.y, hi4.y, li.y);
+          split_tf32(vi.z, hi4.z, li.z); split_tf32(vi.w, hi4.w, li.w);
+          r_re[q] = hr;
+          r_im[q] = hi4;
+          p_re[q] = lr;
+          p_im[q] = li;
+        }
+      }
+      fence_proxy_async_smem();
+      mbar_arrive(&conv[s]);
+    }
+
+    // ---- epilogue ----
+    const int quarter = warp & 3;          // TMEM lanes 32*quarter .. +31
+    const int row = 32 * quarter + lane;
+    const int k = m0 + row;
+    const bool accok = mbar_wait(accf, 0);
+    if (!accok) set_err(g.err, 4);
+    tc_fence_after();
+    const bool valid = accok && k < g.nb && !(g.cg && g.done[k]);
+    const int64_t img = (int64_t)2 * g.ny * g.nx;
+    const size_t col = (size_t)k * img + (size_t)j * 2 * g.ny;
+    const float bk = beta_s[row];
+    double pq = 0.0;
+    __syncwarp();
+    for (int c = 0; c < NT / 16; ++c) {   // NT is a multiple of 16
+      float dr[16], di[16];
+      const uint32_t ta = tbase + ((uint32_t)(32 * quarter) << 16) + 16u * c;
+      tmem_ld16(ta, dr);
+      tmem_ld16(ta + (uint32_t)NT, di);
+      if (valid) {
+        const int y0 = n0 + 16 * c;
+        const float4* inr = reinterpret_cast<const float4*>(g.in + col + y0);
+        const float4* ini = reinterpret_cast<const float4*>(g.in + col + g.ny + y0);
+        const float4* por = use_pold ? reinterpret_cast<const float4*>(g.pold + col + y0) : nullptr;
+        const float4* poi = use_pold ? reinterpret_cast<const float4*>(g.pold + col + g.ny + y0) : nullptr;
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+          float4 pr = inr[v], pi = ini[v];
+          if (use_pold) {
+            const float4 wr = por[v], wi = poi[v];
+            pr.x = fmaf(bk, wr.x, pr.x); pr.y = fmaf(bk, wr.y, pr.y);
+            pr.z = fmaf(bk, wr.z, pr.z); pr.w = fmaf(bk, wr.w, pr.w);
+            pi.x = fmaf(bk, wi.x, pi.x); pi.y = fmaf(bk, wi.y, pi.y);
+            pi.z = fmaf(bk, wi.z, pi.z); pi.w = fmaf(bk, wi.w, pi.w);
+          }
+          float4 qr, qi;
+          qr.x = fmaf(g.lam, pr.x, dr[4 * v + 0]); qr.y = fmaf(g.lam, pr.y, dr[4 * v + 1]);
+          qr.z = fmaf(g.lam, pr.z, dr[4 * v + 2]); qr.w = fmaf(g.lam, pr.w, dr[4 * v + 3]);
+          qi.x = fmaf(g.lam, pi.x, di[4 * v + 0]); qi.y = fmaf(g.lam, pi.y, di[4 * v + 1]);
+          qi.z = fmaf(g.lam, pi.z, di[4 * v + 2]); qi.w = fmaf(g.lam, pi.w, di[4 * v + 3]);
+          reinterpret_cast<float4*>(g.q + col + y0)[v] = qr;
+          reinterpret_cast<float4*>(g.q + col + g.ny + y0)[v] = qi;
+          if (g.pnew) {
+            reinterpret_cast<float4*>(g.pnew + col + y0)[v] = pr;
+            reinterpret_cast<float4*>(g.pnew + col + g.ny + y0)[v] = pi;
+          }
+          float acc = 0.f;
+          acc = fmaf(pr.x, qr.x, acc); acc = fmaf(pr.y, qr.y, acc);
+          acc = fmaf(pr.z, qr.z, acc); acc = fmaf(pr.w, qr.w, acc);
+          acc = fmaf(pi.x, qi.x, acc); acc = fmaf(pi.y, qi.y, acc);
+          acc = fmaf(pi.z, qi.z, acc); acc = fmaf(pi.w, qi.w, acc);
+          pq += (double)acc;
+        }
+      }
+    }
+    if (valid && g.pq) g.pq[((size_t)k * g.itmax + g.it) * g.PA + (size_t)j * g.nyt + ytile] = pq;
+  }
+
+  // teardown: every TMA issued has been consumed by the split warps (or they
+  // timed out); the accumulator barrier orders the MMAs before the free
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    __syncwarp();
+    tc_fence_after();
+    tmem_dealloc(tbase, g.tmem_cols);
+  }
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      p = nullptr;
+    return reinterpret_cast<EncodeTiledFn>(p);
+  }();
+  return fn;
+}
+
+}  // namespace
+
+bool gram_supported(int ny, int nx) {
+  if (ny < 32 || ny % kGramKC != 0 || ny > 1024 || nx < 1) return false;
+  return gram_tile(ny) > 0;
+}
+
+int gram_tile(int ny) {
+  if (ny % 16) return 0;
+  if (ny <= 256) return ny;
+  for (int t = 256; t >= 16; t -= 16)
+    if (ny % t == 0) return t;
+  return 0;
+}
+
+size_t gram_bytes(int ny, int nx) { return (size_t)2 * nx * 2 * ny * ny * sizeof(float); }
+
+int gram_pa(int ny, int nx) { return nx * (ny / gram_tile(ny)); }
+
+bool gram_encode_x(CUtensorMap* m, float* base, int ny, int nx, int B) {
+  EncodeTiledFn enc = encode_fn();
+  if (!enc) return false;
+  cuuint64_t dims[4] = {(cuuint64_t)ny, 2, (cuuint64_t)nx, (cuuint64_t)B};
+  cuuint64_t strides[3] = {(cuuint64_t)ny * 4, (cuuint64_t)2 * ny * 4, (cuuint64_t)2 * ny * nx * 4};
+  cuuint32_t box[4] = {kGramKC, 1, 1, kGramRows}, es[4] = {1, 1, 1, 1};
+  return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, base, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+             CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+bool gram_encode_g(CUtensorMap* m, float* base, int ny, int nx) {
+  EncodeTiledFn enc = encode_fn();
+  if (!enc) return false;
+  const int nt = gram_tile(ny);
+  cuuint64_t dims[4] = {(cuuint64_t)ny, (cuuint64_t)ny, 2, (cuuint64_t)nx};
+  cuuint64_t strides[3] = {(cuuint64_t)ny * 4, (cuuint64_t)ny * ny * 4, (cuuint64_t)2 * ny * ny * 4};
+  cuuint32_t box[4] = {kGramKC, (cuuint32_t)nt, 1, 1}, es[4] = {1, 1, 1, 1};
+  return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, base, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+             CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+void launch_gram_build(const float2* smaps, const uint8_t* mask_host, int nc, int ny, int nx, float* Ghi, float* Glo,
+                       double2* pbuf, cudaStream_t s) {
+  // P[d] = (1/ny) sum_k m_k exp(2 pi i k d / ny), in FP64 on the host
+  std::vector<double2> P(ny);
+  const double pi2 = 6.283185307179586476925286766559;
+  for (int d = 0; d < ny; ++d) {
+    double re = 0.0, im = 0.0;
+    for (int k = 0; k < ny; ++k)
+      if (mask_host[k]) {
+        const int e = (int)(((int64_t)k * d) % ny);
+        re += std::cos(pi2 * e / ny);
+        im += std::sin(pi2 * e / ny);
+      }
+    P[d] = make_double2(re / ny, im / ny);
+  }
+  cudaMemcpyAsync(pbuf, P.data(), ny * sizeof(double2), cudaMemcpyHostToDevice, s);
+  const int64_t tot = (int64_t)ny * ny;
+  k_gram_build<<<dim3((unsigned)((tot + 255) / 256), nx), 256, 0, s>>>(smaps, pbuf, nc, ny, nx, Ghi, Glo);
+  cudaStreamSynchronize(s);  // P lives on the host stack until the copy has run
+}
+
+void launch_gram_scalars(const CgArgs& a, int nb, int it, float* beta, int* done, cudaStream_t s) {
+  k_gram_scalars<<<nb, 32, 0, s>>>(a, it, beta, done);
+}
+
+size_t gram_smem(int ny, int* stages) {
+  const int nt = gram_tile(ny);
+  const size_t stage = 4 * (size_t)kATile + 4 * (size_t)nt * kGramKC * 4;
+  int S = (int)((220 * 1024 - 2048) / stage);
+  if (S > 4) S = 4;
+  if (S < 2) S = 2;
+  *stages = S;
+  return 1024 + (size_t)S * stage + (3 * (size_t)S + 1) * 8 + 16 + kGramRows * 4 + 64;
+}
+
+void launch_gram_normal(const GramOp& op, const CUtensorMap& mIn, const CUtensorMap& mPold, GramArgs g,
+                        cudaStream_t s) {
+  int S = 0;
+  const size_t smem = gram_smem(op.ny, &S);
+  static thread_local size_t configured = 0;
+  if (configured < smem) {
+    cudaFuncSetAttribute(k_gram_normal, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    configured = smem;
+  }
+  g.ny = op.ny;
+  g.nx = op.nx;
+  g.nt = op.nt;
+  g.nyt = op.ny / op.nt;
+  g.stages = S;
+  g.tmem_cols = 32;
+  while (g.tmem_cols < 2 * op.nt) g.tmem_cols *= 2;
+  const unsigned itiles = (unsigned)((g.nb + kGramRows - 1) / kGramRows);
+  k_gram_normal<<<dim3((unsigned)g.nyt * itiles, op.nx), kGramThreads, smem, s>>>(mIn, mPold, op.mGhi, op.mGlo, g);
+}
+
+void launch_to_cp(const float2* in, float* out, int ny, int nx, int nb, cudaStream_t s) {
+  k_to_cp<<<dim3((nx + 31) / 32, (ny + 31) / 32, nb), dim3(32, 8), 0, s>>>(in, out, ny, nx);
+}
+void launch_from_cp(const float* in, float2* out, int ny, int nx, int nb, cudaStream_t s) {
+  k_from_cp<<<dim3((nx + 31) / 32, (ny + 31) / 32, nb), dim3(32, 8), 0, s>>>(in, out, ny, nx);
+}
+
+}  // namespace pico

@@ -1,6 +1,7 @@
 // Kernel launch interface shared by the C-ABI layer (api.cu) and the kernel
 // translation units.  Host-side only declarations; no torch types anywhere.
 #pragma once
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -76,6 +77,41 @@ void launch_cart_pmr_cols(const CartOp& op, float2* G, int nb, uint64_t seed, in
                           cudaStream_t s, const float2* data = nullptr);
 // out[b] = sum_c conj(S_c) . F^H_x G[b][c]
 void launch_cart_rows_adjoint(const CartOp& op, const float2* G, float2* out, int nb, cudaStream_t s);
+
+// ---- gram.cu: dense per-column normal operator on the tensor cores ----
+struct GramOp {
+  int ny, nx, nt;           // nt: output rows per CTA (divides ny, <= 256)
+  float* Ghi;               // [nx][2][ny][ny] TF32 head of G_j (re, im planes)
+  float* Glo;               // remainder
+  CUtensorMap mGhi, mGlo;
+};
+struct GramArgs {
+  const float* in;          // r (CG) or x (apply), column-planar [B][nx][2][ny]
+  const float* pold;        // previous direction (CG, it > 0)
+  float* pnew;              // new direction (CG) or nullptr
+  float* q;                 // (A^H A + lam) p
+  const float* beta;        // [B] (CG)
+  const int* done;          // [B] (CG)
+  double* pq;               // pq partials [B][itmax][PA] or nullptr
+  int itmax, PA, it, nb, cg;
+  float lam;
+  int* err;                 // first failure code (bounded waits)
+  // filled by the launcher
+  int ny, nx, nt, nyt, stages, tmem_cols;
+};
+bool gram_supported(int ny, int nx);
+int gram_tile(int ny);
+size_t gram_bytes(int ny, int nx);  // both G planes, head and remainder
+int gram_pa(int ny, int nx);
+bool gram_encode_x(CUtensorMap* m, float* base, int ny, int nx, int B);
+bool gram_encode_g(CUtensorMap* m, float* base, int ny, int nx);
+void launch_gram_build(const float2* smaps, const uint8_t* mask_host, int nc, int ny, int nx, float* Ghi, float* Glo,
+                       double2* pbuf, cudaStream_t s);
+void launch_gram_scalars(const CgArgs& a, int nb, int it, float* beta, int* done, cudaStream_t s);
+void launch_gram_normal(const GramOp& op, const CUtensorMap& mIn, const CUtensorMap& mPold, GramArgs g,
+                        cudaStream_t s);
+void launch_to_cp(const float2* in, float* out, int ny, int nx, int nb, cudaStream_t s);
+void launch_from_cp(const float* in, float2* out, int ny, int nx, int nb, cudaStream_t s);
 
 // ---- spiral.cu: non-Cartesian (Toeplitz normal operator, KB gridding) ----
 struct SpiralOp {

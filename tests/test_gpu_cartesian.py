@@ -31,6 +31,13 @@ def _built():
     pico.load_library()
 
 
+@pytest.fixture(autouse=True)
+def _column_fft_path(monkeypatch):
+    # this module covers the column-FFT normal operator; the tensor-core Gram
+    # operator (the default for ny >= 128) has its own module
+    monkeypatch.setenv("PICO_NORMAL_OP", "fft")
+
+
 def case(ny, nx, nc, R=2, acs=0, corr=False, seed=0):
     S = synth.coil_maps(ny, nx, nc, seed)
     cov = synth.noise_cov(nc, seed) if corr else None

@@ -1,0 +1,224 @@
+"""GPU parity of the tensor-core (dense per-column Gram) Cartesian normal operator.
+
+Cartesian contexts with a phase-encode mask and ny a multiple of 16, ny >= 128,
+apply A^H A inside CG as nx dense ny x ny products on the tcgen05 tensor cores
+with a 3-term TF32 split.  These tests compare that path with the FP64 oracle
+(operator, CG, PICO, PMR), with the column-FFT path of the same library
+(PICO_NORMAL_OP=fft), and check its determinism across batch sizes.
+
+Tolerances: one operator application agrees with the oracle to 1e-5 relative
+in norm (the split keeps about 21 mantissa bits per product; the tensor-memory
+FP32 accumulation over 6 ny products dominates, about 6e-6 at ny = 384);
+after 30 CG iterations the same 1e-4 bounds as the FFT path.
+"""
+import os
+
+import numpy as np
+import pytest
+
+import synth
+from oracle import ops as O
+from oracle import pico as OP
+from oracle import rng as ORNG
+from oracle import solvers as OS
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import paper_2605_09590_gb300 as pico  # noqa: E402
+from paper_2605_09590_gb300 import build as pico_build  # noqa: E402
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA device")
+    pico_build.build()
+    pico.load_library()
+
+
+def case(ny, nx, nc, R=2, acs=8, corr=True, seed=0):
+    S = synth.coil_maps(ny, nx, nc, seed)
+    cov = synth.noise_cov(nc, seed) if corr else None
+    return S, cov, synth.mask_pe(ny, R, acs)
+
+
+def to_dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.complex64)).cuda()
+
+
+def rand_imgs(nb, ny, nx, seed):
+    g = np.random.default_rng(seed)
+    return (g.standard_normal((nb, ny, nx)) + 1j * g.standard_normal((nb, ny, nx))).astype(np.complex64)
+
+
+def fft_path_operator(*args, **kw):
+    old = os.environ.get("PICO_NORMAL_OP")
+    os.environ["PICO_NORMAL_OP"] = "fft"
+    try:
+        return pico.Operator(*args, **kw)
+    finally:
+        if old is None:
+            del os.environ["PICO_NORMAL_OP"]
+        else:
+            os.environ["PICO_NORMAL_OP"] = old
+
+
+def test_path_selection():
+    S, cov, mask = case(320, 24, 4)
+    assert pico.Operator(S, mask=mask, noise_cov=cov, power_iters=0).info["normal_op"] == 1
+    assert fft_path_operator(S, mask=mask, noise_cov=cov, power_iters=0).info["normal_op"] == 0
+    S, cov, mask = case(64, 64, 4)
+    assert pico.Operator(S, mask=mask, noise_cov=cov, power_iters=0).info["normal_op"] == 0
+
+
+# (ny, nx): one and two output-row tiles, ragged column counts, several tile widths
+@pytest.mark.parametrize("ny,nx", [(128, 20), (160, 33), (192, 8), (240, 17), (256, 12), (320, 21), (384, 10)])
+@pytest.mark.parametrize("lam", [0.0, 0.05])
+def test_apply_normal_matches_oracle(ny, nx, lam):
+    S, cov, mask = case(ny, nx, 5, acs=6, seed=ny + nx)
+    op = pico.Operator(S, mask=mask, noise_cov=cov, lam=lam, power_iters=0, max_batch=4)
+    assert op.info["normal_op"] == 1
+    oop = O.Operator(S, cov, mask=mask)
+    x = rand_imgs(5, ny, nx, 1)                       # two batches of 4 + 1
+    y = op.apply_normal(to_dev(x)).cpu().numpy()
+    for b in range(5):
+        want = oop.normal(x[b].astype(np.complex128), lam)
+        err = np.linalg.norm(y[b] - want) / np.linalg.norm(want)
+        assert err < 1e-5, (b, err)
+    assert pico.pico_sync(op.ctx) is None
+
+
+def test_apply_normal_across_image_tiles():
+    # 130 images: a full 128-image tile and a ragged second one
+    ny, nx = 160, 6
+    S, cov, mask = case(ny, nx, 4, seed=5)
+    op = pico.Operator(S, mask=mask, noise_cov=cov, power_iters=0, max_batch=130)
+    oop = O.Operator(S, cov, mask=mask)
+    x = rand_imgs(130, ny, nx, 2)
+    y = op.apply_normal(to_dev(x)).cpu().numpy()
+    for b in (0, 63, 127, 128, 129):
+        want = oop.normal(x[b].astype(np.complex128))
+        assert np.linalg.norm(y[b] - want) / np.linalg.norm(want) < 1e-5, b
+    # each image's result does not depend on where it sits in the batch
+    y1 = op.apply_normal(to_dev(x[129:130])).cpu().numpy()
+    assert np.array_equal(y1[0], y[129])
+
+
+@pytest.mark.parametrize("ny,nx,nc,lam", [(128, 24, 6, 0.0), (160, 18, 5, 0.1)])
+def test_cg_fixed_iterations_matches_oracle(ny, nx, nc, lam):
+    S, cov, mask = case(ny, nx, nc, seed=7)
+    op = pico.Operator(S, mask=mask, noise_cov=cov, lam=lam, power_iters=0, max_batch=4)
+    oop = O.Operator(S, cov, mask=mask)
+    rhs = rand_imgs(5, ny, nx, 11)
+    x, iters, relres = op.cg(to_dev(rhs), 30, 0.0, stats=True)
+    x = x.cpu().numpy()
+    assert np.all(iters == 30)
+    for b in range(5):
+        want, it, rr = OS.cg(lambda z: oop.normal(z, lam), rhs[b].astype(np.complex128), 30, 0.0)
+        err = np.linalg.norm(x[b] - want) / np.linalg.norm(want)
+        assert err < 1e-4, err
+        assert abs(relres[b] - rr) <= 1e-3 * rr + 1e-6
+
+
+def test_cg_stopping_rule_matches_oracle():
+    S, cov, mask = case(128, 16, 6, seed=9)
+    op = pico.Operator(S, mask=mask, noise_cov=cov, power_iters=0, max_batch=8)
+    oop = O.Operator(S, cov, mask=mask)
+    rhs = rand_imgs(3, 128, 16, 5)
+    x, iters, relres = op.cg(to_dev(rhs), 100, 1e-3, stats=True)
+    for b in range(3):
+        _, it, rr = OS.cg(lambda z: oop.normal(z), rhs[b].astype(np.complex128), 100, 1e-3)
+        assert abs(int(iters[b]) - it) <= 1, (iters[b], it)
+        assert relres[b] <= 1e-3
+
+
+def test_variance_map_same_seed_parity_and_fft_path_agreement():
+    ny, nx = 128, 16
+    S, cov, mask = case(ny, nx, 6, seed=3)
+    oop = O.Operator(S, cov, mask=mask)
+    d, _, _ = OP.column_exact(oop)
+    K = 12
+    op = pico.Operator(S, mask=mask, noise_cov=cov, power_iters=0, max_batch=8)
+    s, _ = op.variance_sums(31, K, 30, 0.0)
+    so, _ = OP.pico(oop, 31, 0, K, 0.0, 30, 0.0)
+    assert (np.abs(s.cpu().numpy() - so) / K / d).max() < 1e-4
+    opf = fft_path_operator(S, mask=mask, noise_cov=cov, power_iters=0, max_batch=8)
+    sf, _ = opf.variance_sums(31, K, 30, 0.0)
+    assert (np.abs(s.cpu().numpy() - sf.cpu().numpy()) / K / d).max() < 1e-4
+
+
+def test_pmr_same_seed_parity():
+    ny, nx = 160, 32                      # the PMR adjoint needs an x-FFT length of this build
+    S, cov, mask = case(ny, nx, 6, seed=2)
+    op = pico.Operator(S, mask=mask, noise_cov=cov, power_iters=0, max_batch=8)
+    oop = O.Operator(S, cov, mask=mask)
+    N, sigma = 10, 1e-2
+    s, _ = op.pmr_sums(21, N, sigma, 30)
+    so, _ = OP.pmr(oop, 21, 0, N, sigma, 0.0, 30, 0.0)
+    d, _, _ = OP.column_exact(oop)
+    assert (np.abs(s.cpu().numpy() - so) / N / d).max() < 1e-4
+
+
+def test_batch_grouping_and_resume_are_bitwise_identical():
+    ny, nx = 128, 10
+    S, cov, mask = case(ny, nx, 5, seed=4)
+    op = pico.Operator(S, mask=mask, noise_cov=cov, power_iters=0, max_batch=8)
+    full_s, full_ss = op.variance_sums(5, 20, 20, 0.0)
+    s, ss = op.variance_sums(5, 7, 20, 0.0, probe_begin=0)
+    op.variance_sums(5, 13, 20, 0.0, probe_begin=7, sum_=s, sumsq=ss)
+    assert torch.equal(full_s, s) and torch.equal(full_ss, ss)
+    op2 = pico.Operator(S, mask=mask, noise_cov=cov, power_iters=0, max_batch=3)
+    s2, _ = op2.variance_sums(5, 20, 20, 0.0)
+    assert torch.equal(full_s, s2)
+
+
+def test_lambda_positive_composition_matches_oracle():
+    # Sigma v = (M + lam)^-1 M (M + lam)^-1 v: solve, A^H A on the solution, solve
+    ny, nx, lam = 128, 12, 0.1
+    S, cov, mask = case(ny, nx, 5, seed=8)
+    op = pico.Operator(S, mask=mask, noise_cov=cov, lam=lam, power_iters=0, max_batch=4)
+    oop = O.Operator(S, cov, mask=mask)
+    K = 6
+    s, _ = op.variance_sums(13, K, 30, 0.0)
+    so, _ = OP.pico(oop, 13, 0, K, lam, 30, 0.0)
+    d, _, _ = OP.column_exact(oop, lam)
+    assert (np.abs(s.cpu().numpy() - so) / K / d).max() < 1e-4
+
+
+# ---------------------------------------------------------------------------
+# full size: 320x320, 15 correlated coils, R=2 + 24 calibration lines, K=256
+# (the benchmark's launch shape)
+# ---------------------------------------------------------------------------
+@pytest.fixture(scope="module")
+def knee():
+    w = synth.WORKLOADS["knee320_r2"]
+    inp = w.inputs()
+    oop = O.Operator(inp["smaps"], inp["noise_cov"], mask=inp["mask"])
+    return w, inp, oop
+
+
+def test_full_size_cg_batch_sampled_parity(knee):
+    w, inp, oop = knee
+    op = pico.Operator(inp["smaps"], mask=inp["mask"], noise_cov=inp["noise_cov"], power_iters=0,
+                       max_batch=w.probes)
+    assert op.info["normal_op"] == 1
+    n = w.ny * w.nx
+    rhs = np.stack([ORNG.probe(77, i, n).reshape(w.ny, w.nx) for i in range(w.probes)]).astype(np.complex64)
+    x = op.cg(to_dev(rhs), w.max_iter, 0.0).cpu().numpy()
+    for i in (0, 127, 128, 255):
+        want, _, _ = OS.cg(lambda z: oop.normal(z), rhs[i].astype(np.complex128), w.max_iter, 0.0)
+        err = np.linalg.norm(x[i] - want) / np.linalg.norm(want)
+        assert err < 1e-4, (i, err)
+
+
+def test_full_size_variance_map_band(knee):
+    w, inp, oop = knee
+    op = pico.Operator(inp["smaps"], mask=inp["mask"], noise_cov=inp["noise_cov"], max_batch=w.probes)
+    s, _ = op.variance_sums(2026, w.probes, w.max_iter, 0.0)
+    d, _, half = OP.column_exact(oop)
+    K = w.probes
+    z = (s.cpu().numpy() / K - d) / np.sqrt(half / K)
+    assert np.mean(np.abs(z) > 4) < 0.01, np.mean(np.abs(z) > 4)
+    assert np.abs(s.cpu().numpy() / K - d).max() / d.max() < 0.2
+    assert pico.pico_sync(op.ctx) is None
