@@ -91,6 +91,35 @@ def flops_2d_normal(w):
     return w.nc * (4 * n * 5 * n * math.log2(n) + 18 * n * n)
 
 
+def measured_peaks():
+    with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+        return json.load(f)
+
+
+def gram_roofline(w, K, avg_s, launches):
+    """Roofline of the tensor-core normal operator (k_gram_normal).
+
+    Algorithmic work per launch: nx dense complex (ny x ny) x (ny x K)
+    products, 8 ny^2 nx flops per image; the tensor pipe issues three TF32
+    products per complex term (the FP32-accurate split), so the executed TF32
+    work is 3x that.  Peak: TF32 = measured bf16 burst x (1.1 / 2.25), the
+    nominal dense TF32 / bf16 ratio.  HBM bytes per launch: r, p_old read and
+    p, q written (4 images per probe) plus the split G planes once."""
+    mp = measured_peaks()
+    alg = 8.0 * w.ny * w.ny * w.nx * K
+    tf32 = 3.0 * alg
+    peak = mp["bf16_tflops"] * 1.1 / 2.25
+    achieved = tf32 / avg_s / 1e12
+    gbytes = 2 * w.nx * 2 * w.ny * w.ny * 4
+    hbm = (4 * K * w.ny * w.nx * 8 + gbytes) / avg_s / 1e9
+    return {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            "traffic": None, "kernel": "k_gram_normal (tcgen05 kind::tf32, 3-term split, fused CG direction update)",
+            "avg_launch_ms": avg_s * 1e3, "launches": launches,
+            "algorithmic_TFLOPs": alg / avg_s / 1e12,
+            "hbm_GBps_algorithmic": hbm, "hbm_frac_of_measured": hbm / mp["hbm_gbs"],
+            "peak_note": "TF32 dense peak derived from the measured bf16 burst (of measured x nominal ratio)"}
+
+
 def normal_ops_per_probe(w):
     """Normal-operator applications per probe: one CG solve (lam = 0) or two
     solves and one A^H A (lam > 0)."""
@@ -471,16 +500,19 @@ def main():
 
     # roofline of the dominant kernel (the fused CG normal operator)
     avg_norm_s = norm_ms / max(norm_n, 1) / 1e3
-    flops_launch = K * flops_per_probe(w)   # one class-0 launch (group) = one normal op on K images
-    achieved = flops_launch / avg_norm_s / 1e12
-    peak = N_SM * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
-    roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-            "traffic": None,
-            "kernel": "k_col_normal (fused CG prologue)" if w.kind == "cartesian" else
-                      "k_toep_rows_fwd + k_toep_cols + k_toep_rows_inv (one normal operator)",
-            "avg_launch_ms": avg_norm_s * 1e3, "launches": norm_n,
-            "hbm_GBps_algorithmic": K * bytes_per_probe_normal(w) / avg_norm_s / 1e9,
-            "peak_note": "FP32 FMA peak 152 SM x 128 lanes x 2 x 2070 MHz (nominal max clock)"}
+    if op.info["normal_op"] == 1 and K >= 64:
+        roof = gram_roofline(w, K, avg_norm_s, norm_n)
+    else:
+        flops_launch = K * flops_per_probe(w)   # one class-0 launch (group) = one normal op on K images
+        achieved = flops_launch / avg_norm_s / 1e12
+        peak = N_SM * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": None,
+                "kernel": "k_col_normal (fused CG prologue)" if w.kind == "cartesian" else
+                          "k_toep_rows_fwd + k_toep_cols + k_toep_rows_inv (one normal operator)",
+                "avg_launch_ms": avg_norm_s * 1e3, "launches": norm_n,
+                "hbm_GBps_algorithmic": K * bytes_per_probe_normal(w) / avg_norm_s / 1e9,
+                "peak_note": "FP32 FMA peak 152 SM x 128 lanes x 2 x 2070 MHz (nominal max clock)"}
     share = {"normal_op_ms": norm_ms, "cg_vector_ms": upd_ms, "pmr_adjoint_ms": pmr_ms, "accumulate_ms": acc_ms}
 
     line = {

@@ -9,6 +9,7 @@
 #include <tuple>
 #include <cstdio>
 #include <algorithm>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -69,7 +70,9 @@ struct pico_ctx {
   pico::Wavelet wav{};
   // dense per-column normal operator on the tensor cores (Cartesian phase-encode
   // masks): CG vectors in the column-planar layout, two direction buffers
-  bool gram = false;
+  bool gram = false;     // G built: batches of at least kGramMinBatch images use it
+  bool gram_on = false;  // the batch in flight uses it (CG vectors column-planar)
+  int pa_fft = 0, pa_gram = 0, gram_min_batch = 64;
   pico::GramOp gop{};
   CUtensorMap mR{}, mX{}, mP0{}, mP1{};
   float* P2 = nullptr;
@@ -220,6 +223,16 @@ void prof_collect(pico_ctx* c) {
 }
 
 float* cpf(float2* p) { return reinterpret_cast<float*>(p); }
+
+// Pick the normal operator for a batch of nb images (sets the layout of the
+// CG vectors and the number of p^H q partials per iteration).  Below
+// gram_min_batch images (64 unless PICO_GRAM_MIN_BATCH says otherwise) the
+// column-FFT kernel is as fast as the Gram operator, whose cost is dominated
+// by streaming G once per launch.
+void select_path(pico_ctx* c, int nb) {
+  c->gram_on = c->gram && nb >= c->gram_min_batch;
+  c->cg.PA = c->gram_on ? c->pa_gram : c->pa_fft;
+}
 // Gram mode: the direction written by CG iteration `it` (two buffers alternate,
 // because the operator reads the previous direction while writing the new one)
 float* gram_pbuf(pico_ctx* c, int it) { return (it & 1) ? c->P2 : cpf(c->P); }
@@ -233,7 +246,7 @@ pico::CgArgs gram_cg(pico_ctx* c, int it) {
 // (A^H A + lam) x for nb images (class 0).  Gram mode: x is one of the
 // context's column-planar buffers X or R.
 void op_apply(pico_ctx* c, const float2* x, float2* y, int nb, float lam) {
-  if (c->gram) {
+  if (c->gram_on) {
     const CUtensorMap& m = x == c->X ? c->mX : c->mR;
     pico::GramArgs g{};
     g.in = reinterpret_cast<const float*>(x);
@@ -257,7 +270,7 @@ void op_apply(pico_ctx* c, const float2* x, float2* y, int nb, float lam) {
 
 // CG iteration `it`, operator half (class 0)
 void op_cg_normal(pico_ctx* c, int nb, int it, float lam) {
-  if (c->gram) {
+  if (c->gram_on) {
     { Launch L(c, 1); pico::launch_gram_scalars(c->cg, nb, it, c->g_beta, c->g_done, c->stream); }
     pico::GramArgs g{};
     g.in = cpf(c->R);
@@ -295,7 +308,7 @@ void cg_iterations(pico_ctx* c, int nb, int max_iter, double rtol, float lam) {
   auto direct = [&]() {
     for (int it = 0; it < max_iter; ++it) {
       op_cg_normal(c, nb, it, lam);
-      { Launch L(c, 1); pico::launch_cg_update(c->gram ? gram_cg(c, it) : c->cg, nb, it, c->stream); }
+      { Launch L(c, 1); pico::launch_cg_update(c->gram_on ? gram_cg(c, it) : c->cg, nb, it, c->stream); }
     }
   };
   if (c->profiling || !c->use_graphs || max_iter == 0) return direct();
@@ -339,7 +352,7 @@ pico_status run_cg(pico_ctx* c, int nb, int max_iter, double rtol, float lam) {
 pico_status run_cg_from_probe(pico_ctx* c, int nb, int max_iter, double rtol, float lam, uint64_t seed,
                               int64_t begin, int kind) {
   c->cg.rtol2 = rtol * rtol;
-  if (c->gram) {
+  if (c->gram_on) {
     // probes drawn in the natural layout into Q, then rearranged into R
     pico::CgArgs a = c->cg;
     a.R = c->Q;
@@ -646,6 +659,7 @@ pico_status gram_setup(pico_ctx* c, const pico_operator_desc* d) {
   if ((st = dalloc(c, &c->g_err, (size_t)4)) != PICO_OK) return st;
   if ((st = dalloc(c, &c->g_pbuf, (size_t)c->ny)) != PICO_OK) return st;
   cudaMemsetAsync(c->g_err, 0, 4 * sizeof(int), c->stream);
+  if (const char* e = std::getenv("PICO_GRAM_MIN_BATCH")) c->gram_min_batch = std::max(1, std::atoi(e));
   c->gop.ny = c->ny;
   c->gop.nx = c->nx;
   c->gop.nt = pico::gram_tile(c->ny);
@@ -737,7 +751,9 @@ pico_status init_impl(const pico_operator_desc* d, void* cuda_stream, size_t hbm
     PA = pico::cart_normal_tiles(c->nx);
     extra = (size_t)c->ny * 13 + (size_t)c->nx * 8;
     if (want_gram(d)) {
-      PA = std::max(PA, pico::gram_pa(c->ny, c->nx));
+      c->pa_gram = pico::gram_pa(c->ny, c->nx);
+      c->pa_fft = PA;
+      PA = std::max(PA, c->pa_gram);
       extra += gram_extra_bytes(d, B);
     }
   } else {
@@ -795,7 +811,8 @@ pico_status init_impl(const pico_operator_desc* d, void* cuda_stream, size_t hbm
   TRY(dalloc(c, &c->d_norm, (size_t)PB + 1));
   cudaMemcpyAsync(c->smaps, S.data(), S.size() * sizeof(float2), cudaMemcpyHostToDevice, c->stream);
   cudaMemsetAsync(c->status, 0, (size_t)B * sizeof(int), c->stream);
-  c->cg = pico::CgArgs{n, c->X, c->R, c->P, c->Q, c->rr_part, c->pq_part, c->status, PB, PA, c->itmax, 0.0};
+  if (!c->pa_gram) c->pa_fft = PA;
+  c->cg = pico::CgArgs{n, c->X, c->R, c->P, c->Q, c->rr_part, c->pq_part, c->status, PB, c->pa_fft, c->itmax, 0.0};
 
   if (c->mask2d) {
     TRY(cart2d_setup(c, d, img, P1, P2));
@@ -896,12 +913,14 @@ pico_status pico_get_info(const pico_ctx* c, pico_info* info) {
 pico_status pico_apply_normal(pico_ctx* c, const void* x, void* y, int32_t nbatch) {
   if (!c || !c->smaps) return PICO_E_INVALID;
   if (nbatch < 0 || (nbatch > 0 && (!x || !y))) return fail(c, PICO_E_INVALID, "bad batch or pointer");
-  const int chunk = c->kind == PICO_CARTESIAN && !c->gram ? 65535 : c->max_batch;
+  const bool gram = c->gram && std::min(nbatch, c->max_batch) >= c->gram_min_batch;
+  const int chunk = c->kind == PICO_CARTESIAN && !gram ? 65535 : c->max_batch;
   for (int32_t b0 = 0; b0 < nbatch; b0 += chunk) {
     const int nb = std::min(chunk, nbatch - b0);
     const float2* xi = static_cast<const float2*>(x) + (size_t)b0 * c->n;
     float2* yo = static_cast<float2*>(y) + (size_t)b0 * c->n;
-    if (c->gram) {
+    select_path(c, nb);
+    if (c->gram_on) {
       { Launch L(c, 3); pico::launch_to_cp(xi, cpf(c->R), c->ny, c->nx, nb, c->stream); }
       op_apply(c, c->R, c->Q, nb, (float)c->lam_phys);
       { Launch L(c, 3); pico::launch_from_cp(cpf(c->Q), yo, c->ny, c->nx, nb, c->stream); }
@@ -923,14 +942,15 @@ pico_status pico_cg_batch(pico_ctx* c, const void* rhs, void* x, int32_t nbatch,
     const int nb = std::min(c->max_batch, nbatch - b0);
     const float2* rb = reinterpret_cast<const float2*>(static_cast<const char*>(rhs) + (size_t)b0 * bytes_img);
     float2* xb = reinterpret_cast<float2*>(static_cast<char*>(x) + (size_t)b0 * bytes_img);
-    if (c->gram) {
+    select_path(c, nb);
+    if (c->gram_on) {
       Launch L(c, 3);
       pico::launch_to_cp(rb, cpf(c->R), c->ny, c->nx, nb, c->stream);
     } else {
       cudaMemcpyAsync(c->R, rb, (size_t)nb * bytes_img, cudaMemcpyDeviceToDevice, c->stream);
     }
     if ((st = run_cg(c, nb, max_iter, rtol, (float)c->lam_phys)) != PICO_OK) return st;
-    if (c->gram) {
+    if (c->gram_on) {
       Launch L(c, 3);
       pico::launch_from_cp(cpf(c->X), xb, c->ny, c->nx, nb, c->stream);
     } else {
@@ -966,6 +986,7 @@ pico_status pico_variance_map(pico_ctx* c, uint64_t seed, int64_t probe_begin, i
   const float lam = (float)c->lam_phys;
   for (int32_t b0 = 0; b0 < nprobes; b0 += c->max_batch) {
     const int nb = std::min(c->max_batch, nprobes - b0);
+    select_path(c, nb);
     if ((st = run_cg_from_probe(c, nb, max_iter, rtol, lam, seed, probe_begin + b0, kind)) != PICO_OK) return st;
     if (c->lam_phys != 0.0) {
       // Sigma v = (M + lam)^-1 M (M + lam)^-1 v: apply M to the first solution, solve again
@@ -973,7 +994,7 @@ pico_status pico_variance_map(pico_ctx* c, uint64_t seed, int64_t probe_begin, i
       if ((st = run_cg(c, nb, max_iter, rtol, lam)) != PICO_OK) return st;
     }
     const float2* xs = c->X;
-    if (c->gram) {  // back to the natural layout for the probe-indexed accumulation
+    if (c->gram_on) {  // back to the natural layout for the probe-indexed accumulation
       { Launch L(c, 3); pico::launch_from_cp(cpf(c->X), c->Q, c->ny, c->nx, nb, c->stream); }
       xs = c->Q;
     }
@@ -1037,7 +1058,8 @@ pico_status pico_pmr(pico_ctx* c, uint64_t seed, int64_t rep_begin, int32_t nrep
   const float lam = (float)c->lam_phys;
   for (int32_t b0 = 0; b0 < nreps; b0 += c->max_batch) {
     const int nb = std::min(c->max_batch, nreps - b0);
-    if (c->gram) {
+    select_path(c, nb);
+    if (c->gram_on) {
       noise_adjoint(c, c->Q, nb, seed, rep_begin + b0, sigma);
       { Launch L(c, 2); pico::launch_to_cp(c->Q, cpf(c->R), c->ny, c->nx, nb, c->stream); }
     } else {
@@ -1045,7 +1067,7 @@ pico_status pico_pmr(pico_ctx* c, uint64_t seed, int64_t rep_begin, int32_t nrep
     }
     if ((st = run_cg(c, nb, max_iter, rtol, lam)) != PICO_OK) return st;
     const float2* xs = c->X;
-    if (c->gram) {
+    if (c->gram_on) {
       { Launch L(c, 3); pico::launch_from_cp(cpf(c->X), c->Q, c->ny, c->nx, nb, c->stream); }
       xs = c->Q;
     }

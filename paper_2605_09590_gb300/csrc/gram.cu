@@ -255,7 +255,12 @@ __global__ void __launch_bounds__(kGramThreads, 1)
     }
   } else {
     // ---- split p = r + beta p_old into TF32 head / remainder, in place ----
+    // The chunks inside this CTA's output rows [n0, n0 + NT) also store p to
+    // the new direction buffer (un-swizzling the 16-byte chunk index: the
+    // 64-byte swizzle XORs byte-offset bits 4-5 with bits 7-8).
     const int e = threadIdx.x - 64;  // 0..127
+    const int kc_lo = n0 / kGramKC, kc_hi = (n0 + NT) / kGramKC;
+    const size_t img2 = (size_t)2 * g.ny * g.nx;
     bool ok = true;
     for (int kc = 0; kc < nkc; ++kc) {
       const int s = kc % S;
@@ -280,6 +285,15 @@ __global__ void __launch_bounds__(kGramThreads, 1)
             vi.x = fmaf(b, wi.x, vi.x); vi.y = fmaf(b, wi.y, vi.y);
             vi.z = fmaf(b, wi.z, vi.z); vi.w = fmaf(b, wi.w, vi.w);
           }
+          if (g.pnew && kc >= kc_lo && kc < kc_hi) {
+            const int rowi = q >> 2, kimg = m0 + rowi;
+            if (kimg < g.nb) {
+              const int chunk = (q & 3) ^ ((rowi >> 1) & 3);
+              const size_t o = (size_t)kimg * img2 + (size_t)j * 2 * g.ny + (size_t)kc * kGramKC + 4 * chunk;
+              *reinterpret_cast<float4*>(g.pnew + o) = vr;
+              *reinterpret_cast<float4*>(g.pnew + o + g.ny) = vi;
+            }
+          }
           float4 hr, lr, hi4, li;
           split_tf32(vr.x, hr.x, lr.x); split_tf32(vr.y, hr.y, lr.y);
           split_tf32(vr.z, hr.z, lr.z); split_tf32(vr.w, hr.w, lr.w);
@@ -296,6 +310,10 @@ __global__ void __launch_bounds__(kGramThreads, 1)
     }
 
     // ---- epilogue ----
+    // p (this CTA's rows) was stored by the split warps above: make those
+    // stores visible to the other epilogue threads, then read it back (L2).
+    __threadfence_block();
+    asm volatile("bar.sync 1, 128;" ::: "memory");
     const int quarter = warp & 3;          // TMEM lanes 32*quarter .. +31
     const int row = 32 * quarter + lane;
     const int k = m0 + row;
@@ -303,32 +321,33 @@ __global__ void __launch_bounds__(kGramThreads, 1)
     if (!accok) set_err(g.err, 4);
     tc_fence_after();
     const bool valid = accok && k < g.nb && !(g.cg && g.done[k]);
-    const int64_t img = (int64_t)2 * g.ny * g.nx;
-    const size_t col = (size_t)k * img + (size_t)j * 2 * g.ny;
-    const float bk = beta_s[row];
+    const size_t col = (size_t)(valid ? k : 0) * img2 + (size_t)j * 2 * g.ny;
+    const float* psrc = g.cg ? g.pnew : g.in;
     double pq = 0.0;
+    float4 cur[8], nxt[8];
+    auto load_p = [&](int c, float4* dst) {
+      const float4* pr = reinterpret_cast<const float4*>(psrc + col + n0 + 16 * c);
+      const float4* pi = reinterpret_cast<const float4*>(psrc + col + g.ny + n0 + 16 * c);
+#pragma unroll
+      for (int v = 0; v < 4; ++v) {
+        dst[v] = pr[v];
+        dst[4 + v] = pi[v];
+      }
+    };
+    if (valid) load_p(0, cur);
     __syncwarp();
-    for (int c = 0; c < NT / 16; ++c) {   // NT is a multiple of 16
+    const int nch = NT / 16;               // NT is a multiple of 16
+    for (int c = 0; c < nch; ++c) {
+      if (valid && c + 1 < nch) load_p(c + 1, nxt);
       float dr[16], di[16];
       const uint32_t ta = tbase + ((uint32_t)(32 * quarter) << 16) + 16u * c;
       tmem_ld16(ta, dr);
       tmem_ld16(ta + (uint32_t)NT, di);
       if (valid) {
         const int y0 = n0 + 16 * c;
-        const float4* inr = reinterpret_cast<const float4*>(g.in + col + y0);
-        const float4* ini = reinterpret_cast<const float4*>(g.in + col + g.ny + y0);
-        const float4* por = use_pold ? reinterpret_cast<const float4*>(g.pold + col + y0) : nullptr;
-        const float4* poi = use_pold ? reinterpret_cast<const float4*>(g.pold + col + g.ny + y0) : nullptr;
 #pragma unroll
         for (int v = 0; v < 4; ++v) {
-          float4 pr = inr[v], pi = ini[v];
-          if (use_pold) {
-            const float4 wr = por[v], wi = poi[v];
-            pr.x = fmaf(bk, wr.x, pr.x); pr.y = fmaf(bk, wr.y, pr.y);
-            pr.z = fmaf(bk, wr.z, pr.z); pr.w = fmaf(bk, wr.w, pr.w);
-            pi.x = fmaf(bk, wi.x, pi.x); pi.y = fmaf(bk, wi.y, pi.y);
-            pi.z = fmaf(bk, wi.z, pi.z); pi.w = fmaf(bk, wi.w, pi.w);
-          }
+          const float4 pr = cur[v], pi = cur[4 + v];
           float4 qr, qi;
           qr.x = fmaf(g.lam, pr.x, dr[4 * v + 0]); qr.y = fmaf(g.lam, pr.y, dr[4 * v + 1]);
           qr.z = fmaf(g.lam, pr.z, dr[4 * v + 2]); qr.w = fmaf(g.lam, pr.w, dr[4 * v + 3]);
@@ -336,10 +355,6 @@ __global__ void __launch_bounds__(kGramThreads, 1)
           qi.z = fmaf(g.lam, pi.z, di[4 * v + 2]); qi.w = fmaf(g.lam, pi.w, di[4 * v + 3]);
           reinterpret_cast<float4*>(g.q + col + y0)[v] = qr;
           reinterpret_cast<float4*>(g.q + col + g.ny + y0)[v] = qi;
-          if (g.pnew) {
-            reinterpret_cast<float4*>(g.pnew + col + y0)[v] = pr;
-            reinterpret_cast<float4*>(g.pnew + col + g.ny + y0)[v] = pi;
-          }
           float acc = 0.f;
           acc = fmaf(pr.x, qr.x, acc); acc = fmaf(pr.y, qr.y, acc);
           acc = fmaf(pr.z, qr.z, acc); acc = fmaf(pr.w, qr.w, acc);
@@ -348,6 +363,8 @@ __global__ void __launch_bounds__(kGramThreads, 1)
           pq += (double)acc;
         }
       }
+#pragma unroll
+      for (int v = 0; v < 8; ++v) cur[v] = nxt[v];
     }
     if (valid && g.pq) g.pq[((size_t)k * g.itmax + g.it) * g.PA + (size_t)j * g.nyt + ytile] = pq;
   }

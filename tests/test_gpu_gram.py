@@ -5,6 +5,8 @@ apply A^H A inside CG as nx dense ny x ny products on the tcgen05 tensor cores
 with a 3-term TF32 split.  These tests compare that path with the FP64 oracle
 (operator, CG, PICO, PMR), with the column-FFT path of the same library
 (PICO_NORMAL_OP=fft), and check its determinism across batch sizes.
+PICO_GRAM_MIN_BATCH=1 makes every batch use the Gram operator here (contexts
+keep batches below 64 images on the column-FFT kernel by default).
 
 Tolerances: one operator application agrees with the oracle to 1e-5 relative
 in norm (the split keeps about 21 mantissa bits per product; the tensor-memory
@@ -35,6 +37,13 @@ def _built():
         pytest.skip("needs a CUDA device")
     pico_build.build()
     pico.load_library()
+
+
+@pytest.fixture(autouse=True)
+def _gram_for_every_batch(monkeypatch):
+    # contexts use the Gram operator for batches of 64+ images by default;
+    # these small cases exercise it at every batch size
+    monkeypatch.setenv("PICO_GRAM_MIN_BATCH", "1")
 
 
 def case(ny, nx, nc, R=2, acs=8, corr=True, seed=0):
