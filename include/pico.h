@@ -88,9 +88,11 @@ typedef struct {
   int64_t nsamp;
   uint64_t device_bytes;    /* device memory held by the context                              */
   int32_t normal_op;        /* how (A^H A + lam I) is applied inside CG: 0 column FFTs,
-                               1 dense per-column Gram matrices on the tensor cores
-                               (phase-encode masks, ny % 16 == 0, ny >= 128; environment
-                               PICO_NORMAL_OP=fft selects 0), 2 Toeplitz 2-D FFT passes   */
+                               1 dense per-column Gram matrices on the tensor cores for
+                               batches of at least 64 images (PICO_GRAM_MIN_BATCH) and
+                               column FFTs below (phase-encode masks, ny % 16 == 0,
+                               ny >= 128; PICO_NORMAL_OP=fft in the environment selects 0),
+                               2 Toeplitz 2-D FFT passes                                   */
 } pico_info;
 
 /* Create a context: validates the descriptor, whitens the sensitivities,
@@ -271,8 +273,11 @@ pico_status pico_footprint(const pico_operator_desc* desc, int32_t with_kspace, 
  * hbm_budget (0 = unlimited), builds each request's operator on its own CUDA
  * stream with stream-ordered allocation, enqueues its probes in batches of
  * `chunk`, and retires it when its work completes.  Work of admitted requests
- * overlaps on the GPU.  A request's result depends only on its own inputs and
- * seed: it is bit-identical alone or in any mix.  The server uses the device
+ * overlaps on the GPU.  A request's result depends only on its own inputs, seed
+ * and the chunk size: it is bit-identical in any mix and alone on a context with
+ * max_batch = chunk (batches of at least 64 images of a Cartesian phase-encode
+ * operator run on the tensor-core Gram operator, smaller ones on the column-FFT
+ * kernel; the two agree to about 1e-6 relative, not bitwise).  The server uses the device
  * current at pico_server_create. */
 typedef struct pico_server pico_server;
 

@@ -37,6 +37,8 @@ struct pico_ctx {
   double *rr_part = nullptr, *pq_part = nullptr;
   int* status = nullptr;
   int* d_iters = nullptr;
+  float* cg_alpha = nullptr;  // [B] per-system step of the current CG iteration
+  int* cg_state = nullptr;    // [B] 0 update, 1 converged, 2 breakdown
   double* d_relres = nullptr;
   double* d_norm = nullptr;
   double* d_adapt = nullptr;
@@ -193,11 +195,15 @@ struct Launch {
   cudaEvent_t a = nullptr;
   Launch(pico_ctx* c_, int cls_, int kernels = 1) : c(c_), cls(cls_) {
     c->launches += kernels;
+    count_ = kernels;
     if (c->profiling) {
       a = take_event(c);
       cudaEventRecord(a, c->stream);
     }
   }
+  int count_ = 0;
+  // correct the kernel count when fewer kernels than announced were launched
+  void count(int delta) { c->launches += delta; count_ += delta; }
   ~Launch() {
     if (a) {
       cudaEvent_t b = take_event(c);
@@ -308,7 +314,14 @@ void cg_iterations(pico_ctx* c, int nb, int max_iter, double rtol, float lam) {
   auto direct = [&]() {
     for (int it = 0; it < max_iter; ++it) {
       op_cg_normal(c, nb, it, lam);
-      { Launch L(c, 1); pico::launch_cg_update(c->gram_on ? gram_cg(c, it) : c->cg, nb, it, c->stream); }
+      {
+        Launch L(c, 1, 2);
+        const pico::CgArgs a = c->gram_on ? gram_cg(c, it) : c->cg;
+        if (!pico::launch_cg_step(a, nb, it, c->cg_alpha, c->cg_state, c->stream)) {
+          L.count(-1);
+          pico::launch_cg_update(a, nb, it, c->stream);
+        }
+      }
     }
   };
   if (c->profiling || !c->use_graphs || max_iter == 0) return direct();
@@ -663,14 +676,17 @@ pico_status gram_setup(pico_ctx* c, const pico_operator_desc* d) {
   c->gop.ny = c->ny;
   c->gop.nx = c->nx;
   c->gop.nt = pico::gram_tile(c->ny);
+  c->gop.kc = 16;
+  if (const char* e = std::getenv("PICO_GRAM_KC")) c->gop.kc = std::atoi(e) == 8 ? 8 : 16;
+  const int kc = c->gop.kc;
   pico::launch_gram_build(c->smaps, d->mask, c->nc, c->ny, c->nx, c->gop.Ghi, c->gop.Glo, c->g_pbuf, c->stream);
   const int B = c->max_batch;
-  const bool ok = pico::gram_encode_g(&c->gop.mGhi, c->gop.Ghi, c->ny, c->nx) &&
-                  pico::gram_encode_g(&c->gop.mGlo, c->gop.Glo, c->ny, c->nx) &&
-                  pico::gram_encode_x(&c->mR, cpf(c->R), c->ny, c->nx, B) &&
-                  pico::gram_encode_x(&c->mX, cpf(c->X), c->ny, c->nx, B) &&
-                  pico::gram_encode_x(&c->mP0, cpf(c->P), c->ny, c->nx, B) &&
-                  pico::gram_encode_x(&c->mP1, c->P2, c->ny, c->nx, B);
+  const bool ok = pico::gram_encode_g(&c->gop.mGhi, c->gop.Ghi, c->ny, c->nx, kc) &&
+                  pico::gram_encode_g(&c->gop.mGlo, c->gop.Glo, c->ny, c->nx, kc) &&
+                  pico::gram_encode_x(&c->mR, cpf(c->R), c->ny, c->nx, B, kc) &&
+                  pico::gram_encode_x(&c->mX, cpf(c->X), c->ny, c->nx, B, kc) &&
+                  pico::gram_encode_x(&c->mP0, cpf(c->P), c->ny, c->nx, B, kc) &&
+                  pico::gram_encode_x(&c->mP1, c->P2, c->ny, c->nx, B, kc);
   if (!ok) return fail(c, PICO_E_CUDA, "tensor map encoding for the Gram operator failed");
   if (cudaStreamSynchronize(c->stream) != cudaSuccess) return cuda_check(c, "Gram operator set-up");
   c->gram = true;
@@ -807,6 +823,8 @@ pico_status init_impl(const pico_operator_desc* d, void* cuda_stream, size_t hbm
   TRY(dalloc(c, &c->pq_part, (size_t)B * c->itmax * PA));
   TRY(dalloc(c, &c->status, (size_t)B));
   TRY(dalloc(c, &c->d_iters, (size_t)B));
+  TRY(dalloc(c, &c->cg_alpha, (size_t)B));
+  TRY(dalloc(c, &c->cg_state, (size_t)B));
   TRY(dalloc(c, &c->d_relres, (size_t)B));
   TRY(dalloc(c, &c->d_norm, (size_t)PB + 1));
   cudaMemcpyAsync(c->smaps, S.data(), S.size() * sizeof(float2), cudaMemcpyHostToDevice, c->stream);

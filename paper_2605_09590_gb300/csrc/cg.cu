@@ -122,6 +122,71 @@ __global__ void __launch_bounds__(kVecThreads) k_cg_update(CgArgs a, int it) {
   if (threadIdx.x == 0) rr_at_w(a, b, it + 1)[blockIdx.x] = s;
 }
 
+// Per-system CG step of iteration it, once per system: state 0 update,
+// 1 converged / stopped, 2 breakdown; alpha = rr / pq.
+__global__ void k_cg_alpha(CgArgs a, int it, float* alpha, int* state) {
+  const int b = blockIdx.x;
+  const double rr = warp_sum_parts(rr_at(a, b, it), a.PB);
+  const double rr0 = warp_sum_parts(rr_at(a, b, 0), a.PB);
+  const double pq = warp_sum_parts(pq_at(a, b, it), a.PA);
+  if (threadIdx.x == 0) {
+    int st = 0;
+    if (!(rr > a.rtol2 * rr0)) st = 1;
+    else if (!(pq > 0.0) || !isfinite(pq)) st = 2;
+    state[b] = st;
+    alpha[b] = (float)(rr / pq);
+  }
+}
+
+// x += alpha p; r -= alpha q with the per-system scalars of k_cg_alpha; two
+// complex values per 16-byte access (n even), the same blocks of
+// kVecPerBlock values and the same r^H r partials as k_cg_update.
+__global__ void __launch_bounds__(kVecThreads) k_cg_update_v(CgArgs a, int it, const float* __restrict__ alpha_b,
+                                                             const int* __restrict__ state_b) {
+  __shared__ double scratch[kVecThreads / 32];
+  const int b = blockIdx.y;
+  const int st = state_b[b];
+  if (st == 1) {
+    if (threadIdx.x == 0) rr_at_w(a, b, it + 1)[blockIdx.x] = rr_at(a, b, it)[blockIdx.x];
+    return;
+  }
+  if (st == 2) {
+    if (threadIdx.x == 0) {
+      rr_at_w(a, b, it + 1)[blockIdx.x] = 0.0;
+      if (blockIdx.x == 0) a.status[b] = 5;
+    }
+    return;
+  }
+  const float alpha = alpha_b[b];
+  float4* X = reinterpret_cast<float4*>(a.X + (size_t)b * a.n);
+  float4* R = reinterpret_cast<float4*>(a.R + (size_t)b * a.n);
+  const float4* P = reinterpret_cast<const float4*>(a.P + (size_t)b * a.n);
+  const float4* Q = reinterpret_cast<const float4*>(a.Q + (size_t)b * a.n);
+  const int64_t n4 = a.n / 2;
+  float acc = 0.f;
+#pragma unroll
+  for (int j = 0; j < kVecPerThread / 2; ++j) {
+    const int64_t i = (int64_t)blockIdx.x * (kVecPerBlock / 2) + j * kVecThreads + threadIdx.x;
+    if (i < n4) {
+      const float4 p = P[i], q = Q[i];
+      float4 x = X[i], r = R[i];
+      x.x = fmaf(alpha, p.x, x.x);
+      x.y = fmaf(alpha, p.y, x.y);
+      x.z = fmaf(alpha, p.z, x.z);
+      x.w = fmaf(alpha, p.w, x.w);
+      r.x = fmaf(-alpha, q.x, r.x);
+      r.y = fmaf(-alpha, q.y, r.y);
+      r.z = fmaf(-alpha, q.z, r.z);
+      r.w = fmaf(-alpha, q.w, r.w);
+      X[i] = x;
+      R[i] = r;
+      acc += fmaf(r.x, r.x, r.y * r.y) + fmaf(r.z, r.z, r.w * r.w);
+    }
+  }
+  const double s = block_sum_d((double)acc, scratch);
+  if (threadIdx.x == 0) rr_at_w(a, b, it + 1)[blockIdx.x] = s;
+}
+
 // iterations performed and final relative residual per right-hand side
 __global__ void k_cg_report(CgArgs a, int max_iter, int* iters, double* relres) {
   const int b = blockIdx.x;
@@ -268,6 +333,12 @@ void launch_cg_init_rhs(const CgArgs& a, int nb, cudaStream_t s) {
 }
 void launch_cg_update(const CgArgs& a, int nb, int it, cudaStream_t s) {
   k_cg_update<<<dim3(a.PB, nb), kVecThreads, 0, s>>>(a, it);
+}
+bool launch_cg_step(const CgArgs& a, int nb, int it, float* alpha, int* state, cudaStream_t s) {
+  if (a.n % 2) return false;
+  k_cg_alpha<<<nb, 32, 0, s>>>(a, it, alpha, state);
+  k_cg_update_v<<<dim3(a.PB, nb), kVecThreads, 0, s>>>(a, it, alpha, state);
+  return true;
 }
 void launch_cg_report(const CgArgs& a, int nb, int max_iter, int* iters, double* relres, cudaStream_t s) {
   k_cg_report<<<nb, 32, 0, s>>>(a, max_iter, iters, relres);

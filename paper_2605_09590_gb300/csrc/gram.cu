@@ -29,9 +29,30 @@ namespace {
 using namespace tc;
 
 constexpr int kGramRows = 128;   // images per CTA (MMA M)
-constexpr int kGramKC = 16;      // contraction chunk (64 B rows, 64-byte swizzle)
 constexpr int kGramThreads = 192;
-constexpr uint32_t kATile = kGramRows * kGramKC * 4;  // 8 KB
+
+// Contraction chunk per pipeline stage: KC = 16 values (64-byte rows, 64-byte
+// swizzle) or KC = 8 (32-byte rows, 32-byte swizzle, twice the stages).
+template <int KC>
+struct GramTile {
+  static constexpr uint32_t kATile = kGramRows * KC * 4;
+  static constexpr uint32_t kRowBytes = KC * 4;
+  // descriptor of a K-major tile: rows of KC*4 bytes, 8-row atoms
+  static __device__ __forceinline__ uint64_t desc(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+    d |= (uint64_t)1u << 16;
+    d |= (uint64_t)((8u * kRowBytes) >> 4) << 32;
+    d |= (uint64_t)1u << 46;
+    d |= (uint64_t)(KC == 16 ? 4u : 6u) << 61;  // 64-byte or 32-byte swizzle
+    return d;
+  }
+  // logical 16-byte chunk of a row from its position in shared memory: the
+  // swizzle XORs byte-offset bits 4.. with bits 7..
+  static __device__ __forceinline__ int chunk(int phys, int row) {
+    return KC == 16 ? (phys ^ ((row >> 1) & 3)) : (phys ^ ((row >> 2) & 1));
+  }
+};
 
 __device__ __forceinline__ void set_err(int* err, int code) {
   if (err) atomicCAS(err, 0, code);
@@ -67,6 +88,44 @@ __global__ void k_gram_build(const float2* __restrict__ S, const double2* __rest
   Ghi[o + plane] = hi_;
   Glo[o] = (float)(gr - (double)hr);
   Glo[o + plane] = (float)(gi - (double)hi_);
+}
+
+// The same G_j with the sensitivities of column j staged in shared memory
+// (block = column j x 32 output rows; all y' per block).
+__global__ void __launch_bounds__(256) k_gram_build_smem(const float2* __restrict__ S, const double2* __restrict__ P,
+                                                         int nc, int ny, int nx, float* __restrict__ Ghi,
+                                                         float* __restrict__ Glo) {
+  extern __shared__ float2 sc[];  // [nc][ny] sensitivities of column j
+  const int j = blockIdx.x, y_lo = blockIdx.y * 32;
+  const int64_t n = (int64_t)ny * nx;
+  for (int i = threadIdx.x; i < nc * ny; i += blockDim.x) {
+    const int c = i / ny, y = i % ny;
+    sc[i] = S[c * n + (int64_t)y * nx + j];
+  }
+  __syncthreads();
+  const size_t plane = (size_t)ny * ny;
+  for (int t = threadIdx.x; t < 32 * ny; t += blockDim.x) {
+    const int y = y_lo + t / ny, yp = t % ny;
+    if (y >= ny) break;
+    double re = 0.0, im = 0.0;
+    for (int c = 0; c < nc; ++c) {
+      const float2 a = sc[c * ny + y], b = sc[c * ny + yp];
+      re += (double)a.x * b.x + (double)a.y * b.y;
+      im += (double)a.x * b.y - (double)a.y * b.x;
+    }
+    int d = y - yp;
+    if (d < 0) d += ny;
+    const double2 p = P[d];
+    const double gr = p.x * re - p.y * im, gi = p.x * im + p.y * re;
+    const size_t o = (size_t)j * 2 * plane + (size_t)y * ny + yp;
+    float hr, lr, hi_, li;
+    split_tf32((float)gr, hr, lr);
+    split_tf32((float)gi, hi_, li);
+    Ghi[o] = hr;
+    Ghi[o + plane] = hi_;
+    Glo[o] = (float)(gr - (double)hr);
+    Glo[o + plane] = (float)(gi - (double)hi_);
+  }
 }
 
 // per-image CG scalars of iteration it: beta = rr(it) / rr(it-1) (0 at it = 0), done flag
@@ -137,26 +196,30 @@ __global__ void k_from_cp(const float* __restrict__ in, float2* __restrict__ out
 //   B: [G_re hi | G_im hi | G_re lo | G_im lo] NT x 16 fp32 each
 // and D_re (columns 0..NT-1), D_im (NT..2NT-1) accumulate in tensor memory:
 //   D_re += p_re G_re^T - p_im G_im^T,  D_im += p_re G_im^T + p_im G_re^T.
+template <int KC>
 __global__ void __launch_bounds__(kGramThreads, 1)
     k_gram_normal(const __grid_constant__ CUtensorMap mIn, const __grid_constant__ CUtensorMap mPold,
                   const __grid_constant__ CUtensorMap mGhi, const __grid_constant__ CUtensorMap mGlo, GramArgs g) {
   extern __shared__ uint8_t smraw[];
   uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smraw) + 1023) & ~(uintptr_t)1023);
   const int NT = g.nt, S = g.stages;
-  const uint32_t btile = (uint32_t)NT * kGramKC * 4;
+  using T = GramTile<KC>;
+  constexpr uint32_t kATile = T::kATile;
+  const uint32_t btile = (uint32_t)NT * KC * 4;
   const uint32_t stage_bytes = 4 * kATile + 4 * btile;
   uint64_t* bars = reinterpret_cast<uint64_t*>(sm + (size_t)S * stage_bytes);
   uint64_t* full = bars;
   uint64_t* conv = bars + S;
   uint64_t* empty = bars + 2 * S;
   uint64_t* accf = bars + 3 * S;
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + 3 * S + 1);
+  uint64_t* pbar = bars + 3 * S + 1;   // epilogue staging of p, one phase per pass
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + 3 * S + 2);
   float* beta_s = reinterpret_cast<float*>(tslot + 4);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int ytile = blockIdx.x % g.nyt, itile = blockIdx.x / g.nyt, j = blockIdx.y;
   const int n0 = ytile * NT, m0 = itile * kGramRows;
-  const int nkc = g.ny / kGramKC;
+  const int nkc = g.ny / KC;
   const bool use_pold = g.cg && g.it > 0;
 
   if (threadIdx.x == 0) {
@@ -166,6 +229,7 @@ __global__ void __launch_bounds__(kGramThreads, 1)
       mbar_init(&empty[s], 1);
     }
     mbar_init(accf, 1);
+    mbar_init(pbar, 1);
     fence_mbar_init();
   }
   if (warp >= 2) {
@@ -198,7 +262,7 @@ __global__ void __launch_bounds__(kGramThreads, 1)
           break;
         }
         mbar_expect_tx(&full[s], bytes);
-        const int y0 = kc * kGramKC;
+        const int y0 = kc * KC;
         tma_load_4d(slotA(s, 0), &mIn, &full[s], y0, 0, j, m0);
         tma_load_4d(slotA(s, 1), &mIn, &full[s], y0, 1, j, m0);
         if (use_pold) {
@@ -227,13 +291,13 @@ __global__ void __launch_bounds__(kGramThreads, 1)
         const uint32_t bhr = smem_u32(slotB(s, 0)), bhi = smem_u32(slotB(s, 1));
         const uint32_t blr = smem_u32(slotB(s, 2)), bli = smem_u32(slotB(s, 3));
 #pragma unroll
-        for (int kk = 0; kk < kGramKC / 8; ++kk) {
+        for (int kk = 0; kk < KC / 8; ++kk) {
           const uint32_t o = 32u * kk;
           const uint32_t acc0 = (kc == 0 && kk == 0) ? 0u : 1u;
-          const uint64_t Ahr = desc_k_sw64(ahr + o), Ahi = desc_k_sw64(ahi + o);
-          const uint64_t Alr = desc_k_sw64(alr + o), Ali = desc_k_sw64(ali + o);
-          const uint64_t Bhr = desc_k_sw64(bhr + o), Bhi = desc_k_sw64(bhi + o);
-          const uint64_t Blr = desc_k_sw64(blr + o), Bli = desc_k_sw64(bli + o);
+          const uint64_t Ahr = T::desc(ahr + o), Ahi = T::desc(ahi + o);
+          const uint64_t Alr = T::desc(alr + o), Ali = T::desc(ali + o);
+          const uint64_t Bhr = T::desc(bhr + o), Bhi = T::desc(bhi + o);
+          const uint64_t Blr = T::desc(blr + o), Bli = T::desc(bli + o);
           // D_re += p_re G_re^T - p_im G_im^T
           mma_tf32(dre, Ahr, Bhr, id, acc0);
           mma_tf32(dre, Ahr, Blr, id, 1);
@@ -256,10 +320,9 @@ __global__ void __launch_bounds__(kGramThreads, 1)
   } else {
     // ---- split p = r + beta p_old into TF32 head / remainder, in place ----
     // The chunks inside this CTA's output rows [n0, n0 + NT) also store p to
-    // the new direction buffer (un-swizzling the 16-byte chunk index: the
-    // 64-byte swizzle XORs byte-offset bits 4-5 with bits 7-8).
+    // the new direction buffer (un-swizzling the 16-byte chunk index).
     const int e = threadIdx.x - 64;  // 0..127
-    const int kc_lo = n0 / kGramKC, kc_hi = (n0 + NT) / kGramKC;
+    const int kc_lo = n0 / KC, kc_hi = (n0 + NT) / KC;
     const size_t img2 = (size_t)2 * g.ny * g.nx;
     bool ok = true;
     for (int kc = 0; kc < nkc; ++kc) {
@@ -274,9 +337,9 @@ __global__ void __launch_bounds__(kGramThreads, 1)
         float4* p_re = reinterpret_cast<float4*>(slotA(s, 2));
         float4* p_im = reinterpret_cast<float4*>(slotA(s, 3));
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
-          const int q = e + 128 * i;  // float4 index in the 128 x 16 tile; row = q / 4
-          const float b = beta_s[q >> 2];
+        for (int i = 0; i < KC / 4; ++i) {
+          const int q = e + 128 * i;  // float4 index in the 128 x KC tile; row = q / (KC/4)
+          const float b = beta_s[q / (KC / 4)];
           float4 vr = r_re[q], vi = r_im[q];
           if (use_pold) {
             const float4 wr = p_re[q], wi = p_im[q];
@@ -286,10 +349,10 @@ __global__ void __launch_bounds__(kGramThreads, 1)
             vi.z = fmaf(b, wi.z, vi.z); vi.w = fmaf(b, wi.w, vi.w);
           }
           if (g.pnew && kc >= kc_lo && kc < kc_hi) {
-            const int rowi = q >> 2, kimg = m0 + rowi;
+            const int rowi = q / (KC / 4), kimg = m0 + rowi;
             if (kimg < g.nb) {
-              const int chunk = (q & 3) ^ ((rowi >> 1) & 3);
-              const size_t o = (size_t)kimg * img2 + (size_t)j * 2 * g.ny + (size_t)kc * kGramKC + 4 * chunk;
+              const int chunk = T::chunk(q % (KC / 4), rowi);
+              const size_t o = (size_t)kimg * img2 + (size_t)j * 2 * g.ny + (size_t)kc * KC + 4 * chunk;
               *reinterpret_cast<float4*>(g.pnew + o) = vr;
               *reinterpret_cast<float4*>(g.pnew + o + g.ny) = vi;
             }
@@ -310,8 +373,11 @@ __global__ void __launch_bounds__(kGramThreads, 1)
     }
 
     // ---- epilogue ----
-    // p (this CTA's rows) was stored by the split warps above: make those
-    // stores visible to the other epilogue threads, then read it back (L2).
+    // p of this CTA's rows (stored above by the split warps, or the input x in
+    // apply mode) is staged into the now idle pipeline buffers by bulk copies,
+    // [row][re|im][W] with a 16-byte pad per row (conflict-free row reads),
+    // in passes of W output rows.
+    fence_proxy_async_global();
     __threadfence_block();
     asm volatile("bar.sync 1, 128;" ::: "memory");
     const int quarter = warp & 3;          // TMEM lanes 32*quarter .. +31
@@ -320,51 +386,58 @@ __global__ void __launch_bounds__(kGramThreads, 1)
     const bool accok = mbar_wait(accf, 0);
     if (!accok) set_err(g.err, 4);
     tc_fence_after();
-    const bool valid = accok && k < g.nb && !(g.cg && g.done[k]);
-    const size_t col = (size_t)(valid ? k : 0) * img2 + (size_t)j * 2 * g.ny;
+    const bool inb = k < g.nb;
+    const bool valid = accok && inb && !(g.cg && g.done[k]);
+    const size_t col = (size_t)(inb ? k : 0) * img2 + (size_t)j * 2 * g.ny;
     const float* psrc = g.cg ? g.pnew : g.in;
+    const int rows_in = min(kGramRows, g.nb - m0);
+    int W = NT;
+    while ((size_t)kGramRows * (8u * W + 16u) > (size_t)S * stage_bytes) W -= 16;
+    const uint32_t pitch = 8u * W + 16u;
+    float* prow = reinterpret_cast<float*>(sm + (size_t)row * pitch);
     double pq = 0.0;
-    float4 cur[8], nxt[8];
-    auto load_p = [&](int c, float4* dst) {
-      const float4* pr = reinterpret_cast<const float4*>(psrc + col + n0 + 16 * c);
-      const float4* pi = reinterpret_cast<const float4*>(psrc + col + g.ny + n0 + 16 * c);
-#pragma unroll
-      for (int v = 0; v < 4; ++v) {
-        dst[v] = pr[v];
-        dst[4 + v] = pi[v];
+    int pphase = 0;
+    for (int w0 = 0; w0 < NT; w0 += W, pphase ^= 1) {
+      const int wn = min(W, NT - w0);
+      if (row == 0) mbar_expect_tx(pbar, (uint32_t)rows_in * 8u * wn);
+      asm volatile("bar.sync 1, 128;" ::: "memory");
+      if (accok && inb) {
+        bulk_load(prow, psrc + col + n0 + w0, 4u * wn, pbar);
+        bulk_load(prow + W, psrc + col + g.ny + n0 + w0, 4u * wn, pbar);
       }
-    };
-    if (valid) load_p(0, cur);
-    __syncwarp();
-    const int nch = NT / 16;               // NT is a multiple of 16
-    for (int c = 0; c < nch; ++c) {
-      if (valid && c + 1 < nch) load_p(c + 1, nxt);
-      float dr[16], di[16];
-      const uint32_t ta = tbase + ((uint32_t)(32 * quarter) << 16) + 16u * c;
-      tmem_ld16(ta, dr);
-      tmem_ld16(ta + (uint32_t)NT, di);
-      if (valid) {
-        const int y0 = n0 + 16 * c;
+      const bool pok = mbar_wait(pbar, pphase);
+      if (!pok) set_err(g.err, 5);
+      __syncwarp();
+      for (int c = 0; c < wn / 16; ++c) {
+        float dr[16], di[16];
+        const uint32_t ta = tbase + ((uint32_t)(32 * quarter) << 16) + (uint32_t)(w0 + 16 * c);
+        tmem_ld16(ta, dr);
+        tmem_ld16(ta + (uint32_t)NT, di);
+        if (valid && pok) {
+          const int y0 = n0 + w0 + 16 * c;
+          const float4* pr4 = reinterpret_cast<const float4*>(prow + 16 * c);
+          const float4* pi4 = reinterpret_cast<const float4*>(prow + W + 16 * c);
 #pragma unroll
-        for (int v = 0; v < 4; ++v) {
-          const float4 pr = cur[v], pi = cur[4 + v];
-          float4 qr, qi;
-          qr.x = fmaf(g.lam, pr.x, dr[4 * v + 0]); qr.y = fmaf(g.lam, pr.y, dr[4 * v + 1]);
-          qr.z = fmaf(g.lam, pr.z, dr[4 * v + 2]); qr.w = fmaf(g.lam, pr.w, dr[4 * v + 3]);
-          qi.x = fmaf(g.lam, pi.x, di[4 * v + 0]); qi.y = fmaf(g.lam, pi.y, di[4 * v + 1]);
-          qi.z = fmaf(g.lam, pi.z, di[4 * v + 2]); qi.w = fmaf(g.lam, pi.w, di[4 * v + 3]);
-          reinterpret_cast<float4*>(g.q + col + y0)[v] = qr;
-          reinterpret_cast<float4*>(g.q + col + g.ny + y0)[v] = qi;
-          float acc = 0.f;
-          acc = fmaf(pr.x, qr.x, acc); acc = fmaf(pr.y, qr.y, acc);
-          acc = fmaf(pr.z, qr.z, acc); acc = fmaf(pr.w, qr.w, acc);
-          acc = fmaf(pi.x, qi.x, acc); acc = fmaf(pi.y, qi.y, acc);
-          acc = fmaf(pi.z, qi.z, acc); acc = fmaf(pi.w, qi.w, acc);
-          pq += (double)acc;
+          for (int v = 0; v < 4; ++v) {
+            const float4 pr = pr4[v], pi = pi4[v];
+            float4 qr, qi;
+            qr.x = fmaf(g.lam, pr.x, dr[4 * v + 0]); qr.y = fmaf(g.lam, pr.y, dr[4 * v + 1]);
+            qr.z = fmaf(g.lam, pr.z, dr[4 * v + 2]); qr.w = fmaf(g.lam, pr.w, dr[4 * v + 3]);
+            qi.x = fmaf(g.lam, pi.x, di[4 * v + 0]); qi.y = fmaf(g.lam, pi.y, di[4 * v + 1]);
+            qi.z = fmaf(g.lam, pi.z, di[4 * v + 2]); qi.w = fmaf(g.lam, pi.w, di[4 * v + 3]);
+            reinterpret_cast<float4*>(g.q + col + y0)[v] = qr;
+            reinterpret_cast<float4*>(g.q + col + g.ny + y0)[v] = qi;
+            float acc = 0.f;
+            acc = fmaf(pr.x, qr.x, acc); acc = fmaf(pr.y, qr.y, acc);
+            acc = fmaf(pr.z, qr.z, acc); acc = fmaf(pr.w, qr.w, acc);
+            acc = fmaf(pi.x, qi.x, acc); acc = fmaf(pi.y, qi.y, acc);
+            acc = fmaf(pi.z, qi.z, acc); acc = fmaf(pi.w, qi.w, acc);
+            pq += (double)acc;
+          }
         }
       }
-#pragma unroll
-      for (int v = 0; v < 8; ++v) cur[v] = nxt[v];
+      // every row of this pass has been read before the next pass overwrites it
+      asm volatile("bar.sync 1, 128;" ::: "memory");
     }
     if (valid && g.pq) g.pq[((size_t)k * g.itmax + g.it) * g.PA + (size_t)j * g.nyt + ytile] = pq;
   }
@@ -399,7 +472,7 @@ EncodeTiledFn encode_fn() {
 }  // namespace
 
 bool gram_supported(int ny, int nx) {
-  if (ny < 32 || ny % kGramKC != 0 || ny > 1024 || nx < 1) return false;
+  if (ny < 32 || ny % 16 != 0 || ny > 1024 || nx < 1) return false;
   return gram_tile(ny) > 0;
 }
 
@@ -415,26 +488,26 @@ size_t gram_bytes(int ny, int nx) { return (size_t)2 * nx * 2 * ny * ny * sizeof
 
 int gram_pa(int ny, int nx) { return nx * (ny / gram_tile(ny)); }
 
-bool gram_encode_x(CUtensorMap* m, float* base, int ny, int nx, int B) {
+bool gram_encode_x(CUtensorMap* m, float* base, int ny, int nx, int B, int kc) {
   EncodeTiledFn enc = encode_fn();
   if (!enc) return false;
   cuuint64_t dims[4] = {(cuuint64_t)ny, 2, (cuuint64_t)nx, (cuuint64_t)B};
   cuuint64_t strides[3] = {(cuuint64_t)ny * 4, (cuuint64_t)2 * ny * 4, (cuuint64_t)2 * ny * nx * 4};
-  cuuint32_t box[4] = {kGramKC, 1, 1, kGramRows}, es[4] = {1, 1, 1, 1};
+  cuuint32_t box[4] = {(cuuint32_t)kc, 1, 1, kGramRows}, es[4] = {1, 1, 1, 1};
   return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, base, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
-             CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+             kc == 16 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_32B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-bool gram_encode_g(CUtensorMap* m, float* base, int ny, int nx) {
+bool gram_encode_g(CUtensorMap* m, float* base, int ny, int nx, int kc) {
   EncodeTiledFn enc = encode_fn();
   if (!enc) return false;
   const int nt = gram_tile(ny);
   cuuint64_t dims[4] = {(cuuint64_t)ny, (cuuint64_t)ny, 2, (cuuint64_t)nx};
   cuuint64_t strides[3] = {(cuuint64_t)ny * 4, (cuuint64_t)ny * ny * 4, (cuuint64_t)2 * ny * ny * 4};
-  cuuint32_t box[4] = {kGramKC, (cuuint32_t)nt, 1, 1}, es[4] = {1, 1, 1, 1};
+  cuuint32_t box[4] = {(cuuint32_t)kc, (cuuint32_t)nt, 1, 1}, es[4] = {1, 1, 1, 1};
   return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, base, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
-             CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+             kc == 16 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_32B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
@@ -454,8 +527,14 @@ void launch_gram_build(const float2* smaps, const uint8_t* mask_host, int nc, in
     P[d] = make_double2(re / ny, im / ny);
   }
   cudaMemcpyAsync(pbuf, P.data(), ny * sizeof(double2), cudaMemcpyHostToDevice, s);
-  const int64_t tot = (int64_t)ny * ny;
-  k_gram_build<<<dim3((unsigned)((tot + 255) / 256), nx), 256, 0, s>>>(smaps, pbuf, nc, ny, nx, Ghi, Glo);
+  const size_t sbytes = (size_t)nc * ny * sizeof(float2);
+  if (sbytes <= 200 * 1024) {
+    cudaFuncSetAttribute(k_gram_build_smem, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sbytes);
+    k_gram_build_smem<<<dim3(nx, (ny + 31) / 32), 256, sbytes, s>>>(smaps, pbuf, nc, ny, nx, Ghi, Glo);
+  } else {
+    const int64_t tot = (int64_t)ny * ny;
+    k_gram_build<<<dim3((unsigned)((tot + 255) / 256), nx), 256, 0, s>>>(smaps, pbuf, nc, ny, nx, Ghi, Glo);
+  }
   cudaStreamSynchronize(s);  // P lives on the host stack until the copy has run
 }
 
@@ -463,24 +542,26 @@ void launch_gram_scalars(const CgArgs& a, int nb, int it, float* beta, int* done
   k_gram_scalars<<<nb, 32, 0, s>>>(a, it, beta, done);
 }
 
-size_t gram_smem(int ny, int* stages) {
+size_t gram_smem(int ny, int kc, int* stages) {
   const int nt = gram_tile(ny);
-  const size_t stage = 4 * (size_t)kATile + 4 * (size_t)nt * kGramKC * 4;
+  const size_t stage = 4 * (size_t)kGramRows * kc * 4 + 4 * (size_t)nt * kc * 4;
   int S = (int)((220 * 1024 - 2048) / stage);
-  if (S > 4) S = 4;
+  if (S > 8) S = 8;
   if (S < 2) S = 2;
   *stages = S;
-  return 1024 + (size_t)S * stage + (3 * (size_t)S + 1) * 8 + 16 + kGramRows * 4 + 64;
+  return 1024 + (size_t)S * stage + (3 * (size_t)S + 2) * 8 + 16 + kGramRows * 4 + 64;
 }
 
 void launch_gram_normal(const GramOp& op, const CUtensorMap& mIn, const CUtensorMap& mPold, GramArgs g,
                         cudaStream_t s) {
   int S = 0;
-  const size_t smem = gram_smem(op.ny, &S);
-  static thread_local size_t configured = 0;
-  if (configured < smem) {
-    cudaFuncSetAttribute(k_gram_normal, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    configured = smem;
+  const size_t smem = gram_smem(op.ny, op.kc, &S);
+  static thread_local size_t configured[2] = {0, 0};
+  const int ki = op.kc == 16 ? 0 : 1;
+  if (configured[ki] < smem) {
+    if (ki == 0) cudaFuncSetAttribute(k_gram_normal<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    else cudaFuncSetAttribute(k_gram_normal<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    configured[ki] = smem;
   }
   g.ny = op.ny;
   g.nx = op.nx;
@@ -490,7 +571,9 @@ void launch_gram_normal(const GramOp& op, const CUtensorMap& mIn, const CUtensor
   g.tmem_cols = 32;
   while (g.tmem_cols < 2 * op.nt) g.tmem_cols *= 2;
   const unsigned itiles = (unsigned)((g.nb + kGramRows - 1) / kGramRows);
-  k_gram_normal<<<dim3((unsigned)g.nyt * itiles, op.nx), kGramThreads, smem, s>>>(mIn, mPold, op.mGhi, op.mGlo, g);
+  const dim3 grid((unsigned)g.nyt * itiles, op.nx);
+  if (op.kc == 16) k_gram_normal<16><<<grid, kGramThreads, smem, s>>>(mIn, mPold, op.mGhi, op.mGlo, g);
+  else k_gram_normal<8><<<grid, kGramThreads, smem, s>>>(mIn, mPold, op.mGhi, op.mGlo, g);
 }
 
 void launch_to_cp(const float2* in, float* out, int ny, int nx, int nb, cudaStream_t s) {

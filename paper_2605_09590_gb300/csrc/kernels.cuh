@@ -33,6 +33,9 @@ struct CgArgs {
 void launch_cg_init_probe(const CgArgs& a, int nb, uint64_t seed, int64_t probe_begin, int kind, cudaStream_t s);
 void launch_cg_init_rhs(const CgArgs& a, int nb, cudaStream_t s);
 void launch_cg_update(const CgArgs& a, int nb, int it, cudaStream_t s);
+// the same update as launch_cg_update with the per-system scalars computed once
+// (two launches, 16-byte accesses); false (nothing launched) when n is odd
+bool launch_cg_step(const CgArgs& a, int nb, int it, float* alpha, int* state, cudaStream_t s);
 void launch_cg_report(const CgArgs& a, int nb, int max_iter, int* iters, double* relres, cudaStream_t s);
 void launch_accum_pico(const float2* X, int64_t n, int nb, uint64_t seed, int64_t probe_begin, int kind,
                        double* sum, double* sumsq, cudaStream_t s);
@@ -81,6 +84,7 @@ void launch_cart_rows_adjoint(const CartOp& op, const float2* G, float2* out, in
 // ---- gram.cu: dense per-column normal operator on the tensor cores ----
 struct GramOp {
   int ny, nx, nt;           // nt: output rows per CTA (divides ny, <= 256)
+  int kc;                   // contraction values per pipeline stage (16 or 8)
   float* Ghi;               // [nx][2][ny][ny] TF32 head of G_j (re, im planes)
   float* Glo;               // remainder
   CUtensorMap mGhi, mGlo;
@@ -103,8 +107,8 @@ bool gram_supported(int ny, int nx);
 int gram_tile(int ny);
 size_t gram_bytes(int ny, int nx);  // both G planes, head and remainder
 int gram_pa(int ny, int nx);
-bool gram_encode_x(CUtensorMap* m, float* base, int ny, int nx, int B);
-bool gram_encode_g(CUtensorMap* m, float* base, int ny, int nx);
+bool gram_encode_x(CUtensorMap* m, float* base, int ny, int nx, int B, int kc);
+bool gram_encode_g(CUtensorMap* m, float* base, int ny, int nx, int kc);
 void launch_gram_build(const float2* smaps, const uint8_t* mask_host, int nc, int ny, int nx, float* Ghi, float* Glo,
                        double2* pbuf, cudaStream_t s);
 void launch_gram_scalars(const CgArgs& a, int nb, int it, float* beta, int* done, cudaStream_t s);

@@ -54,8 +54,11 @@ def alone(r):
 
 
 def test_mix_equals_alone_bitwise():
+    # the server launches `chunk` probes at a time, as the context built alone
+    # does with max_batch = chunk: batches of 64+ images of the 320x320 request
+    # run on the tensor-core Gram operator, the others on the column-FFT kernel
     reqs = requests()
-    sv = pico.Server(max_active=3, chunk=16)
+    sv = pico.Server(max_active=3, chunk=64)
     ids = [None] * len(reqs)
 
     def submit(i):
