@@ -290,6 +290,14 @@ typedef struct {
   double rtol;              /* CG relative-residual stop (0 = max_iter exactly)            */
   int32_t pmr_reps;         /* PMR replicas (0 = no PMR map)                               */
   double pmr_sigma;         /* PMR noise standard deviation                                */
+  /* Nonlinear CS request (Sec. 2.2.5): with cs_data != NULL the maps are those
+   * of the L1-wavelet FISTA reconstruction of cs_data (whitened k-space, layout
+   * of pico_forward, host, copied at submit) -- Jacobian PICO and CS PMR --
+   * with weight cs_lambda, cs_iters iterations and cs_levels DWT levels
+   * (max_iter and rtol do not apply; the descriptor needs power_iters > 0). */
+  const void* cs_data;
+  double cs_lambda;
+  int32_t cs_iters, cs_levels;
 } pico_request;
 
 typedef struct {

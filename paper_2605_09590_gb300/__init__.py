@@ -61,6 +61,8 @@ class pico_request(ctypes.Structure):
         ("op", pico_operator_desc), ("seed", ctypes.c_uint64), ("nprobes", ctypes.c_int32),
         ("probe_kind", ctypes.c_int32), ("max_iter", ctypes.c_int32), ("rtol", ctypes.c_double),
         ("pmr_reps", ctypes.c_int32), ("pmr_sigma", ctypes.c_double),
+        ("cs_data", ctypes.c_void_p), ("cs_lambda", ctypes.c_double), ("cs_iters", ctypes.c_int32),
+        ("cs_levels", ctypes.c_int32),
     ]
 
 
@@ -483,12 +485,19 @@ class Server:
 
     def submit(self, smaps, mask=None, traj=None, noise_cov=None, lam=0.0, seed=0, nprobes=32,
                probe_kind=PICO_PROBE_PHASE, max_iter=30, rtol=0.0, pmr_reps=0, pmr_sigma=1.0,
-               power_iters=15, max_batch=64) -> int:
+               power_iters=15, max_batch=64, cs_data=None, cs_lambda=0.0, cs_iters=100, cs_levels=4) -> int:
+        """Queue one request; with ``cs_data`` (whitened k-space, complex64,
+        layout of ``Operator.forward``) the maps are those of the L1-wavelet
+        CS reconstruction (Jacobian PICO and CS PMR)."""
         d, keep = make_desc(smaps, mask, noise_cov, traj, lam, power_iters, 1.01, max_batch, 128)
         r = pico_request()
         r.op = d
         r.seed, r.nprobes, r.probe_kind, r.max_iter, r.rtol = seed & (2 ** 64 - 1), nprobes, probe_kind, max_iter, rtol
         r.pmr_reps, r.pmr_sigma = pmr_reps, pmr_sigma
+        if cs_data is not None:
+            cs = np.ascontiguousarray(cs_data, dtype=np.complex64)
+            keep.append(cs)
+            r.cs_data, r.cs_lambda, r.cs_iters, r.cs_levels = cs.ctypes.data, cs_lambda, cs_iters, cs_levels
         rid = ctypes.c_int64()
         st = self.lib.pico_server_submit(self.h, ctypes.byref(r), ctypes.byref(rid))
         if st != PICO_OK:

@@ -884,7 +884,11 @@ size_t footprint_bytes(const pico_operator_desc* d, bool with_kbuf) {
   const int64_t nc = d->ncoils, n = (int64_t)d->ny * d->nx;
   const int64_t PB = (n + kVecPerBlock - 1) / kVecPerBlock;
   int64_t PA, extra, kbuf;
-  if (d->kind == PICO_CARTESIAN) {
+  if (d->kind == PICO_CARTESIAN && d->mask_2d) {
+    PA = (d->ny + 15) / 16;
+    extra = std::max(B * nc * n, n) * 8 + n * 5 + (int64_t)d->ny * 8;
+    kbuf = B * nc * n * 8;
+  } else if (d->kind == PICO_CARTESIAN) {
     PA = cart_normal_tiles(d->nx);
     extra = (int64_t)d->ny * 13 + (int64_t)d->nx * 8;
     kbuf = B * nc * n * 8;

@@ -107,24 +107,33 @@ __global__ void __launch_bounds__(256) k_gram_build_smem(const float2* __restric
   for (int t = threadIdx.x; t < 32 * ny; t += blockDim.x) {
     const int y = y_lo + t / ny, yp = t % ny;
     if (y >= ny) break;
-    double re = 0.0, im = 0.0;
+    // FP32 with compensated (Kahan) summation over the coils: FP64 arithmetic
+    // is a small fraction of the FP32 rate on this part
+    float re = 0.f, rc = 0.f, im = 0.f, ic = 0.f;
     for (int c = 0; c < nc; ++c) {
       const float2 a = sc[c * ny + y], b = sc[c * ny + yp];
-      re += (double)a.x * b.x + (double)a.y * b.y;
-      im += (double)a.x * b.y - (double)a.y * b.x;
+      const float tr = fmaf(a.x, b.x, a.y * b.y) - rc;
+      const float sr = re + tr;
+      rc = (sr - re) - tr;
+      re = sr;
+      const float ti = fmaf(a.x, b.y, -a.y * b.x) - ic;
+      const float si = im + ti;
+      ic = (si - im) - ti;
+      im = si;
     }
     int d = y - yp;
     if (d < 0) d += ny;
     const double2 p = P[d];
-    const double gr = p.x * re - p.y * im, gi = p.x * im + p.y * re;
+    const float px = (float)p.x, py = (float)p.y;
+    const float gr = fmaf(px, re, -py * im), gi = fmaf(px, im, py * re);
     const size_t o = (size_t)j * 2 * plane + (size_t)y * ny + yp;
     float hr, lr, hi_, li;
-    split_tf32((float)gr, hr, lr);
-    split_tf32((float)gi, hi_, li);
+    split_tf32(gr, hr, lr);
+    split_tf32(gi, hi_, li);
     Ghi[o] = hr;
     Ghi[o + plane] = hi_;
-    Glo[o] = (float)(gr - (double)hr);
-    Glo[o + plane] = (float)(gi - (double)hi_);
+    Glo[o] = lr;
+    Glo[o + plane] = li;
   }
 }
 

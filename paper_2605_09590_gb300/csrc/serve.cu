@@ -39,6 +39,7 @@ struct Request {
   std::vector<float> smaps, traj;
   std::vector<double> cov;
   std::vector<uint8_t> mask;
+  std::vector<float> cs_data;  // whitened k-space of a CS request
   size_t footprint = 0;
   double t_arrival = 0, t_admit = 0, t_done = 0;
   // device state while active
@@ -46,6 +47,7 @@ struct Request {
   cudaEvent_t done_ev = nullptr;
   pico_ctx* ctx = nullptr;
   double *d_sum = nullptr, *d_sumsq = nullptr, *d_psum = nullptr;
+  float* d_cs = nullptr;  // device copy of the CS data and the reconstruction
   // results
   std::vector<double> var, pmr;
   pico_status status = PICO_OK;
@@ -84,6 +86,26 @@ pico_status launch_request(pico_server* sv, Request& r) {
   if (cudaMallocAsync((void**)&r.d_sum, 3 * n * sizeof(double), r.stream) != cudaSuccess) return PICO_E_OOM;
   r.d_sumsq = r.d_sum + n;
   r.d_psum = r.d_sum + 2 * n;
+  if (r.req.cs_data) {
+    const size_t kf = r.cs_data.size();
+    if (cudaMallocAsync((void**)&r.d_cs, (kf + 2 * n) * sizeof(float), r.stream) != cudaSuccess) return PICO_E_OOM;
+    if (cudaMemcpyAsync(r.d_cs, r.cs_data.data(), kf * sizeof(float), cudaMemcpyHostToDevice, r.stream) != cudaSuccess)
+      return PICO_E_CUDA;
+    st = pico_cs_recon(r.ctx, r.d_cs, r.req.cs_lambda, r.req.cs_iters, r.req.cs_levels, r.d_cs + kf);
+    if (st != PICO_OK) return st;
+    for (int32_t b = 0; b < r.req.nprobes; b += sv->chunk) {
+      const int32_t nb = std::min(sv->chunk, r.req.nprobes - b);
+      st = pico_cs_variance_map(r.ctx, r.req.seed, b, nb, r.req.probe_kind, r.d_sum, r.d_sumsq, b > 0);
+      if (st != PICO_OK) return st;
+    }
+    for (int32_t b = 0; b < r.req.pmr_reps; b += sv->chunk) {
+      const int32_t nb = std::min(sv->chunk, r.req.pmr_reps - b);
+      st = pico_cs_pmr(r.ctx, r.req.seed, b, nb, r.req.pmr_sigma, r.d_psum, nullptr, b > 0);
+      if (st != PICO_OK) return st;
+    }
+    if (cudaEventRecord(r.done_ev, r.stream) != cudaSuccess) return PICO_E_CUDA;
+    return PICO_OK;
+  }
   for (int32_t b = 0; b < r.req.nprobes; b += sv->chunk) {
     const int32_t nb = std::min(sv->chunk, r.req.nprobes - b);
     st = pico_variance_map(r.ctx, r.req.seed, b, nb, r.req.probe_kind, r.req.max_iter, r.req.rtol, r.d_sum,
@@ -102,6 +124,8 @@ pico_status launch_request(pico_server* sv, Request& r) {
 void release_request(Request& r) {
   if (r.d_sum) cudaFreeAsync(r.d_sum, r.stream);
   r.d_sum = nullptr;
+  if (r.d_cs) cudaFreeAsync(r.d_cs, r.stream);
+  r.d_cs = nullptr;
   if (r.ctx) pico_destroy(r.ctx);
   r.ctx = nullptr;
   if (r.stream) cudaStreamSynchronize(r.stream);
@@ -229,6 +253,18 @@ pico_status pico_server_submit(pico_server* sv, const pico_request* rq, int64_t*
     r->req.op.traj = r->traj.data();
   }
   r->footprint = pico::footprint_bytes(&r->req.op, rq->pmr_reps > 0) + 3 * n * sizeof(double);
+  if (rq->cs_data) {
+    if (d.kind != PICO_CARTESIAN || d.power_iters <= 0 || rq->cs_iters < 1 || rq->cs_levels < 1)
+      return PICO_E_INVALID;
+    const size_t kf = 2 * (size_t)d.ncoils * n;  // k-space floats (layout of pico_forward)
+    r->cs_data.assign((const float*)rq->cs_data, (const float*)rq->cs_data + kf);
+    r->req.cs_data = r->cs_data.data();
+    // k-space buffer (the adjoint of the data), six CS work images per batch
+    // slot, the iterates' coefficients, A^H b and f(b), the data and the image
+    const size_t B = d.max_batch > 0 ? (size_t)d.max_batch : 64;
+    r->footprint = pico::footprint_bytes(&r->req.op, true) + 3 * n * sizeof(double) + 6 * B * n * 8 +
+                   (size_t)rq->cs_iters * n * 8 + 2 * n * 8 + (kf + 2 * n) * sizeof(float);
+  }
   if (sv->budget && r->footprint > sv->budget) return PICO_E_OOM;
   std::lock_guard<std::mutex> lk(sv->mu);
   r->id = sv->next_id++;

@@ -92,3 +92,51 @@ def test_admission_respects_memory_budget():
         assert b["t_admit"] >= a["t_done"] - 1e-6
     with pytest.raises(pico.PicoError):
         pico.Server(hbm_budget=1000).submit(**reqs[0])
+
+
+def _cs_request(n=64, nc=8, seed=21):
+    """A nonlinear-CS request: Poisson-disc mask, phantom data, weight 1e-2 max|W A^H b|."""
+    S = synth.coil_maps(n, n, nc, seed)
+    mask = synth.poisson_disc_mask(n, n, 2.0, 12, seed)
+    op = pico.Operator(S, mask=mask, power_iters=15, max_batch=8)
+    x0 = torch.from_numpy(synth.phantom(n, seed).astype(np.complex64)).cuda().reshape(1, n, n)
+    b = op.forward(x0)
+    coef = torch.empty_like(x0)
+    pico.pico_wavelet(op.ctx, op.adjoint(b), coef, 4)
+    lam = 1e-2 * float(coef.abs().max())
+    op.close()
+    return dict(smaps=S, mask=mask, seed=seed, nprobes=12, pmr_reps=10, pmr_sigma=1e-3,
+                cs_data=b[0].cpu().numpy(), cs_lambda=lam, cs_iters=30, cs_levels=4)
+
+
+def _cs_alone(r, chunk):
+    n = r["smaps"].shape[1]
+    op = pico.Operator(r["smaps"], mask=r["mask"], power_iters=15, max_batch=chunk)
+    x = torch.empty((n, n), dtype=torch.complex64, device="cuda")
+    pico.pico_cs_recon(op.ctx, torch.from_numpy(r["cs_data"]).cuda(), r["cs_lambda"], r["cs_iters"], r["cs_levels"],
+                       x)
+    s = torch.zeros((n, n), dtype=torch.float64, device="cuda")
+    ss = torch.zeros_like(s)
+    p = torch.zeros_like(s)
+    for b in range(0, r["nprobes"], chunk):
+        pico.pico_cs_variance_map(op.ctx, r["seed"], b, min(chunk, r["nprobes"] - b), 0, s, ss, b > 0)
+    for b in range(0, r["pmr_reps"], chunk):
+        pico.pico_cs_pmr(op.ctx, r["seed"], b, min(chunk, r["pmr_reps"] - b), r["pmr_sigma"], p, None, b > 0)
+    out = s.cpu().numpy() / r["nprobes"], p.cpu().numpy() / r["pmr_reps"]
+    op.close()
+    return out
+
+
+def test_cs_requests_in_the_mix_equal_alone_bitwise():
+    cs = _cs_request()
+    reqs = [cs, requests()[0], requests()[1]]
+    sv = pico.Server(max_active=3, chunk=8)
+    ids = [sv.submit(**r) for r in reqs]
+    got = [sv.wait(i) for i in ids]
+    sv.close()
+    var, pmr, info = got[0]
+    assert info["status"] == 0
+    v0, p0 = _cs_alone(cs, 8)
+    assert np.array_equal(var, v0) and np.array_equal(pmr, p0)
+    # a 12-probe Jacobian PICO map may dip below zero voxelwise; its mean may not
+    assert var.mean() > 0 and np.all(pmr >= 0)
