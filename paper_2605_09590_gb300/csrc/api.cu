@@ -37,6 +37,9 @@ struct pico_ctx {
   double *rr_part = nullptr, *pq_part = nullptr;
   int* status = nullptr;
   int* d_iters = nullptr;
+  int* cg_done = nullptr;     // [B] per-system stop flag of the current iteration (Toeplitz passes)
+  int* d_flag = nullptr;      // device flag of the early-stop check
+  int* h_flag = nullptr;      // pinned host copy
   float* cg_alpha = nullptr;  // [B] per-system step of the current CG iteration
   int* cg_state = nullptr;    // [B] 0 update, 1 converged, 2 breakdown
   double* d_relres = nullptr;
@@ -101,8 +104,8 @@ struct pico_ctx {
   // CUDA graphs of the CG iteration loop, keyed by (nb, max_iter, rtol, lam)
   cudaStream_t cap = nullptr;
   bool use_graphs = true;
-  std::map<std::tuple<int, int, double, float>, std::pair<cudaGraphExec_t, int64_t>> graphs;
-  std::set<std::tuple<int, int, double, float>> seen;
+  std::map<std::tuple<int, int, int, double, float>, std::pair<cudaGraphExec_t, int64_t>> graphs;
+  std::set<std::tuple<int, int, int, double, float>> seen;
 };
 
 namespace {
@@ -309,10 +312,13 @@ void op_cg_normal(pico_ctx* c, int nb, int it, float lam) {
 // The CG iterations of one batch: 2 * max_iter kernels (normal operator + update).
 // Replayed from a CUDA graph (captured on a private stream the second time a
 // (nb, max_iter, rtol, lam) combination is used) unless profiling is on.
-void cg_iterations(pico_ctx* c, int nb, int max_iter, double rtol, float lam) {
-  c->cg.rtol2 = rtol * rtol;
+// CG iterations [it0, it1) of one batch: 2-3 kernels per iteration (normal
+// operator, step, update), replayed from a CUDA graph (captured on a private
+// stream the second time a (nb, it0, it1, rtol, lam) combination is used)
+// unless profiling is on.
+void cg_range(pico_ctx* c, int nb, int it0, int it1, double rtol, float lam) {
   auto direct = [&]() {
-    for (int it = 0; it < max_iter; ++it) {
+    for (int it = it0; it < it1; ++it) {
       op_cg_normal(c, nb, it, lam);
       {
         Launch L(c, 1, 2);
@@ -324,8 +330,8 @@ void cg_iterations(pico_ctx* c, int nb, int max_iter, double rtol, float lam) {
       }
     }
   };
-  if (c->profiling || !c->use_graphs || max_iter == 0) return direct();
-  const auto key = std::make_tuple(nb, max_iter, rtol, lam);
+  if (c->profiling || !c->use_graphs || it1 <= it0) return direct();
+  const auto key = std::make_tuple(nb, it0, it1, rtol, lam);
   auto itg = c->graphs.find(key);
   if (itg == c->graphs.end()) {
     if (c->seen.insert(key).second) return direct();  // first use: plain launches (sets kernel attributes)
@@ -353,6 +359,26 @@ void cg_iterations(pico_ctx* c, int nb, int max_iter, double rtol, float lam) {
   }
   cudaGraphLaunch(itg->second.first, c->stream);
   c->launches += itg->second.second;
+}
+
+// With a residual tolerance the iterations run in chunks of kStopChunk; after
+// each chunk one small kernel reports whether every system of the batch has
+// met the stopping rule (or broken down), and the host stops there -- the
+// remaining iterations would only skip converged systems.  Fixed-count
+// solves (rtol = 0) run as one range without host synchronisation.
+constexpr int kStopChunk = 4;
+void cg_iterations(pico_ctx* c, int nb, int max_iter, double rtol, float lam) {
+  c->cg.rtol2 = rtol * rtol;
+  if (!(rtol > 0.0) || !c->h_flag) return cg_range(c, nb, 0, max_iter, rtol, lam);
+  for (int it0 = 0; it0 < max_iter; it0 += kStopChunk) {
+    const int it1 = std::min(max_iter, it0 + kStopChunk);
+    cg_range(c, nb, it0, it1, rtol, lam);
+    if (it1 == max_iter) break;
+    { Launch L(c, 1); pico::launch_cg_all_done(c->cg, nb, it1, c->d_flag, c->stream); }
+    cudaMemcpyAsync(c->h_flag, c->d_flag, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess) return;
+    if (*c->h_flag) break;
+  }
 }
 
 pico_status run_cg(pico_ctx* c, int nb, int max_iter, double rtol, float lam) {
@@ -824,13 +850,20 @@ pico_status init_impl(const pico_operator_desc* d, void* cuda_stream, size_t hbm
   TRY(dalloc(c, &c->status, (size_t)B));
   TRY(dalloc(c, &c->d_iters, (size_t)B));
   TRY(dalloc(c, &c->cg_alpha, (size_t)B));
+  TRY(dalloc(c, &c->d_flag, (size_t)1));
+  TRY(dalloc(c, &c->cg_done, (size_t)B));
+  if (cudaMallocHost(&c->h_flag, sizeof(int)) != cudaSuccess) {
+    cudaGetLastError();
+    c->h_flag = nullptr;  // no early stop: tolerance-stopped solves run all max_iter iterations
+  }
   TRY(dalloc(c, &c->cg_state, (size_t)B));
   TRY(dalloc(c, &c->d_relres, (size_t)B));
   TRY(dalloc(c, &c->d_norm, (size_t)PB + 1));
   cudaMemcpyAsync(c->smaps, S.data(), S.size() * sizeof(float2), cudaMemcpyHostToDevice, c->stream);
   cudaMemsetAsync(c->status, 0, (size_t)B * sizeof(int), c->stream);
   if (!c->pa_gram) c->pa_fft = PA;
-  c->cg = pico::CgArgs{n, c->X, c->R, c->P, c->Q, c->rr_part, c->pq_part, c->status, PB, c->pa_fft, c->itmax, 0.0};
+  c->cg = pico::CgArgs{n,     c->X,      c->R,     c->P,      c->Q,   c->rr_part, c->pq_part,
+                       c->status, PB, c->pa_fft, c->itmax, 0.0, c->cg_done};
 
   if (c->mask2d) {
     TRY(cart2d_setup(c, d, img, P1, P2));
@@ -1372,6 +1405,7 @@ void pico_destroy(pico_ctx* c) {
   for (cudaEvent_t e : c->event_pool) cudaEventDestroy(e);
   for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second.first);
   if (c->cap) cudaStreamDestroy(c->cap);
+  if (c->h_flag) cudaFreeHost(c->h_flag);
   for (void* p : c->allocs) {
     if (c->async_alloc)
       cudaFreeAsync(p, c->stream);

@@ -187,6 +187,15 @@ __global__ void __launch_bounds__(kVecThreads) k_cg_update_v(CgArgs a, int it, c
   if (threadIdx.x == 0) rr_at_w(a, b, it + 1)[blockIdx.x] = s;
 }
 
+// flag = 1 when every system of the batch meets the stopping rule at iteration
+// it (or has broken down, which zeroes its r^H r); cleared by any other
+__global__ void k_cg_all_done(CgArgs a, int it, int* flag) {
+  const int b = blockIdx.x;
+  const double rr = warp_sum_parts(rr_at(a, b, it), a.PB);
+  const double rr0 = warp_sum_parts(rr_at(a, b, 0), a.PB);
+  if (threadIdx.x == 0 && rr > a.rtol2 * rr0) atomicExch(flag, 0);
+}
+
 // iterations performed and final relative residual per right-hand side
 __global__ void k_cg_report(CgArgs a, int max_iter, int* iters, double* relres) {
   const int b = blockIdx.x;
@@ -339,6 +348,10 @@ bool launch_cg_step(const CgArgs& a, int nb, int it, float* alpha, int* state, c
   k_cg_alpha<<<nb, 32, 0, s>>>(a, it, alpha, state);
   k_cg_update_v<<<dim3(a.PB, nb), kVecThreads, 0, s>>>(a, it, alpha, state);
   return true;
+}
+void launch_cg_all_done(const CgArgs& a, int nb, int it, int* flag, cudaStream_t s) {
+  cudaMemsetAsync(flag, 0xFF, sizeof(int), s);  // nonzero: all done unless a block clears it
+  k_cg_all_done<<<nb, 32, 0, s>>>(a, it, flag);
 }
 void launch_cg_report(const CgArgs& a, int nb, int max_iter, int* iters, double* relres, cudaStream_t s) {
   k_cg_report<<<nb, 32, 0, s>>>(a, max_iter, iters, relres);

@@ -27,6 +27,8 @@ struct CgArgs {
   int* status;       // [B] 0 ok, 5 breakdown
   int PB, PA, itmax;
   double rtol2;      // squared relative residual tolerance
+  int* done;         // [B] or nullptr: stop flag of the current iteration, written by the
+                     // first pass of the Toeplitz operator for the passes after it
 };
 
 // ---- cg.cu ----
@@ -37,6 +39,8 @@ void launch_cg_update(const CgArgs& a, int nb, int it, cudaStream_t s);
 // (two launches, 16-byte accesses); false (nothing launched) when n is odd
 bool launch_cg_step(const CgArgs& a, int nb, int it, float* alpha, int* state, cudaStream_t s);
 void launch_cg_report(const CgArgs& a, int nb, int max_iter, int* iters, double* relres, cudaStream_t s);
+// *flag (device) != 0 iff every one of the nb systems has stopped at iteration it
+void launch_cg_all_done(const CgArgs& a, int nb, int it, int* flag, cudaStream_t s);
 void launch_accum_pico(const float2* X, int64_t n, int nb, uint64_t seed, int64_t probe_begin, int kind,
                        double* sum, double* sumsq, cudaStream_t s);
 void launch_accum_pmr(const float2* X, int64_t n, int nb, float inv_sigma2, double* sum, double* sumsq,

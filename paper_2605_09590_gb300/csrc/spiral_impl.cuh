@@ -66,6 +66,7 @@ __global__ void __launch_bounds__(Split<P1, P2>::NT, 1)
   for (int i = t; i < L; i += NT) tws[i] = op.tw2[i];
   if (CG) cg_scalars(a, b, it, &sh_done, &sh_beta);
   __syncthreads();
+  if (CG && blockIdx.x == 0 && t == 0 && a.done) a.done[b] = sh_done;  // for the column pass
   if (CG && sh_done) return;
 
   const int ra = t / P1, n1 = t % P1;
@@ -129,8 +130,11 @@ __global__ void __launch_bounds__(Split<P1, P2>::NT, 1)
 // ---------------------------------------------------------------------------
 // Pass 2: columns of the grid: FFT (rows >= N zero), x T^, inverse FFT, rows < N
 // ---------------------------------------------------------------------------
+// done: per-image stop flags of the CG iteration (nullptr outside CG); planes of
+// converged images are skipped
 template <int P1, int P2, bool PAD>
-__global__ void __launch_bounds__(Split<P1, P2>::NT, 1) k_toep_cols(SpiralOp op, float2* __restrict__ G) {
+__global__ void __launch_bounds__(Split<P1, P2>::NT, 1)
+    k_toep_cols(SpiralOp op, float2* __restrict__ G, const int* __restrict__ done) {
   constexpr int NIN = PAD ? P2 / 2 : P2;
   constexpr int L = P1 * P2;
   constexpr int NT = Split<P1, P2>::NT;
@@ -138,6 +142,7 @@ __global__ void __launch_bounds__(Split<P1, P2>::NT, 1) k_toep_cols(SpiralOp op,
   float2* buf = reinterpret_cast<float2*>(smraw);
   float2* tws = buf + L * kLines;
   const int t = threadIdx.x, N = op.n;
+  if (done && done[blockIdx.y / op.nc]) return;
   for (int i = t; i < L; i += NT) tws[i] = op.tw2[i];
   __syncthreads();
   const int ln = t % kLines, job = t / kLines;
@@ -392,7 +397,7 @@ void toep_normal_impl(const SpiralOp& op, const float2* x, float2* y, float2* G,
   }
   auto k2 = k_toep_cols<P1, P2, PAD>;
   cudaFuncSetAttribute(k2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smc);
-  k2<<<dim3(L / kLines, nb * op.nc), Sp::NT, smc, s>>>(op, G);
+  k2<<<dim3(L / kLines, nb * op.nc), Sp::NT, smc, s>>>(op, G, a ? a->done : nullptr);
   if (a) {
     auto k3 = k_toep_rows_inv<P1, P2, true, PAD>;
     cudaFuncSetAttribute(k3, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smr);

@@ -59,12 +59,16 @@ def test_ctypes_structs_match_the_c_layout(lib):
 int main(void) {
   printf("pico_operator_desc size %zu\n", sizeof(pico_operator_desc));
   printf("pico_info size %zu\n", sizeof(pico_info));
+  printf("pico_request size %zu\n", sizeof(pico_request));
   P(pico_operator_desc, smaps) P(pico_operator_desc, noise_cov) P(pico_operator_desc, mask)
   P(pico_operator_desc, mask_2d) P(pico_operator_desc, traj) P(pico_operator_desc, nsamp)
   P(pico_operator_desc, oversamp) P(pico_operator_desc, kb_width) P(pico_operator_desc, lambda)
   P(pico_operator_desc, power_iters) P(pico_operator_desc, power_margin) P(pico_operator_desc, max_batch)
   P(pico_operator_desc, max_iter_cap)
   P(pico_info, lambda_max) P(pico_info, lambda_phys) P(pico_info, kind) P(pico_info, nsamp) P(pico_info, device_bytes)
+  P(pico_info, normal_op)
+  P(pico_request, seed) P(pico_request, nprobes) P(pico_request, rtol) P(pico_request, pmr_sigma)
+  P(pico_request, cs_data) P(pico_request, cs_lambda) P(pico_request, cs_iters) P(pico_request, cs_levels)
   return 0;
 }
 '''
@@ -81,10 +85,13 @@ int main(void) {
             got[(t, f)] = int(v)
     assert got[("pico_operator_desc", "size")] == ctypes.sizeof(pico.pico_operator_desc)
     assert got[("pico_info", "size")] == ctypes.sizeof(pico.pico_info)
+    assert got[("pico_request", "size")] == ctypes.sizeof(pico.pico_request)
+    classes = {"pico_operator_desc": pico.pico_operator_desc, "pico_info": pico.pico_info,
+               "pico_request": pico.pico_request}
     for (t, f), v in got.items():
         if f == "size":
             continue
-        cls = pico.pico_operator_desc if t == "pico_operator_desc" else pico.pico_info
+        cls = classes[t]
         name = "lambda_" if f == "lambda" else f
         assert getattr(cls, name).offset == v, (t, f)
 
