@@ -728,6 +728,7 @@ pico_status wavelet_check(pico_ctx* c, int levels) {
 pico_status cs_check(pico_ctx* c) {
   if (!c || !c->smaps) return PICO_E_INVALID;
   if (!c->cs_ready) return fail(c, PICO_E_INVALID, "run pico_cs_recon first");
+  select_path(c, 0);  // the CS iterations keep images in the natural layout
   return PICO_OK;
 }
 }  // namespace
@@ -1207,6 +1208,7 @@ pico_status pico_cs_recon(pico_ctx* c, const void* b_dev, double lambda_l1, int3
   if (st != PICO_OK) return st;
   if (!(c->lambda_max > 0.0)) return fail(c, PICO_E_INVALID, "CS needs the power-method lambda_max (power_iters > 0)");
   if ((st = cs_buffers(c)) != PICO_OK) return st;
+  select_path(c, 0);  // the CS iterations keep images in the natural layout
   if (c->cs_traj_cap < iters) {
     if ((st = dalloc(c, &c->cs_traj, (size_t)iters * c->n)) != PICO_OK) return st;
     c->cs_traj_cap = iters;

@@ -565,12 +565,16 @@ void launch_gram_normal(const GramOp& op, const CUtensorMap& mIn, const CUtensor
                         cudaStream_t s) {
   int S = 0;
   const size_t smem = gram_smem(op.ny, op.kc, &S);
-  static thread_local size_t configured[2] = {0, 0};
+  // the shared-memory opt-in is per device and kernel; cache it per (thread, device)
+  constexpr int kMaxDev = 16;
+  static thread_local size_t configured[kMaxDev][2] = {};
+  int dev = 0;
+  cudaGetDevice(&dev);
   const int ki = op.kc == 16 ? 0 : 1;
-  if (configured[ki] < smem) {
+  if (dev < 0 || dev >= kMaxDev || configured[dev][ki] < smem) {
     if (ki == 0) cudaFuncSetAttribute(k_gram_normal<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     else cudaFuncSetAttribute(k_gram_normal<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    configured[ki] = smem;
+    if (dev >= 0 && dev < kMaxDev) configured[dev][ki] = smem;
   }
   g.ny = op.ny;
   g.nx = op.nx;

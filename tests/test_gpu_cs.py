@@ -163,3 +163,23 @@ def test_cs_pmr_same_seed_matches_oracle(case64):
     xs = x.clone()
     pico.pico_cs_recon(op.ctx, dev(b), lam, 30, 4, x)
     assert torch.equal(x, xs)
+
+
+def test_cs_on_a_phase_encode_context_after_tensor_core_batches(monkeypatch):
+    # a 1-D-mask context whose CG batches ran on the tensor-core Gram operator
+    # (column-planar CG vectors) still reconstructs in the natural layout
+    monkeypatch.setenv("PICO_GRAM_MIN_BATCH", "1")
+    n, nc = 128, 4
+    S = synth.coil_maps(n, n, nc, 9)
+    mask = synth.mask_pe(n, 2, 8)
+    op = pico.Operator(S, mask=mask, power_iters=15, max_batch=8)
+    assert op.info["normal_op"] == 1
+    op.variance_sums(3, 8, 10, 0.0)
+    oop = O.Operator(S, None, mask=mask)
+    b = oop.forward(synth.phantom(n, 9).astype(np.complex128))
+    h, g = OCS.wavelet_filters(4)
+    lam = 1e-2 * np.abs(OCS.dwt2(oop.adjoint(b), 4, h, g)).max()
+    f = OCS.Fista(oop, b, lam, 20, levels=4)
+    x = torch.empty((n, n), dtype=torch.complex64, device="cuda")
+    pico.pico_cs_recon(op.ctx, dev(b), lam, 20, 4, x)
+    assert rel(x.cpu().numpy(), f.x) < 1e-4
