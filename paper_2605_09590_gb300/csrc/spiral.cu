@@ -90,10 +90,17 @@ __global__ void k_toep_finalize(const float2* c, int64_t count, float scale, flo
 
 // Gather-form Kaiser-Bessel gridding of PMR noise onto the 2n grid.
 // CTA: one 16x16 grid tile, one replica, kCoilGroup coils; thread = grid point.
+// The kernel is separable, phi(dx) phi(dy): for each staged sample the loader
+// threads evaluate the 1-D weights at the integer offsets of its window once
+// (kMaxTaps of them, zero outside |d| <= W/2), and every grid point then only
+// looks its two weights up -- no Bessel evaluation per (point, sample) pair.
 constexpr int kCoilGroup = 4;
+constexpr int kMaxTaps = 10;  // window integers for kb_width <= 8, plus one
 __global__ void __launch_bounds__(256) k_grid_pmr(SpiralOp op, float2* __restrict__ Q, uint64_t seed,
                                                   int64_t rep_begin, float sigma, const float2* __restrict__ data) {
-  __shared__ float2 s_u[kChunk];
+  __shared__ float s_wx[kChunk][kMaxTaps];
+  __shared__ float s_wy[kChunk][kMaxTaps];
+  __shared__ int2 s_o[kChunk];               // wrapped first grid index of each window (x, y)
   __shared__ float2 s_w[kChunk][kCoilGroup];
   const int L = op.L;
   const int tiles_x = L / 16;
@@ -107,13 +114,29 @@ __global__ void __launch_bounds__(256) k_grid_pmr(SpiralOp op, float2* __restric
   float2 acc[kCoilGroup];
 #pragma unroll
   for (int g = 0; g < kCoilGroup; ++g) acc[g] = make_float2(0.f, 0.f);
-  const float fL = (float)L, hw = op.halfw;
+  const float hw = op.halfw;
+  const int ntaps = min(kMaxTaps, (int)(2.f * hw) + 2);
   for (int p0 = beg; p0 < end; p0 += kChunk) {
     __syncthreads();
     const int cnt = min(kChunk, end - p0);
     if ((int)threadIdx.x < cnt) {
-      const int m = op.tile_idx[p0 + threadIdx.x];
-      s_u[threadIdx.x] = op.u[m];
+      const int i = threadIdx.x;
+      const int m = op.tile_idx[p0 + i];
+      const float2 u = op.u[m];
+      const int ix0 = (int)floorf(u.x - hw), iy0 = (int)floorf(u.y - hw);
+      for (int k = 0; k < kMaxTaps; ++k) {
+        float wx = 0.f, wy = 0.f;
+        if (k < ntaps) {
+          const float dx = (float)(ix0 + k) - u.x, dy = (float)(iy0 + k) - u.y;
+          if (fabsf(dx) <= hw)
+            wx = cyl_bessel_i0f(op.beta * sqrtf(fmaxf(0.f, 1.f - (dx / hw) * (dx / hw)))) * op.inv_i0beta;
+          if (fabsf(dy) <= hw)
+            wy = cyl_bessel_i0f(op.beta * sqrtf(fmaxf(0.f, 1.f - (dy / hw) * (dy / hw)))) * op.inv_i0beta;
+        }
+        s_wx[i][k] = wx;
+        s_wy[i][k] = wy;
+      }
+      s_o[i] = make_int2(((ix0 % L) + L) % L, ((iy0 % L) + L) % L);
       const float2 ph = op.cphase[m];
 #pragma unroll
       for (int g = 0; g < kCoilGroup; ++g) {
@@ -123,24 +146,23 @@ __global__ void __launch_bounds__(256) k_grid_pmr(SpiralOp op, float2* __restric
           const uint64_t e = (uint64_t)c * (uint64_t)op.M + (uint64_t)m;
           v = cmul(data ? data[(size_t)b * op.nc * op.M + e] : draw_cnoise(key, e, sigma), ph);
         }
-        s_w[threadIdx.x][g] = v;
+        s_w[i][g] = v;
       }
     }
     __syncthreads();
     for (int i = 0; i < cnt; ++i) {
-      const float2 u = s_u[i];
-      float dx = (float)gx - u.x, dy = (float)gy - u.y;
-      dx -= fL * rintf(dx / fL);
-      dy -= fL * rintf(dy / fL);
-      if (fabsf(dx) <= hw && fabsf(dy) <= hw) {
-        const float ax = fmaxf(0.f, 1.f - (dx / hw) * (dx / hw));
-        const float ay = fmaxf(0.f, 1.f - (dy / hw) * (dy / hw));
-        const float wgt = cyl_bessel_i0f(op.beta * sqrtf(ax)) * cyl_bessel_i0f(op.beta * sqrtf(ay)) *
-                          (op.inv_i0beta * op.inv_i0beta);
+      const int2 o = s_o[i];
+      int kx = gx - o.x, ky = gy - o.y;
+      if (kx < 0) kx += L;
+      if (ky < 0) ky += L;
+      if (kx < ntaps && ky < ntaps) {
+        const float wgt = s_wx[i][kx] * s_wy[i][ky];
+        if (wgt != 0.f) {
 #pragma unroll
-        for (int g = 0; g < kCoilGroup; ++g) {
-          acc[g].x = fmaf(wgt, s_w[i][g].x, acc[g].x);
-          acc[g].y = fmaf(wgt, s_w[i][g].y, acc[g].y);
+          for (int g = 0; g < kCoilGroup; ++g) {
+            acc[g].x = fmaf(wgt, s_w[i][g].x, acc[g].x);
+            acc[g].y = fmaf(wgt, s_w[i][g].y, acc[g].y);
+          }
         }
       }
     }
