@@ -183,3 +183,41 @@ def test_cs_on_a_phase_encode_context_after_tensor_core_batches(monkeypatch):
     x = torch.empty((n, n), dtype=torch.complex64, device="cuda")
     pico.pico_cs_recon(op.ctx, dev(b), lam, 20, 4, x)
     assert rel(x.cpu().numpy(), f.x) < 1e-4
+
+
+# ---------------------------------------------------------------------------
+# full size: 320x320, 15 correlated coils, Poisson-disc R=2, 100 FISTA
+# iterations, the benchmark's launch shape (64 probes per launch)
+# ---------------------------------------------------------------------------
+def test_full_size_cs_sampled_parity():
+    w = synth.WORKLOADS["cs320_r2"]
+    inp = w.inputs()
+    levels, iters = w.extra["levels"], w.max_iter
+    oop = O.Operator(inp["smaps"], inp["noise_cov"], mask=inp["mask"])
+    b = oop.forward(inp["phantom"].astype(np.complex128))
+    h, g = OCS.wavelet_filters(4)
+    lam = w.extra["lam_l1_rel"] * np.abs(OCS.dwt2(oop.adjoint(b), levels, h, g)).max()
+    f = OCS.Fista(oop, b, lam, iters, levels=levels)
+    op = pico.Operator(inp["smaps"], mask=inp["mask"], noise_cov=inp["noise_cov"], power_iters=15,
+                       max_batch=w.probes)
+    x = torch.empty((w.ny, w.nx), dtype=torch.complex64, device="cuda")
+    pico.pico_cs_recon(op.ctx, dev(b), lam, iters, levels, x)
+    assert rel(x.cpu().numpy(), f.x) < 2e-4            # 100 FP32 iterations
+    K, i0 = w.probes, 5
+    s64 = torch.zeros((w.ny, w.nx), dtype=torch.float64, device="cuda")
+    pico.pico_cs_variance_map(op.ctx, 77, 0, K, 0, s64)           # one launch of 64 probes
+    parts = torch.zeros_like(s64)
+    one = torch.zeros_like(s64)
+    for i in range(K):                                             # the same probes one at a time
+        pico.pico_cs_variance_map(op.ctx, 77, i, 1, 0, one)
+        parts += one
+        if i == i0:
+            probe5 = one.cpu().numpy().copy()
+    assert torch.allclose(s64, parts, rtol=1e-9, atol=0)           # batching does not change a probe
+    so, _ = OCS.pico_cs(f, 77, i0, 1)                              # one probe through the oracle
+    assert rel(probe5, so) < 1e-3
+    sigma = 0.1 * float(np.sqrt(np.mean(np.abs(b[:, inp["mask"].astype(bool)]) ** 2)))
+    pm = torch.zeros_like(s64)
+    pico.pico_cs_pmr(op.ctx, 78, 3, 1, sigma, pm)
+    po, _ = OCS.pmr_cs(f, 78, 3, 1, sigma)
+    assert rel(pm.cpu().numpy(), po) < 2e-3
