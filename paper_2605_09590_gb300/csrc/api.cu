@@ -812,30 +812,39 @@ pico_status init_impl(const pico_operator_desc* d, void* cuda_stream, size_t hbm
   }
 
   // footprint check before allocating anything
-  const size_t need = (size_t)nc * n * 8 + (size_t)4 * B * n * 8 + (size_t)B * (c->itmax + 1) * PB * 8 +
+  const size_t need = (size_t)nc * n * 8 + (size_t)nc * nc * 16 + (size_t)4 * B * n * 8 + (size_t)B * (c->itmax + 1) * PB * 8 +
                       (size_t)B * c->itmax * PA * 8 + (size_t)B * 16 + (size_t)PB * 8 + 64 + extra;
   if (hbm_budget && need > hbm_budget)
     return fail(c, PICO_E_OOM, "operator and workspace need " + std::to_string(need) + " bytes > hbm_budget");
 
-  // whitening (Eq. 3): S' = L^-1 S with L L^H = Sigma_n
-  std::vector<float2> S((size_t)nc * n);
-  std::memcpy(S.data(), d->smaps, S.size() * sizeof(float2));
+  // whitening (Eq. 3): S' = L^-1 S with L L^H = Sigma_n.  L^-1 (nc x nc) is
+  // formed on the host; the per-voxel product runs on the device (FP64) for up
+  // to pico::kWhitenMaxCoils coils, on the host beyond that.
+  std::vector<float2> S;
+  std::vector<double2> Li_dev;
   if (d->noise_cov) {
     std::vector<cd> Lc((size_t)nc * nc);
     for (int i = 0; i < nc * nc; ++i) Lc[i] = cd(d->noise_cov[2 * i], d->noise_cov[2 * i + 1]);
     if (!cholesky(Lc, nc)) return fail(c, PICO_E_INVALID, "noise_cov is not Hermitian positive definite");
     const std::vector<cd> Li = tril_inverse(Lc, nc);
-    std::vector<float2> W((size_t)nc * n);
-    std::vector<cd> col(nc);
-    for (int64_t v = 0; v < n; ++v) {
-      for (int k = 0; k < nc; ++k) col[k] = cd(S[(size_t)k * n + v].x, S[(size_t)k * n + v].y);
-      for (int i = 0; i < nc; ++i) {
-        cd acc = 0.0;
-        for (int k = 0; k <= i; ++k) acc += Li[i * nc + k] * col[k];
-        W[(size_t)i * n + v] = make_float2((float)acc.real(), (float)acc.imag());
+    if (nc <= pico::kWhitenMaxCoils) {
+      Li_dev.resize((size_t)nc * nc);
+      for (int i = 0; i < nc * nc; ++i) Li_dev[i] = make_double2(Li[i].real(), Li[i].imag());
+    } else {
+      S.resize((size_t)nc * n);
+      std::memcpy(S.data(), d->smaps, S.size() * sizeof(float2));
+      std::vector<float2> W((size_t)nc * n);
+      std::vector<cd> col(nc);
+      for (int64_t v = 0; v < n; ++v) {
+        for (int k = 0; k < nc; ++k) col[k] = cd(S[(size_t)k * n + v].x, S[(size_t)k * n + v].y);
+        for (int i = 0; i < nc; ++i) {
+          cd acc = 0.0;
+          for (int k = 0; k <= i; ++k) acc += Li[i * nc + k] * col[k];
+          W[(size_t)i * n + v] = make_float2((float)acc.real(), (float)acc.imag());
+        }
       }
+      S.swap(W);
     }
-    S.swap(W);
   }
 
   pico_status st = PICO_OK;
@@ -860,7 +869,16 @@ pico_status init_impl(const pico_operator_desc* d, void* cuda_stream, size_t hbm
   TRY(dalloc(c, &c->cg_state, (size_t)B));
   TRY(dalloc(c, &c->d_relres, (size_t)B));
   TRY(dalloc(c, &c->d_norm, (size_t)PB + 1));
-  cudaMemcpyAsync(c->smaps, S.data(), S.size() * sizeof(float2), cudaMemcpyHostToDevice, c->stream);
+  cudaMemcpyAsync(c->smaps, S.empty() ? d->smaps : static_cast<const void*>(S.data()), (size_t)nc * n * sizeof(float2),
+                  cudaMemcpyHostToDevice, c->stream);
+  if (!Li_dev.empty()) {
+    double2* li = nullptr;
+    TRY(dalloc(c, &li, Li_dev.size()));
+    cudaMemcpyAsync(li, Li_dev.data(), Li_dev.size() * sizeof(double2), cudaMemcpyHostToDevice, c->stream);
+    { Launch L(c, 3); pico::launch_whiten(c->smaps, li, nc, n, c->stream); }
+    // Li_dev lives on the host stack until the copy has run
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess) return cuda_check(c, "pico_init whitening");
+  }
   cudaMemsetAsync(c->status, 0, (size_t)B * sizeof(int), c->stream);
   if (!c->pa_gram) c->pa_fft = PA;
   c->cg = pico::CgArgs{n,     c->X,      c->R,     c->P,      c->Q,   c->rr_part, c->pq_part,
@@ -937,7 +955,7 @@ size_t footprint_bytes(const pico_operator_desc* d, bool with_kbuf) {
             (L / 16) * (L / 16) * 4 + 64;
     kbuf = B * nc * 4 * n * 8;
   }
-  const int64_t need = nc * n * 8 + 4 * B * n * 8 + B * (itmax + 1) * PB * 8 + B * itmax * PA * 8 + B * 16 +
+  const int64_t need = nc * n * 8 + nc * nc * 16 + 4 * B * n * 8 + B * (itmax + 1) * PB * 8 + B * itmax * PA * 8 + B * 16 +
                        PB * 8 + 64 + extra + (with_kbuf ? kbuf : 0);
   return (size_t)need;
 }

@@ -91,4 +91,29 @@ void launch_nufft_interp(const SpiralOp& op, const float2* G, float2* y, int nb,
   k_nufft_interp<<<dim3((unsigned)((op.M + 127) / 128), nb * op.nc), 128, 0, s>>>(op, G, y);
 }
 
+// Pre-whitening S' = L^-1 S (Eq. 3) per voxel, FP64 accumulation, in place:
+// each thread reads all coils of its voxel before writing any.
+__global__ void k_whiten(float2* __restrict__ S, const double2* __restrict__ Li, int nc, int64_t n) {
+  const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= n) return;
+  double2 col[kWhitenMaxCoils];
+  for (int k = 0; k < nc; ++k) {
+    const float2 a = S[(size_t)k * n + v];
+    col[k] = make_double2(a.x, a.y);
+  }
+  for (int i = 0; i < nc; ++i) {
+    double re = 0.0, im = 0.0;
+    for (int k = 0; k <= i; ++k) {
+      const double2 l = Li[i * nc + k], x = col[k];
+      re += l.x * x.x - l.y * x.y;
+      im += l.x * x.y + l.y * x.x;
+    }
+    S[(size_t)i * n + v] = make_float2((float)re, (float)im);
+  }
+}
+
+void launch_whiten(float2* S, const double2* Li, int nc, int64_t n, cudaStream_t s) {
+  k_whiten<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(S, Li, nc, n);
+}
+
 }  // namespace pico

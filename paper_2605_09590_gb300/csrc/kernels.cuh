@@ -31,6 +31,11 @@ struct CgArgs {
                      // first pass of the Toeplitz operator for the passes after it
 };
 
+// ---- encode.cu: pre-whitening of the sensitivities (Eq. 3) ----
+constexpr int kWhitenMaxCoils = 64;
+// S[c][v] <- sum_{k <= c} Li[c][k] S[k][v] in place, Li lower-triangular nc x nc (FP64)
+void launch_whiten(float2* S, const double2* Li, int nc, int64_t n, cudaStream_t s);
+
 // ---- cg.cu ----
 void launch_cg_init_probe(const CgArgs& a, int nb, uint64_t seed, int64_t probe_begin, int kind, cudaStream_t s);
 void launch_cg_init_rhs(const CgArgs& a, int nb, cudaStream_t s);
