@@ -523,15 +523,16 @@ bool gram_encode_g(CUtensorMap* m, float* base, int ny, int nx, int kc) {
 void launch_gram_build(const float2* smaps, const uint8_t* mask_host, int nc, int ny, int nx, float* Ghi, float* Glo,
                        double2* pbuf, cudaStream_t s) {
   // P[d] = (1/ny) sum_k m_k exp(2 pi i k d / ny), in FP64 on the host
-  std::vector<double2> P(ny);
+  std::vector<double2> P(ny), tw(ny);
   const double pi2 = 6.283185307179586476925286766559;
+  for (int e = 0; e < ny; ++e) tw[e] = make_double2(std::cos(pi2 * e / ny), std::sin(pi2 * e / ny));
   for (int d = 0; d < ny; ++d) {
     double re = 0.0, im = 0.0;
     for (int k = 0; k < ny; ++k)
       if (mask_host[k]) {
-        const int e = (int)(((int64_t)k * d) % ny);
-        re += std::cos(pi2 * e / ny);
-        im += std::sin(pi2 * e / ny);
+        const double2 w = tw[(int)(((int64_t)k * d) % ny)];
+        re += w.x;
+        im += w.y;
       }
     P[d] = make_double2(re / ny, im / ny);
   }

@@ -23,7 +23,9 @@ constexpr int kChunk = 256;   // samples staged in shared memory at a time
 // (scaled later).  Grid row gy holds dy = gy (gy < n) or gy - 2n (gy > n);
 // row/column n is zero.  One thread: one row, kStrip consecutive columns; the
 // phase of the first column is reduced in FP64, the rest follow by rotation;
-// the sums over samples are accumulated in FP64 in sample order.
+// each chunk of kChunk samples is summed in FP32 (at most kChunk unit-modulus
+// terms) and the chunk sums are accumulated in FP64 in sample order -- FP64
+// arithmetic runs at a small fraction of the FP32 rate on this part.
 __global__ void __launch_bounds__(256) k_toep_h(const float* __restrict__ traj, int64_t M, int n, float2* c) {
   __shared__ float2 s_k[kChunk];
   __shared__ float2 s_rot[kChunk];
@@ -57,6 +59,9 @@ __global__ void __launch_bounds__(256) k_toep_h(const float* __restrict__ traj, 
     __syncthreads();
     const int cnt = (int)((M - m0) < kChunk ? (M - m0) : kChunk);
     if (active) {
+      float fx[kStrip], fy[kStrip];
+#pragma unroll
+      for (int j = 0; j < kStrip; ++j) fx[j] = fy[j] = 0.f;
       for (int i = 0; i < cnt; ++i) {
         const float2 kk = s_k[i];
         double ph = ((double)kk.x * dx0 + (double)kk.y * dy) / (double)n;
@@ -67,10 +72,15 @@ __global__ void __launch_bounds__(256) k_toep_h(const float* __restrict__ traj, 
         const float2 r = s_rot[i];
 #pragma unroll
         for (int j = 0; j < kStrip; ++j) {
-          accx[j] += (double)w.x;
-          accy[j] += (double)w.y;
+          fx[j] += w.x;
+          fy[j] += w.y;
           w = cmul(w, r);
         }
+      }
+#pragma unroll
+      for (int j = 0; j < kStrip; ++j) {
+        accx[j] += (double)fx[j];
+        accy[j] += (double)fy[j];
       }
     }
   }
