@@ -190,6 +190,28 @@ def oracle_sample(w, inp, nprobe=1, nrep=1):
                                              f"{normal_ops_per_probe(w)} per probe and {w.max_iter} per replica")
 
 
+def arm_config(w, world=1):
+    """The workload description both arms print (``--impl ours`` adds the
+    values it computes on the device, such as the CS weight and noise level)."""
+    K = w.probes
+    n = w.ny * w.nx
+    if w.kind == "cs":
+        return {"workload": w.name, "ny": w.ny, "nx": w.nx, "coils": w.nc, "R": w.R,
+                "mask": f"Poisson-disc, {w.acs}x{w.acs} calibration", "noise_cov": "correlated",
+                "recon": f"L1-wavelet FISTA (db4, {w.extra['levels']} levels), {w.max_iter} iterations, "
+                         f"lambda = {w.extra['lam_l1_rel']} max|W A^H b|",
+                "probes_per_step": K, "replicas_per_step": K,
+                "unit_note": "one solve = one Jacobian-probe product J(J^T v) or one FISTA replica",
+                "l2": f"working set {6 * K * n * 8 / 1e9:.2f} GB of images + "
+                      f"{w.max_iter * n * 8 / 1e6:.0f} MB trajectory > 129 MB L2",
+                "parallelism": f"probe shards x{world}"}
+    return {"workload": w.name, "ny": w.ny, "nx": w.nx, "coils": w.nc, "R": w.R, "acs": w.acs,
+            "noise_cov": "correlated" if w.noise_corr else "white", "lambda_rel": w.lam,
+            "cg_iters": w.max_iter, "probes_per_step": K, "replicas_per_step": K,
+            "l2": f"working set {4 * K * n * 8 / 1e9:.2f} GB of CG vectors > 129 MB L2",
+            "parallelism": f"probe shards x{world}"}
+
+
 def cs_sigma(w, data_rms):
     """PMR noise level of the CS workload: ``pmr_snr_db`` below the data rms."""
     return float(data_rms) * 10.0 ** (-w.extra["pmr_snr_db"] / 20.0)
@@ -214,9 +236,7 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128", "data": "synthetic",
-        "config": {"workload": args.workload, "ny": w.ny, "nx": w.nx, "coils": w.nc, "R": w.R, "acs": w.acs,
-                   "iters": w.max_iter, "probes_per_step": w.probes if w.kind == "cs" else 1,
-                   "replicas_per_step": w.probes if w.kind == "cs" else 1},
+        "config": arm_config(w),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -565,11 +585,7 @@ def main():
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "c64", "data": "synthetic",
-        "config": {"workload": args.workload, "ny": w.ny, "nx": w.nx, "coils": w.nc, "R": w.R, "acs": w.acs,
-                   "noise_cov": "correlated" if w.noise_corr else "white", "lambda_rel": w.lam,
-                   "cg_iters": w.max_iter, "probes_per_step": K,
-                   "replicas_per_step": K, "l2": f"working set {4 * K * n * 8 / 1e9:.2f} GB of CG vectors > 129 MB L2",
-                   "parallelism": f"probe shards x{world}"},
+        "config": arm_config(w, world),
         "roofline": roof, "kernel_ms_in_timed_region": share,
         "gpu_launches": launches,
         "clocks": clk,
@@ -798,15 +814,7 @@ def main_cs(args, w, inp, torch, dist, pico, world, rank, local):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "c64", "data": "synthetic",
-        "config": {"workload": args.workload, "ny": w.ny, "nx": w.nx, "coils": w.nc, "R": w.R,
-                   "mask": f"Poisson-disc, {w.acs}x{w.acs} calibration", "noise_cov": "correlated",
-                   "recon": f"L1-wavelet FISTA (db4, {levels} levels), {iters} iterations, "
-                            f"lambda = {w.extra['lam_l1_rel']} max|W A^H b| = {lam:.4g}",
-                   "probes_per_step": K, "replicas_per_step": K, "pmr_sigma": sigma,
-                   "unit_note": "one solve = one Jacobian-probe product J(J^T v) or one FISTA replica",
-                   "l2": f"working set {6 * K * w.ny * w.nx * 8 / 1e9:.2f} GB of images + "
-                         f"{iters * img / 1e6:.0f} MB trajectory > 129 MB L2",
-                   "parallelism": f"probe shards x{world}"},
+        "config": dict(arm_config(w, world), lambda_l1=lam, pmr_sigma=sigma),
         "roofline": roof,
         "kernel_ms_in_timed_region": {"normal_op_ms": norm_ms, "cg_vector_ms": prof[1][0],
                                       "noise_adjoint_ms": prof[2][0], "elementwise_and_dwt_ms": prof[3][0]},
