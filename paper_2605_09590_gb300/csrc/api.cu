@@ -689,9 +689,7 @@ size_t gram_extra_bytes(const pico_operator_desc* d, int64_t B) {
 
 pico_status gram_setup(pico_ctx* c, const pico_operator_desc* d) {
   pico_status st = PICO_OK;
-  const size_t half = pico::gram_bytes(c->ny, c->nx) / 2 / sizeof(float);
-  if ((st = dalloc(c, &c->gop.Ghi, half)) != PICO_OK) return st;
-  if ((st = dalloc(c, &c->gop.Glo, half)) != PICO_OK) return st;
+  if ((st = dalloc(c, &c->gop.G, pico::gram_bytes(c->ny, c->nx) / sizeof(float))) != PICO_OK) return st;
   if ((st = dalloc(c, &c->P2, (size_t)2 * c->max_batch * c->n)) != PICO_OK) return st;
   if ((st = dalloc(c, &c->g_beta, (size_t)c->max_batch)) != PICO_OK) return st;
   if ((st = dalloc(c, &c->g_done, (size_t)c->max_batch)) != PICO_OK) return st;
@@ -704,12 +702,14 @@ pico_status gram_setup(pico_ctx* c, const pico_operator_desc* d) {
   c->gop.nt = pico::gram_tile(c->ny);
   c->gop.kc = 16;
   if (const char* e = std::getenv("PICO_GRAM_KC")) c->gop.kc = std::atoi(e) == 8 ? 8 : 16;
+  // the direction's split can also be staged in tensor memory (measured about
+  // 1 % slower than shared memory on the 320 x 320 knee operator; kept as an option)
+  c->gop.a_tmem = 0;
+  if (const char* e = std::getenv("PICO_GRAM_ATMEM")) c->gop.a_tmem = std::atoi(e) != 0;
   const int kc = c->gop.kc;
-  pico::launch_gram_build(c->smaps, d->mask, c->nc, c->ny, c->nx, c->gop.Ghi, c->gop.Glo, c->g_pbuf, c->stream);
+  pico::launch_gram_build(c->smaps, d->mask, c->nc, c->gop, c->g_pbuf, c->stream);
   const int B = c->max_batch;
-  const bool ok = pico::gram_encode_g(&c->gop.mGhi, c->gop.Ghi, c->ny, c->nx, kc) &&
-                  pico::gram_encode_g(&c->gop.mGlo, c->gop.Glo, c->ny, c->nx, kc) &&
-                  pico::gram_encode_x(&c->mR, cpf(c->R), c->ny, c->nx, B, kc) &&
+  const bool ok = pico::gram_encode_x(&c->mR, cpf(c->R), c->ny, c->nx, B, kc) &&
                   pico::gram_encode_x(&c->mX, cpf(c->X), c->ny, c->nx, B, kc) &&
                   pico::gram_encode_x(&c->mP0, cpf(c->P), c->ny, c->nx, B, kc) &&
                   pico::gram_encode_x(&c->mP1, c->P2, c->ny, c->nx, B, kc);

@@ -59,10 +59,23 @@ __device__ __forceinline__ void set_err(int* err, int code) {
 }
 
 // ---------------------------------------------------------------------------
-// set-up: G_j split into TF32 head and remainder, layout [j][re|im][y][y']
+// set-up: G_j split into TF32 head and remainder, stored stage-tiled
 // ---------------------------------------------------------------------------
+// Position of G_j[y, y'] (plane q: 0 re head, 1 im head, 2 re remainder, 3 im
+// remainder) in the stage-tiled layout: block (j, y tile, chunk of kc values
+// of y') holds the four planes of nt rows x kc values exactly as one pipeline
+// stage holds them in shared memory, the 16-byte groups of a row swizzled
+// (64-byte swizzle for kc = 16, 32-byte for kc = 8), so that one bulk copy
+// fills the B operand of a stage.
+__device__ __forceinline__ size_t gt_offset(int j, int y, int yp, int q, int ny, int nt, int kc) {
+  const int t = y / nt, r = y - t * nt, c = yp / kc, e = yp - c * kc;
+  const int grp = e >> 2, phys = kc == 16 ? (grp ^ ((r >> 1) & 3)) : (grp ^ ((r >> 2) & 1));
+  return ((((size_t)j * (ny / nt) + t) * (ny / kc) + c) * 4 + q) * (size_t)nt * kc + (size_t)r * kc + 4 * phys +
+         (e & 3);
+}
+
 __global__ void k_gram_build(const float2* __restrict__ S, const double2* __restrict__ P, int nc, int ny, int nx,
-                             float* __restrict__ Ghi, float* __restrict__ Glo) {
+                             int nt, int kc, float* __restrict__ G) {
   const int j = blockIdx.y;
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= (int64_t)ny * ny) return;
@@ -79,22 +92,20 @@ __global__ void k_gram_build(const float2* __restrict__ S, const double2* __rest
   if (d < 0) d += ny;
   const double2 p = P[d];
   const double gr = p.x * re - p.y * im, gi = p.x * im + p.y * re;
-  const size_t plane = (size_t)ny * ny;
-  const size_t o = (size_t)j * 2 * plane + (size_t)y * ny + yp;
   float hr, lr, hi_, li;
   split_tf32((float)gr, hr, lr);
   split_tf32((float)gi, hi_, li);
-  Ghi[o] = hr;
-  Ghi[o + plane] = hi_;
-  Glo[o] = (float)(gr - (double)hr);
-  Glo[o + plane] = (float)(gi - (double)hi_);
+  G[gt_offset(j, y, yp, 0, ny, nt, kc)] = hr;
+  G[gt_offset(j, y, yp, 1, ny, nt, kc)] = hi_;
+  G[gt_offset(j, y, yp, 2, ny, nt, kc)] = (float)(gr - (double)hr);
+  G[gt_offset(j, y, yp, 3, ny, nt, kc)] = (float)(gi - (double)hi_);
 }
 
 // The same G_j with the sensitivities of column j staged in shared memory
 // (block = column j x 32 output rows; all y' per block).
 __global__ void __launch_bounds__(256) k_gram_build_smem(const float2* __restrict__ S, const double2* __restrict__ P,
-                                                         int nc, int ny, int nx, float* __restrict__ Ghi,
-                                                         float* __restrict__ Glo) {
+                                                         int nc, int ny, int nx, int nt, int kc,
+                                                         float* __restrict__ G) {
   extern __shared__ float2 sc[];  // [nc][ny] sensitivities of column j
   const int j = blockIdx.x, y_lo = blockIdx.y * 32;
   const int64_t n = (int64_t)ny * nx;
@@ -103,7 +114,6 @@ __global__ void __launch_bounds__(256) k_gram_build_smem(const float2* __restric
     sc[i] = S[c * n + (int64_t)y * nx + j];
   }
   __syncthreads();
-  const size_t plane = (size_t)ny * ny;
   for (int t = threadIdx.x; t < 32 * ny; t += blockDim.x) {
     const int y = y_lo + t / ny, yp = t % ny;
     if (y >= ny) break;
@@ -126,14 +136,13 @@ __global__ void __launch_bounds__(256) k_gram_build_smem(const float2* __restric
     const double2 p = P[d];
     const float px = (float)p.x, py = (float)p.y;
     const float gr = fmaf(px, re, -py * im), gi = fmaf(px, im, py * re);
-    const size_t o = (size_t)j * 2 * plane + (size_t)y * ny + yp;
     float hr, lr, hi_, li;
     split_tf32(gr, hr, lr);
     split_tf32(gi, hi_, li);
-    Ghi[o] = hr;
-    Ghi[o + plane] = hi_;
-    Glo[o] = lr;
-    Glo[o + plane] = li;
+    G[gt_offset(j, y, yp, 0, ny, nt, kc)] = hr;
+    G[gt_offset(j, y, yp, 1, ny, nt, kc)] = hi_;
+    G[gt_offset(j, y, yp, 2, ny, nt, kc)] = lr;
+    G[gt_offset(j, y, yp, 3, ny, nt, kc)] = li;
   }
 }
 
@@ -205,10 +214,16 @@ __global__ void k_from_cp(const float* __restrict__ in, float2* __restrict__ out
 //   B: [G_re hi | G_im hi | G_re lo | G_im lo] NT x 16 fp32 each
 // and D_re (columns 0..NT-1), D_im (NT..2NT-1) accumulate in tensor memory:
 //   D_re += p_re G_re^T - p_im G_im^T,  D_im += p_re G_im^T + p_im G_re^T.
-template <int KC>
+// With AT (tiles with 2 NT + 4 KC S <= 512 tensor-memory columns) the split
+// direction goes to tensor memory instead, [p_re hi | p_im hi | p_re lo |
+// p_im lo] KC columns each per stage from column 2 NT, one image per lane,
+// and the MMAs read A from there: shared memory then carries only the TMA
+// tiles and the B operand reads, which keeps the tensor pipe, not the
+// shared-memory bandwidth, the limit of the main loop.
+template <int KC, bool AT>
 __global__ void __launch_bounds__(kGramThreads, 1)
     k_gram_normal(const __grid_constant__ CUtensorMap mIn, const __grid_constant__ CUtensorMap mPold,
-                  const __grid_constant__ CUtensorMap mGhi, const __grid_constant__ CUtensorMap mGlo, GramArgs g) {
+                  const __grid_constant__ CUtensorMap mPe, const __grid_constant__ CUtensorMap mQe, GramArgs g) {
   extern __shared__ uint8_t smraw[];
   uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smraw) + 1023) & ~(uintptr_t)1023);
   const int NT = g.nt, S = g.stages;
@@ -221,8 +236,8 @@ __global__ void __launch_bounds__(kGramThreads, 1)
   uint64_t* conv = bars + S;
   uint64_t* empty = bars + 2 * S;
   uint64_t* accf = bars + 3 * S;
-  uint64_t* pbar = bars + 3 * S + 1;   // epilogue staging of p, one phase per pass
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + 3 * S + 2);
+  uint64_t* pbar = bars + 3 * S + 1;   // epilogue staging of p: up to 8 buffers, one phase per use
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + 3 * S + 9);
   float* beta_s = reinterpret_cast<float*>(tslot + 4);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -231,6 +246,24 @@ __global__ void __launch_bounds__(kGramThreads, 1)
   const int nkc = g.ny / KC;
   const bool use_pold = g.cg && g.it > 0;
 
+  auto slotA = [&](int s, int q) { return sm + (size_t)s * stage_bytes + (size_t)q * kATile; };
+  auto slotB = [&](int s, int q) { return sm + (size_t)s * stage_bytes + 4 * kATile + (size_t)q * btile; };
+  // one stage: the A inputs by TMA (r, and p_old after the first iteration),
+  // the stage-tiled B block of G_j by one bulk copy
+  const uint32_t stage_tx = (use_pold ? 4u : 2u) * kATile + 4u * btile;
+  const float* gsrc = g.G + ((size_t)j * g.nyt + ytile) * nkc * 4 * NT * KC;
+  auto issue = [&](int kc) {
+    const int s = kc % S, y0 = kc * KC;
+    mbar_expect_tx(&full[s], stage_tx);
+    tma_load_4d(slotA(s, 0), &mIn, &full[s], y0, 0, j, m0);
+    tma_load_4d(slotA(s, 1), &mIn, &full[s], y0, 1, j, m0);
+    if (use_pold) {
+      tma_load_4d(slotA(s, 2), &mPold, &full[s], y0, 0, j, m0);
+      tma_load_4d(slotA(s, 3), &mPold, &full[s], y0, 1, j, m0);
+    }
+    bulk_load(slotB(s, 0), gsrc + (size_t)kc * 4 * NT * KC, 4u * btile, &full[s]);
+  };
+
   if (threadIdx.x == 0) {
     for (int s = 0; s < S; ++s) {
       mbar_init(&full[s], 1);
@@ -238,8 +271,18 @@ __global__ void __launch_bounds__(kGramThreads, 1)
       mbar_init(&empty[s], 1);
     }
     mbar_init(accf, 1);
-    mbar_init(pbar, 1);
+    if (g.tma_epi) {
+      for (int b = 0; b < 8; ++b) mbar_init(&pbar[b], 1);
+    } else {
+      mbar_init(&pbar[0], 128);
+      mbar_init(&pbar[1], 128);
+    }
     fence_mbar_init();
+    // the first S stages need no free-slot wait: start them before the
+    // tensor-memory allocation and the block-wide barrier
+    tma_prefetch_desc(&mIn);
+    if (use_pold) tma_prefetch_desc(&mPold);
+    for (int kc = 0; kc < S && kc < nkc; ++kc) issue(kc);
   }
   if (warp >= 2) {
     const int r = threadIdx.x - 64;
@@ -252,36 +295,14 @@ __global__ void __launch_bounds__(kGramThreads, 1)
   tc_fence_after();
   const uint32_t tbase = *tslot;
 
-  auto slotA = [&](int s, int q) { return sm + (size_t)s * stage_bytes + (size_t)q * kATile; };
-  auto slotB = [&](int s, int q) { return sm + (size_t)s * stage_bytes + 4 * kATile + (size_t)q * btile; };
-
   if (warp == 0) {
     if (lane == 0) {
-      tma_prefetch_desc(&mIn);
-      tma_prefetch_desc(&mGhi);
-      tma_prefetch_desc(&mGlo);
-      if (use_pold) tma_prefetch_desc(&mPold);
-      const uint32_t bytes = (use_pold ? 4u : 2u) * kATile + 4u * btile;
-      bool ok = true;
-      for (int kc = 0; kc < nkc && ok; ++kc) {
-        const int s = kc % S;
-        if (kc >= S && !mbar_wait(&empty[s], ((kc / S) - 1) & 1)) {
+      for (int kc = S; kc < nkc; ++kc) {
+        if (!mbar_wait(&empty[kc % S], ((kc / S) - 1) & 1)) {
           set_err(g.err, 1);
-          ok = false;
           break;
         }
-        mbar_expect_tx(&full[s], bytes);
-        const int y0 = kc * KC;
-        tma_load_4d(slotA(s, 0), &mIn, &full[s], y0, 0, j, m0);
-        tma_load_4d(slotA(s, 1), &mIn, &full[s], y0, 1, j, m0);
-        if (use_pold) {
-          tma_load_4d(slotA(s, 2), &mPold, &full[s], y0, 0, j, m0);
-          tma_load_4d(slotA(s, 3), &mPold, &full[s], y0, 1, j, m0);
-        }
-        tma_load_4d(slotB(s, 0), &mGhi, &full[s], y0, n0, 0, j);
-        tma_load_4d(slotB(s, 1), &mGhi, &full[s], y0, n0, 1, j);
-        tma_load_4d(slotB(s, 2), &mGlo, &full[s], y0, n0, 0, j);
-        tma_load_4d(slotB(s, 3), &mGlo, &full[s], y0, n0, 1, j);
+        issue(kc);
       }
     }
   } else if (warp == 1) {
@@ -295,6 +316,33 @@ __global__ void __launch_bounds__(kGramThreads, 1)
           break;
         }
         tc_fence_after();
+        if constexpr (AT) {
+          const uint32_t a0 = tbase + 2u * NT + (uint32_t)(s * 4 * KC);
+          const uint32_t bhr = smem_u32(slotB(s, 0)), bhi = smem_u32(slotB(s, 1));
+          const uint32_t blr = smem_u32(slotB(s, 2)), bli = smem_u32(slotB(s, 3));
+#pragma unroll
+          for (int kk = 0; kk < KC / 8; ++kk) {
+            const uint32_t o = 32u * kk, c = 8u * kk;
+            const uint32_t acc0 = (kc == 0 && kk == 0) ? 0u : 1u;
+            const uint32_t Ahr = a0 + c, Ahi = a0 + KC + c, Alr = a0 + 2 * KC + c, Ali = a0 + 3 * KC + c;
+            const uint64_t Bhr = T::desc(bhr + o), Bhi = T::desc(bhi + o);
+            const uint64_t Blr = T::desc(blr + o), Bli = T::desc(bli + o);
+            mma_tf32_ts(dre, Ahr, Bhr, id, acc0);
+            mma_tf32_ts(dre, Ahr, Blr, id, 1);
+            mma_tf32_ts(dre, Alr, Bhr, id, 1);
+            mma_tf32_ts(dre, Ahi, Bhi, idn, 1);
+            mma_tf32_ts(dre, Ahi, Bli, idn, 1);
+            mma_tf32_ts(dre, Ali, Bhi, idn, 1);
+            mma_tf32_ts(dim, Ahr, Bhi, id, acc0);
+            mma_tf32_ts(dim, Ahr, Bli, id, 1);
+            mma_tf32_ts(dim, Alr, Bhi, id, 1);
+            mma_tf32_ts(dim, Ahi, Bhr, id, 1);
+            mma_tf32_ts(dim, Ahi, Blr, id, 1);
+            mma_tf32_ts(dim, Ali, Bhr, id, 1);
+          }
+          mma_commit(&empty[s]);
+          continue;
+        }
         const uint32_t ahr = smem_u32(slotA(s, 0)), ahi = smem_u32(slotA(s, 1));
         const uint32_t alr = smem_u32(slotA(s, 2)), ali = smem_u32(slotA(s, 3));
         const uint32_t bhr = smem_u32(slotB(s, 0)), bhi = smem_u32(slotB(s, 1));
@@ -334,6 +382,66 @@ __global__ void __launch_bounds__(kGramThreads, 1)
     const int kc_lo = n0 / KC, kc_hi = (n0 + NT) / KC;
     const size_t img2 = (size_t)2 * g.ny * g.nx;
     bool ok = true;
+    if constexpr (AT) {
+      // one image per thread: row = tensor-memory lane of this warp's quarter
+      const int rowi = 32 * (warp & 3) + lane, kimg = m0 + rowi;
+      const float b = beta_s[rowi];
+      const uint32_t tl = tbase + ((uint32_t)(32 * (warp & 3)) << 16) + 2u * NT;
+      float* pdst = (g.pnew && kimg < g.nb) ? g.pnew + (size_t)kimg * img2 + (size_t)j * 2 * g.ny : nullptr;
+      for (int kc = 0; kc < nkc; ++kc) {
+        const int s = kc % S;
+        if (ok && !mbar_wait(&full[s], (kc / S) & 1)) {
+          set_err(g.err, 3);
+          ok = false;
+        }
+        ok = __all_sync(0xffffffffu, ok);  // the tensor-memory stores are warp-collective
+        tc_fence_after();
+        if (ok) {
+          const float4* r_re = reinterpret_cast<const float4*>(slotA(s, 0)) + rowi * (KC / 4);
+          const float4* r_im = reinterpret_cast<const float4*>(slotA(s, 1)) + rowi * (KC / 4);
+          const float4* o_re = reinterpret_cast<const float4*>(slotA(s, 2)) + rowi * (KC / 4);
+          const float4* o_im = reinterpret_cast<const float4*>(slotA(s, 3)) + rowi * (KC / 4);
+          float vr[KC], vi[KC];
+#pragma unroll
+          for (int c = 0; c < KC / 4; ++c) {
+            const int ph = T::chunk(c, rowi);  // the swizzle is an involution
+            float4 a = r_re[ph], d = r_im[ph];
+            if (use_pold) {
+              const float4 w = o_re[ph], u = o_im[ph];
+              a.x = fmaf(b, w.x, a.x); a.y = fmaf(b, w.y, a.y); a.z = fmaf(b, w.z, a.z); a.w = fmaf(b, w.w, a.w);
+              d.x = fmaf(b, u.x, d.x); d.y = fmaf(b, u.y, d.y); d.z = fmaf(b, u.z, d.z); d.w = fmaf(b, u.w, d.w);
+            }
+            vr[4 * c] = a.x; vr[4 * c + 1] = a.y; vr[4 * c + 2] = a.z; vr[4 * c + 3] = a.w;
+            vi[4 * c] = d.x; vi[4 * c + 1] = d.y; vi[4 * c + 2] = d.z; vi[4 * c + 3] = d.w;
+            if (pdst && kc >= kc_lo && kc < kc_hi) {
+              reinterpret_cast<float4*>(pdst + kc * KC)[c] = a;
+              reinterpret_cast<float4*>(pdst + g.ny + kc * KC)[c] = d;
+            }
+          }
+          float hr[KC], lr[KC], hi_[KC], li[KC];
+#pragma unroll
+          for (int i = 0; i < KC; ++i) {
+            split_tf32(vr[i], hr[i], lr[i]);
+            split_tf32(vi[i], hi_[i], li[i]);
+          }
+          const uint32_t ta = tl + (uint32_t)(s * 4 * KC);
+          if constexpr (KC == 16) {
+            tmem_st16(ta, hr);
+            tmem_st16(ta + KC, hi_);
+            tmem_st16(ta + 2 * KC, lr);
+            tmem_st16(ta + 3 * KC, li);
+          } else {
+            tmem_st8(ta, hr);
+            tmem_st8(ta + KC, hi_);
+            tmem_st8(ta + 2 * KC, lr);
+            tmem_st8(ta + 3 * KC, li);
+          }
+          tmem_wait_st();
+        }
+        tc_fence_before();
+        mbar_arrive(&conv[s]);
+      }
+    } else
     for (int kc = 0; kc < nkc; ++kc) {
       const int s = kc % S;
       if (ok && !mbar_wait(&full[s], (kc / S) & 1)) {
@@ -384,8 +492,13 @@ __global__ void __launch_bounds__(kGramThreads, 1)
     // ---- epilogue ----
     // p of this CTA's rows (stored above by the split warps, or the input x in
     // apply mode) is staged into the now idle pipeline buffers by bulk copies,
-    // [row][re|im][W] with a 16-byte pad per row (conflict-free row reads),
-    // in passes of W output rows.
+    // [row][re|im][W] with a 16-byte pad per row (conflict-free row reads), in
+    // passes of W output rows over two buffers: the next pass's p arrives, and
+    // the previous pass's q leaves, while a pass computes.  Each thread
+    // overwrites its row with q and stores it back with two contiguous bulk
+    // copies (one image per thread, so direct stores would touch 32 cache
+    // lines per warp instruction).  Rows are private to their thread, so a
+    // buffer is reloaded as soon as its own thread's stores have read it.
     fence_proxy_async_global();
     __threadfence_block();
     asm volatile("bar.sync 1, 128;" ::: "memory");
@@ -399,33 +512,110 @@ __global__ void __launch_bounds__(kGramThreads, 1)
     const bool valid = accok && inb && !(g.cg && g.done[k]);
     const size_t col = (size_t)(inb ? k : 0) * img2 + (size_t)j * 2 * g.ny;
     const float* psrc = g.cg ? g.pnew : g.in;
-    const int rows_in = min(kGramRows, g.nb - m0);
-    int W = NT;
-    while ((size_t)kGramRows * (8u * W + 16u) > (size_t)S * stage_bytes) W -= 16;
-    const uint32_t pitch = 8u * W + 16u;
-    float* prow = reinterpret_cast<float*>(sm + (size_t)row * pitch);
-    double pq = 0.0;
-    int pphase = 0;
-    for (int w0 = 0; w0 < NT; w0 += W, pphase ^= 1) {
-      const int wn = min(W, NT - w0);
-      if (row == 0) mbar_expect_tx(pbar, (uint32_t)rows_in * 8u * wn);
-      asm volatile("bar.sync 1, 128;" ::: "memory");
-      if (accok && inb) {
-        bulk_load(prow, psrc + col + n0 + w0, 4u * wn, pbar);
-        bulk_load(prow + W, psrc + col + g.ny + n0 + w0, 4u * wn, pbar);
+    if (g.tma_epi) {
+      // Passes of 32 output rows: p re / im of the 128 images arrive as two
+      // 128-byte-swizzled tensor tiles (rows = images), q overwrites them in
+      // place and leaves by two tensor stores; as many passes as fit are in
+      // flight at once.  The maps cover exactly this launch's nb images, so
+      // rows past the batch are neither read nor written.
+      constexpr uint32_t kPlane = kGramRows * 128;
+      const int ng = NT / 32;
+      const int nbuf = min(min(ng, 8), (int)((size_t)S * stage_bytes / (2 * kPlane)));
+      const bool leader = threadIdx.x == 64;
+      auto ebuf = [&](int gi) { return sm + (size_t)(gi % nbuf) * 2 * kPlane; };
+      auto eload = [&](int gi) {
+        uint64_t* b = &pbar[gi % nbuf];
+        mbar_expect_tx(b, 2 * kPlane);
+        tma_load_4d(ebuf(gi), &mPe, b, n0 + 32 * gi, 0, j, m0);
+        tma_load_4d(ebuf(gi) + kPlane, &mPe, b, n0 + 32 * gi, 1, j, m0);
+      };
+      if (leader && accok)
+        for (int gi = 0; gi < nbuf; ++gi) eload(gi);
+      double pq = 0.0;
+      const int sw = row & 7;  // 16-byte group swizzle of this row
+      for (int gi = 0; gi < ng; ++gi) {
+        const bool pok = accok && mbar_wait(&pbar[gi % nbuf], (gi / nbuf) & 1);
+        if (accok && !pok) set_err(g.err, 5);
+        float4* pre = reinterpret_cast<float4*>(ebuf(gi) + (size_t)row * 128);
+        float4* pim = reinterpret_cast<float4*>(ebuf(gi) + kPlane + (size_t)row * 128);
+        const uint32_t ta = tbase + ((uint32_t)(32 * quarter) << 16) + (uint32_t)(32 * gi);
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          float dr[16], di[16];
+          tmem_ld16x2(ta + 16 * h, ta + (uint32_t)NT + 16 * h, dr, di);
+          if (valid && pok) {
+            float acc = 0.f;  // p^H q over these 16 rows in FP32, then summed in FP64
+#pragma unroll
+            for (int v = 0; v < 4; ++v) {
+              const int ph = (4 * h + v) ^ sw;
+              const float4 pr = pre[ph], pi = pim[ph];
+              float4 qr, qi;
+              qr.x = fmaf(g.lam, pr.x, dr[4 * v + 0]); qr.y = fmaf(g.lam, pr.y, dr[4 * v + 1]);
+              qr.z = fmaf(g.lam, pr.z, dr[4 * v + 2]); qr.w = fmaf(g.lam, pr.w, dr[4 * v + 3]);
+              qi.x = fmaf(g.lam, pi.x, di[4 * v + 0]); qi.y = fmaf(g.lam, pi.y, di[4 * v + 1]);
+              qi.z = fmaf(g.lam, pi.z, di[4 * v + 2]); qi.w = fmaf(g.lam, pi.w, di[4 * v + 3]);
+              pre[ph] = qr;
+              pim[ph] = qi;
+              acc = fmaf(pr.x, qr.x, acc); acc = fmaf(pr.y, qr.y, acc);
+              acc = fmaf(pr.z, qr.z, acc); acc = fmaf(pr.w, qr.w, acc);
+              acc = fmaf(pi.x, qi.x, acc); acc = fmaf(pi.y, qi.y, acc);
+              acc = fmaf(pi.z, qi.z, acc); acc = fmaf(pi.w, qi.w, acc);
+            }
+            pq += (double)acc;
+          }
+        }
+        // every row of this pass is written before one thread stores the tiles
+        // (rows of converged images still hold p: the CG update skips them)
+        fence_proxy_async_smem();
+        asm volatile("bar.sync 1, 128;" ::: "memory");
+        if (leader && pok) {
+          tma_store_4d(&mQe, ebuf(gi), n0 + 32 * gi, 0, j, m0);
+          tma_store_4d(&mQe, ebuf(gi) + kPlane, n0 + 32 * gi, 1, j, m0);
+          bulk_commit();
+          if (gi + nbuf < ng) {
+            bulk_wait_read();
+            eload(gi + nbuf);
+          }
+        }
       }
-      const bool pok = mbar_wait(pbar, pphase);
+      if (leader) bulk_wait_read();
+      if (valid && g.pq) g.pq[((size_t)k * g.itmax + g.it) * g.PA + (size_t)j * g.nyt + ytile] = pq;
+    } else {
+    int W2 = NT;  // widest pass for which two buffers fit
+    while (W2 > 16 && 2 * (size_t)kGramRows * (8u * W2 + 16u) > (size_t)S * stage_bytes) W2 -= 16;
+    const int np = (NT + W2 - 1) / W2;
+    const int W = ((NT + np - 1) / np + 15) / 16 * 16;
+    const uint32_t pitch = 8u * W + 16u;
+    auto rowbuf = [&](int i) { return reinterpret_cast<float*>(sm + ((size_t)(i & 1) * kGramRows + row) * pitch); };
+    auto stage_p = [&](int i) {
+      // every thread arrives once per use, announcing its own bytes before
+      // issuing them
+      const int w0 = i * W, wn = min(W, NT - w0);
+      if (accok && inb) {
+        float* pr = rowbuf(i);
+        mbar_expect_tx(&pbar[i & 1], 8u * wn);
+        bulk_load(pr, psrc + col + n0 + w0, 4u * wn, &pbar[i & 1]);
+        bulk_load(pr + W, psrc + col + g.ny + n0 + w0, 4u * wn, &pbar[i & 1]);
+      } else {
+        mbar_arrive(&pbar[i & 1]);
+      }
+    };
+    stage_p(0);
+    if (np > 1) stage_p(1);
+    double pq = 0.0;
+    for (int i = 0; i < np; ++i) {
+      const int w0 = i * W, wn = min(W, NT - w0);
+      const bool pok = mbar_wait(&pbar[i & 1], (i >> 1) & 1);
       if (!pok) set_err(g.err, 5);
-      __syncwarp();
+      float* prow = rowbuf(i);
       for (int c = 0; c < wn / 16; ++c) {
         float dr[16], di[16];
         const uint32_t ta = tbase + ((uint32_t)(32 * quarter) << 16) + (uint32_t)(w0 + 16 * c);
-        tmem_ld16(ta, dr);
-        tmem_ld16(ta + (uint32_t)NT, di);
+        tmem_ld16x2(ta, ta + (uint32_t)NT, dr, di);
         if (valid && pok) {
-          const int y0 = n0 + w0 + 16 * c;
-          const float4* pr4 = reinterpret_cast<const float4*>(prow + 16 * c);
-          const float4* pi4 = reinterpret_cast<const float4*>(prow + W + 16 * c);
+          float4* pr4 = reinterpret_cast<float4*>(prow + 16 * c);
+          float4* pi4 = reinterpret_cast<float4*>(prow + W + 16 * c);
+          float acc = 0.f;  // p^H q over these 16 rows in FP32, then summed in FP64
 #pragma unroll
           for (int v = 0; v < 4; ++v) {
             const float4 pr = pr4[v], pi = pi4[v];
@@ -434,21 +624,31 @@ __global__ void __launch_bounds__(kGramThreads, 1)
             qr.z = fmaf(g.lam, pr.z, dr[4 * v + 2]); qr.w = fmaf(g.lam, pr.w, dr[4 * v + 3]);
             qi.x = fmaf(g.lam, pi.x, di[4 * v + 0]); qi.y = fmaf(g.lam, pi.y, di[4 * v + 1]);
             qi.z = fmaf(g.lam, pi.z, di[4 * v + 2]); qi.w = fmaf(g.lam, pi.w, di[4 * v + 3]);
-            reinterpret_cast<float4*>(g.q + col + y0)[v] = qr;
-            reinterpret_cast<float4*>(g.q + col + g.ny + y0)[v] = qi;
-            float acc = 0.f;
+            pr4[v] = qr;
+            pi4[v] = qi;
             acc = fmaf(pr.x, qr.x, acc); acc = fmaf(pr.y, qr.y, acc);
             acc = fmaf(pr.z, qr.z, acc); acc = fmaf(pr.w, qr.w, acc);
             acc = fmaf(pi.x, qi.x, acc); acc = fmaf(pi.y, qi.y, acc);
             acc = fmaf(pi.z, qi.z, acc); acc = fmaf(pi.w, qi.w, acc);
-            pq += (double)acc;
           }
+          pq += (double)acc;
         }
       }
-      // every row of this pass has been read before the next pass overwrites it
-      asm volatile("bar.sync 1, 128;" ::: "memory");
+      if (valid && pok) {
+        fence_proxy_async_smem();
+        bulk_store(g.q + col + n0 + w0, prow, 4u * wn);
+        bulk_store(g.q + col + g.ny + n0 + w0, prow + W, 4u * wn);
+        bulk_commit();
+      }
+      if (i + 2 < np) {
+        bulk_wait_read();  // this thread's row of buffer i & 1 has been stored
+        stage_p(i + 2);
+      }
     }
+    bulk_wait_read();  // shared memory is read by the stores before the block exits
+
     if (valid && g.pq) g.pq[((size_t)k * g.itmax + g.it) * g.PA + (size_t)j * g.nyt + ytile] = pq;
+    }
   }
 
   // teardown: every TMA issued has been consumed by the split warps (or they
@@ -508,20 +708,20 @@ bool gram_encode_x(CUtensorMap* m, float* base, int ny, int nx, int B, int kc) {
              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-bool gram_encode_g(CUtensorMap* m, float* base, int ny, int nx, int kc) {
+bool gram_encode_e(CUtensorMap* m, float* base, int ny, int nx, int B) {
   EncodeTiledFn enc = encode_fn();
-  if (!enc) return false;
-  const int nt = gram_tile(ny);
-  cuuint64_t dims[4] = {(cuuint64_t)ny, (cuuint64_t)ny, 2, (cuuint64_t)nx};
-  cuuint64_t strides[3] = {(cuuint64_t)ny * 4, (cuuint64_t)ny * ny * 4, (cuuint64_t)2 * ny * ny * 4};
-  cuuint32_t box[4] = {(cuuint32_t)kc, (cuuint32_t)nt, 1, 1}, es[4] = {1, 1, 1, 1};
+  if (!enc || !base || (reinterpret_cast<uintptr_t>(base) & 15)) return false;
+  cuuint64_t dims[4] = {(cuuint64_t)ny, 2, (cuuint64_t)nx, (cuuint64_t)B};
+  cuuint64_t strides[3] = {(cuuint64_t)ny * 4, (cuuint64_t)2 * ny * 4, (cuuint64_t)2 * ny * nx * 4};
+  cuuint32_t box[4] = {32, 1, 1, kGramRows}, es[4] = {1, 1, 1, 1};
   return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, base, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
-             kc == 16 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_32B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+             CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-void launch_gram_build(const float2* smaps, const uint8_t* mask_host, int nc, int ny, int nx, float* Ghi, float* Glo,
-                       double2* pbuf, cudaStream_t s) {
+void launch_gram_build(const float2* smaps, const uint8_t* mask_host, int nc, const GramOp& op, double2* pbuf,
+                       cudaStream_t s) {
+  const int ny = op.ny, nx = op.nx;
   // P[d] = (1/ny) sum_k m_k exp(2 pi i k d / ny), in FP64 on the host
   std::vector<double2> P(ny), tw(ny);
   const double pi2 = 6.283185307179586476925286766559;
@@ -540,10 +740,12 @@ void launch_gram_build(const float2* smaps, const uint8_t* mask_host, int nc, in
   const size_t sbytes = (size_t)nc * ny * sizeof(float2);
   if (sbytes <= 200 * 1024) {
     cudaFuncSetAttribute(k_gram_build_smem, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sbytes);
-    k_gram_build_smem<<<dim3(nx, (ny + 31) / 32), 256, sbytes, s>>>(smaps, pbuf, nc, ny, nx, Ghi, Glo);
+    k_gram_build_smem<<<dim3(nx, (ny + 31) / 32), 256, sbytes, s>>>(smaps, pbuf, nc, ny, nx, op.nt, op.kc,
+                                                                     op.G);
   } else {
     const int64_t tot = (int64_t)ny * ny;
-    k_gram_build<<<dim3((unsigned)((tot + 255) / 256), nx), 256, 0, s>>>(smaps, pbuf, nc, ny, nx, Ghi, Glo);
+    k_gram_build<<<dim3((unsigned)((tot + 255) / 256), nx), 256, 0, s>>>(smaps, pbuf, nc, ny, nx, op.nt, op.kc,
+                                                                          op.G);
   }
   cudaStreamSynchronize(s);  // P lives on the host stack until the copy has run
 }
@@ -559,22 +761,26 @@ size_t gram_smem(int ny, int kc, int* stages) {
   if (S > 8) S = 8;
   if (S < 2) S = 2;
   *stages = S;
-  return 1024 + (size_t)S * stage + (3 * (size_t)S + 2) * 8 + 16 + kGramRows * 4 + 64;
+  return 1024 + (size_t)S * stage + (3 * (size_t)S + 9) * 8 + 16 + kGramRows * 4 + 64;
 }
 
 void launch_gram_normal(const GramOp& op, const CUtensorMap& mIn, const CUtensorMap& mPold, GramArgs g,
                         cudaStream_t s) {
   int S = 0;
   const size_t smem = gram_smem(op.ny, op.kc, &S);
+  // the split direction goes to tensor memory when it fits beside the accumulators
+  const bool at = op.a_tmem && 2 * op.nt + 4 * op.kc * S <= 512;
+  void (*kern)(const CUtensorMap, const CUtensorMap, const CUtensorMap, const CUtensorMap, GramArgs) =
+      op.kc == 16 ? (at ? k_gram_normal<16, true> : k_gram_normal<16, false>)
+                  : (at ? k_gram_normal<8, true> : k_gram_normal<8, false>);
   // the shared-memory opt-in is per device and kernel; cache it per (thread, device)
   constexpr int kMaxDev = 16;
-  static thread_local size_t configured[kMaxDev][2] = {};
+  static thread_local size_t configured[kMaxDev][4] = {};
   int dev = 0;
   cudaGetDevice(&dev);
-  const int ki = op.kc == 16 ? 0 : 1;
+  const int ki = (op.kc == 16 ? 0 : 2) + (at ? 1 : 0);
   if (dev < 0 || dev >= kMaxDev || configured[dev][ki] < smem) {
-    if (ki == 0) cudaFuncSetAttribute(k_gram_normal<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    else cudaFuncSetAttribute(k_gram_normal<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (dev >= 0 && dev < kMaxDev) configured[dev][ki] = smem;
   }
   g.ny = op.ny;
@@ -582,12 +788,19 @@ void launch_gram_normal(const GramOp& op, const CUtensorMap& mIn, const CUtensor
   g.nt = op.nt;
   g.nyt = op.ny / op.nt;
   g.stages = S;
+  g.G = op.G;
   g.tmem_cols = 32;
-  while (g.tmem_cols < 2 * op.nt) g.tmem_cols *= 2;
+  const int need = at ? 2 * op.nt + 4 * op.kc * S : 2 * op.nt;
+  while (g.tmem_cols < need) g.tmem_cols *= 2;
   const unsigned itiles = (unsigned)((g.nb + kGramRows - 1) / kGramRows);
   const dim3 grid((unsigned)g.nyt * itiles, op.nx);
-  if (op.kc == 16) k_gram_normal<16><<<grid, kGramThreads, smem, s>>>(mIn, mPold, op.mGhi, op.mGlo, g);
-  else k_gram_normal<8><<<grid, kGramThreads, smem, s>>>(mIn, mPold, op.mGhi, op.mGlo, g);
+  // epilogue maps over exactly the nb images of this launch (128-byte swizzle,
+  // 32-value boxes of 128 images)
+  CUtensorMap mPe{}, mQe{};
+  const float* psrc = g.cg ? g.pnew : g.in;
+  g.tma_epi = op.nt % 32 == 0 && g.nb > 0 && gram_encode_e(&mPe, const_cast<float*>(psrc), op.ny, op.nx, g.nb) &&
+              gram_encode_e(&mQe, g.q, op.ny, op.nx, g.nb);
+  kern<<<grid, kGramThreads, smem, s>>>(mIn, mPold, mPe, mQe, g);
 }
 
 void launch_to_cp(const float2* in, float* out, int ny, int nx, int nb, cudaStream_t s) {

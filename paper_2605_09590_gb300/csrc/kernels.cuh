@@ -94,15 +94,17 @@ void launch_cart_rows_adjoint(const CartOp& op, const float2* G, float2* out, in
 struct GramOp {
   int ny, nx, nt;           // nt: output rows per CTA (divides ny, <= 256)
   int kc;                   // contraction values per pipeline stage (16 or 8)
-  float* Ghi;               // [nx][2][ny][ny] TF32 head of G_j (re, im planes)
-  float* Glo;               // remainder
-  CUtensorMap mGhi, mGlo;
+  int a_tmem;               // 1: the split direction is staged in tensor memory
+  // G_j split into TF32 head and remainder, stored as the kernel's pipeline
+  // stages consume it: [j][y tile][chunk][re hi | im hi | re lo | im lo]
+  // [nt rows][kc values, 16-byte groups swizzled as in shared memory]
+  float* G;
 };
 struct GramArgs {
   const float* in;          // r (CG) or x (apply), column-planar [B][nx][2][ny]
   const float* pold;        // previous direction (CG, it > 0)
   float* pnew;              // new direction (CG) or nullptr
-  float* q;                 // (A^H A + lam) p
+  float* q;                 // (A^H A + lam) p; every vector 16-byte aligned (bulk copies)
   const float* beta;        // [B] (CG)
   const int* done;          // [B] (CG)
   double* pq;               // pq partials [B][itmax][PA] or nullptr
@@ -110,16 +112,17 @@ struct GramArgs {
   float lam;
   int* err;                 // first failure code (bounded waits)
   // filled by the launcher
+  const float* G;
   int ny, nx, nt, nyt, stages, tmem_cols;
+  int tma_epi;              // epilogue moves p and q by tensor copies (nt a multiple of 32)
 };
 bool gram_supported(int ny, int nx);
 int gram_tile(int ny);
 size_t gram_bytes(int ny, int nx);  // both G planes, head and remainder
 int gram_pa(int ny, int nx);
 bool gram_encode_x(CUtensorMap* m, float* base, int ny, int nx, int B, int kc);
-bool gram_encode_g(CUtensorMap* m, float* base, int ny, int nx, int kc);
-void launch_gram_build(const float2* smaps, const uint8_t* mask_host, int nc, int ny, int nx, float* Ghi, float* Glo,
-                       double2* pbuf, cudaStream_t s);
+void launch_gram_build(const float2* smaps, const uint8_t* mask_host, int nc, const GramOp& op, double2* pbuf,
+                       cudaStream_t s);
 void launch_gram_scalars(const CgArgs& a, int nb, int it, float* beta, int* done, cudaStream_t s);
 void launch_gram_normal(const GramOp& op, const CUtensorMap& mIn, const CUtensorMap& mPold, GramArgs g,
                         cudaStream_t s);

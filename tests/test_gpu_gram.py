@@ -73,6 +73,38 @@ def fft_path_operator(*args, **kw):
             os.environ["PICO_NORMAL_OP"] = old
 
 
+def operator_with_env(var, val, *args, **kw):
+    old = os.environ.get(var)
+    os.environ[var] = val
+    try:
+        return pico.Operator(*args, **kw)
+    finally:
+        if old is None:
+            del os.environ[var]
+        else:
+            os.environ[var] = old
+
+
+# With PICO_GRAM_ATMEM=1 the split direction is staged in tensor memory for
+# tiles of up to 192 output rows (ny 128, 160, 320, 384 here; 240 and 256 stay
+# in shared memory); the default stages it in shared memory.  Both feed the
+# same products to the same FP32 accumulation, so the two agree to rounding.
+@pytest.mark.parametrize("ny,nx", [(128, 9), (160, 7), (320, 5), (384, 4)])
+def test_tensor_memory_operand_matches_shared_memory_operand(ny, nx):
+    S, cov, mask = case(ny, nx, 4, acs=6, seed=ny)
+    x = to_dev(rand_imgs(130, ny, nx, 3))
+    ops = [operator_with_env("PICO_GRAM_ATMEM", v, S, mask=mask, noise_cov=cov, lam=0.02, power_iters=0,
+                             max_batch=130) for v in ("1", "0")]
+    ya, yb = (o.apply_normal(x) for o in ops)
+    assert ((ya - yb).abs().max() / yb.abs().max()).item() < 1e-6
+    xa, ia, ra = ops[0].cg(x, 12, 0.0, stats=True)
+    xb, ib, rb = ops[1].cg(x, 12, 0.0, stats=True)
+    assert ((xa - xb).abs().max() / xb.abs().max()).item() < 1e-5
+    assert np.allclose(ra, rb, rtol=1e-3, atol=1e-7)
+    for o in ops:
+        assert pico.pico_sync(o.ctx) is None
+
+
 def test_path_selection():
     S, cov, mask = case(320, 24, 4)
     assert pico.Operator(S, mask=mask, noise_cov=cov, power_iters=0).info["normal_op"] == 1
