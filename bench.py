@@ -22,6 +22,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import threading
 import time
 
@@ -44,6 +45,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-t1pct", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the default launch shapes instead of pico_autotune's choice")
     ap.add_argument("--serving", type=int, default=0, help="also run the serving mix with this many requests")
     ap.add_argument("--t1pct-spiral", action="store_true",
                     help="time to 1%% on the spiral workload (exact reference by unit-vector probing, minutes)")
@@ -514,6 +517,14 @@ def main():
     stream = torch.cuda.current_stream()
     op = pico.Operator(inp["smaps"], mask=inp.get("mask"), traj=inp.get("traj"), noise_cov=inp["noise_cov"],
                        lam=w.lam, max_batch=K, power_iters=15, stream=stream.cuda_stream)
+    # launch shapes measured on this GPU (pico_autotune), kept in a JSON cache
+    # that the end-to-end contexts below read back
+    tune_cache = os.environ.get("PICO_TUNE_CACHE") or os.path.join(
+        tempfile.gettempdir(), "pico_tune_%d_%d.json" % (os.getpid(), rank))
+    if not os.environ.get("PICO_TUNE_CACHE"):
+        import atexit
+        atexit.register(lambda: os.path.exists(tune_cache) and os.remove(tune_cache))
+    tuning = None if args.no_autotune else op.autotune(cache=tune_cache)
     s = torch.zeros((w.ny, w.nx), dtype=torch.float64, device=dev)
     ss, ps, pss = torch.zeros_like(s), torch.zeros_like(s), torch.zeros_like(s)
     red = torch.zeros((2, w.ny, w.nx), dtype=torch.float64, device=dev)
@@ -588,6 +599,8 @@ def main():
         "config": arm_config(w, world),
         "roofline": roof, "kernel_ms_in_timed_region": share,
         "gpu_launches": launches,
+        "tuning": {"applied": op.tuning, "autotuned": tuning is not None,
+                   "us_per_image_iteration": getattr(op, "autotune_table", None)},
         "clocks": clk,
         "latency_ms": {"p50": statistics.median(per_step), "p99": max(per_step) if len(per_step) < 100 else
                        sorted(per_step)[int(0.99 * len(per_step))]},
@@ -606,6 +619,8 @@ def main():
             kw = {"mask": m_h} if w.kind == "cartesian" else {"traj": m_h}
             op2 = pico.Operator(S_h, noise_cov=C_h, lam=w.lam, max_batch=K, power_iters=15,
                                 stream=stream.cuda_stream, **kw)
+            if tuning is not None:
+                op2.autotune(cache=tune_cache)   # a cache hit: the tuning measured above
             a, _ = op2.variance_sums(SEED_PICO, K, w.max_iter, 0.0, probe_begin=(i * world + rank) * K)
             b, _ = op2.pmr_sums(SEED_PMR, K, w.sigma, w.max_iter, 0.0, rep_begin=(i * world + rank) * K)
             out_h[0] = a.cpu().numpy()
@@ -620,7 +635,8 @@ def main():
         line["e2e"] = {"value": 2 * K * e2e_steps * world / dt, "unit": UNIT,
                        "h2d_bytes_per_step": int(S_h.nbytes + m_h.nbytes + (C_h.nbytes if C_h is not None else 0)),
                        "d2h_bytes_per_step": int(out_h.nbytes), "steps": e2e_steps,
-                       "includes": "pico_init (upload, whitening, power method, workspace) + maps + read-back"}
+                       "includes": "pico_init (upload, whitening, power method, workspace) + tuning from the "
+                                   "JSON cache + maps + read-back"}
 
     if rank == 0 and world == 1 and not args.no_t1pct and (w.kind == "cartesian" or args.t1pct_spiral):
         t1 = measure_time_to_1pct(op, w, torch, pico, step=10 if w.kind == "cartesian" else 50)

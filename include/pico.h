@@ -89,7 +89,8 @@ typedef struct {
   uint64_t device_bytes;    /* device memory held by the context                              */
   int32_t normal_op;        /* how (A^H A + lam I) is applied inside CG: 0 column FFTs,
                                1 dense per-column Gram matrices on the tensor cores for
-                               batches of at least 64 images (PICO_GRAM_MIN_BATCH) and
+                               batches of at least gram_min_batch images (64 unless
+                               tuned, pico_set_tuning / PICO_GRAM_MIN_BATCH) and
                                column FFTs below (phase-encode masks, ny % 16 == 0,
                                ny >= 128; PICO_NORMAL_OP=fft in the environment selects 0),
                                2 Toeplitz 2-D FFT passes                                   */
@@ -330,6 +331,51 @@ pico_status pico_profile_read(pico_ctx* ctx, int32_t kernel_class, double* total
 /* Kernels launched by this context so far (all classes); reset = 1 zeroes the
  * counter after reading it. */
 pico_status pico_launch_count(pico_ctx* ctx, int64_t* count, int32_t reset);
+
+/* ---- Tuning ----------------------------------------------------------------
+ * Launch shapes a context picks at run time.  Not a step of the method (the
+ * paper has no counterpart): every setting gives the same result up to
+ * rounding (bitwise the same for a given setting).
+ *   gram_min_batch  CG batches of at least this many images use the tensor-core
+ *                   Gram operator, smaller ones the column-FFT kernel (Cartesian
+ *                   phase-encode contexts with normal_op == 1; 0 keeps the
+ *                   current value, a value above max_batch disables the Gram path)
+ *   gram_kc         contraction values per pipeline stage of the Gram operator,
+ *                   16 or 8 (a change rebuilds the stage-tiled G_j, ~1 ms)
+ *   gram_a_tmem     1: the split direction is staged in tensor memory and read
+ *                   by the MMA from there (tiles that fit), 0: shared memory
+ *   probe_batch     probes / replicas per CG batch in pico_variance_map and
+ *                   pico_pmr, 1..max_batch (0 = max_batch)
+ * pico_set_tuning validates every field (PICO_E_INVALID, nothing changed) and
+ * drops the context's captured CUDA graphs.  Fields that do not apply to the
+ * context's operator are kept but have no effect. */
+typedef struct {
+  int32_t gram_min_batch;
+  int32_t gram_kc;
+  int32_t gram_a_tmem;
+  int32_t probe_batch;
+} pico_tuning;
+pico_status pico_get_tuning(const pico_ctx* ctx, pico_tuning* out);
+pico_status pico_set_tuning(pico_ctx* ctx, const pico_tuning* in);
+
+/* Measure and apply the fastest tuning for this context on this GPU.  Each
+ * candidate runs `iters` CG iterations (2..32; 0 = 4) on a batch of random-phase
+ * probes with CUDA events on the context stream (one untimed run first, which
+ * also captures the iteration graph); the time per image and iteration is
+ * compared.  Candidates: batch sizes 16, 32, 64, 128, 256 up to max_batch (and
+ * max_batch itself) for the column-FFT or Toeplitz operator and, on contexts
+ * with normal_op == 1, for the Gram operator with (kc, a_tmem) = (16, 0),
+ * (16, 1), (8, 0).  The Gram variant is the fastest at the largest batch;
+ * gram_min_batch the smallest batch from which on the Gram operator is at
+ * least as fast as the column FFTs; probe_batch the batch with the lowest
+ * time per image on the chosen operator.
+ *   out       receives the applied tuning (may be NULL)
+ *   times_us  NULL or room for `ntimes` doubles: [candidate][batch] microseconds
+ *             per image and iteration, candidates (column FFT / Toeplitz, Gram
+ *             16/0, Gram 16/1, Gram 8/0) x batches (16, 32, 64, 128, 256,
+ *             max_batch); NaN where not measured (ntimes >= 24 for all)
+ * Overwrites the context's CG workspace; synchronises the stream. */
+pico_status pico_autotune(pico_ctx* ctx, int32_t iters, pico_tuning* out, double* times_us, int32_t ntimes);
 
 /* Wait for all work of the context; returns the first asynchronous error
  * (PICO_E_CUDA) or PICO_E_BREAKDOWN if a CG system broke down since the last

@@ -56,6 +56,13 @@ class pico_info(ctypes.Structure):
     ]
 
 
+class pico_tuning(ctypes.Structure):
+    _fields_ = [
+        ("gram_min_batch", ctypes.c_int32), ("gram_kc", ctypes.c_int32), ("gram_a_tmem", ctypes.c_int32),
+        ("probe_batch", ctypes.c_int32),
+    ]
+
+
 class pico_request(ctypes.Structure):
     _fields_ = [
         ("op", pico_operator_desc), ("seed", ctypes.c_uint64), ("nprobes", ctypes.c_int32),
@@ -107,6 +114,9 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "pico_profile": ([vp, i32], i32),
         "pico_profile_read": ([vp, i32, ctypes.POINTER(f64), ctypes.POINTER(i64)], i32),
         "pico_launch_count": ([vp, ctypes.POINTER(i64), i32], i32),
+        "pico_get_tuning": ([vp, ctypes.POINTER(pico_tuning)], i32),
+        "pico_set_tuning": ([vp, ctypes.POINTER(pico_tuning)], i32),
+        "pico_autotune": ([vp, i32, ctypes.POINTER(pico_tuning), ctypes.POINTER(f64), i32], i32),
         "pico_footprint": ([ctypes.POINTER(pico_operator_desc), i32, ctypes.POINTER(ctypes.c_size_t)], i32),
         "pico_server_create": ([ctypes.c_size_t, i32, i32, ctypes.POINTER(vp)], i32),
         "pico_server_submit": ([vp, ctypes.POINTER(pico_request), ctypes.POINTER(i64)], i32),
@@ -331,6 +341,35 @@ def pico_launch_count(ctx, reset: bool = False) -> int:
     return n.value
 
 
+def pico_get_tuning(ctx) -> dict:
+    t = pico_tuning()
+    _check(ctx, load_library().pico_get_tuning(ctx, ctypes.byref(t)))
+    return {f: getattr(t, f) for f, _ in pico_tuning._fields_}
+
+
+def pico_set_tuning(ctx, tuning: dict) -> None:
+    t = pico_tuning(**{f: int(tuning[f]) for f, _ in pico_tuning._fields_})
+    _check(ctx, load_library().pico_set_tuning(ctx, ctypes.byref(t)))
+
+
+AUTOTUNE_CANDIDATES = ("fft", "gram16", "gram16_tmem", "gram8")
+
+
+def pico_autotune(ctx, iters: int = 0) -> tuple[dict, dict]:
+    """Measure and apply the fastest tuning; returns (tuning, {candidate: {batch: us per image-iteration}})."""
+    t = pico_tuning()
+    times = (ctypes.c_double * 24)()
+    _check(ctx, load_library().pico_autotune(ctx, iters, ctypes.byref(t), times, 24))
+    mb = pico_get_info(ctx)["max_batch"]
+    batches = (16, 32, 64, 128, 256, mb)
+    table = {}
+    for k, name in enumerate(AUTOTUNE_CANDIDATES):
+        row = {b: times[k * 6 + i] for i, b in enumerate(batches) if times[k * 6 + i] == times[k * 6 + i]}
+        if row:
+            table[name] = row
+    return {f: getattr(t, f) for f, _ in pico_tuning._fields_}, table
+
+
 def pico_sync(ctx) -> None:
     _check(ctx, load_library().pico_sync(ctx))
 
@@ -356,6 +395,49 @@ class Operator:
         self.ctx = pico_init(smaps, mask=mask, noise_cov=noise_cov, traj=traj, **kw)
         self.info = pico_get_info(self.ctx)
         self.ny, self.nx = self.info["ny"], self.info["nx"]
+        import hashlib
+        h = hashlib.sha1()
+        for a in (mask, traj):
+            if a is not None:
+                h.update(np.ascontiguousarray(np.asarray(a)).tobytes())
+        self._shape_key = "k{kind}_{ny}x{nx}_c{ncoils}_b{max_batch}_op{normal_op}".format(**self.info) + \
+            "_" + h.hexdigest()[:16]
+
+    @property
+    def tuning(self) -> dict:
+        return pico_get_tuning(self.ctx)
+
+    def set_tuning(self, **fields) -> None:
+        t = self.tuning
+        t.update(fields)
+        pico_set_tuning(self.ctx, t)
+
+    def autotune(self, cache: Optional[str] = None, iters: int = 0) -> dict:
+        """Pick the launch shapes for this operator on this GPU (pico_autotune).
+
+        With ``cache`` (a JSON file path) a tuning measured earlier for the same
+        operator shape, mask / trajectory, batch capacity and device is reused,
+        and a new measurement is stored there."""
+        import json
+        key = self._shape_key + "_" + self.torch.cuda.get_device_name().replace(" ", "-")
+        db = {}
+        if cache and os.path.exists(cache):
+            with open(cache) as f:
+                db = json.load(f)
+            if key in db:
+                pico_set_tuning(self.ctx, db[key]["tuning"])
+                self.autotune_table = db[key].get("us_per_image_iteration", {})
+                return self.tuning
+        tuning, table = pico_autotune(self.ctx, iters)
+        self.autotune_table = table
+        if cache:
+            db[key] = {"tuning": tuning,
+                       "us_per_image_iteration": {k: {str(b): v for b, v in r.items()} for k, r in table.items()}}
+            tmp = cache + ".tmp"
+            with open(tmp, "w") as f:
+                json.dump(db, f, indent=1, sort_keys=True)
+            os.replace(tmp, cache)
+        return tuning
 
     def close(self):
         if self.ctx:

@@ -78,6 +78,8 @@ struct pico_ctx {
   bool gram = false;     // G built: batches of at least kGramMinBatch images use it
   bool gram_on = false;  // the batch in flight uses it (CG vectors column-planar)
   int pa_fft = 0, pa_gram = 0, gram_min_batch = 64;
+  int probe_batch = 0;          // probes per CG batch of the map entry points (0: max_batch)
+  std::vector<uint8_t> gmask;   // host copy of the phase-encode mask (rebuilding G)
   pico::GramOp gop{};
   CUtensorMap mR{}, mX{}, mP0{}, mP1{};
   float* P2 = nullptr;
@@ -388,9 +390,8 @@ pico_status run_cg(pico_ctx* c, int nb, int max_iter, double rtol, float lam) {
   return cuda_check(c, "cg");
 }
 
-pico_status run_cg_from_probe(pico_ctx* c, int nb, int max_iter, double rtol, float lam, uint64_t seed,
-                              int64_t begin, int kind) {
-  c->cg.rtol2 = rtol * rtol;
+// CG start from probes: x = 0, r = v (the probes of indices begin ..)
+void init_from_probe(pico_ctx* c, int nb, uint64_t seed, int64_t begin, int kind) {
   if (c->gram_on) {
     // probes drawn in the natural layout into Q, then rearranged into R
     pico::CgArgs a = c->cg;
@@ -401,8 +402,26 @@ pico_status run_cg_from_probe(pico_ctx* c, int nb, int max_iter, double rtol, fl
     Launch L(c, 1);
     pico::launch_cg_init_probe(c->cg, nb, seed, begin, kind, c->stream);
   }
+}
+
+pico_status run_cg_from_probe(pico_ctx* c, int nb, int max_iter, double rtol, float lam, uint64_t seed,
+                              int64_t begin, int kind) {
+  c->cg.rtol2 = rtol * rtol;
+  init_from_probe(c, nb, seed, begin, kind);
   cg_iterations(c, nb, max_iter, rtol, lam);
   return cuda_check(c, "cg");
+}
+
+// captured CG graphs depend on the operator choice, which their key omits
+void clear_graphs(pico_ctx* c) {
+  for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second.first);
+  c->graphs.clear();
+  c->seen.clear();
+}
+
+// probes / replicas per CG batch of the map entry points
+int probe_chunk(const pico_ctx* c) {
+  return c->probe_batch > 0 ? std::min(c->probe_batch, c->max_batch) : c->max_batch;
 }
 
 // k-space / grid work buffer shared by PMR, the forward and the adjoint operator:
@@ -687,6 +706,20 @@ size_t gram_extra_bytes(const pico_operator_desc* d, int64_t B) {
   return pico::gram_bytes(d->ny, d->nx) + (size_t)B * d->ny * d->nx * 8 + (size_t)B * 8 + (size_t)d->ny * 16 + 16;
 }
 
+// (re)build the stage-tiled G_j for gop.kc and the tensor maps of the CG vectors
+pico_status gram_configure(pico_ctx* c) {
+  const int kc = c->gop.kc;
+  pico::launch_gram_build(c->smaps, c->gmask.data(), c->nc, c->gop, c->g_pbuf, c->stream);
+  const int B = c->max_batch;
+  const bool ok = pico::gram_encode_x(&c->mR, cpf(c->R), c->ny, c->nx, B, kc) &&
+                  pico::gram_encode_x(&c->mX, cpf(c->X), c->ny, c->nx, B, kc) &&
+                  pico::gram_encode_x(&c->mP0, cpf(c->P), c->ny, c->nx, B, kc) &&
+                  pico::gram_encode_x(&c->mP1, c->P2, c->ny, c->nx, B, kc);
+  if (!ok) return fail(c, PICO_E_CUDA, "tensor map encoding for the Gram operator failed");
+  if (cudaStreamSynchronize(c->stream) != cudaSuccess) return cuda_check(c, "Gram operator set-up");
+  return cuda_check(c, "Gram operator set-up");
+}
+
 pico_status gram_setup(pico_ctx* c, const pico_operator_desc* d) {
   pico_status st = PICO_OK;
   if ((st = dalloc(c, &c->gop.G, pico::gram_bytes(c->ny, c->nx) / sizeof(float))) != PICO_OK) return st;
@@ -706,17 +739,10 @@ pico_status gram_setup(pico_ctx* c, const pico_operator_desc* d) {
   // 1 % slower than shared memory on the 320 x 320 knee operator; kept as an option)
   c->gop.a_tmem = 0;
   if (const char* e = std::getenv("PICO_GRAM_ATMEM")) c->gop.a_tmem = std::atoi(e) != 0;
-  const int kc = c->gop.kc;
-  pico::launch_gram_build(c->smaps, d->mask, c->nc, c->gop, c->g_pbuf, c->stream);
-  const int B = c->max_batch;
-  const bool ok = pico::gram_encode_x(&c->mR, cpf(c->R), c->ny, c->nx, B, kc) &&
-                  pico::gram_encode_x(&c->mX, cpf(c->X), c->ny, c->nx, B, kc) &&
-                  pico::gram_encode_x(&c->mP0, cpf(c->P), c->ny, c->nx, B, kc) &&
-                  pico::gram_encode_x(&c->mP1, c->P2, c->ny, c->nx, B, kc);
-  if (!ok) return fail(c, PICO_E_CUDA, "tensor map encoding for the Gram operator failed");
-  if (cudaStreamSynchronize(c->stream) != cudaSuccess) return cuda_check(c, "Gram operator set-up");
+  c->gmask.assign(d->mask, d->mask + c->ny);
+  if ((st = gram_configure(c)) != PICO_OK) return st;
   c->gram = true;
-  return cuda_check(c, "Gram operator set-up");
+  return PICO_OK;
 }
 
 pico_status wavelet_check(pico_ctx* c, int levels) {
@@ -1058,8 +1084,9 @@ pico_status pico_variance_map(pico_ctx* c, uint64_t seed, int64_t probe_begin, i
     if (sumsq) cudaMemsetAsync(sumsq, 0, (size_t)c->n * sizeof(double), c->stream);
   }
   const float lam = (float)c->lam_phys;
-  for (int32_t b0 = 0; b0 < nprobes; b0 += c->max_batch) {
-    const int nb = std::min(c->max_batch, nprobes - b0);
+  const int chunk = probe_chunk(c);
+  for (int32_t b0 = 0; b0 < nprobes; b0 += chunk) {
+    const int nb = std::min(chunk, nprobes - b0);
     select_path(c, nb);
     if ((st = run_cg_from_probe(c, nb, max_iter, rtol, lam, seed, probe_begin + b0, kind)) != PICO_OK) return st;
     if (c->lam_phys != 0.0) {
@@ -1130,8 +1157,9 @@ pico_status pico_pmr(pico_ctx* c, uint64_t seed, int64_t rep_begin, int32_t nrep
     if (sumsq) cudaMemsetAsync(sumsq, 0, (size_t)c->n * sizeof(double), c->stream);
   }
   const float lam = (float)c->lam_phys;
-  for (int32_t b0 = 0; b0 < nreps; b0 += c->max_batch) {
-    const int nb = std::min(c->max_batch, nreps - b0);
+  const int chunk = probe_chunk(c);
+  for (int32_t b0 = 0; b0 < nreps; b0 += chunk) {
+    const int nb = std::min(chunk, nreps - b0);
     select_path(c, nb);
     if (c->gram_on) {
       noise_adjoint(c, c->Q, nb, seed, rep_begin + b0, sigma);
@@ -1410,6 +1438,137 @@ pico_status pico_launch_count(pico_ctx* c, int64_t* count, int32_t reset) {
   if (!c || !count) return PICO_E_INVALID;
   *count = c->launches;
   if (reset) c->launches = 0;
+  return PICO_OK;
+}
+
+pico_status pico_get_tuning(const pico_ctx* c, pico_tuning* out) {
+  if (!c || !out) return PICO_E_INVALID;
+  out->gram_min_batch = c->gram_min_batch;
+  out->gram_kc = c->gop.kc ? c->gop.kc : 16;
+  out->gram_a_tmem = c->gop.a_tmem;
+  out->probe_batch = c->probe_batch;
+  return PICO_OK;
+}
+
+pico_status pico_set_tuning(pico_ctx* c, const pico_tuning* t) {
+  if (!c || !c->smaps || !t) return PICO_E_INVALID;
+  if (t->gram_min_batch < 0 || !(t->gram_kc == 0 || t->gram_kc == 8 || t->gram_kc == 16) ||
+      !(t->gram_a_tmem == 0 || t->gram_a_tmem == 1) || t->probe_batch < 0 || t->probe_batch > c->max_batch)
+    return fail(c, PICO_E_INVALID, "tuning out of range (gram_kc 8/16, gram_a_tmem 0/1, probe_batch <= max_batch)");
+  clear_graphs(c);
+  if (t->gram_min_batch > 0) c->gram_min_batch = t->gram_min_batch;
+  c->gop.a_tmem = t->gram_a_tmem;
+  c->probe_batch = t->probe_batch;
+  if (t->gram_kc != 0 && t->gram_kc != c->gop.kc) {
+    c->gop.kc = t->gram_kc;
+    if (c->gram) return gram_configure(c);
+  }
+  return cuda_check(c, "pico_set_tuning");
+}
+
+pico_status pico_autotune(pico_ctx* c, int32_t iters, pico_tuning* out, double* times_us, int32_t ntimes) {
+  if (!c || !c->smaps) return PICO_E_INVALID;
+  if (iters == 0) iters = 4;
+  if (iters < 2 || iters > 32 || iters > c->itmax) return fail(c, PICO_E_INVALID, "autotune iters must be 2..32");
+  constexpr int kCand = 4, kNb = 6;
+  const int cand_kc[kCand] = {0, 16, 16, 8}, cand_at[kCand] = {0, 0, 1, 0};
+  int nbs[kNb] = {16, 32, 64, 128, 256, c->max_batch};
+  bool nb_ok[kNb];
+  for (int i = 0; i < kNb; ++i) {
+    nb_ok[i] = nbs[i] <= c->max_batch;
+    for (int k = 0; k < i; ++k) nb_ok[i] = nb_ok[i] && nbs[k] != nbs[i];
+  }
+  double t[kCand][kNb];
+  for (auto& row : t)
+    for (double& v : row) v = NAN;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    if (e0) cudaEventDestroy(e0);
+    return cuda_check(c, "pico_autotune");
+  }
+  const float lam = (float)c->lam_phys;
+  const bool prof = c->profiling;
+  c->profiling = false;
+  c->cg.rtol2 = 0.0;
+  // us per image and iteration of `iters` CG iterations on nb probes: the
+  // first run launches directly, the second captures the graph, the best of
+  // the next two replays counts
+  auto time_cg = [&](int nb, bool gram) -> double {
+    c->gram_on = gram;
+    c->cg.PA = gram ? c->pa_gram : c->pa_fft;
+    float best = INFINITY;
+    for (int rep = 0; rep < 4; ++rep) {
+      init_from_probe(c, nb, 0x7a11ull, 0, PICO_PROBE_PHASE);
+      cudaEventRecord(e0, c->stream);
+      cg_range(c, nb, 0, iters, 0.0, lam);
+      cudaEventRecord(e1, c->stream);
+      float ms = INFINITY;
+      if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess)
+        return (double)NAN;
+      if (rep >= 2) best = std::min(best, ms);
+    }
+    return 1e3 * (double)best / ((double)nb * iters);
+  };
+  pico_tuning cur{};
+  pico_get_tuning(c, &cur);
+  pico_status st = PICO_OK;
+  for (int k = 0; k < kCand && st == PICO_OK; ++k) {
+    if (k > 0) {
+      if (!c->gram) break;
+      clear_graphs(c);
+      c->gop.a_tmem = cand_at[k];
+      if (c->gop.kc != cand_kc[k]) {
+        c->gop.kc = cand_kc[k];
+        if ((st = gram_configure(c)) != PICO_OK) break;
+      }
+    }
+    for (int i = 0; i < kNb; ++i)
+      if (nb_ok[i]) t[k][i] = time_cg(nbs[i], k > 0);
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  c->profiling = prof;
+  if (st != PICO_OK) return st;
+  if ((st = cuda_check(c, "pico_autotune")) != PICO_OK) return st;
+  // largest measured batch
+  int top = -1;
+  for (int i = 0; i < kNb; ++i)
+    if (nb_ok[i] && (top < 0 || nbs[i] > nbs[top])) top = i;
+  pico_tuning best = cur;
+  int vg = 0;  // Gram candidate: fastest at the largest batch
+  if (c->gram)
+    for (int k = 1; k < kCand; ++k)
+      if (std::isfinite(t[k][top]) && (vg == 0 || t[k][top] < t[vg][top])) vg = k;
+  auto chosen = [&](int i) { return (vg && nbs[i] >= best.gram_min_batch) ? t[vg][i] : t[0][i]; };
+  if (vg) {
+    best.gram_kc = cand_kc[vg];
+    best.gram_a_tmem = cand_at[vg];
+    // smallest batch from which on the Gram operator is never slower
+    best.gram_min_batch = c->max_batch + 1;
+    std::vector<int> order;
+    for (int i = 0; i < kNb; ++i)
+      if (nb_ok[i]) order.push_back(i);
+    std::sort(order.begin(), order.end(), [&](int a, int b) { return nbs[a] > nbs[b]; });
+    for (int i : order) {
+      if (!(t[vg][i] <= t[0][i])) break;
+      best.gram_min_batch = nbs[i];
+    }
+  }
+  // the largest batch within 3 % of the lowest time per image
+  double tmin = INFINITY;
+  for (int i = 0; i < kNb; ++i)
+    if (nb_ok[i] && std::isfinite(chosen(i))) tmin = std::min(tmin, chosen(i));
+  int pb = top;
+  for (int i = 0; i < kNb; ++i)
+    if (nb_ok[i] && chosen(i) <= 1.03 * tmin && (pb < 0 || !(chosen(pb) <= 1.03 * tmin) || nbs[i] > nbs[pb])) pb = i;
+  best.probe_batch = (pb >= 0 && nbs[pb] < c->max_batch) ? nbs[pb] : 0;
+  if (times_us)
+    for (int k = 0; k < kCand; ++k)
+      for (int i = 0; i < kNb; ++i)
+        if (k * kNb + i < ntimes) times_us[k * kNb + i] = t[k][i];
+  if (!c->gram) best.gram_kc = 0;
+  if ((st = pico_set_tuning(c, &best)) != PICO_OK) return st;
+  if (out) pico_get_tuning(c, out);
   return PICO_OK;
 }
 

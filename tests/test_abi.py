@@ -47,6 +47,9 @@ def test_null_arguments_are_rejected_without_a_gpu(lib):
     assert lib.pico_init(None, None, 0, ctypes.byref(h)) == pico.PICO_E_INVALID
     assert lib.pico_sync(None) == pico.PICO_E_INVALID
     assert lib.pico_get_info(None, None) == pico.PICO_E_INVALID
+    assert lib.pico_get_tuning(None, None) == pico.PICO_E_INVALID
+    assert lib.pico_set_tuning(None, None) == pico.PICO_E_INVALID
+    assert lib.pico_autotune(None, 0, None, None, 0) == pico.PICO_E_INVALID
     lib.pico_destroy(None)
 
 
@@ -60,6 +63,7 @@ int main(void) {
   printf("pico_operator_desc size %zu\n", sizeof(pico_operator_desc));
   printf("pico_info size %zu\n", sizeof(pico_info));
   printf("pico_request size %zu\n", sizeof(pico_request));
+  printf("pico_tuning size %zu\n", sizeof(pico_tuning));
   P(pico_operator_desc, smaps) P(pico_operator_desc, noise_cov) P(pico_operator_desc, mask)
   P(pico_operator_desc, mask_2d) P(pico_operator_desc, traj) P(pico_operator_desc, nsamp)
   P(pico_operator_desc, oversamp) P(pico_operator_desc, kb_width) P(pico_operator_desc, lambda)
@@ -69,6 +73,7 @@ int main(void) {
   P(pico_info, normal_op)
   P(pico_request, seed) P(pico_request, nprobes) P(pico_request, rtol) P(pico_request, pmr_sigma)
   P(pico_request, cs_data) P(pico_request, cs_lambda) P(pico_request, cs_iters) P(pico_request, cs_levels)
+  P(pico_tuning, gram_min_batch) P(pico_tuning, gram_kc) P(pico_tuning, gram_a_tmem) P(pico_tuning, probe_batch)
   return 0;
 }
 '''
@@ -86,8 +91,9 @@ int main(void) {
     assert got[("pico_operator_desc", "size")] == ctypes.sizeof(pico.pico_operator_desc)
     assert got[("pico_info", "size")] == ctypes.sizeof(pico.pico_info)
     assert got[("pico_request", "size")] == ctypes.sizeof(pico.pico_request)
+    assert got[("pico_tuning", "size")] == ctypes.sizeof(pico.pico_tuning)
     classes = {"pico_operator_desc": pico.pico_operator_desc, "pico_info": pico.pico_info,
-               "pico_request": pico.pico_request}
+               "pico_request": pico.pico_request, "pico_tuning": pico.pico_tuning}
     for (t, f), v in got.items():
         if f == "size":
             continue
