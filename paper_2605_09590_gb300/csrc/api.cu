@@ -472,6 +472,7 @@ pico_status cart2d_setup(pico_ctx* c, const pico_operator_desc* d, int img, int 
   c->sop.smaps = c->smaps;
   c->sop.tw2 = c->tw2;
   c->sop.That = c->That;
+  c->sop.err = c->g_err;
   c->twx = c->tw2;
   c->tw = c->tw2;
   if (cudaStreamSynchronize(c->stream) != cudaSuccess) return cuda_check(c, "2-D mask set-up");
@@ -577,7 +578,7 @@ pico_status spiral_setup(pico_ctx* c, const pico_operator_desc* d, int img, int 
 
   c->sop = pico::SpiralOp{img,      L,         nc,         P1,          P2,           c->smaps,
                           c->tw2,   c->That,   c->deapod,  M,           c->u,         c->cphase,
-                          c->tile_ptr, c->tile_idx, (float)beta, (float)hw, (float)(1.0 / i0b)};
+                          c->tile_ptr, c->tile_idx, (float)beta, (float)hw, (float)(1.0 / i0b), c->g_err};
   // Toeplitz kernel: h on the 2N grid (in the Toeplitz buffer), 2-D DFT, real part, scale
   float2* cbuf = c->Gt;  // max_batch * nc * N * 2N >= (2N)^2 complex values
   { Launch Lh(c, 3); pico::launch_toep_h(c->traj, M, img, cbuf, c->stream); }
@@ -726,7 +727,7 @@ pico_status gram_setup(pico_ctx* c, const pico_operator_desc* d) {
   if ((st = dalloc(c, &c->P2, (size_t)2 * c->max_batch * c->n)) != PICO_OK) return st;
   if ((st = dalloc(c, &c->g_beta, (size_t)c->max_batch)) != PICO_OK) return st;
   if ((st = dalloc(c, &c->g_done, (size_t)c->max_batch)) != PICO_OK) return st;
-  if ((st = dalloc(c, &c->g_err, (size_t)4)) != PICO_OK) return st;
+  if (!c->g_err && (st = dalloc(c, &c->g_err, (size_t)4)) != PICO_OK) return st;
   if ((st = dalloc(c, &c->g_pbuf, (size_t)c->ny)) != PICO_OK) return st;
   cudaMemsetAsync(c->g_err, 0, 4 * sizeof(int), c->stream);
   if (const char* e = std::getenv("PICO_GRAM_MIN_BATCH")) c->gram_min_batch = std::max(1, std::atoi(e));
@@ -893,6 +894,8 @@ pico_status init_impl(const pico_operator_desc* d, void* cuda_stream, size_t hbm
     c->h_flag = nullptr;  // no early stop: tolerance-stopped solves run all max_iter iterations
   }
   TRY(dalloc(c, &c->cg_state, (size_t)B));
+  TRY(dalloc(c, &c->g_err, (size_t)4));  // first failure code of a bounded wait in any kernel
+  cudaMemsetAsync(c->g_err, 0, 4 * sizeof(int), c->stream);
   TRY(dalloc(c, &c->d_relres, (size_t)B));
   TRY(dalloc(c, &c->d_norm, (size_t)PB + 1));
   cudaMemcpyAsync(c->smaps, S.empty() ? d->smaps : static_cast<const void*>(S.data()), (size_t)nc * n * sizeof(float2),
@@ -982,7 +985,7 @@ size_t footprint_bytes(const pico_operator_desc* d, bool with_kbuf) {
     kbuf = B * nc * 4 * n * 8;
   }
   const int64_t need = nc * n * 8 + nc * nc * 16 + 4 * B * n * 8 + B * (itmax + 1) * PB * 8 + B * itmax * PA * 8 + B * 16 +
-                       PB * 8 + 64 + extra + (with_kbuf ? kbuf : 0);
+                       PB * 8 + 64 + 16 + extra + (with_kbuf ? kbuf : 0);
   return (size_t)need;
 }
 
@@ -1397,7 +1400,7 @@ pico_status pico_sync(pico_ctx* c) {
     if (cudaMemcpy(&e, c->g_err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return cuda_check(c, "pico_sync");
     if (e) {
       cudaMemset(c->g_err, 0, sizeof(int));
-      return fail(c, PICO_E_TIMEOUT, "Gram operator pipeline wait timed out (stage " + std::to_string(e) + ")");
+      return fail(c, PICO_E_TIMEOUT, "a kernel's bounded pipeline wait timed out (code " + std::to_string(e) + ")");
     }
   }
   if (c->status) {

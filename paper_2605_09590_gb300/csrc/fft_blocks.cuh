@@ -30,39 +30,39 @@ struct Split {
   static constexpr size_t row_buf = (size_t)kLines * P2 * LD * sizeof(float2);
 };
 
-// ---- column layout ----
+// ---- column layout (LS lines per block, kLines unless stated) ----
 template <int P, int SIGN, int NZ>
 __device__ __forceinline__ void dft_nz(float2 (&z)[P]);
-template <int P1, int P2, int SIGN, int NZ = P2>
+template <int P1, int P2, int SIGN, int NZ = P2, int LS = kLines>
 __device__ __forceinline__ void cola_store(float2 (&z)[P2], int n1, int ln, float2* buf, const float2* tws) {
   dft_nz<P2, SIGN, NZ>(z);
 #pragma unroll
   for (int k = 0; k < P2; ++k) {
     const float2 w = tws[n1 * k];
-    buf[(k * P1 + n1) * kLines + ln] = k == 0 ? z[0] : (SIGN < 0 ? cmul(z[k], w) : cmul_cb(z[k], w));
+    buf[(k * P1 + n1) * LS + ln] = k == 0 ? z[0] : (SIGN < 0 ? cmul(z[k], w) : cmul_cb(z[k], w));
   }
 }
-template <int P1, int P2>
+template <int P1, int P2, int LS = kLines>
 __device__ __forceinline__ void colb_load(float2 (&y)[P1], int k2, int ln, const float2* buf) {
 #pragma unroll
-  for (int m = 0; m < P1; ++m) y[m] = buf[(k2 * P1 + m) * kLines + ln];
+  for (int m = 0; m < P1; ++m) y[m] = buf[(k2 * P1 + m) * LS + ln];
 }
-template <int P1, int P2>
+template <int P1, int P2, int LS = kLines>
 __device__ __forceinline__ void colb_store(const float2 (&y)[P1], int k2, int ln, float2* buf) {
 #pragma unroll
-  for (int m = 0; m < P1; ++m) buf[(k2 * P1 + m) * kLines + ln] = y[m];
+  for (int m = 0; m < P1; ++m) buf[(k2 * P1 + m) * LS + ln] = y[m];
 }
 // inverse DFT_P1 of a b-job and the conjugate twiddle, stored for the a-jobs
-template <int P1, int P2>
+template <int P1, int P2, int LS = kLines>
 __device__ __forceinline__ void colb_inv_store(float2 (&y)[P1], int k2, int ln, float2* buf, const float2* tws) {
   DFT<P1, 1>::run(y);
 #pragma unroll
-  for (int m = 0; m < P1; ++m) buf[(k2 * P1 + m) * kLines + ln] = m == 0 ? y[0] : cmul_cb(y[m], tws[m * k2]);
+  for (int m = 0; m < P1; ++m) buf[(k2 * P1 + m) * LS + ln] = m == 0 ? y[0] : cmul_cb(y[m], tws[m * k2]);
 }
-template <int P1, int P2, int SIGN>
+template <int P1, int P2, int SIGN, int LS = kLines>
 __device__ __forceinline__ void cola_load(float2 (&z)[P2], int n1, int ln, const float2* buf) {
 #pragma unroll
-  for (int k = 0; k < P2; ++k) z[k] = buf[(k * P1 + n1) * kLines + ln];
+  for (int k = 0; k < P2; ++k) z[k] = buf[(k * P1 + n1) * LS + ln];
   DFT<P2, SIGN>::run(z);
 }
 

@@ -708,6 +708,19 @@ bool gram_encode_x(CUtensorMap* m, float* base, int ny, int nx, int B, int kc) {
              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+bool encode_plane_map(CUtensorMap* m, const void* base, int rows, int L, int64_t planes, int cols, int box_rows) {
+  EncodeTiledFn enc = encode_fn();
+  if (!enc || !base || (reinterpret_cast<uintptr_t>(base) & 15) || (L * 8) % 16 || (cols * 8) % 16 || cols > 256 ||
+      box_rows > 256 || box_rows < 1)
+    return false;
+  cuuint64_t dims[3] = {(cuuint64_t)L, (cuuint64_t)rows, (cuuint64_t)planes};
+  cuuint64_t strides[2] = {(cuuint64_t)L * 8, (cuuint64_t)rows * L * 8};
+  cuuint32_t box[3] = {(cuuint32_t)cols, (cuuint32_t)box_rows, 1}, es[3] = {1, 1, 1};
+  return enc(m, CU_TENSOR_MAP_DATA_TYPE_INT64, 3, const_cast<void*>(base), dims, strides, box, es,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 bool gram_encode_e(CUtensorMap* m, float* base, int ny, int nx, int B) {
   EncodeTiledFn enc = encode_fn();
   if (!enc || !base || (reinterpret_cast<uintptr_t>(base) & 15)) return false;

@@ -146,7 +146,11 @@ struct SpiralOp {
   const int* tile_ptr;      // [ntiles + 1] CSR over 16x16 grid tiles
   const int* tile_idx;      // samples touching each tile (with the kernel half-width)
   float beta, halfw, inv_i0beta;
+  int* err;                 // first failure code of a bounded wait (device), or nullptr
 };
+// 3-D tensor map over `planes` planes of rows x L complex64 values (8-byte
+// elements), boxes of `cols` x `box_rows` values (the column pass's staging)
+bool encode_plane_map(CUtensorMap* m, const void* base, int rows, int L, int64_t planes, int cols, int box_rows);
 bool spiral_supported(int n, int* P1, int* P2);
 bool grid_split(int L, int* P1, int* P2);  // split of a 2-D pass length (Toeplitz or 2-D Cartesian)
 void launch_toep_h(const float* traj, int64_t M, int n, float2* c, cudaStream_t s);

@@ -23,6 +23,7 @@
 #include "common.cuh"
 #include "fft_blocks.cuh"
 #include "kernels.cuh"
+#include "tc_util.cuh"
 
 namespace pico {
 
@@ -173,6 +174,84 @@ __global__ void __launch_bounds__(Split<P1, P2>::NT, 1)
     cola_load<P1, P2, 1>(z, n1, ln, buf);
 #pragma unroll
     for (int n2 = 0; n2 < NIN; ++n2) g[(size_t)(n1 + P1 * n2) * L + kx] = z[n2];  // rows < N only
+  }
+}
+
+// The same pass for splits with P1 > P2, persistent: each block walks work
+// items (plane, group of P1 grid columns) and one thread brings the next
+// item's N x P1 input values into a staging buffer with TMA tensor loads
+// while the block transforms the current item, so the global-load latency of
+// a plane no longer stalls every thread at its start.  With P1 columns per
+// item the b-jobs (the heavy DFT_P1 pair and the T^ product) occupy all
+// P2 x P1 threads; the light DFT_P2 a-jobs take P1 / P2 rounds.
+template <int P1, int P2, bool PAD>
+__global__ void __launch_bounds__(P1 * P2, (P1 * P2 <= 320 ? 2 : 1))
+    k_toep_cols_w(SpiralOp op, const __grid_constant__ CUtensorMap mG, float2* __restrict__ G,
+                  const int* __restrict__ done, int nplanes, int box_rows) {
+  constexpr int NIN = PAD ? P2 / 2 : P2;
+  constexpr int L = P1 * P2;
+  constexpr int NT = L;
+  constexpr int CL = P1;  // grid columns per item
+  extern __shared__ __align__(16) unsigned char smraw[];
+  unsigned char* sm = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smraw) + 1023) & ~(uintptr_t)1023);
+  const int t = threadIdx.x, N = op.n;          // N input rows per plane
+  float2* stage = reinterpret_cast<float2*>(sm);  // [N][CL] input rows of the item
+  float2* buf = stage + (size_t)N * CL;           // [k2][n1][CL]
+  float2* tws = buf + (size_t)L * CL;
+  uint64_t* bar = reinterpret_cast<uint64_t*>(tws + L);
+  const int items = P2 * nplanes;
+  const uint32_t bytes = (uint32_t)N * CL * sizeof(float2);
+  if (t == 0) {
+    tc::mbar_init(bar, 1);
+    tc::fence_mbar_init();
+  }
+  for (int i = t; i < L; i += NT) tws[i] = op.tw2[i];
+  __syncthreads();
+  auto issue = [&](int w) {
+    const int plane = w / P2, cg = w - plane * P2;
+    tc::mbar_expect_tx(bar, bytes);
+    for (int r0 = 0; r0 < N; r0 += box_rows) tc::tma_load_3d(stage + (size_t)r0 * CL, &mG, bar, cg * CL, r0, plane);
+  };
+  if (t == 0 && (int)blockIdx.x < items) issue(blockIdx.x);
+  int phase = 0;
+  for (int w = blockIdx.x; w < items; w += gridDim.x, phase ^= 1) {
+    const int plane = w / P2, cg = w - plane * P2, x0 = cg * CL;
+    if (!tc::mbar_wait(bar, phase)) {
+      if (t == 0 && op.err) atomicCAS(op.err, 0, 10);
+      return;
+    }
+    const bool skip = done && done[plane / op.nc];
+    float2* __restrict__ g = G + (size_t)plane * N * L;  // (b, c) plane [N][L]
+    if (!skip)
+      for (int jj = t; jj < P1 * CL; jj += NT) {
+        const int n1 = jj / CL, ln = jj - n1 * CL;
+        float2 z[P2];
+#pragma unroll
+        for (int n2 = 0; n2 < P2; ++n2) z[n2] = n2 < NIN ? stage[(n1 + P1 * n2) * CL + ln] : make_float2(0.f, 0.f);
+        cola_store<P1, P2, -1, NIN, CL>(z, n1, ln, buf, tws);
+      }
+    __syncthreads();  // the staging buffer is free: fetch the next item
+    if (t == 0 && w + (int)gridDim.x < items) issue(w + gridDim.x);
+    if (!skip) {
+      {
+        const int k2 = t / CL, ln = t - k2 * CL, kx = x0 + ln;
+        float2 y[P1];
+        colb_load<P1, P2, CL>(y, k2, ln, buf);
+        DFT<P1, -1>::run(y);
+#pragma unroll
+        for (int k1 = 0; k1 < P1; ++k1) y[k1] = cscale(y[k1], __ldg(op.That + (size_t)(k2 + P2 * k1) * L + kx));
+        colb_inv_store<P1, P2, CL>(y, k2, ln, buf, tws);
+      }
+      __syncthreads();
+      for (int jj = t; jj < P1 * CL; jj += NT) {
+        const int n1 = jj / CL, ln = jj - n1 * CL;
+        float2 z[P2];
+        cola_load<P1, P2, 1, CL>(z, n1, ln, buf);
+#pragma unroll
+        for (int n2 = 0; n2 < NIN; ++n2) g[(size_t)(n1 + P1 * n2) * L + x0 + ln] = z[n2];  // rows < N only
+      }
+    }
+    __syncthreads();  // buf is rewritten by the next item
   }
 }
 
@@ -395,9 +474,33 @@ void toep_normal_impl(const SpiralOp& op, const float2* x, float2* y, float2* G,
     cudaFuncSetAttribute(k1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smr);
     k1<<<grow, Sp::NT, smr, s>>>(op, x, G, dummy, 0);
   }
-  auto k2 = k_toep_cols<P1, P2, PAD>;
-  cudaFuncSetAttribute(k2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smc);
-  k2<<<dim3(L / kLines, nb * op.nc), Sp::NT, smc, s>>>(op, G, a ? a->done : nullptr);
+  // persistent column pass (P1 > P2): N rows staged per item, TMA boxes of at
+  // most 256 rows, every TMA destination 128-byte aligned
+  bool wide = false;
+  if constexpr (P1 > P2) {
+    const int box_rows = op.n <= 256 ? op.n : op.n / 2;
+    CUtensorMap mG{};
+    const size_t smw = 1024 + ((size_t)op.n * P1 + (size_t)L * P1 + L) * sizeof(float2) + 16;
+    wide = op.n % box_rows == 0 && ((size_t)box_rows * P1 * 8) % 128 == 0 && smw <= 227 * 1024 &&
+           encode_plane_map(&mG, G, op.n, L, (int64_t)nb * op.nc, P1, box_rows);
+    if (wide) {
+      auto k2 = k_toep_cols_w<P1, P2, PAD>;
+      static thread_local int bps = 0;
+      cudaFuncSetAttribute(k2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smw);
+      if (bps == 0 && cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k2, L, smw) != cudaSuccess) bps = 1;
+      int dev = 0, nsm = 0;
+      cudaGetDevice(&dev);
+      cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+      const int64_t items = (int64_t)P2 * nb * op.nc;
+      const int grid = (int)std::min<int64_t>(items, (int64_t)std::max(1, bps) * std::max(1, nsm));
+      k2<<<grid, L, smw, s>>>(op, mG, G, a ? a->done : nullptr, nb * op.nc, box_rows);
+    }
+  }
+  if (!wide) {
+    auto k2 = k_toep_cols<P1, P2, PAD>;
+    cudaFuncSetAttribute(k2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smc);
+    k2<<<dim3(L / kLines, nb * op.nc), Sp::NT, smc, s>>>(op, G, a ? a->done : nullptr);
+  }
   if (a) {
     auto k3 = k_toep_rows_inv<P1, P2, true, PAD>;
     cudaFuncSetAttribute(k3, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smr);
