@@ -377,6 +377,15 @@ pico_status pico_set_tuning(pico_ctx* ctx, const pico_tuning* in);
  * Overwrites the context's CG workspace; synchronises the stream. */
 pico_status pico_autotune(pico_ctx* ctx, int32_t iters, pico_tuning* out, double* times_us, int32_t ntimes);
 
+/* The choice pico_autotune makes from its measurements, as a host-only pure
+ * function (no context, no GPU): times_us is the [4][6] table described above
+ * (NaN = not measured; a batch counts only where the column-FFT / Toeplitz
+ * time is finite), max_batch the batch capacity, gram != 0 if the Gram rows
+ * may be chosen.  Fills every field of *out (gram_kc = 0 and gram_min_batch =
+ * max_batch + 1 when no Gram candidate applies; probe_batch = 0 when the
+ * choice is max_batch).  PICO_E_INVALID without any measured batch. */
+pico_status pico_tune_select(const double* times_us, int32_t max_batch, int32_t gram, pico_tuning* out);
+
 /* Wait for all work of the context; returns the first asynchronous error
  * (PICO_E_CUDA) or PICO_E_BREAKDOWN if a CG system broke down since the last
  * pico_sync. */

@@ -117,6 +117,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "pico_get_tuning": ([vp, ctypes.POINTER(pico_tuning)], i32),
         "pico_set_tuning": ([vp, ctypes.POINTER(pico_tuning)], i32),
         "pico_autotune": ([vp, i32, ctypes.POINTER(pico_tuning), ctypes.POINTER(f64), i32], i32),
+        "pico_tune_select": ([ctypes.POINTER(f64), i32, i32, ctypes.POINTER(pico_tuning)], i32),
         "pico_footprint": ([ctypes.POINTER(pico_operator_desc), i32, ctypes.POINTER(ctypes.c_size_t)], i32),
         "pico_server_create": ([ctypes.c_size_t, i32, i32, ctypes.POINTER(vp)], i32),
         "pico_server_submit": ([vp, ctypes.POINTER(pico_request), ctypes.POINTER(i64)], i32),
@@ -368,6 +369,19 @@ def pico_autotune(ctx, iters: int = 0) -> tuple[dict, dict]:
         if row:
             table[name] = row
     return {f: getattr(t, f) for f, _ in pico_tuning._fields_}, table
+
+
+def pico_tune_select(table: dict, max_batch: int, gram: bool = True) -> dict:
+    """The autotuner's choice for a table {candidate: {batch: us per image-iteration}} (host only)."""
+    batches = (16, 32, 64, 128, 256, max_batch)
+    times = (ctypes.c_double * 24)(*([float("nan")] * 24))
+    for k, name in enumerate(AUTOTUNE_CANDIDATES):
+        for i, b in enumerate(batches):
+            if b in table.get(name, {}):
+                times[k * 6 + i] = table[name][b]
+    t = pico_tuning()
+    _check(None, load_library().pico_tune_select(times, max_batch, 1 if gram else 0, ctypes.byref(t)))
+    return {f: getattr(t, f) for f, _ in pico_tuning._fields_}
 
 
 def pico_sync(ctx) -> None:

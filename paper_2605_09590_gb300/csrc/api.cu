@@ -1533,45 +1533,71 @@ pico_status pico_autotune(pico_ctx* c, int32_t iters, pico_tuning* out, double* 
   c->profiling = prof;
   if (st != PICO_OK) return st;
   if ((st = cuda_check(c, "pico_autotune")) != PICO_OK) return st;
-  // largest measured batch
-  int top = -1;
-  for (int i = 0; i < kNb; ++i)
-    if (nb_ok[i] && (top < 0 || nbs[i] > nbs[top])) top = i;
-  pico_tuning best = cur;
-  int vg = 0;  // Gram candidate: fastest at the largest batch
-  if (c->gram)
-    for (int k = 1; k < kCand; ++k)
-      if (std::isfinite(t[k][top]) && (vg == 0 || t[k][top] < t[vg][top])) vg = k;
-  auto chosen = [&](int i) { return (vg && nbs[i] >= best.gram_min_batch) ? t[vg][i] : t[0][i]; };
-  if (vg) {
-    best.gram_kc = cand_kc[vg];
-    best.gram_a_tmem = cand_at[vg];
-    // smallest batch from which on the Gram operator is never slower
-    best.gram_min_batch = c->max_batch + 1;
-    std::vector<int> order;
-    for (int i = 0; i < kNb; ++i)
-      if (nb_ok[i]) order.push_back(i);
-    std::sort(order.begin(), order.end(), [&](int a, int b) { return nbs[a] > nbs[b]; });
-    for (int i : order) {
-      if (!(t[vg][i] <= t[0][i])) break;
-      best.gram_min_batch = nbs[i];
-    }
+  double flat[kCand * kNb];
+  for (int k = 0; k < kCand; ++k)
+    for (int i = 0; i < kNb; ++i) flat[k * kNb + i] = t[k][i];
+  pico_tuning best{};
+  if ((st = pico_tune_select(flat, c->max_batch, c->gram ? 1 : 0, &best)) != PICO_OK)
+    return fail(c, st, "no candidate could be timed");
+  if (!c->gram) {  // nothing to choose for the Gram operator: keep its settings
+    best.gram_min_batch = cur.gram_min_batch;
+    best.gram_a_tmem = cur.gram_a_tmem;
   }
-  // the largest batch within 3 % of the lowest time per image
-  double tmin = INFINITY;
-  for (int i = 0; i < kNb; ++i)
-    if (nb_ok[i] && std::isfinite(chosen(i))) tmin = std::min(tmin, chosen(i));
-  int pb = top;
-  for (int i = 0; i < kNb; ++i)
-    if (nb_ok[i] && chosen(i) <= 1.03 * tmin && (pb < 0 || !(chosen(pb) <= 1.03 * tmin) || nbs[i] > nbs[pb])) pb = i;
-  best.probe_batch = (pb >= 0 && nbs[pb] < c->max_batch) ? nbs[pb] : 0;
   if (times_us)
     for (int k = 0; k < kCand; ++k)
       for (int i = 0; i < kNb; ++i)
         if (k * kNb + i < ntimes) times_us[k * kNb + i] = t[k][i];
-  if (!c->gram) best.gram_kc = 0;
   if ((st = pico_set_tuning(c, &best)) != PICO_OK) return st;
   if (out) pico_get_tuning(c, out);
+  return PICO_OK;
+}
+
+pico_status pico_tune_select(const double* t, int32_t max_batch, int32_t gram, pico_tuning* out) {
+  if (!t || !out || max_batch < 1) return PICO_E_INVALID;
+  constexpr int kCand = 4, kNb = 6;
+  const int cand_kc[kCand] = {0, 16, 16, 8}, cand_at[kCand] = {0, 0, 1, 0};
+  const int nbs[kNb] = {16, 32, 64, 128, 256, max_batch};
+  bool ok[kNb];
+  for (int i = 0; i < kNb; ++i) {
+    ok[i] = nbs[i] <= max_batch && std::isfinite(t[i]);
+    for (int k = 0; k < i; ++k) ok[i] = ok[i] && nbs[k] != nbs[i];
+  }
+  int top = -1;  // largest batch the column-FFT / Toeplitz operator was timed at
+  for (int i = 0; i < kNb; ++i)
+    if (ok[i] && (top < 0 || nbs[i] > nbs[top])) top = i;
+  if (top < 0) return PICO_E_INVALID;
+  pico_tuning best{};
+  best.gram_min_batch = max_batch + 1;
+  best.gram_kc = 0;
+  best.gram_a_tmem = 0;
+  int vg = 0;  // Gram candidate: the fastest at the largest batch
+  if (gram)
+    for (int k = 1; k < kCand; ++k)
+      if (std::isfinite(t[k * kNb + top]) && (vg == 0 || t[k * kNb + top] < t[vg * kNb + top])) vg = k;
+  if (vg) {
+    best.gram_kc = cand_kc[vg];
+    best.gram_a_tmem = cand_at[vg];
+    // the smallest batch from which on the Gram operator is never slower
+    int order[kNb], no = 0;
+    for (int i = 0; i < kNb; ++i)
+      if (ok[i]) order[no++] = i;
+    std::sort(order, order + no, [&](int a, int b) { return nbs[a] > nbs[b]; });
+    for (int j = 0; j < no; ++j) {
+      const int i = order[j];
+      if (!(t[vg * kNb + i] <= t[i])) break;
+      best.gram_min_batch = nbs[i];
+    }
+  }
+  auto chosen = [&](int i) { return (vg && nbs[i] >= best.gram_min_batch) ? t[vg * kNb + i] : t[i]; };
+  // the largest batch within 3 % of the lowest time per image
+  double tmin = INFINITY;
+  for (int i = 0; i < kNb; ++i)
+    if (ok[i] && std::isfinite(chosen(i))) tmin = std::min(tmin, chosen(i));
+  int pb = -1;
+  for (int i = 0; i < kNb; ++i)
+    if (ok[i] && chosen(i) <= 1.03 * tmin && (pb < 0 || nbs[i] > nbs[pb])) pb = i;
+  best.probe_batch = (pb >= 0 && nbs[pb] < max_batch) ? nbs[pb] : 0;
+  *out = best;
   return PICO_OK;
 }
 
