@@ -341,7 +341,7 @@ __global__ void __launch_bounds__(ColShape<N1, N2>::NT, 1)
 // n1 + M1 n2 for every coil.
 // ---------------------------------------------------------------------------
 template <int M1, int M2>
-__global__ void __launch_bounds__(RowShape<M1, M2>::NT, 1)
+__global__ void __launch_bounds__(RowShape<M1, M2>::NT, (RowShape<M1, M2>::NT <= 320 ? 2 : 1))
     k_row_adjoint(CartOp op, const float2* __restrict__ G, float2* __restrict__ out) {
   constexpr int M = M1 * M2;
   constexpr int NT = RowShape<M1, M2>::NT;
