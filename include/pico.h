@@ -387,8 +387,9 @@ pico_status pico_autotune(pico_ctx* ctx, int32_t iters, pico_tuning* out, double
 pico_status pico_tune_select(const double* times_us, int32_t max_batch, int32_t gram, pico_tuning* out);
 
 /* Wait for all work of the context; returns the first asynchronous error
- * (PICO_E_CUDA) or PICO_E_BREAKDOWN if a CG system broke down since the last
- * pico_sync. */
+ * (PICO_E_CUDA), PICO_E_TIMEOUT if a kernel's bounded pipeline wait (the
+ * tensor-core Gram operator, the TMA-staged Toeplitz column pass) gave up, or
+ * PICO_E_BREAKDOWN if a CG system broke down since the last pico_sync. */
 pico_status pico_sync(pico_ctx* ctx);
 
 /* Text of the last error of this context ("" if none).  Owned by the context. */
