@@ -10,12 +10,24 @@ Cartesian workload.  ``value`` is CG solves (probes + replicas) per second
 over all ranks, inputs resident in HBM; ``e2e`` is the same metric through the
 C ABI from host buffers (operator upload, maps read back) per step.
 
+With one GPU the same line also carries, under their own keys, the spiral
+240x240 R=2 workload (throughput and time to a 1 %-error map under both
+solver rules), the nonlinear CS workload and the serving mix (p50 / p99
+request latency); ``--no-extra`` leaves them out.
+
+``--gpus N`` runs N ranks (one per GPU): started by torch.distributed.run, or
+re-launched through it when the environment has no WORLD_SIZE.  Each rank
+takes its own probe range and the partial running sums are combined with one
+all-reduce per step.
+
 ``--impl reference`` times the CPU oracle on the host cores instead (a bounded
-sample of the same workload per step).
+sample of the same workload per step, one single-threaded oracle process per
+core).
 """
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import math
 import os
@@ -33,6 +45,7 @@ METRIC = "time to 1%-error noise map, PICO vs PMR on one GB300; probe-solves/s; 
 UNIT = "probe-solves/s"
 SEED_PICO, SEED_PMR = 20260521, 7700417
 FP32_LANES_PER_SM, N_SM, SM_MAX_MHZ = 128, 152, 2070.0
+CSRC = os.path.join(ROOT, "paper_2605_09590_gb300", "csrc")
 
 
 def parse():
@@ -45,14 +58,34 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-t1pct", action="store_true")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="leave out the spiral, CS and serving keys of the default one-GPU line")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the default launch shapes instead of pico_autotune's choice")
-    ap.add_argument("--serving", type=int, default=0, help="also run the serving mix with this many requests")
+    ap.add_argument("--serving", type=int, default=200, help="requests of the serving mix (0: none)")
+    ap.add_argument("--serving-load", type=float, default=0.8, help="offered load of the serving mix")
     ap.add_argument("--t1pct-spiral", action="store_true",
-                    help="time to 1%% on the spiral workload (exact reference by unit-vector probing, minutes)")
+                    help="with --workload spiral240_rN: time to 1%% against the full exact diagonal (minutes)")
     ap.add_argument("--t1pct-cs", type=int, default=0, metavar="NREF",
                     help="time to 1%% on the CS workload against method-specific references of NREF samples")
     return ap.parse_args()
+
+
+def maybe_relaunch(args):
+    """``--gpus N`` without a launcher: re-exec this script under
+    torch.distributed.run with N ranks; a mismatch with WORLD_SIZE is an error."""
+    env = os.environ.get("WORLD_SIZE")
+    if args.gpus > 1 and env is None:
+        import socket
+        s = socket.socket()
+        s.bind(("127.0.0.1", 0))
+        port = s.getsockname()[1]
+        s.close()
+        cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", f"--nproc-per-node={args.gpus}",
+               "--master-addr", "127.0.0.1", f"--master-port={port}", os.path.abspath(__file__)] + sys.argv[1:]
+        os.execv(sys.executable, cmd)
+    if env is not None and int(env) != args.gpus:
+        sys.exit(f"bench.py: --gpus {args.gpus} does not match WORLD_SIZE={env}")
 
 
 def workload(name):
@@ -78,13 +111,17 @@ def flops_per_probe(w):
     return w.nc * ((2 * n + 2 * L) * fft + 16 * n * n + 2 * L * L)
 
 
-def bytes_per_probe_normal(w):
-    """HBM bytes of one normal-operator application per image in the CG loop.
-    Cartesian: reads r and p_old, writes p and q.  Spiral: the same four images
-    plus the coil grids written and read twice (4 x nc x n x 2n complex64)."""
-    if w.kind == "cartesian":
-        return 4 * w.ny * w.nx * 8
-    return 4 * w.ny * w.nx * 8 + 4 * w.nc * w.ny * 2 * w.ny * 8
+def alg_bytes_normal(w, K):
+    """Algorithmic HBM bytes of one normal-operator launch over K images inside
+    CG: every image reads r and p_old and writes p and q (4 images of 8 bytes
+    per voxel), plus one pass over the operator's own data -- the whitened
+    sensitivities S (Cartesian) or S and the real Toeplitz kernel T^ on the
+    2n x 2n grid (spiral)."""
+    V = w.ny * w.nx * 8
+    S = w.nc * V
+    if w.kind == "spiral":
+        S += (2 * w.ny) ** 2 * 4
+    return 4 * K * V + S
 
 
 def flops_2d_normal(w):
@@ -96,10 +133,20 @@ def flops_2d_normal(w):
     return w.nc * (4 * n * 5 * n * math.log2(n) + 18 * n * n)
 
 
-# dram__bytes_read.sum + dram__bytes_write.sum per launch of k_gram_normal<16>
-# (ncu --set full, the capture summarised in the profiles folder); remove the
-# entry whenever the kernel changes.
-GRAM_TRAFFIC = {("knee320_r2", 256): 1011.871e6 + 387.489e6}
+def kernel_digest(*names):
+    """Short hash of the kernel sources a measured counter belongs to."""
+    h = hashlib.sha256()
+    for nm in names:
+        with open(os.path.join(CSRC, nm), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+# dram__bytes_read.sum + dram__bytes_write.sum per launch of the dominant
+# kernel from one ncu capture (the summaries in the profiles folder), keyed by
+# (workload, images per launch, digest of the kernel sources at capture time):
+# a changed kernel no longer matches and its traffic is reported as null.
+TRAFFIC = {}
 
 
 def measured_peaks():
@@ -107,31 +154,59 @@ def measured_peaks():
         return json.load(f)
 
 
-def gram_roofline(w, K, avg_s, launches):
-    """Roofline of the tensor-core normal operator (k_gram_normal).
+def traffic_of(w, K, kernel_files):
+    dig = kernel_digest(*kernel_files)
+    return TRAFFIC.get((w.name, K, dig)), dig
 
-    Algorithmic work per launch: nx dense complex (ny x ny) x (ny x K)
-    products, 8 ny^2 nx flops per image; the tensor pipe issues three TF32
-    products per complex term (the FP32-accurate split), so the executed TF32
-    work is 3x that.  Peak: TF32 = measured bf16 burst x (1.1 / 2.25), the
-    nominal dense TF32 / bf16 ratio.  HBM bytes per launch: r, p_old read and
-    p, q written (4 images per probe) plus the split G planes once."""
+
+def gram_roofline(w, K, avg_s, launches):
+    """Roofline of the tensor-core normal operator (k_gram_normal), HBM-bound.
+
+    achieved = algorithmic bytes per launch (alg_bytes_normal: r, p_old read,
+    p, q written per image, one pass over S) / the launch's average CUDA-event
+    time, against the measured copy bandwidth.  The split G planes the kernel
+    streams instead of S are not algorithmic bytes; they show up in `traffic`.
+    The tensor view is kept as a secondary key: nx dense complex
+    (ny x ny) x (ny x K) products, 8 ny^2 nx flops per image, issued as three
+    TF32 products (dense-equivalent work, not the method's own flop count)."""
     mp = measured_peaks()
-    alg = 8.0 * w.ny * w.ny * w.nx * K
-    tf32 = 3.0 * alg
-    peak = mp["bf16_tflops"] * 1.1 / 2.25
-    achieved = tf32 / avg_s / 1e12
-    gbytes = 2 * w.nx * 2 * w.ny * w.ny * 4
-    hbm = (4 * K * w.ny * w.nx * 8 + gbytes) / avg_s / 1e9
-    # DRAM bytes per launch from one ncu capture of the current kernel on this workload
-    traffic = GRAM_TRAFFIC.get((w.name, K))
-    return {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-            "traffic": traffic,
-            "kernel": "k_gram_normal (tcgen05 kind::tf32, 3-term split, fused CG direction update, TMA-tensor epilogue)",
+    alg = alg_bytes_normal(w, K)
+    achieved = alg / avg_s / 1e9
+    traffic, dig = traffic_of(w, K, ("gram.cu", "tc_util.cuh", "kernels.cuh"))
+    cplx = 8.0 * w.ny * w.ny * w.nx * K
+    tf32_peak = mp["bf16_tflops"] * 1.1 / 2.25
+    return {"bound": "hbm", "achieved": achieved, "peak": mp["hbm_gbs"], "unit": "GB/s",
+            "frac": achieved / mp["hbm_gbs"], "traffic": traffic,
+            "traffic_over_algorithmic": traffic / alg if traffic else None,
+            "kernel": "k_gram_normal (tcgen05 kind::tf32, 3-term split, fused CG direction update, TMA epilogue)",
+            "kernel_digest": dig, "avg_launch_ms": avg_s * 1e3, "launches": launches,
+            "algorithmic_bytes_per_launch": alg,
+            "peak_note": "measured copy bandwidth (of measured)",
+            "tensor_dense_equivalent": {"achieved_TFLOPs": 3.0 * cplx / avg_s / 1e12, "peak_TFLOPs": tf32_peak,
+                                        "frac": 3.0 * cplx / avg_s / 1e12 / tf32_peak,
+                                        "note": "3 TF32 products per complex term of the dense per-column "
+                                                "Gram contraction; peak = measured bf16 burst x 1.1/2.25"}}
+
+
+def fft_roofline(w, K, avg_s, launches):
+    """Roofline of an FFT-based normal operator (column FFTs or the three
+    Toeplitz passes), bound by FP32 issue; the HBM view of the same launch
+    (alg_bytes_normal) is a secondary key."""
+    mp = measured_peaks()
+    flops = K * flops_per_probe(w)
+    achieved = flops / avg_s / 1e12
+    peak = N_SM * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    files = ("cart_impl.cuh", "kernels.cuh") if w.kind == "cartesian" else ("spiral_impl.cuh", "kernels.cuh")
+    traffic, dig = traffic_of(w, K, files)
+    alg = alg_bytes_normal(w, K)
+    return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            "traffic": traffic, "kernel_digest": dig,
+            "kernel": "k_col_normal (fused CG prologue)" if w.kind == "cartesian" else
+                      "k_toep_rows_fwd + k_toep_cols_w + k_toep_rows_inv (one normal operator)",
             "avg_launch_ms": avg_s * 1e3, "launches": launches,
-            "algorithmic_TFLOPs": alg / avg_s / 1e12,
-            "hbm_GBps_algorithmic": hbm, "hbm_frac_of_measured": hbm / mp["hbm_gbs"],
-            "peak_note": "TF32 dense peak derived from the measured bf16 burst (of measured x nominal ratio)"}
+            "peak_note": "FP32 FMA peak 152 SM x 128 lanes x 2 x 2070 MHz (nominal max clock)",
+            "hbm": {"achieved_GBps": alg / avg_s / 1e9, "peak_GBps": mp["hbm_gbs"],
+                    "frac": alg / avg_s / 1e9 / mp["hbm_gbs"], "algorithmic_bytes_per_launch": alg}}
 
 
 def normal_ops_per_probe(w):
@@ -151,7 +226,8 @@ def cores_in_use():
 # CPU oracle (reference arm and cpu_baseline leg)
 # ---------------------------------------------------------------------------
 def oracle_sample(w, inp, nprobe=1, nrep=1):
-    """Time the oracle on a bounded sample; returns (probe-solves/s, seconds, description)."""
+    """Time the oracle on a bounded sample in this process (one core);
+    returns (probe-solves/s, seconds, description)."""
     import numpy as np
     from oracle import ops as O
     from oracle import pico as OP
@@ -176,12 +252,10 @@ def oracle_sample(w, inp, nprobe=1, nrep=1):
         sigma = cs_sigma(w, np.sqrt(np.mean(np.abs(b[:, inp["mask"].astype(bool)]) ** 2)))
         OCS.pmr_cs(f, SEED_PMR, 0, nrep, sigma)
         t2 = time.perf_counter()
-        # a step = one reconstruction + K probes + K replicas; the sample runs one of each
         per_pair = (t2 - t1)
         value = 2.0 * w.probes / ((t1 - t0) + w.probes * per_pair)
         return value, t2 - t0, (f"FISTA reconstruction ({t1 - t0:.1f} s) + {nprobe} Jacobian probe + {nrep} "
                                 f"PMR replica ({per_pair:.1f} s), scaled to a step of {w.probes} + {w.probes}")
-    # spiral: one exact-NUDFT normal operator application, scaled to whole probes/replicas
     op = O.Operator(inp["smaps"], inp["noise_cov"], traj=inp["traj"])
     x = np.ones((w.ny, w.nx), dtype=np.complex128)
     t0 = time.perf_counter()
@@ -191,6 +265,57 @@ def oracle_sample(w, inp, nprobe=1, nrep=1):
     per_rep = w.max_iter * dt
     return 2.0 / (per_probe + per_rep), dt, (f"one exact-NUDFT A^H A application ({dt:.1f} s), scaled to "
                                              f"{normal_ops_per_probe(w)} per probe and {w.max_iter} per replica")
+
+
+_OW = {}   # per-process state of the oracle pool workers
+
+
+def _oracle_worker_init(name):
+    from oracle import ops as O
+    w, inp = workload(name)
+    _OW["w"] = w
+    _OW["op"] = O.Operator(inp["smaps"], inp["noise_cov"], mask=inp["mask"])
+
+
+def _oracle_task(task):
+    from oracle import pico as OP
+    kind, i = task
+    w, op = _OW["w"], _OW["op"]
+    if kind == "ready":
+        time.sleep(0.2)
+        return os.getpid()
+    if kind == "pico":
+        OP.pico(op, SEED_PICO, i, 1, 0.0, w.max_iter, 0.0)
+    else:
+        OP.pmr(op, SEED_PMR, i, 1, w.sigma, 0.0, w.max_iter, 0.0)
+    return os.getpid()
+
+
+class OraclePool:
+    """One single-threaded oracle process per host core (spawned, so that no
+    process is forked after the first GPU call).  A step solves one PICO probe
+    and one PMR replica per core; the value is solves per wall-clock second."""
+
+    def __init__(self, name):
+        import multiprocessing as mp
+        for var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+            os.environ[var] = "1"
+        self.cores = cores_in_use()
+        self.pool = mp.get_context("spawn").Pool(self.cores, initializer=_oracle_worker_init, initargs=(name,))
+        self.pool.map(_oracle_task, [("ready", i) for i in range(self.cores)], chunksize=1)
+        self.next = 0
+
+    def step(self):
+        tasks = [(k, self.next + i) for i in range(self.cores) for k in ("pico", "pmr")]
+        self.next += self.cores
+        t0 = time.perf_counter()
+        pids = self.pool.map(_oracle_task, tasks, chunksize=1)
+        dt = time.perf_counter() - t0
+        return len(tasks) / dt, dt, len(set(pids))
+
+    def close(self):
+        self.pool.close()
+        self.pool.join()
 
 
 def arm_config(w, world=1):
@@ -211,7 +336,10 @@ def arm_config(w, world=1):
     return {"workload": w.name, "ny": w.ny, "nx": w.nx, "coils": w.nc, "R": w.R, "acs": w.acs,
             "noise_cov": "correlated" if w.noise_corr else "white", "lambda_rel": w.lam,
             "cg_iters": w.max_iter, "probes_per_step": K, "replicas_per_step": K,
-            "l2": f"working set {4 * K * n * 8 / 1e9:.2f} GB of CG vectors > 129 MB L2",
+            "l2": (f"working set {4 * K * n * 8 / 1e9:.2f} GB of CG vectors > 129 MB L2 (no flush needed)"
+                   if 4 * K * n * 8 > 129e6 else
+                   f"working set {4 * K * n * 8 / 1e6:.1f} MB fits in L2: steps run back to back without a "
+                   f"flush (a latency-bound workload)"),
             "parallelism": f"probe shards x{world}"}
 
 
@@ -225,22 +353,37 @@ def run_reference(args):
     if rank != 0:
         return
     w, inp = workload(args.workload)
-    for _ in range(args.warmup):
-        oracle_sample(w, inp)
-    times, vals = [], []
-    for _ in range(args.steps):
-        v, dt, sample = oracle_sample(w, inp)
-        times.append(dt)
-        vals.append(v)
+    if w.kind == "cartesian":
+        pool = OraclePool(w.name)
+        for _ in range(args.warmup):
+            pool.step()
+        times, vals, procs = [], [], 0
+        for _ in range(args.steps):
+            v, dt, procs = pool.step()
+            times.append(dt)
+            vals.append(v)
+        pool.close()
+        cores = pool.cores
+        sample = (f"one PICO probe + one PMR replica ({w.max_iter} CG iterations each) per core in "
+                  f"{cores} single-threaded FP64 NumPy oracle processes ({procs} took work), per step")
+    else:
+        for _ in range(args.warmup):
+            oracle_sample(w, inp)
+        times, vals = [], []
+        for _ in range(args.steps):
+            v, dt, sample = oracle_sample(w, inp)
+            times.append(dt)
+            vals.append(v)
+        cores = 1
+        sample = sample + ", FP64 NumPy on one core, per step"
     total = sum(times)
-    value = len(vals) / sum(1.0 / v for v in vals)
-    sample = sample + ", FP64 NumPy, per step"
+    value = sum(v * t for v, t in zip(vals, times)) / total
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128", "data": "synthetic",
         "config": arm_config(w),
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -316,52 +459,65 @@ def exact_variance_cartesian(op, w, torch):
         rhs[torch.arange(nb), torch.arange(y0, y0 + nb)] = 1.0
         x = op.cg(rhs, 100, 1e-6)
         diag[y0:y0 + nb] = x[torch.arange(nb), torch.arange(y0, y0 + nb)].real.double()
-    return diag
+    return diag.flatten(), None
 
 
-def exact_variance_unit_probes(op, w, torch, batch=256):
-    """Exact diag(Sigma) of any operator by unit-vector probing on the GPU:
+def exact_variance_unit_probes(op, w, torch, voxels=None, batch=256):
+    """Exact diag(Sigma) by unit-vector probing on the GPU:
     Sigma_kk = x_k^H M x_k with x_k = (M + lam)^-1 e_k (one converged solve and
-    one normal-operator application per voxel, batched)."""
+    one normal-operator application per voxel, batched).  With ``voxels`` only
+    those (flat) voxel indices are computed."""
     n = w.ny * w.nx
+    idx = torch.arange(n, device="cuda") if voxels is None else voxels
     lam = op.info["lambda_phys"]
-    diag = torch.empty(n, dtype=torch.float64, device="cuda")
-    for k0 in range(0, n, batch):
-        nb = min(batch, n - k0)
+    diag = torch.empty(idx.numel(), dtype=torch.float64, device="cuda")
+    for k0 in range(0, idx.numel(), batch):
+        nb = min(batch, idx.numel() - k0)
         rhs = torch.zeros((nb, n), dtype=torch.complex64, device="cuda")
-        rhs[torch.arange(nb), torch.arange(k0, k0 + nb)] = 1.0
+        rhs[torch.arange(nb), idx[k0:k0 + nb]] = 1.0
         x = op.cg(rhs.view(nb, w.ny, w.nx), 100, 1e-6)
         y = op.apply_normal(x)                       # (M + lam) x
         xy = (x.conj() * y).real.double().flatten(1).sum(1)
         xx = (x.abs() ** 2).double().flatten(1).sum(1)
         diag[k0:k0 + nb] = xy - lam * xx
-    return diag.view(w.ny, w.nx)
+    return diag, voxels
 
 
 _EXACT = {}   # exact reference diagonals, computed once per workload
 
 
-def measure_time_to_1pct(op, w, torch, pico, max_n=20000, step=10, cg=None):
+def measure_time_to_1pct(op, w, torch, pico, max_n=20000, step=10, cg=None, arms=None, subset=0):
     """cg = (max_iter, rtol) of the estimators' solves; default the workload's
-    fixed iteration count (the reference is always the converged diagonal)."""
+    fixed iteration count (the reference is always the converged diagonal).
+    With ``subset`` > 0 the reference and the NRMSE cover that many seeded
+    random voxels (unit-vector probing of the whole image takes minutes)."""
     max_iter, rtol = cg if cg else (w.max_iter, 0.0)
-    if w.name in _EXACT:
-        ref, how = _EXACT[w.name]
-    elif w.kind == "cartesian":
-        ref = exact_variance_cartesian(op, w, torch)
+    key = (w.name, subset)
+    if key in _EXACT:
+        ref, vox, how = _EXACT[key]
+    elif w.kind == "cartesian" and not subset:
+        ref, vox = exact_variance_cartesian(op, w, torch)
         how = f"exact diag(Sigma) from {w.ny} structured converged CG solves"
+    elif subset:
+        import numpy as np
+        g = np.random.default_rng(0x5EB)
+        vox = torch.from_numpy(np.sort(g.choice(w.ny * w.nx, subset, replace=False))).cuda()
+        ref, vox = exact_variance_unit_probes(op, w, torch, vox)
+        how = (f"exact diag(Sigma) by unit-vector probing of {subset} seeded random voxels; NRMSE over "
+               f"those voxels")
     else:
-        ref = exact_variance_unit_probes(op, w, torch)
+        ref, vox = exact_variance_unit_probes(op, w, torch)
         how = f"exact diag(Sigma) by unit-vector probing ({w.ny * w.nx} converged solves)"
-    _EXACT[w.name] = (ref, how)
+    _EXACT[key] = (ref, vox, how)
     ref_std = ref.clamp_min(0).sqrt()
     nref = torch.linalg.vector_norm(ref_std)
     out = {"reference": how, "step": step, "cg": {"max_iter": max_iter, "rtol": rtol},
            "threshold": 0.01, "nrmse_on": "std maps",
            "reference_range": [float(ref.min()), float(ref.max())]}
-    # the three probe families of the ablation (Sec. 3.2.2; Eqs. 18-20) and PMR
-    arms = (("pico", pico.PICO_PROBE_PHASE), ("pico_rademacher", pico.PICO_PROBE_RADEMACHER),
-            ("pico_gauss", pico.PICO_PROBE_GAUSS), ("pmr", None))
+    if arms is None:
+        # the three probe families of the ablation (Sec. 3.2.2; Eqs. 18-20) and PMR
+        arms = (("pico", pico.PICO_PROBE_PHASE), ("pico_rademacher", pico.PICO_PROBE_RADEMACHER),
+                ("pico_gauss", pico.PICO_PROBE_GAUSS), ("pmr", None))
     for name, kind in arms:
         s = torch.zeros((w.ny, w.nx), dtype=torch.float64, device="cuda")
         ss = torch.zeros_like(s)
@@ -378,15 +534,14 @@ def measure_time_to_1pct(op, w, torch, pico, max_n=20000, step=10, cg=None):
             torch.cuda.synchronize()
             elapsed += ev0.elapsed_time(ev1) / 1e3
             n += step
-            err = float(torch.linalg.vector_norm((s / n).clamp_min(0).sqrt() - ref_std) / nref)
-            if n == step:
-                out[name + "_first_map_range"] = [float((s / n).min()), float((s / n).max())]
+            est = (s.flatten() if vox is None else s.flatten()[vox]) / n
+            err = float(torch.linalg.vector_norm(est.clamp_min(0).sqrt() - ref_std) / nref)
             if n in (10, 50, 100, 200, 500, 1000, 2000, 5000, 10000):
                 curve.append((n, round(err, 5)))
             if err <= 0.01:
                 hit = (n, elapsed, err)
                 break
-        out[name] = ({"N": hit[0], "seconds_in_steps_of_10": hit[1], "nrmse": hit[2], "curve": curve}
+        out[name] = ({"N": hit[0], "seconds_in_steps": hit[1], "nrmse": hit[2], "curve": curve}
                      if hit else {"N": None, "nrmse_at_max": err, "max_n": max_n, "curve": curve})
     return out
 
@@ -438,7 +593,11 @@ def cs_request_inputs(pico, torch, seed, mask, n=320, nc=15, iters=100, levels=4
                 cs_levels=levels)
 
 
-def run_serving(pico, nreq=24, loads=(0.5, 0.8, 0.95), max_active=4):
+def run_serving(pico, nreq=200, loads=(0.8,), max_active=4, ncap=60):
+    """Capacity from a closed loop over the first ``ncap`` requests of the mix
+    (all submitted at once), then an open loop of ``nreq`` Poisson arrivals at
+    each offered load (a fraction of that capacity): p50 / p99 of the request
+    latency (done - arrival) and maps/s."""
     import numpy as np
     import torch
     import synth
@@ -449,18 +608,23 @@ def run_serving(pico, nreq=24, loads=(0.5, 0.8, 0.95), max_active=4):
             if r.pop("cs", False):
                 r.update(cs_request_inputs(pico, torch, r["seed"], mask))
     strip = lambda r: {k: v for k, v in r.items() if k != "kind"}
-    # closed loop: everything submitted at once -> capacity
+    ncap = min(ncap, nreq)
     sv = pico.Server(max_active=max_active, chunk=64)
     t0 = time.perf_counter()
-    ids = [sv.submit(**strip(r)) for r in reqs]
+    ids = [sv.submit(**strip(r)) for r in reqs[:ncap]]
     for i in ids:
         sv.wait(i)
-    cap = nreq / (time.perf_counter() - t0)
+    cap = ncap / (time.perf_counter() - t0)
     sv.close()
-    out = {"requests": nreq, "mix": "50% Cartesian 192-384 / 8-32 coils, 30% spiral 240 R=2-4 (30 CG "
-                                   "iterations), 20% nonlinear CS 320x320 15 coils Poisson-disc R=2 (FISTA 100 "
-                                   "iterations, Jacobian PICO); K in {32,64,128,256}",
-           "capacity_maps_per_s": cap, "max_active": max_active, "loads": []}
+    kinds = {}
+    for r in reqs:
+        k = r["kind"].split("x")[0] if r["kind"].startswith("cart") else r["kind"]
+        kinds[k] = kinds.get(k, 0) + 1
+    out = {"requests": nreq, "request_kinds": kinds,
+           "mix": "50% Cartesian 192-384 / 8-32 coils, 30% spiral 240 R=2-4 (30 CG iterations), 20% "
+                  "nonlinear CS 320x320 15 coils Poisson-disc R=2 (FISTA 100 iterations, Jacobian PICO); "
+                  "K in {32,64,128,256}",
+           "capacity_maps_per_s": cap, "capacity_from_requests": ncap, "max_active": max_active, "loads": []}
     rng = np.random.default_rng(1)
     for rho in loads:
         rate = rho * cap
@@ -476,143 +640,104 @@ def run_serving(pico, nreq=24, loads=(0.5, 0.8, 0.95), max_active=4):
         sv.close()
         lat = np.array([i["t_done"] - i["t_arrival"] for i in infos])
         out["loads"].append({"offered": rho, "p50_s": float(np.percentile(lat, 50)),
-                             "p99_s": float(np.percentile(lat, 99)), "maps_per_s": nreq / wall})
+                             "p99_s": float(np.percentile(lat, 99)), "max_s": float(lat.max()),
+                             "maps_per_s": nreq / wall, "latency_samples": int(lat.size)})
     return out
 
 
 # ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
-def main():
-    args = parse()
-    if args.impl == "reference":
-        run_reference(args)
-        return
-    import numpy as np
-    import torch
-    import torch.distributed as dist
-
-    import paper_2605_09590_gb300 as pico
-    from paper_2605_09590_gb300 import build as pico_build
-
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    torch.cuda.set_device(local)
-    if world > 1:
-        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    if rank == 0:
-        pico_build.build()
-    if world > 1:
-        dist.barrier()
-    pico.load_library()
-
-    w, inp = workload(args.workload)
-    if w.kind == "cs":
-        return main_cs(args, w, inp, torch, dist, pico, world, rank, local)
-    K = w.probes
-    n = w.ny * w.nx
-    dev = torch.device("cuda", local)
-    stream = torch.cuda.current_stream()
-    op = pico.Operator(inp["smaps"], mask=inp.get("mask"), traj=inp.get("traj"), noise_cov=inp["noise_cov"],
-                       lam=w.lam, max_batch=K, power_iters=15, stream=stream.cuda_stream)
-    # launch shapes measured on this GPU (pico_autotune), kept in a JSON cache
-    # that the end-to-end contexts below read back
-    tune_cache = os.environ.get("PICO_TUNE_CACHE") or os.path.join(
-        tempfile.gettempdir(), "pico_tune_%d_%d.json" % (os.getpid(), rank))
-    if not os.environ.get("PICO_TUNE_CACHE"):
-        import atexit
-        atexit.register(lambda: os.path.exists(tune_cache) and os.remove(tune_cache))
-    tuning = None if args.no_autotune else op.autotune(cache=tune_cache)
-    s = torch.zeros((w.ny, w.nx), dtype=torch.float64, device=dev)
-    ss, ps, pss = torch.zeros_like(s), torch.zeros_like(s), torch.zeros_like(s)
-    red = torch.zeros((2, w.ny, w.nx), dtype=torch.float64, device=dev)
-
-    def step(i):
-        begin = (i * world + rank) * K
-        pico.pico_variance_map(op.ctx, SEED_PICO, begin, K, pico.PICO_PROBE_PHASE, w.max_iter, 0.0, s, ss, True)
-        pico.pico_pmr(op.ctx, SEED_PMR, begin, K, w.sigma, w.max_iter, 0.0, ps, pss, True)
-        if world > 1:   # combine the partial maps of all ranks (one exchange per map)
-            red[0].copy_(s)
-            red[1].copy_(ps)
-            dist.all_reduce(red)
-
-    for i in range(args.warmup):
+def timed_steps(step, steps, warmup, torch, dist, world, stream, dev_index, ctxs, pico):
+    """Warm up, then time `steps` calls of step(i) with CUDA events on the
+    launching stream, bracketed by a barrier and a synchronisation on both
+    sides; clocks are sampled meanwhile.  Returns (total_ms, per-step ms,
+    clocks, launches, per-class (ms, launches) of the first context)."""
+    for i in range(warmup):
         step(i)
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
-    clocks = ClockSampler(local)
+    clocks = ClockSampler(dev_index)
     clocks.start()
     time.sleep(0.3)
-    pico.pico_launch_count(op.ctx, reset=True)
-    pico.pico_profile(op.ctx, True)
-    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    for c in ctxs:
+        pico.pico_launch_count(c, reset=True)
+        pico.pico_profile(c, True)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
     ev[0].record(stream)
-    for i in range(args.steps):
-        step(args.warmup + i)
+    for i in range(steps):
+        step(warmup + i)
         ev[i + 1].record(stream)
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
     clk = clocks.stop()
-    per_step = [ev[i].elapsed_time(ev[i + 1]) for i in range(args.steps)]
+    per_step = [ev[i].elapsed_time(ev[i + 1]) for i in range(steps)]
     total_ms = ev[0].elapsed_time(ev[-1])
-    launches = pico.pico_launch_count(op.ctx)
-    norm_ms, norm_n = pico.pico_profile_read(op.ctx, 0)
-    upd_ms, upd_n = pico.pico_profile_read(op.ctx, 1)
-    pmr_ms, pmr_n = pico.pico_profile_read(op.ctx, 2)
-    acc_ms, acc_n = pico.pico_profile_read(op.ctx, 3)
-    pico.pico_profile(op.ctx, False)
+    launches = sum(pico.pico_launch_count(c) for c in ctxs)
+    prof = [pico.pico_profile_read(ctxs[0], k) for k in range(4)]
+    for c in ctxs:
+        pico.pico_profile(c, False)
     if world > 1:
-        t = torch.tensor([total_ms], device=dev)
+        t = torch.tensor([total_ms], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         total_ms = float(t.item())
-    solves = 2 * K * args.steps * world
+    return total_ms, per_step, clk, launches, prof
+
+
+def bench_linear(args, w, inp, pico, torch, dist, world, rank, local, steps, warmup, primary, tune_cache):
+    """One step = PICO map of K probes + PMR map of K replicas on a linear
+    (CG-SENSE) workload; returns (sub-line, operator)."""
+    import numpy as np
+    K = w.probes
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    op = pico.Operator(inp["smaps"], mask=inp.get("mask"), traj=inp.get("traj"), noise_cov=inp["noise_cov"],
+                       lam=w.lam, max_batch=K, power_iters=15, stream=stream.cuda_stream)
+    tuning = None if args.no_autotune else op.autotune(cache=tune_cache)
+    maps = [torch.zeros((w.ny, w.nx), dtype=torch.float64, device=dev) for _ in range(4)]
+    s, ss, ps, pss = maps
+
+    def step(i):
+        begin = (i * world + rank) * K
+        pico.pico_variance_map(op.ctx, SEED_PICO, begin, K, pico.PICO_PROBE_PHASE, w.max_iter, 0.0, s, ss, False)
+        pico.pico_pmr(op.ctx, SEED_PMR, begin, K, w.sigma, w.max_iter, 0.0, ps, pss, False)
+        if world > 1:   # this step's maps over all ranks' probes: the one exchange per step
+            pico.reduce_running_sums(maps)
+
+    total_ms, per_step, clk, launches, prof = timed_steps(step, steps, warmup, torch, dist, world, stream, local,
+                                                          [op.ctx], pico)
+    op.sync()
+    solves = 2 * K * steps * world
     value = solves / (total_ms / 1e3)
-
-    # roofline of the dominant kernel (the fused CG normal operator)
+    (norm_ms, norm_n), (upd_ms, _), (pmr_ms, _), (acc_ms, _) = prof
     avg_norm_s = norm_ms / max(norm_n, 1) / 1e3
-    if op.info["normal_op"] == 1 and K >= 64:
-        roof = gram_roofline(w, K, avg_norm_s, norm_n)
-    else:
-        flops_launch = K * flops_per_probe(w)   # one class-0 launch (group) = one normal op on K images
-        achieved = flops_launch / avg_norm_s / 1e12
-        peak = N_SM * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
-        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": None,
-                "kernel": "k_col_normal (fused CG prologue)" if w.kind == "cartesian" else
-                          "k_toep_rows_fwd + k_toep_cols + k_toep_rows_inv (one normal operator)",
-                "avg_launch_ms": avg_norm_s * 1e3, "launches": norm_n,
-                "hbm_GBps_algorithmic": K * bytes_per_probe_normal(w) / avg_norm_s / 1e9,
-                "peak_note": "FP32 FMA peak 152 SM x 128 lanes x 2 x 2070 MHz (nominal max clock)"}
-    share = {"normal_op_ms": norm_ms, "cg_vector_ms": upd_ms, "pmr_adjoint_ms": pmr_ms, "accumulate_ms": acc_ms}
-
+    gram_on = op.info["normal_op"] == 1 and K >= op.tuning["gram_min_batch"]
+    roof = gram_roofline(w, K, avg_norm_s, norm_n) if gram_on else fft_roofline(w, K, avg_norm_s, norm_n)
+    nsamp = K * world
     line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "c64", "data": "synthetic",
-        "config": arm_config(w, world),
-        "roofline": roof, "kernel_ms_in_timed_region": share,
+        "value": value, "unit": UNIT, "steps": steps, "warmup": warmup, "ms_per_step": total_ms / steps,
+        "config": arm_config(w, world), "roofline": roof,
+        "kernel_ms_in_timed_region": {"normal_op_ms": norm_ms, "cg_vector_ms": upd_ms, "pmr_adjoint_ms": pmr_ms,
+                                      "accumulate_ms": acc_ms},
         "gpu_launches": launches,
         "tuning": {"applied": op.tuning, "autotuned": tuning is not None,
                    "us_per_image_iteration": getattr(op, "autotune_table", None)},
         "clocks": clk,
-        "latency_ms": {"p50": statistics.median(per_step), "p99": max(per_step) if len(per_step) < 100 else
-                       sorted(per_step)[int(0.99 * len(per_step))]},
+        "step_ms": {"p50": statistics.median(per_step), "max": max(per_step)},
+        "last_step_maps": {"pico_mean_variance": float(s.mean() / nsamp), "pmr_mean_variance":
+                           float(ps.mean() / nsamp), "samples_per_map": nsamp},
     }
-
-    # end to end through the C ABI from host buffers
-    if not args.no_e2e:
+    if primary and not args.no_e2e:
         S_h = np.ascontiguousarray(inp["smaps"])
         m_h = inp["mask"] if w.kind == "cartesian" else inp["traj"]
         C_h = inp["noise_cov"]
         out_h = np.empty((2, w.ny, w.nx), dtype=np.float64)
-        e2e_steps = max(2, min(args.steps, 3))
+        e2e_steps = max(2, min(steps, 3))
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for i in range(e2e_steps):
@@ -637,42 +762,41 @@ def main():
                        "d2h_bytes_per_step": int(out_h.nbytes), "steps": e2e_steps,
                        "includes": "pico_init (upload, whitening, power method, workspace) + tuning from the "
                                    "JSON cache + maps + read-back"}
+    return line, op
 
-    if rank == 0 and world == 1 and not args.no_t1pct and (w.kind == "cartesian" or args.t1pct_spiral):
-        t1 = measure_time_to_1pct(op, w, torch, pico, step=10 if w.kind == "cartesian" else 50)
-        if w.kind == "spiral":
-            # the paper's spiral solver rule: at most 100 iterations, relative residual 1e-2 (Sec. 3.2.2)
-            t1["paper_cg_rule"] = measure_time_to_1pct(op, w, torch, pico, step=50, cg=(100, 1e-2))
-        # device seconds per probe and per replica at the bench's batch size, timed separately
-        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
-        s.zero_()
-        ps.zero_()
-        e0.record(stream)
-        pico.pico_variance_map(op.ctx, SEED_PICO, 0, K, pico.PICO_PROBE_PHASE, w.max_iter, 0.0, s, ss, True)
-        e1.record(stream)
-        pico.pico_pmr(op.ctx, SEED_PMR, 0, K, w.sigma, w.max_iter, 0.0, ps, pss, True)
-        e2.record(stream)
-        torch.cuda.synchronize()
-        per = {"pico": e0.elapsed_time(e1) / 1e3 / K, "pmr": e1.elapsed_time(e2) / 1e3 / K}
-        for name in ("pico", "pmr"):
-            t1[name]["seconds_per_sample_batched"] = per[name]
-            if t1[name].get("N"):
-                t1[name]["seconds_at_batched_rate"] = t1[name]["N"] * per[name]
-        line["time_to_1pct"] = t1
 
-    if rank == 0 and world == 1 and args.serving > 0:
-        line["serving"] = run_serving(pico, args.serving)
-
-    if rank == 0 and world == 1 and not args.no_cpu:
-        v, dt, desc = oracle_sample(w, inp)
-        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-                                "sample": f"{desc}, {dt:.1f} s, NumPy FP64 (single-threaded pocketfft; "
-                                          f"{cores_in_use()} cores visible)"}
-    if rank == 0:
-        print(json.dumps(line), flush=True)
-    op.close()
-    if world > 1:
-        dist.destroy_process_group()
+def t1pct_linear(op, w, torch, pico, spiral_subset):
+    """Time to a 1 %-NRMSE standard-deviation map.  Cartesian: the ablation's
+    three probe families and PMR against the exact diagonal.  Spiral: PICO and
+    PMR with 30 fixed CG iterations and with the paper's solver rule (at most
+    100 iterations, relative residual 1e-2, Sec. 3.2.2)."""
+    K = w.probes
+    if w.kind == "cartesian":
+        t1 = measure_time_to_1pct(op, w, torch, pico, step=10)
+        names = ("pico", "pmr")
+    else:
+        arms = (("pico", pico.PICO_PROBE_PHASE), ("pmr", None))
+        t1 = measure_time_to_1pct(op, w, torch, pico, step=50, arms=arms, subset=spiral_subset)
+        t1["paper_cg_rule"] = measure_time_to_1pct(op, w, torch, pico, step=50, cg=(100, 1e-2), arms=arms,
+                                                   subset=spiral_subset)
+        names = ("pico", "pmr")
+    # device seconds per probe and per replica at the bench's batch size, timed separately
+    s = torch.zeros((w.ny, w.nx), dtype=torch.float64, device="cuda")
+    ss, ps, pss = torch.zeros_like(s), torch.zeros_like(s), torch.zeros_like(s)
+    stream = torch.cuda.current_stream()
+    e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+    e0.record(stream)
+    pico.pico_variance_map(op.ctx, SEED_PICO, 0, K, pico.PICO_PROBE_PHASE, w.max_iter, 0.0, s, ss, True)
+    e1.record(stream)
+    pico.pico_pmr(op.ctx, SEED_PMR, 0, K, w.sigma, w.max_iter, 0.0, ps, pss, True)
+    e2.record(stream)
+    torch.cuda.synchronize()
+    per = {"pico": e0.elapsed_time(e1) / 1e3 / K, "pmr": e1.elapsed_time(e2) / 1e3 / K}
+    for name in names:
+        t1[name]["seconds_per_sample_batched"] = per[name]
+        if t1[name].get("N"):
+            t1[name]["seconds_at_batched_rate"] = t1[name]["N"] * per[name]
+    return t1
 
 
 def measure_time_to_1pct_cs(op, w, torch, pico, sigma, nref, step=10, max_n=20000):
@@ -705,9 +829,6 @@ def measure_time_to_1pct_cs(op, w, torch, pico, sigma, nref, step=10, max_n=2000
         m = (rs / nref).clamp_min(0)
         var_m = ((rss / nref - m * m).clamp_min(0) / (nref - 1))
         ref_std = m.sqrt()
-        # NRMSE over the support of the reference map (std >= 10 % of its
-        # maximum): where the linearised variance is near zero (inactive wavelet
-        # coefficients) the square root amplifies sampling noise of either map
         sup = ref_std >= 0.1 * ref_std.max()
         nref_norm = torch.linalg.vector_norm(ref_std[sup])
         floor2 = float((var_m[sup] / (4 * m[sup])).sum() / (nref_norm ** 2))
@@ -741,7 +862,7 @@ def measure_time_to_1pct_cs(op, w, torch, pico, sigma, nref, step=10, max_n=2000
     return out
 
 
-def main_cs(args, w, inp, torch, dist, pico, world, rank, local):
+def bench_cs(args, w, inp, pico, torch, dist, world, rank, local, steps, warmup, primary):
     """Nonlinear CS workload: one step = the L1-wavelet FISTA reconstruction
     (the linearisation point), K Jacobian-probe products J(J^T v) accumulated
     into the PICO map (Sec. 2.2.5) and K PMR replicas (FISTA reruns on b + n_i,
@@ -763,85 +884,53 @@ def main_cs(args, w, inp, torch, dist, pico, world, rank, local):
     m = torch.from_numpy(inp["mask"].astype(bool)).to(dev)
     sigma = cs_sigma(w, float((b.abs() ** 2)[:, m].mean().sqrt()))
     x = torch.empty((w.ny, w.nx), dtype=torch.complex64, device=dev)
-    s = torch.zeros((w.ny, w.nx), dtype=torch.float64, device=dev)
-    ss, ps, pss = torch.zeros_like(s), torch.zeros_like(s), torch.zeros_like(s)
-    red = torch.zeros((2, w.ny, w.nx), dtype=torch.float64, device=dev)
+    maps = [torch.zeros((w.ny, w.nx), dtype=torch.float64, device=dev) for _ in range(4)]
+    s, ss, ps, pss = maps
 
     def step(i):
         begin = (i * world + rank) * K
         pico.pico_cs_recon(op.ctx, b, lam, iters, levels, x)
-        pico.pico_cs_variance_map(op.ctx, SEED_PICO, begin, K, pico.PICO_PROBE_PHASE, s, ss, True)
-        pico.pico_cs_pmr(op.ctx, SEED_PMR, begin, K, sigma, ps, pss, True)
+        pico.pico_cs_variance_map(op.ctx, SEED_PICO, begin, K, pico.PICO_PROBE_PHASE, s, ss, False)
+        pico.pico_cs_pmr(op.ctx, SEED_PMR, begin, K, sigma, ps, pss, False)
         if world > 1:
-            red[0].copy_(s)
-            red[1].copy_(ps)
-            dist.all_reduce(red)
+            pico.reduce_running_sums(maps)
 
-    for i in range(args.warmup):
-        step(i)
-    torch.cuda.synchronize()
-    if world > 1:
-        dist.barrier()
-    clocks = ClockSampler(local)
-    clocks.start()
-    time.sleep(0.3)
-    pico.pico_launch_count(op.ctx, reset=True)
-    pico.pico_profile(op.ctx, True)
-    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
-    torch.cuda.synchronize()
-    if world > 1:
-        dist.barrier()
-    ev[0].record(stream)
-    for i in range(args.steps):
-        step(args.warmup + i)
-        ev[i + 1].record(stream)
-    torch.cuda.synchronize()
-    if world > 1:
-        dist.barrier()
-    clk = clocks.stop()
-    per_step = [ev[i].elapsed_time(ev[i + 1]) for i in range(args.steps)]
-    total_ms = ev[0].elapsed_time(ev[-1])
-    launches = pico.pico_launch_count(op.ctx)
-    prof = [pico.pico_profile_read(op.ctx, k) for k in range(4)]
-    pico.pico_profile(op.ctx, False)
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = 2 * K * args.steps * world / (total_ms / 1e3)
-
+    total_ms, per_step, clk, launches, prof = timed_steps(step, steps, warmup, torch, dist, world, stream, local,
+                                                          [op.ctx], pico)
+    op.sync()
+    value = 2 * K * steps * world / (total_ms / 1e3)
     norm_ms, norm_n = prof[0]
     # images through the normal operator per step: the reconstruction runs on
     # one image (iters launches); Jacobian PICO (VJP + M g + JVP) and CS PMR
     # (FISTA) run on K images (3 iters + 1 launches)
-    images = args.steps * (iters + (3 * iters + 1) * K)
+    images = steps * (iters + (3 * iters + 1) * K)
     avg_norm_s = norm_ms / max(norm_n, 1) / 1e3
     achieved = images * flops_2d_normal(w) / (norm_ms / 1e3) / 1e12
     peak = N_SM * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
     img = w.ny * w.nx * 8
+    mp = measured_peaks()
+    hbm = images * (2 * img + 4 * w.nc * img) / (norm_ms / 1e3) / 1e9
     roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
             "traffic": None,
             "kernel": "k_toep_rows_fwd + k_toep_cols + k_toep_rows_inv (2-D-mask normal operator, no padding)",
             "avg_launch_ms": avg_norm_s * 1e3, "launches": norm_n, "images": images,
-            "hbm_GBps_incl_coil_grids": images * (2 * img + 4 * w.nc * img) / (norm_ms / 1e3) / 1e9,
             "peak_note": "FP32 FMA peak 152 SM x 128 lanes x 2 x 2070 MHz (nominal max clock); achieved = "
-                         "algorithmic flops of every image through the operator / its total time"}
+                         "algorithmic flops of every image through the operator / its total time",
+            "hbm": {"achieved_GBps_incl_coil_grids": hbm, "peak_GBps": mp["hbm_gbs"], "frac": hbm / mp["hbm_gbs"]}}
     line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "c64", "data": "synthetic",
+        "value": value, "unit": UNIT, "steps": steps, "warmup": warmup, "ms_per_step": total_ms / steps,
         "config": dict(arm_config(w, world), lambda_l1=lam, pmr_sigma=sigma),
         "roofline": roof,
         "kernel_ms_in_timed_region": {"normal_op_ms": norm_ms, "cg_vector_ms": prof[1][0],
                                       "noise_adjoint_ms": prof[2][0], "elementwise_and_dwt_ms": prof[3][0]},
         "gpu_launches": launches, "clocks": clk,
-        "latency_ms": {"p50": statistics.median(per_step), "p99": max(per_step)},
+        "step_ms": {"p50": statistics.median(per_step), "max": max(per_step)},
     }
-    if not args.no_e2e:
+    if primary and not args.no_e2e:
         S_h, m_h, C_h = np.ascontiguousarray(inp["smaps"]), inp["mask"], inp["noise_cov"]
         b_h = b.cpu().pin_memory()
         out_h = np.empty((2, w.ny, w.nx), dtype=np.float64)
-        e2e_steps = max(2, min(args.steps, 3))
+        e2e_steps = max(2, min(steps, 3))
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for i in range(e2e_steps):
@@ -868,16 +957,97 @@ def main_cs(args, w, inp, torch, dist, pico, world, rank, local):
                        "d2h_bytes_per_step": int(out_h.nbytes), "steps": e2e_steps,
                        "includes": "pico_init (upload, whitening, power method) + data upload + reconstruction "
                                    "+ both maps + read-back"}
-    if rank == 0 and world == 1 and args.t1pct_cs > 0:
+    if primary and rank == 0 and world == 1 and args.t1pct_cs > 0:
         line["time_to_1pct"] = measure_time_to_1pct_cs(op, w, torch, pico, sigma, args.t1pct_cs)
-    if rank == 0 and world == 1 and not args.no_cpu:
+    op.close()
+    return line
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    maybe_relaunch(args)
+    import numpy as np  # noqa: F401
+    import torch
+    import torch.distributed as dist
+
+    import paper_2605_09590_gb300 as pico
+    from paper_2605_09590_gb300 import build as pico_build
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if torch.cuda.device_count() < (local + 1):
+        sys.exit(f"bench.py: rank {rank} needs GPU {local}, {torch.cuda.device_count()} visible")
+    # the CPU baseline's process pool is spawned before the first GPU call
+    cpu_pool = None
+    w, inp = workload(args.workload)
+    if rank == 0 and world == 1 and not args.no_cpu and w.kind == "cartesian":
+        cpu_pool = OraclePool(w.name)
+    torch.cuda.set_device(local)
+    if world > 1:
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    if rank == 0:
+        pico_build.build()
+    if world > 1:
+        dist.barrier()
+    pico.load_library()
+
+    tune_cache = os.environ.get("PICO_TUNE_CACHE") or os.path.join(
+        tempfile.gettempdir(), "pico_tune_%d_%d.json" % (os.getpid(), rank))
+    if not os.environ.get("PICO_TUNE_CACHE"):
+        import atexit
+        atexit.register(lambda: os.path.exists(tune_cache) and os.remove(tune_cache))
+
+    if w.kind == "cs":
+        sub = bench_cs(args, w, inp, pico, torch, dist, world, rank, local, args.steps, args.warmup, True)
+        op = None
+    else:
+        sub, op = bench_linear(args, w, inp, pico, torch, dist, world, rank, local, args.steps, args.warmup,
+                               True, tune_cache)
+    line = {"metric": METRIC, "n_gpus": world, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "c64", "data": "synthetic"}
+    line.update(sub)
+    line["config"] = sub["config"]
+
+    if op is not None and rank == 0 and world == 1 and not args.no_t1pct and (
+            w.kind == "cartesian" or args.t1pct_spiral):
+        line["time_to_1pct"] = t1pct_linear(op, w, torch, pico, spiral_subset=0)
+    if op is not None:
+        op.close()
+
+    if rank == 0 and world == 1 and not args.no_extra and args.workload == "knee320_r2":
+        ws, inps = workload("spiral240_r2")
+        spi, sop = bench_linear(args, ws, inps, pico, torch, dist, 1, 0, local, 3, 2, False, tune_cache)
+        if not args.no_t1pct:
+            spi["time_to_1pct"] = t1pct_linear(sop, ws, torch, pico, spiral_subset=2304)
+        sop.close()
+        line["spiral240_r2"] = spi
+        wc, inpc = workload("cs320_r2")
+        line["cs320_r2"] = bench_cs(args, wc, inpc, pico, torch, dist, 1, 0, local, 3, 1, False)
+        if args.serving > 0:
+            line["serving"] = run_serving(pico, args.serving, loads=(args.serving_load,))
+
+    if cpu_pool is not None:
+        vals = []
+        for _ in range(2):
+            v, dt, procs = cpu_pool.step()
+            vals.append((v, dt, procs))
+        cpu_pool.close()
+        v = sum(a * b for a, b, _ in vals) / sum(b for _, b, _ in vals)
+        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cpu_pool.cores, "kind": "oracle",
+                                "sample": f"2 rounds of one PICO probe + one PMR replica ({w.max_iter} CG iterations "
+                                          f"each) per core, {cpu_pool.cores} single-threaded FP64 NumPy oracle "
+                                          f"processes ({vals[-1][2]} took work), {sum(b for _, b, _ in vals):.1f} s"}
+    elif rank == 0 and world == 1 and not args.no_cpu:
         v, dt, desc = oracle_sample(w, inp)
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-                                "sample": f"{desc}, {dt:.1f} s, NumPy FP64 (single-threaded pocketfft; "
-                                          f"{cores_in_use()} cores visible)"}
+                                "sample": f"{desc}, {dt:.1f} s, FP64 NumPy on one core"}
     if rank == 0:
         print(json.dumps(line), flush=True)
-    op.close()
     if world > 1:
         dist.destroy_process_group()
 

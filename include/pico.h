@@ -149,7 +149,7 @@ pico_status pico_variance_map(pico_ctx* ctx, uint64_t seed, int64_t probe_begin,
                               int32_t probe_kind, int32_t max_iter, double rtol, double* sum_dev,
                               double* sumsq_dev, int32_t accumulate);
 
-/* Adaptive PICO (Sec. 4, stopping from the estimator's own variance): runs
+/* Adaptive PICO (Sec. 5, stopping from the estimator's own variance): runs
  * probes 0, 1, ... under seed in chunks of `chunk` (>= 2) and stops once the
  * relative standard error of the running mean map,
  *   ||stderr||_2 / ||sum / N||_2  with  stderr = sqrt((sumsq/N - (sum/N)^2)/(N-1)),
@@ -182,6 +182,13 @@ pico_status pico_pmr(pico_ctx* ctx, uint64_t seed, int64_t rep_begin, int32_t nr
  * the image must be square with ny divisible by 2^levels. */
 pico_status pico_cs_recon(pico_ctx* ctx, const void* b_dev, double lambda_l1, int32_t iters, int32_t levels,
                           void* x_dev);
+
+/* Number of pico_cs_recon calls this context has started (0 before the
+ * first).  The Jacobian calls below linearise around the most recent one; a
+ * caller that keeps a reconstruction's output for a later pico_cs_jvp /
+ * pico_cs_vjp compares the generation it recorded with this value (the
+ * torch.autograd.Function of the Python binding raises on a mismatch). */
+pico_status pico_cs_generation(const pico_ctx* ctx, int64_t* generation);
 
 /* Jacobian-vector product dx = J db of the last pico_cs_recon (tangent of the
  * unrolled iterations; the soft threshold's derivative is R-linear:
@@ -221,8 +228,8 @@ pico_status pico_cs_pmr(pico_ctx* ctx, uint64_t seed, int64_t rep_begin, int32_t
 pico_status pico_wavelet(pico_ctx* ctx, const void* in_dev, void* out_dev, int32_t nbatch, int32_t levels,
                          int32_t inverse);
 
-/* Finalise running sums over `count` samples (Alg. 1 output; Sec. 4
- * "per-voxel standard error of the running mean"):
+/* Finalise running sums over `count` samples (Alg. 1 output; the standard
+ * error of the running mean per voxel, the convergence diagnostic of Sec. 5):
  *   var_dev[k] = sum[k] / count                                   (float32, nullable)
  *   stderr_dev[k] = sqrt((sumsq/count - (sum/count)^2) / (count-1)) (float32, nullable;
  *                                                                   needs sumsq_dev) */
@@ -245,7 +252,8 @@ pico_status pico_gfactor(pico_ctx* ctx, const float* var_acc_dev, const float* v
  *   mask_dev   caller's device uint8 [ny] phase-encode mask (natural DFT order)
  *   lam        physical Tikhonov weight added to A^H A
  *   rhs_dev, x_dev, nbatch, max_iter (<= 128), rtol  as in pico_cg_batch
- *              (no iteration report)
+ *              (no iteration report; a CG breakdown is not reported either:
+ *              such a system keeps the iterate reached before it)
  *   cuda_stream  stream the work is enqueued on (NULL = legacy default)
  * Every temporary lives in one file-scope device array of
  * pico_cg_batch_static_capacity() bytes (64 MiB) that each GPU loading the
@@ -279,7 +287,10 @@ pico_status pico_footprint(const pico_operator_desc* desc, int32_t with_kspace, 
  * max_batch = chunk (batches of at least 64 images of a Cartesian phase-encode
  * operator run on the tensor-core Gram operator, smaller ones on the column-FFT
  * kernel; the two agree to about 1e-6 relative, not bitwise).  The server uses the device
- * current at pico_server_create. */
+ * current at pico_server_create.  Overlap on the GPU covers fixed-count solves
+ * (rtol = 0): a request with rtol > 0 synchronises its stream after every few
+ * CG iterations to test the stopping rule, and the single scheduler thread
+ * admits or retires no other request meanwhile. */
 typedef struct pico_server pico_server;
 
 typedef struct {
@@ -386,11 +397,25 @@ pico_status pico_autotune(pico_ctx* ctx, int32_t iters, pico_tuning* out, double
  * choice is max_batch).  PICO_E_INVALID without any measured batch. */
 pico_status pico_tune_select(const double* times_us, int32_t max_batch, int32_t gram, pico_tuning* out);
 
-/* Wait for all work of the context; returns the first asynchronous error
- * (PICO_E_CUDA), PICO_E_TIMEOUT if a kernel's bounded pipeline wait (the
- * tensor-core Gram operator, the TMA-staged Toeplitz column pass) gave up, or
- * PICO_E_BREAKDOWN if a CG system broke down since the last pico_sync. */
+/* Wait for all work of the context and report its asynchronous status:
+ * PICO_E_CUDA for a CUDA error; otherwise every pending class is named in
+ * pico_last_error and the status is PICO_E_TIMEOUT if a kernel's bounded
+ * pipeline wait (the tensor-core Gram operator, the TMA-staged Toeplitz column
+ * pass) gave up, else PICO_E_BREAKDOWN if a CG system broke down (a non-finite
+ * residual -- NaN or Inf in a right-hand side or the operator -- or
+ * p^H (M + lam) p <= 0) since the last pico_sync.  Broken-down systems keep the
+ * iterate reached before the breakdown (x = 0 for a non-finite right-hand
+ * side).  Both status words are cleared on the context stream, so the context
+ * stays usable. */
 pico_status pico_sync(pico_ctx* ctx);
+
+/* Host-side fault injection for tests of the failure paths: sets the device
+ * status word of class `cls` (PICO_E_TIMEOUT: the bounded-wait error word;
+ * PICO_E_BREAKDOWN: the CG status of system 0) to `code` (nonzero), stream-
+ * ordered and synchronised, exactly as a kernel would; the next pico_sync
+ * reports and clears it.  No kernel is made to fail.  PICO_E_INVALID for any
+ * other class or a zero code.  (No counterpart in the paper.) */
+pico_status pico_inject_error(pico_ctx* ctx, int32_t cls, int32_t code);
 
 /* Text of the last error of this context ("" if none).  Owned by the context. */
 const char* pico_last_error(const pico_ctx* ctx);

@@ -118,6 +118,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "pico_set_tuning": ([vp, ctypes.POINTER(pico_tuning)], i32),
         "pico_autotune": ([vp, i32, ctypes.POINTER(pico_tuning), ctypes.POINTER(f64), i32], i32),
         "pico_tune_select": ([ctypes.POINTER(f64), i32, i32, ctypes.POINTER(pico_tuning)], i32),
+        "pico_inject_error": ([vp, i32, i32], i32),
+        "pico_cs_generation": ([vp, ctypes.POINTER(i64)], i32),
         "pico_footprint": ([ctypes.POINTER(pico_operator_desc), i32, ctypes.POINTER(ctypes.c_size_t)], i32),
         "pico_server_create": ([ctypes.c_size_t, i32, i32, ctypes.POINTER(vp)], i32),
         "pico_server_submit": ([vp, ctypes.POINTER(pico_request), ctypes.POINTER(i64)], i32),
@@ -388,6 +390,18 @@ def pico_sync(ctx) -> None:
     _check(ctx, load_library().pico_sync(ctx))
 
 
+def pico_inject_error(ctx, status: int, code: int = 1) -> None:
+    """Host-side fault injection: the next ``pico_sync`` reports ``status``
+    (PICO_E_TIMEOUT or PICO_E_BREAKDOWN) exactly as if a kernel had set it."""
+    _check(ctx, load_library().pico_inject_error(ctx, status, code))
+
+
+def pico_cs_generation(ctx) -> int:
+    g = ctypes.c_int64()
+    _check(ctx, load_library().pico_cs_generation(ctx, ctypes.byref(g)))
+    return g.value
+
+
 def pico_last_error(ctx) -> str:
     return load_library().pico_last_error(ctx).decode()
 
@@ -534,7 +548,9 @@ def cs_function():
     (``b``: whitened k-space of ``op``'s layout).  Backward returns
     ``J^T grad_x`` (``pico_cs_vjp``; the real-inner-product adjoint, which is
     PyTorch's convention for complex gradients), forward-mode AD ``J db``
-    (``pico_cs_jvp``); both at the point of the last forward call.
+    (``pico_cs_jvp``).  The context keeps the iterates of its most recent
+    reconstruction only, so backward and jvp raise ``PicoError`` if another
+    reconstruction has run on the same operator since this output's forward.
     """
     import torch
 
@@ -545,10 +561,18 @@ def cs_function():
             pico_cs_recon(op.ctx, b.detach().contiguous(), lambda_l1, iters, levels, x)
             ctx.op = op
             ctx.kshape = tuple(b.shape)
+            ctx.generation = pico_cs_generation(op.ctx)
             return x
 
         @staticmethod
+        def _check_point(ctx):
+            if pico_cs_generation(ctx.op.ctx) != ctx.generation:
+                raise PicoError(PICO_E_INVALID, "the operator ran another CS reconstruction after this output's "
+                                                "forward; its Jacobian is no longer stored")
+
+        @staticmethod
         def backward(ctx, grad_x):
+            CSRecon._check_point(ctx)
             op = ctx.op
             bbar = torch.empty((1,) + ctx.kshape, dtype=torch.complex64, device=grad_x.device)
             pico_cs_vjp(op.ctx, grad_x.contiguous().reshape(1, op.ny, op.nx), bbar)
@@ -556,6 +580,7 @@ def cs_function():
 
         @staticmethod
         def jvp(ctx, _op, db, *_):
+            CSRecon._check_point(ctx)
             op = ctx.op
             dx = torch.empty((1, op.ny, op.nx), dtype=torch.complex64, device=db.device)
             pico_cs_jvp(op.ctx, db.contiguous().reshape((1,) + ctx.kshape), dx)
@@ -639,3 +664,28 @@ def shard_range(total: int, world: int, rank: int) -> tuple[int, int]:
     base, extra = divmod(total, world)
     begin = rank * base + min(rank, extra)
     return begin, base + (1 if rank < extra else 0)
+
+
+def reduce_running_sums(sums, group=None) -> None:
+    """Combine the running sums of all ranks in place: the one exchange of a
+    sharded map.  Probes (and PMR replicas) are independent (Alg. 1), so the
+    sums over all probes are the sums of the ranks' partial sums.
+
+    ``sums``: equally shaped float64 tensors on this rank's device (e.g. the
+    PICO ``sum``/``sumsq`` and PMR ``sum``/``sumsq`` maps); they are packed
+    into one buffer, summed over the process group with one all-reduce, and
+    written back, so every rank ends with the totals.  Summation order across
+    ranks is the collective's; within a rank the probe order is kept."""
+    import torch
+    import torch.distributed as dist
+    if not sums:
+        return
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size(group) == 1:
+        return
+    flat = torch.cat([t.reshape(-1) for t in sums])
+    dist.all_reduce(flat, group=group)
+    off = 0
+    for t in sums:
+        n = t.numel()
+        t.copy_(flat[off:off + n].view_as(t))
+        off += n

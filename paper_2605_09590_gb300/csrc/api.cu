@@ -72,6 +72,7 @@ struct pico_ctx {
   float2* cs_ahb = nullptr;    // A^H b of the reconstruction's data [n]
   float2* cs_x0 = nullptr;     // the reconstruction f(b) [n]
   double cs_lam = 0;           // lambda_l1 of the reconstruction
+  int64_t cs_generation = 0;   // pico_cs_recon calls so far (the linearisation point's version)
   pico::Wavelet wav{};
   // dense per-column normal operator on the tensor cores (Cartesian phase-encode
   // masks): CG vectors in the column-planar layout, two direction buffers
@@ -1274,6 +1275,7 @@ pico_status pico_cs_recon(pico_ctx* c, const void* b_dev, double lambda_l1, int3
     c->cs_c[k] = (float)((t - 1.0) / tn);
     t = tn;
   }
+  ++c->cs_generation;  // the stored linearisation point is replaced from here on
   if ((st = pico_adjoint(c, b_dev, c->cs_ahb, 1)) != PICO_OK) return st;
   cs_fista(c, c->cs_ahb, 0, 1, true);
   cudaMemcpyAsync(c->cs_x0, cs_e(c, 0), (size_t)c->n * sizeof(float2), cudaMemcpyDeviceToDevice, c->stream);
@@ -1395,25 +1397,52 @@ pico_status pico_gfactor(pico_ctx* c, const float* va, const float* vr, double R
 pico_status pico_sync(pico_ctx* c) {
   if (!c) return PICO_E_INVALID;
   if (cudaStreamSynchronize(c->stream) != cudaSuccess) return cuda_check(c, "pico_sync");
-  if (c->g_err) {
-    int e = 0;
-    if (cudaMemcpy(&e, c->g_err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return cuda_check(c, "pico_sync");
-    if (e) {
-      cudaMemset(c->g_err, 0, sizeof(int));
-      return fail(c, PICO_E_TIMEOUT, "a kernel's bounded pipeline wait timed out (code " + std::to_string(e) + ")");
-    }
-  }
+  // read and clear the asynchronous status words on the context stream, then
+  // report every class that is pending (a timeout ranks before a breakdown)
+  int e = 0;
+  std::vector<int> s;
+  if (c->g_err && cudaMemcpyAsync(&e, c->g_err, sizeof(int), cudaMemcpyDeviceToHost, c->stream) != cudaSuccess)
+    return cuda_check(c, "pico_sync");
   if (c->status) {
-    std::vector<int> s(c->max_batch);
-    if (cudaMemcpy(s.data(), c->status, s.size() * sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+    s.assign(c->max_batch, 0);
+    if (cudaMemcpyAsync(s.data(), c->status, s.size() * sizeof(int), cudaMemcpyDeviceToHost, c->stream) !=
+        cudaSuccess)
       return cuda_check(c, "pico_sync");
-    for (int v : s)
-      if (v) {
-        cudaMemset(c->status, 0, s.size() * sizeof(int));
-        return fail(c, PICO_E_BREAKDOWN, "CG breakdown (p^H M p <= 0) in at least one system");
-      }
   }
+  if (cudaStreamSynchronize(c->stream) != cudaSuccess) return cuda_check(c, "pico_sync");
+  int broken = 0;
+  for (int v : s) broken += v != 0;
+  if (e) cudaMemsetAsync(c->g_err, 0, sizeof(int), c->stream);
+  if (broken) cudaMemsetAsync(c->status, 0, s.size() * sizeof(int), c->stream);
+  if ((e || broken) && cudaStreamSynchronize(c->stream) != cudaSuccess) return cuda_check(c, "pico_sync");
+  std::string msg;
+  if (e) msg = "a kernel's bounded pipeline wait timed out (code " + std::to_string(e) + ")";
+  if (broken) {
+    if (!msg.empty()) msg += "; ";
+    msg += "CG breakdown (non-finite residual or p^H (M + lam) p <= 0) in " + std::to_string(broken) +
+           " system(s) of the last batch";
+  }
+  if (e) return fail(c, PICO_E_TIMEOUT, msg);
+  if (broken) return fail(c, PICO_E_BREAKDOWN, msg);
   return cuda_check(c, "pico_sync");
+}
+
+pico_status pico_inject_error(pico_ctx* c, int32_t cls, int32_t code) {
+  if (!c || !c->smaps || (cls != PICO_E_TIMEOUT && cls != PICO_E_BREAKDOWN) || code == 0)
+    return c ? fail(c, PICO_E_INVALID, "inject PICO_E_TIMEOUT or PICO_E_BREAKDOWN with a nonzero code")
+             : PICO_E_INVALID;
+  int* word = cls == PICO_E_TIMEOUT ? c->g_err : c->status;
+  if (!word) return fail(c, PICO_E_INVALID, "no status word of that class");
+  if (cudaMemcpyAsync(word, &code, sizeof(int), cudaMemcpyHostToDevice, c->stream) != cudaSuccess ||
+      cudaStreamSynchronize(c->stream) != cudaSuccess)
+    return cuda_check(c, "pico_inject_error");
+  return PICO_OK;
+}
+
+pico_status pico_cs_generation(const pico_ctx* c, int64_t* generation) {
+  if (!c || !generation) return PICO_E_INVALID;
+  *generation = c->cs_generation;
+  return PICO_OK;
 }
 
 pico_status pico_profile(pico_ctx* c, int32_t enable) {

@@ -21,6 +21,17 @@ __device__ __forceinline__ const double* pq_at(const CgArgs& a, int b, int it) {
   return a.pq_part + ((size_t)b * a.itmax + it) * a.PA;
 }
 
+// State of one system before CG update `it`: 0 update, 1 converged or
+// stopped (||r||^2 <= rtol^2 ||r0||^2), 2 breakdown.  A non-finite residual
+// (a NaN or Inf right-hand side or operator) is a breakdown, not convergence;
+// so is p^H (M + lam) p <= 0.
+__device__ __forceinline__ int cg_state_of(double rr, double rr0, double pq, double rtol2) {
+  if (!isfinite(rr) || !isfinite(rr0)) return 2;
+  if (!(rr > rtol2 * rr0)) return 1;
+  if (!(pq > 0.0) || !isfinite(pq)) return 2;
+  return 0;
+}
+
 // x = 0, r = probe(b), rr partial
 __global__ void __launch_bounds__(kVecThreads) k_cg_init_probe(CgArgs a, uint64_t seed, int64_t probe_begin,
                                                                int kind) {
@@ -75,10 +86,7 @@ __global__ void __launch_bounds__(kVecThreads) k_cg_update(CgArgs a, int it) {
     const double rr0 = warp_sum_parts(rr_at(a, b, 0), a.PB);
     const double pq = warp_sum_parts(pq_at(a, b, it), a.PA);
     if (threadIdx.x == 0) {
-      int st = 0;
-      if (!(rr > a.rtol2 * rr0)) st = 1;
-      else if (!(pq > 0.0) || !isfinite(pq)) st = 2;
-      sh_state = st;
+      sh_state = cg_state_of(rr, rr0, pq, a.rtol2);
       sh_alpha = (float)(rr / pq);
     }
   }
@@ -130,10 +138,7 @@ __global__ void k_cg_alpha(CgArgs a, int it, float* alpha, int* state) {
   const double rr0 = warp_sum_parts(rr_at(a, b, 0), a.PB);
   const double pq = warp_sum_parts(pq_at(a, b, it), a.PA);
   if (threadIdx.x == 0) {
-    int st = 0;
-    if (!(rr > a.rtol2 * rr0)) st = 1;
-    else if (!(pq > 0.0) || !isfinite(pq)) st = 2;
-    state[b] = st;
+    state[b] = cg_state_of(rr, rr0, pq, a.rtol2);
     alpha[b] = (float)(rr / pq);
   }
 }
@@ -211,7 +216,7 @@ __global__ void k_cg_report(CgArgs a, int max_iter, int* iters, double* relres) 
   }
   if (threadIdx.x == 0) {
     iters[b] = it;
-    relres[b] = rr0 > 0.0 ? sqrt(rr / rr0) : 0.0;
+    relres[b] = !isfinite(rr0) ? (double)NAN : rr0 > 0.0 ? sqrt(rr / rr0) : 0.0;
   }
 }
 

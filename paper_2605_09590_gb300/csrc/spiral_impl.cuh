@@ -199,6 +199,7 @@ __global__ void __launch_bounds__(P1 * P2, (P1 * P2 <= 320 ? 2 : 1))
   float2* buf = stage + (size_t)N * CL;           // [k2][n1][CL]
   float2* tws = buf + (size_t)L * CL;
   uint64_t* bar = reinterpret_cast<uint64_t*>(tws + L);
+  int* arrived = reinterpret_cast<int*>(bar + 1);
   const int items = P2 * nplanes;
   const uint32_t bytes = (uint32_t)N * CL * sizeof(float2);
   if (t == 0) {
@@ -216,10 +217,20 @@ __global__ void __launch_bounds__(P1 * P2, (P1 * P2 <= 320 ? 2 : 1))
   int phase = 0;
   for (int w = blockIdx.x; w < items; w += gridDim.x, phase ^= 1) {
     const int plane = w / P2, cg = w - plane * P2, x0 = cg * CL;
-    if (!tc::mbar_wait(bar, phase)) {
-      if (t == 0 && op.err) atomicCAS(op.err, 0, 10);
-      return;
+    // One thread decides whether the item's copy arrived and the block
+    // follows that decision together.  On a timeout it records the error,
+    // waits once more (bounded) for the copy still in flight into this
+    // block's shared memory, and the whole block leaves at the same point.
+    if (t == 0) {
+      bool ok = tc::mbar_wait(bar, phase);
+      if (!ok) {
+        if (op.err) atomicCAS(op.err, 0, 10);
+        tc::mbar_wait(bar, phase);
+      }
+      *arrived = ok ? 1 : 0;
     }
+    __syncthreads();
+    if (!*arrived) return;
     const bool skip = done && done[plane / op.nc];
     float2* __restrict__ g = G + (size_t)plane * N * L;  // (b, c) plane [N][L]
     if (!skip)

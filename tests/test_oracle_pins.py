@@ -332,3 +332,16 @@ def test_lambda_phys_uses_power_estimate():
     assert abs(lp - 0.1 * 1.01 * lmax) < 1e-15
     top = np.linalg.eigvalsh(pico.dense_normal(op))[-1]
     assert lmax <= top * (1 + 1e-12) and lmax > 0.5 * top
+
+
+def test_nrmse_hand_computed():
+    # est - ref = (3, -1, 0): ||.|| = sqrt(10); ||ref|| = sqrt(0 + 25 + 4) = sqrt(29)
+    est = np.array([3.0, 4.0, 2.0])
+    ref = np.array([0.0, 5.0, 2.0])
+    assert pico.nrmse(est, ref) == pytest.approx(np.sqrt(10.0 / 29.0), rel=1e-15)
+    # over a support: only the last two voxels, (-1, 0) against (5, 2)
+    sup = np.array([False, True, True])
+    assert pico.nrmse(est, ref, sup) == pytest.approx(1.0 / np.sqrt(29.0), rel=1e-15)
+    # a 2-D map and its flattening give the same value; scaling both maps leaves it unchanged
+    assert pico.nrmse(est.reshape(3, 1), ref.reshape(3, 1)) == pytest.approx(pico.nrmse(est, ref), rel=1e-15)
+    assert pico.nrmse(7 * est, 7 * ref) == pytest.approx(pico.nrmse(est, ref), rel=1e-14)
