@@ -129,28 +129,42 @@ def sense_closed_form(smaps: np.ndarray, R: int):
 # ----------------------------------------------------------------------------
 # Implicit covariance application (Sec. 2.2.3) and PICO (Alg. 1)
 # ----------------------------------------------------------------------------
-def apply_sigma(op: ops.Operator, v: np.ndarray, lam: float, max_iter: int, rtol: float = 0.0):
+def solve(op: ops.Operator, rhs: np.ndarray, lam: float, max_iter: int, rtol: float = 0.0,
+          solver: str = "global") -> np.ndarray:
+    """``(M + lam I)^-1 rhs`` by CG from 0 (Eq. 6): ``solver = "global"`` runs
+    CG on the whole image (``solvers.cg``), ``"columns"`` runs it on every
+    readout column's block of a phase-encode Cartesian operator
+    (``solvers.cg_columns``: same fixed point, other iterates)."""
+    if solver == "columns":
+        return solvers.cg_columns(op, rhs, lam, max_iter, rtol)[0]
+    assert solver == "global", solver
+    return solvers.cg(lambda z: op.normal(z, lam), rhs, max_iter, rtol)[0]
+
+
+def apply_sigma(op: ops.Operator, v: np.ndarray, lam: float, max_iter: int, rtol: float = 0.0,
+                solver: str = "global"):
     """``u = Sigma v`` via CG on the normal equations.
 
     ``lam = 0``: ``u = M^-1 v`` (one solve).  ``lam > 0``:
     ``u = (M + lam)^-1 M (M + lam)^-1 v`` (solve, apply ``M``, solve).
     """
-    x1, _, _ = solvers.cg(lambda z: op.normal(z, lam), v, max_iter, rtol)
+    x1 = solve(op, v, lam, max_iter, rtol, solver)
     if lam == 0.0:
         return x1
     w = op.normal(x1, 0.0)
-    u, _, _ = solvers.cg(lambda z: op.normal(z, lam), w, max_iter, rtol)
-    return u
+    return solve(op, w, lam, max_iter, rtol, solver)
 
 
 def pico(op: ops.Operator, seed: int, probe_begin: int, nprobes: int, lam: float,
-         max_iter: int, rtol: float = 0.0, kind: int = rng.PROBE_PHASE, sigma_apply=None):
+         max_iter: int, rtol: float = 0.0, kind: int = rng.PROBE_PHASE, sigma_apply=None,
+         solver: str = "global"):
     """Running sums of Alg. 1 over probes ``probe_begin .. probe_begin+nprobes-1``.
 
     Returns ``(s, ss)`` with ``s = sum_i Re(conj(v_i) u_i)`` and
     ``ss = sum_i Re(conj(v_i) u_i)^2`` (both ``[ny][nx]`` float64);
     the variance map is ``s / nprobes`` (Alg. 1 output, real part kept).
-    ``sigma_apply`` replaces the CG application (e.g. a dense ``Sigma``).
+    ``sigma_apply`` replaces the CG application (e.g. a dense ``Sigma``);
+    ``solver`` picks the CG of ``solve``.
     """
     ny, nx = op.ny, op.nx
     s = np.zeros((ny, nx))
@@ -158,7 +172,7 @@ def pico(op: ops.Operator, seed: int, probe_begin: int, nprobes: int, lam: float
     for i in range(probe_begin, probe_begin + nprobes):
         v = rng.probe(seed, i, ny * nx, kind).reshape(ny, nx)
         if sigma_apply is None:
-            u = apply_sigma(op, v, lam, max_iter, rtol)
+            u = apply_sigma(op, v, lam, max_iter, rtol, solver)
         else:
             u = sigma_apply(v)
         d = np.real(np.conj(v) * u)
@@ -177,7 +191,7 @@ def pmr_noise(op: ops.Operator, seed: int, rep: int, sigma: float) -> np.ndarray
 
 
 def pmr(op: ops.Operator, seed: int, rep_begin: int, nreps: int, sigma: float, lam: float,
-        max_iter: int, rtol: float = 0.0):
+        max_iter: int, rtol: float = 0.0, solver: str = "global"):
     """Running sums of PMR: ``s = sum_i |x_i|^2 / sigma^2``, ``ss = sum_i (|x_i|^2/sigma^2)^2``."""
     ny, nx = op.ny, op.nx
     s = np.zeros((ny, nx))
@@ -185,7 +199,7 @@ def pmr(op: ops.Operator, seed: int, rep_begin: int, nreps: int, sigma: float, l
     for i in range(rep_begin, rep_begin + nreps):
         n = pmr_noise(op, seed, i, sigma)
         b = op.adjoint(n)
-        x, _, _ = solvers.cg(lambda z: op.normal(z, lam), b, max_iter, rtol)
+        x = solve(op, b, lam, max_iter, rtol, solver)
         d = np.abs(x) ** 2 / sigma ** 2
         s += d
         ss += d * d

@@ -345,3 +345,92 @@ def test_nrmse_hand_computed():
     # a 2-D map and its flattening give the same value; scaling both maps leaves it unchanged
     assert pico.nrmse(est.reshape(3, 1), ref.reshape(3, 1)) == pytest.approx(pico.nrmse(est, ref), rel=1e-15)
     assert pico.nrmse(7 * est, 7 * ref) == pytest.approx(pico.nrmse(est, ref), rel=1e-14)
+
+
+# --------------------------------------------------------------------------
+# per-column CG (phase-encode Cartesian: A^H A block diagonal over columns)
+# --------------------------------------------------------------------------
+def test_cg_batched_follows_cg_on_every_system():
+    g = np.random.default_rng(4)
+    n, B = 12, 5
+    Z = g.standard_normal((n, n)) + 1j * g.standard_normal((n, n))
+    A = Z.conj().T @ Z + 0.3 * np.eye(n)
+    rhs = g.standard_normal((n, B)) + 1j * g.standard_normal((n, B))
+    rhs[:, 3] = 0.0                                                     # a zero system takes no update
+    for max_iter, rtol in ((4, 0.0), (50, 1e-6), (7, 1e-2)):
+        X, it, rel = solvers.cg_batched(lambda P: A @ P, rhs, max_iter, rtol)
+        for b in range(B):
+            x, i1, r1 = solvers.cg(lambda z: A @ z, rhs[:, b], max_iter, rtol)
+            assert it[b] == i1
+            assert np.allclose(X[:, b], x, rtol=1e-9, atol=1e-12)   # BLAS order only
+            if rtol == 1e-6:       # converged: both residuals are rounding-level, below the tolerance
+                assert rel[b] <= 1e-6 and r1 <= 1e-6
+            else:
+                assert abs(rel[b] - r1) <= 1e-9 * r1
+    assert it[3] == 0 and np.all(X[:, 3] == 0)
+
+
+def test_cg_columns_is_global_cg_on_a_single_column():
+    S = synth.coil_maps(16, 1, 3, 2)
+    op = ops.Operator(S, None, mask=synth.mask_pe(16, 2, 2))
+    v = rng.probe(9, 0, 16).reshape(16, 1)
+    for k in (1, 4, 9):
+        xc, itc, relc = solvers.cg_columns(op, v, 0.02, k)
+        xg, itg, relg = solvers.cg(lambda z: op.normal(z, 0.02), v, k)
+        assert itc == itg == k
+        assert np.allclose(xc, xg, rtol=1e-11, atol=1e-13)
+        assert abs(relc - relg) < 1e-11
+
+
+def test_cg_columns_iterate_is_the_per_column_krylov_minimiser_and_converges():
+    op, *_ = _small_cart(12, 5, 3, R=2, acs=2)
+    P = ops.pe_projector(op.mask)
+    lam = 0.03
+    v = rng.probe(5, 1, 12 * 5).reshape(12, 5)
+    for k in (1, 3, 5):
+        x, it, _ = solvers.cg_columns(op, v, lam, k)
+        for col in range(5):
+            G = ops.cart_column_normal(op.S, op.mask, col, P) + lam * np.eye(12)
+            b = v[:, col]
+            K = np.stack([np.linalg.matrix_power(G, j) @ b for j in range(k)], axis=1)
+            Q, _ = np.linalg.qr(K)
+            y = np.linalg.solve(Q.conj().T @ G @ Q, Q.conj().T @ b)    # Galerkin = G-norm minimiser
+            assert np.allclose(x[:, col], Q @ y, rtol=1e-8, atol=1e-10)
+    # converged: the exact solve of the whole normal equations (dense M)
+    M = pico.dense_normal(op) + lam * np.eye(60)
+    xs = np.linalg.solve(M, v.reshape(-1)).reshape(12, 5)
+    x, it, rel = solvers.cg_columns(op, v, lam, 200, 1e-13)
+    assert rel <= 1e-12 and np.allclose(x, xs, rtol=1e-10, atol=1e-12)
+
+
+def test_cg_columns_stops_each_column_on_its_own_residual():
+    op, *_ = _small_cart(16, 6, 3, R=2, acs=2)
+    P = ops.pe_projector(op.mask)
+    v = rng.probe(6, 2, 16 * 6).reshape(16, 6)
+    v[:, 2] = 0.0
+    x, it, rel = solvers.cg_columns(op, v, 0.0, 100, 1e-4)
+    assert np.all(x[:, 2] == 0)
+    for col in (0, 1, 3, 4, 5):
+        G = ops.cart_column_normal(op.S, op.mask, col, P)
+        r = np.linalg.norm(v[:, col] - G @ x[:, col]) / np.linalg.norm(v[:, col])
+        assert r <= 1e-4
+    assert rel <= 1e-4
+    # batch of images = images one by one
+    vb = np.stack([v, 2 * v + 1j])
+    xb, itb, relb = solvers.cg_columns(op, vb, 0.1, 7)
+    for i in range(2):
+        xi, iti, reli = solvers.cg_columns(op, vb[i], 0.1, 7)
+        assert np.allclose(xb[i], xi, rtol=1e-13, atol=1e-15) and itb[i] == iti and abs(relb[i] - reli) < 1e-13
+
+
+def test_pico_with_column_cg_band_against_exact_diagonal():
+    op, *_ = _small_cart(16, 8, 4, R=2, acs=2)
+    d, rowe, half = pico.column_exact(op, 0.0)
+    K = 400
+    s, _ = pico.pico(op, 11, 0, K, 0.0, 60, 0.0, solver="columns")
+    z = (s / K - d) / np.sqrt(half / K)
+    assert np.all(np.abs(z) < 6) and np.mean(np.abs(z) > 3) < 0.02
+    # converged per-column solves and converged global solves give the same per-probe products
+    s1, _ = pico.pico(op, 11, 0, 3, 0.0, 200, 1e-12, solver="columns")
+    s2, _ = pico.pico(op, 11, 0, 3, 0.0, 200, 1e-12)
+    assert np.allclose(s1, s2, rtol=1e-9, atol=1e-12)
