@@ -116,12 +116,18 @@ def alg_bytes_normal(w, K):
     CG: every image reads r and p_old and writes p and q (4 images of 8 bytes
     per voxel), plus one pass over the operator's own data -- the whitened
     sensitivities S (Cartesian) or S and the real Toeplitz kernel T^ on the
-    2n x 2n grid (spiral)."""
+    2n x 2n grid (spiral).  Spiral images also move their coil half-grids
+    through HBM between the three Toeplitz passes (4 x nc x n x 2n complex64
+    per image)."""
     V = w.ny * w.nx * 8
     S = w.nc * V
+    per = 4 * V
     if w.kind == "spiral":
+        # the streaming Toeplitz passes write and read every coil's n x 2n
+        # half-grid twice (the passes are separate launches)
         S += (2 * w.ny) ** 2 * 4
-    return 4 * K * V + S
+        per += 4 * w.nc * w.ny * 2 * w.ny * 8
+    return K * per + S
 
 
 def flops_2d_normal(w):

@@ -51,6 +51,9 @@ typedef enum {
 
 typedef enum { PICO_CARTESIAN = 0, PICO_SPIRAL = 1 } pico_kind;
 
+/* How CG solves the normal equations (Eq. 6), see pico_set_solver. */
+typedef enum { PICO_SOLVER_GLOBAL = 0, PICO_SOLVER_COLUMNS = 1 } pico_solver;
+
 /* Probe families of Sec. 2.2.4: random phase (Eq. 20), real Rademacher
  * (Eq. 19), complex Gaussian (Eq. 18). */
 typedef enum { PICO_PROBE_PHASE = 0, PICO_PROBE_RADEMACHER = 1, PICO_PROBE_GAUSS = 2 } pico_probe;
@@ -135,6 +138,30 @@ pico_status pico_adjoint(pico_ctx* ctx, const void* y_dev, void* x_dev, int32_t 
  * max_iter must be in [0, max_iter_cap]. */
 pico_status pico_cg_batch(pico_ctx* ctx, const void* rhs_dev, void* x_dev, int32_t nbatch, int32_t max_iter,
                           double rtol, int32_t* iters_out, double* relres_out);
+
+/* Choose the CG of every solve of this context (pico_cg_batch, pico_variance_map,
+ * pico_variance_map_adaptive, pico_pmr):
+ *   PICO_SOLVER_GLOBAL   CG on the whole image (Sec. 2.1.3, Eq. 6), the default;
+ *   PICO_SOLVER_COLUMNS  Cartesian phase-encode masks: A^H A is block diagonal
+ *                        over the nx readout columns (the mask acts on ky only,
+ *                        F^H M F = (F_y^H M_y F_y) (x) I), so Eq. 6 splits into nx
+ *                        independent ny x ny systems and CG runs on each one with
+ *                        its own step lengths and its own stopping test
+ *                        ||r_j|| <= rtol ||rhs_j||.  The fixed point is the same
+ *                        (the exact solution); the iterates after a fixed number
+ *                        of updates differ from the global CG's (each column's
+ *                        iterate minimises that column's error in its own energy
+ *                        norm, so no column converges slower).  Every update is
+ *                        one fused launch on the tensor cores.  relres_out of
+ *                        pico_cg_batch is ||r|| / ||rhs|| over the image and
+ *                        iters_out the most updates any column took.
+ * PICO_E_UNSUPPORTED for PICO_SOLVER_COLUMNS unless the context runs the
+ * tensor-core operator (pico_info.normal_op == 1) with a row tile that is a
+ * multiple of 32 and at most 4 tiles per column (e.g. ny = 128, 160, 192, 256,
+ * 320, 384, 512).  Drops the context's captured CUDA graphs; allocates
+ * 28 bytes per (image, column) on first use. */
+pico_status pico_set_solver(pico_ctx* ctx, int32_t solver);
+pico_status pico_get_solver(const pico_ctx* ctx, int32_t* solver);
 
 /* PICO running sums (Alg. 1) over probes probe_begin .. probe_begin+nprobes-1
  * drawn under seed (probe_kind: pico_probe):

@@ -25,6 +25,7 @@ LIB_PATH = os.path.join(_PKG, "libpico.so")
 PICO_OK, PICO_E_INVALID, PICO_E_OOM, PICO_E_CUDA, PICO_E_TIMEOUT, PICO_E_BREAKDOWN, PICO_E_UNSUPPORTED = range(7)
 PICO_CARTESIAN, PICO_SPIRAL = 0, 1
 PICO_PROBE_PHASE, PICO_PROBE_RADEMACHER, PICO_PROBE_GAUSS = 0, 1, 2
+PICO_SOLVER_GLOBAL, PICO_SOLVER_COLUMNS = 0, 1
 STATUS_NAMES = ["PICO_OK", "PICO_E_INVALID", "PICO_E_OOM", "PICO_E_CUDA", "PICO_E_TIMEOUT",
                 "PICO_E_BREAKDOWN", "PICO_E_UNSUPPORTED"]
 
@@ -119,6 +120,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "pico_autotune": ([vp, i32, ctypes.POINTER(pico_tuning), ctypes.POINTER(f64), i32], i32),
         "pico_tune_select": ([ctypes.POINTER(f64), i32, i32, ctypes.POINTER(pico_tuning)], i32),
         "pico_inject_error": ([vp, i32, i32], i32),
+        "pico_set_solver": ([vp, i32], i32),
+        "pico_get_solver": ([vp, ctypes.POINTER(i32)], i32),
         "pico_cs_generation": ([vp, ctypes.POINTER(i64)], i32),
         "pico_footprint": ([ctypes.POINTER(pico_operator_desc), i32, ctypes.POINTER(ctypes.c_size_t)], i32),
         "pico_server_create": ([ctypes.c_size_t, i32, i32, ctypes.POINTER(vp)], i32),
@@ -390,6 +393,18 @@ def pico_sync(ctx) -> None:
     _check(ctx, load_library().pico_sync(ctx))
 
 
+def pico_set_solver(ctx, solver: int) -> None:
+    """PICO_SOLVER_GLOBAL (CG on the whole image) or PICO_SOLVER_COLUMNS (CG per
+    readout column of a phase-encode Cartesian operator)."""
+    _check(ctx, load_library().pico_set_solver(ctx, solver))
+
+
+def pico_get_solver(ctx) -> int:
+    v = ctypes.c_int32()
+    _check(ctx, load_library().pico_get_solver(ctx, ctypes.byref(v)))
+    return v.value
+
+
 def pico_inject_error(ctx, status: int, code: int = 1) -> None:
     """Host-side fault injection: the next ``pico_sync`` reports ``status``
     (PICO_E_TIMEOUT or PICO_E_BREAKDOWN) exactly as if a kernel had set it."""
@@ -434,6 +449,16 @@ class Operator:
     @property
     def tuning(self) -> dict:
         return pico_get_tuning(self.ctx)
+
+    @property
+    def solver(self) -> int:
+        return pico_get_solver(self.ctx)
+
+    def set_solver(self, solver) -> None:
+        """``"global"`` / ``"columns"`` (or the PICO_SOLVER_* values)."""
+        if isinstance(solver, str):
+            solver = {"global": PICO_SOLVER_GLOBAL, "columns": PICO_SOLVER_COLUMNS}[solver]
+        pico_set_solver(self.ctx, solver)
 
     def set_tuning(self, **fields) -> None:
         t = self.tuning

@@ -89,6 +89,14 @@ struct pico_ctx {
   int* g_err = nullptr;
   double2* g_pbuf = nullptr;
   pico::CgArgs cg{};
+  // CG run per readout column (pico_set_solver): per (image, column) scalars
+  int solver = PICO_SOLVER_GLOBAL;
+  double *col_rr0 = nullptr, *col_rr = nullptr;
+  float* col_beta = nullptr;
+  int *col_done = nullptr, *col_iters = nullptr;
+  float2* col_G = nullptr;  // small images: G_j of every column, [nx][ny][ny] (whole solve on chip)
+  bool col_small = false;
+  std::string host_fail;  // a launch that could not be issued (reported by the entry point)
   size_t device_bytes = 0, budget = 0;
   bool async_alloc = false;  // stream-ordered cudaMallocAsync / cudaFreeAsync (serving contexts)
   std::vector<void*> allocs;
@@ -121,6 +129,11 @@ pico_status fail(pico_ctx* c, pico_status st, const std::string& msg) {
 pico_status cuda_check(pico_ctx* c, const char* where) {
   const cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return fail(c, PICO_E_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+  if (c && !c->host_fail.empty()) {
+    const std::string m = std::string(where) + ": " + c->host_fail;
+    c->host_fail.clear();
+    return fail(c, PICO_E_CUDA, m);
+  }
   return PICO_OK;
 }
 
@@ -242,8 +255,14 @@ float* cpf(float2* p) { return reinterpret_cast<float*>(p); }
 // column-FFT kernel is as fast as the Gram operator, whose cost is dominated
 // by streaming G once per launch.
 void select_path(pico_ctx* c, int nb) {
-  c->gram_on = c->gram && nb >= c->gram_min_batch;
+  c->gram_on = c->gram && (nb >= c->gram_min_batch || c->solver == PICO_SOLVER_COLUMNS);
   c->cg.PA = c->gram_on ? c->pa_gram : c->pa_fft;
+}
+bool column_mode(const pico_ctx* c) { return c->solver == PICO_SOLVER_COLUMNS && c->gram_on; }
+bool column_small(const pico_ctx* c) { return c->solver == PICO_SOLVER_COLUMNS && c->col_small; }
+pico::ColCgArgs col_args(pico_ctx* c) {
+  return pico::ColCgArgs{reinterpret_cast<float*>(c->X), reinterpret_cast<float*>(c->R), c->col_rr0, c->col_rr,
+                         c->col_beta, c->col_done, c->col_iters, c->status, c->cg.rtol2};
 }
 // Gram mode: the direction written by CG iteration `it` (two buffers alternate,
 // because the operator reads the previous direction while writing the new one)
@@ -321,6 +340,25 @@ void op_cg_normal(pico_ctx* c, int nb, int it, float lam) {
 // unless profiling is on.
 void cg_range(pico_ctx* c, int nb, int it0, int it1, double rtol, float lam) {
   auto direct = [&]() {
+    if (column_mode(c)) {
+      // one fused launch per update: operator, step, x and r updates, next beta
+      for (int it = it0; it < it1; ++it) {
+        pico::GramArgs g{};
+        g.in = cpf(c->R);
+        g.pold = gram_pbuf(c, it + 1);
+        g.pnew = gram_pbuf(c, it);
+        g.itmax = c->itmax;
+        g.it = it;
+        g.nb = nb;
+        g.cg = 1;
+        g.lam = lam;
+        g.err = c->g_err;
+        Launch L(c, 0);
+        if (!pico::launch_gram_colcg(c->gop, c->mR, gram_pmap(c, it + 1), g, col_args(c), c->stream))
+          c->host_fail = "per-column CG launch failed (tile map encoding or cluster launch)";
+      }
+      return;
+    }
     for (int it = it0; it < it1; ++it) {
       op_cg_normal(c, nb, it, lam);
       {
@@ -377,6 +415,13 @@ void cg_iterations(pico_ctx* c, int nb, int max_iter, double rtol, float lam) {
     const int it1 = std::min(max_iter, it0 + kStopChunk);
     cg_range(c, nb, it0, it1, rtol, lam);
     if (it1 == max_iter) break;
+    if (column_mode(c)) {
+      { Launch L(c, 1); pico::launch_colcg_any_live(col_args(c), c->nx, nb, c->d_flag, c->stream); }
+      cudaMemcpyAsync(c->h_flag, c->d_flag, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+      if (cudaStreamSynchronize(c->stream) != cudaSuccess) return;
+      if (!*c->h_flag) break;
+      continue;
+    }
     { Launch L(c, 1); pico::launch_cg_all_done(c->cg, nb, it1, c->d_flag, c->stream); }
     cudaMemcpyAsync(c->h_flag, c->d_flag, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
     if (cudaStreamSynchronize(c->stream) != cudaSuccess) return;
@@ -384,9 +429,26 @@ void cg_iterations(pico_ctx* c, int nb, int max_iter, double rtol, float lam) {
   }
 }
 
+// the whole per-column CG solve of small images: one launch, rhs in R, x to X (natural layout)
+void run_cg_small(pico_ctx* c, int nb, int max_iter, double rtol, float lam) {
+  Launch L(c, 0);
+  pico::launch_colcg_small(c->col_G, c->R, c->X, c->ny, c->nx, nb, max_iter, rtol * rtol, lam, c->col_rr0,
+                           c->col_rr, c->col_iters, c->status, c->stream);
+}
+
 pico_status run_cg(pico_ctx* c, int nb, int max_iter, double rtol, float lam) {
   c->cg.rtol2 = rtol * rtol;
-  { Launch L(c, 1); pico::launch_cg_init_rhs(c->cg, nb, c->stream); }
+  if (column_small(c)) {
+    run_cg_small(c, nb, max_iter, rtol, lam);
+    return cuda_check(c, "cg");
+  }
+  if (column_mode(c)) {
+    Launch L(c, 1);
+    pico::launch_colcg_init(col_args(c), c->ny, c->nx, nb, c->stream);
+  } else {
+    Launch L(c, 1);
+    pico::launch_cg_init_rhs(c->cg, nb, c->stream);
+  }
   cg_iterations(c, nb, max_iter, rtol, lam);
   return cuda_check(c, "cg");
 }
@@ -409,6 +471,14 @@ pico_status run_cg_from_probe(pico_ctx* c, int nb, int max_iter, double rtol, fl
                               int64_t begin, int kind) {
   c->cg.rtol2 = rtol * rtol;
   init_from_probe(c, nb, seed, begin, kind);
+  if (column_small(c)) {
+    run_cg_small(c, nb, max_iter, rtol, lam);
+    return cuda_check(c, "cg");
+  }
+  if (column_mode(c)) {
+    Launch L(c, 1);
+    pico::launch_colcg_init(col_args(c), c->ny, c->nx, nb, c->stream);
+  }
   cg_iterations(c, nb, max_iter, rtol, lam);
   return cuda_check(c, "cg");
 }
@@ -929,6 +999,7 @@ pico_status init_impl(const pico_operator_desc* d, void* cuda_stream, size_t hbm
     cudaMemcpyAsync(c->twx, twxv.data(), twxv.size() * sizeof(float2), cudaMemcpyHostToDevice, c->stream);
     cudaMemcpyAsync(c->mask, d->mask, (size_t)c->ny, cudaMemcpyHostToDevice, c->stream);
     c->cop = pico::CartOp{c->ny, c->nx, nc, N1, N2, c->smaps, c->ymul, c->tw, c->mask, M1, M2, c->twx};
+    c->gmask.assign(d->mask, d->mask + c->ny);
     // the host vectors above must outlive the asynchronous copies
     if (cudaStreamSynchronize(c->stream) != cudaSuccess) return cuda_check(c, "pico_init upload");
   } else {
@@ -1061,7 +1132,13 @@ pico_status pico_cg_batch(pico_ctx* c, const void* rhs, void* x, int32_t nbatch,
       cudaMemcpyAsync(xb, c->X, (size_t)nb * bytes_img, cudaMemcpyDeviceToDevice, c->stream);
     }
     if (iters_out || relres_out) {
-      { Launch L(c, 3); pico::launch_cg_report(c->cg, nb, max_iter, c->d_iters, c->d_relres, c->stream); }
+      if (column_mode(c) || column_small(c)) {
+        Launch L(c, 3);
+        pico::launch_colcg_report(col_args(c), c->nx, nb, c->d_iters, c->d_relres, c->stream);
+      } else {
+        Launch L(c, 3);
+        pico::launch_cg_report(c->cg, nb, max_iter, c->d_iters, c->d_relres, c->stream);
+      }
       std::vector<int> it(nb);
       std::vector<double> rr(nb);
       cudaMemcpyAsync(it.data(), c->d_iters, nb * sizeof(int), cudaMemcpyDeviceToHost, c->stream);
@@ -1427,6 +1504,45 @@ pico_status pico_sync(pico_ctx* c) {
   return cuda_check(c, "pico_sync");
 }
 
+pico_status pico_set_solver(pico_ctx* c, int32_t solver) {
+  if (!c || !c->smaps) return PICO_E_INVALID;
+  if (solver != PICO_SOLVER_GLOBAL && solver != PICO_SOLVER_COLUMNS)
+    return fail(c, PICO_E_INVALID, "solver must be PICO_SOLVER_GLOBAL or PICO_SOLVER_COLUMNS");
+  if (solver == PICO_SOLVER_COLUMNS) {
+    const bool phase_encode = c->kind == PICO_CARTESIAN && !c->mask2d && !c->gmask.empty();
+    const bool small = phase_encode && !c->gram && pico::colcg_small_supported(c->ny);
+    if (!small && (!c->gram || !pico::gram_colcg_supported(c->ny, c->nx)))
+      return fail(c, PICO_E_UNSUPPORTED,
+                  "per-column CG needs a Cartesian phase-encode context with ny = 32, 64 or 96, or one on the "
+                  "tensor-core operator whose row tile is a multiple of 32 and at most 4 tiles per column");
+    if (small && !c->col_G) {
+      pico_status st = PICO_OK;
+      if ((st = dalloc(c, &c->col_G, (size_t)c->nx * c->ny * c->ny)) != PICO_OK) return st;
+      if (!c->g_pbuf && (st = dalloc(c, &c->g_pbuf, (size_t)c->ny)) != PICO_OK) return st;
+      pico::launch_colcg_small_build(c->smaps, c->gmask.data(), c->nc, c->ny, c->nx, c->col_G, c->g_pbuf,
+                                     c->stream);
+    }
+    c->col_small = small;
+    const size_t n = (size_t)c->max_batch * c->nx;
+    pico_status st = PICO_OK;
+    if ((!c->col_rr0 && (st = dalloc(c, &c->col_rr0, n)) != PICO_OK) ||
+        (!c->col_rr && (st = dalloc(c, &c->col_rr, n)) != PICO_OK) ||
+        (!c->col_beta && (st = dalloc(c, &c->col_beta, n)) != PICO_OK) ||
+        (!c->col_done && (st = dalloc(c, &c->col_done, n)) != PICO_OK) ||
+        (!c->col_iters && (st = dalloc(c, &c->col_iters, n)) != PICO_OK))
+      return st;
+  }
+  clear_graphs(c);
+  c->solver = solver;
+  return cuda_check(c, "pico_set_solver");
+}
+
+pico_status pico_get_solver(const pico_ctx* c, int32_t* solver) {
+  if (!c || !solver) return PICO_E_INVALID;
+  *solver = c->solver;
+  return PICO_OK;
+}
+
 pico_status pico_inject_error(pico_ctx* c, int32_t cls, int32_t code) {
   if (!c || !c->smaps || (cls != PICO_E_TIMEOUT && cls != PICO_E_BREAKDOWN) || code == 0)
     return c ? fail(c, PICO_E_INVALID, "inject PICO_E_TIMEOUT or PICO_E_BREAKDOWN with a nonzero code")
@@ -1520,7 +1636,9 @@ pico_status pico_autotune(pico_ctx* c, int32_t iters, pico_tuning* out, double* 
   }
   const float lam = (float)c->lam_phys;
   const bool prof = c->profiling;
+  const int solver = c->solver;
   c->profiling = false;
+  c->solver = PICO_SOLVER_GLOBAL;  // the tuning is measured on the whole-image CG
   c->cg.rtol2 = 0.0;
   // us per image and iteration of `iters` CG iterations on nb probes: the
   // first run launches directly, the second captures the graph, the best of
@@ -1560,6 +1678,7 @@ pico_status pico_autotune(pico_ctx* c, int32_t iters, pico_tuning* out, double* 
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   c->profiling = prof;
+  c->solver = solver;
   if (st != PICO_OK) return st;
   if ((st = cuda_check(c, "pico_autotune")) != PICO_OK) return st;
   double flat[kCand * kNb];

@@ -1,0 +1,258 @@
+// Per-column CG with the whole solve on chip, for small Cartesian images.
+//
+// With a phase-encode mask A^H A is block diagonal over the readout columns
+// (Sec. 2.1.3 with F^H M F = (F_y^H M_y F_y) (x) I): column j of every image is
+// acted on by the dense Hermitian ny x ny matrix
+//   G_j[y, y'] = P[y - y'] sum_c conj(S_c[y, j]) S_c[y', j],
+//   P[d] = (1/ny) sum_k m_k exp(2 pi i k d / ny),
+// so CG on Eq. 6 splits into independent column systems (G_j + lam I) x_j = b_j.
+// For ny <= 96 a block holds G_j (ny^2 complex64, at most 72 KB) and the CG
+// vectors x, r, p, q of a group of images of that column in shared memory and
+// runs every CG update of the solve in one launch: a latency-bound workload
+// (64 x 64 images, 32 probes) then needs one kernel per solve instead of
+// three per update.  Inner products are FP64 (fixed-order reductions, so the
+// result does not depend on the launch shape); each column stops on its own
+// test ||r_j|| <= rtol ||b_j||.
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace pico {
+
+namespace {
+
+constexpr int kSmallThreads = 256;
+
+// G_j of every column in the plain layout [nx][ny][ny] (row y, column y'),
+// FP64 sums over the coils, then rounded to complex64.
+__global__ void k_colcg_small_build(const float2* __restrict__ S, const double2* __restrict__ P, int nc, int ny,
+                                    int nx, float2* __restrict__ G) {
+  const int j = blockIdx.y;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= ny * ny) return;
+  const int y = t / ny, yp = t % ny;
+  const int64_t n = (int64_t)ny * nx;
+  double re = 0.0, im = 0.0;
+  for (int c = 0; c < nc; ++c) {
+    const float2 a = S[c * n + (int64_t)y * nx + j], b = S[c * n + (int64_t)yp * nx + j];
+    re += (double)a.x * b.x + (double)a.y * b.y;  // conj(a) b
+    im += (double)a.x * b.y - (double)a.y * b.x;
+  }
+  int d = y - yp;
+  if (d < 0) d += ny;
+  const double2 p = P[d];
+  G[((size_t)j * ny + y) * ny + yp] = make_float2((float)(p.x * re - p.y * im), (float)(p.x * im + p.y * re));
+}
+
+// Sum over the NY rows of every image of a per-element value held by the
+// thread that owns element e = k * kSmallThreads + tid (image e / NY, row
+// e % NY): a warp's 32 elements belong to one image; warp sums go to
+// red[t][w], then thread t adds its NY / 32 slots in order.
+template <int NY, int T>
+__device__ __forceinline__ void image_sums(const double (&v)[NY * T / kSmallThreads], double* red, double* out) {
+  constexpr int E = NY * T / kSmallThreads;
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int k = 0; k < E; ++k) {
+    const double s = warp_sum_d(v[k]);
+    const int e = k * kSmallThreads + threadIdx.x;
+    if (lane == 0) red[(e / NY) * (NY / 32) + (e % NY) / 32] = s;
+  }
+  __syncthreads();
+  if (threadIdx.x < T) {
+    double s = 0.0;
+#pragma unroll
+    for (int w = 0; w < NY / 32; ++w) s += red[threadIdx.x * (NY / 32) + w];
+    out[threadIdx.x] = s;
+  }
+  __syncthreads();
+}
+
+// Block = (column j, images b0 .. b0 + T - 1).  rhs and x are natural-layout
+// images [B][NY][nx]; rr0 / rr / iters receive the column's ||b_j||^2, final
+// ||r_j||^2 and update count per image ([B][nx]).
+template <int NY, int T>
+__global__ void __launch_bounds__(kSmallThreads) k_colcg_small(const float2* __restrict__ G, const float2* __restrict__ rhs,
+                                                            float2* __restrict__ X, int nx, int nb, int max_iter,
+                                                            double rtol2, float lam, double* __restrict__ rr0_out,
+                                                            double* __restrict__ rr_out, int* __restrict__ iters_out,
+                                                            int* __restrict__ status) {
+  constexpr int E = NY * T / kSmallThreads;  // elements (image, row) per thread
+  static_assert(NY % 32 == 0 && (NY * T) % kSmallThreads == 0, "tile shape");
+  extern __shared__ __align__(16) unsigned char smraw[];
+  float2* Gs = reinterpret_cast<float2*>(smraw);  // [NY][NY]
+  float2* ps = Gs + NY * NY;                      // [T][NY] direction
+  double* red = reinterpret_cast<double*>(ps + T * NY);  // [T][NY / 32]
+  double* sc = red + T * (NY / 32);               // rr0[T], rr[T], tmp[T]
+  double* s_rr0 = sc;
+  double* s_rr = sc + T;
+  double* s_tmp = sc + 2 * T;
+  float* s_alpha = reinterpret_cast<float*>(sc + 3 * T);
+  float* s_beta = s_alpha + T;
+  int* s_live = reinterpret_cast<int*>(s_beta + T);
+  int* s_any = s_live + T;
+
+  const int j = blockIdx.x, b0 = blockIdx.y * T, tid = threadIdx.x;
+  const int64_t n = (int64_t)NY * nx;
+  for (int i = tid; i < NY * NY; i += kSmallThreads) Gs[i] = G[(size_t)j * NY * NY + i];
+  // this thread's elements: image t = e / NY, row y = e % NY (a warp's 32 share t)
+  float2 x[E], r[E], q[E];
+  double v[E];
+#pragma unroll
+  for (int k = 0; k < E; ++k) {
+    const int e = k * kSmallThreads + tid, t = e / NY, y = e % NY, b = b0 + t;
+    r[k] = b < nb ? rhs[(size_t)b * n + (int64_t)y * nx + j] : make_float2(0.f, 0.f);
+    x[k] = make_float2(0.f, 0.f);
+    v[k] = (double)r[k].x * r[k].x + (double)r[k].y * r[k].y;
+  }
+  image_sums<NY, T>(v, red, s_rr0);
+  if (tid < T) {
+    const double rr = s_rr0[tid];
+    s_rr[tid] = rr;
+    s_beta[tid] = 0.f;
+    if (b0 + tid < nb) {
+      iters_out[(size_t)(b0 + tid) * nx + j] = 0;
+      if (!isfinite(rr)) status[b0 + tid] = 5;  // a non-finite right-hand side: x stays 0
+    }
+  }
+  __syncthreads();
+  for (int it = 0; it < max_iter; ++it) {
+    // which systems take this update (block-uniform "any" decides whether to go on)
+    if (tid == 0) *s_any = 0;
+    __syncthreads();
+    if (tid < T) {
+      const double rr = s_rr[tid], rr0 = s_rr0[tid];
+      const int live = b0 + tid < nb && isfinite(rr) && isfinite(rr0) && rr > rtol2 * rr0;
+      s_live[tid] = live;
+      if (live) *s_any = 1;
+    }
+    __syncthreads();
+    if (!*s_any) break;
+    // p = r + beta p
+#pragma unroll
+    for (int k = 0; k < E; ++k) {
+      const int e = k * kSmallThreads + tid, t = e / NY;
+      if (s_live[t]) {
+        const float bt = s_beta[t];
+        const float2 po = it > 0 ? ps[e] : make_float2(0.f, 0.f);
+        ps[e] = make_float2(fmaf(bt, po.x, r[k].x), fmaf(bt, po.y, r[k].y));
+      }
+    }
+    __syncthreads();
+    // q = (G_j + lam) p: q[y] = sum_y' G[y][y'] p[y'] = sum_y' conj(G[y'][y]) p[y'] (Hermitian);
+    // a warp reads G[y'][y .. y+31] (consecutive) and broadcasts p[t][y']
+#pragma unroll
+    for (int k = 0; k < E; ++k) {
+      const int e = k * kSmallThreads + tid, t = e / NY, y = e % NY;
+      const float2* pt = ps + t * NY;
+      float ar = 0.f, ai = 0.f;
+#pragma unroll 8
+      for (int yp = 0; yp < NY; ++yp) {
+        const float2 g = Gs[yp * NY + y], p = pt[yp];
+        ar = fmaf(g.x, p.x, fmaf(g.y, p.y, ar));   // Re(conj(g) p)
+        ai = fmaf(g.x, p.y, fmaf(-g.y, p.x, ai));  // Im(conj(g) p)
+      }
+      const float2 pe = pt[y];
+      q[k] = make_float2(fmaf(lam, pe.x, ar), fmaf(lam, pe.y, ai));
+      v[k] = (double)pe.x * q[k].x + (double)pe.y * q[k].y;
+    }
+    image_sums<NY, T>(v, red, s_tmp);
+    if (tid < T) {
+      float a = 0.f;
+      if (s_live[tid]) {
+        const double pq = s_tmp[tid];
+        if (!(pq > 0.0) || !isfinite(pq)) {
+          s_live[tid] = 0;  // breakdown: this system keeps its iterate
+          s_rr[tid] = 0.0;
+          status[b0 + tid] = 5;
+        } else {
+          a = (float)(s_rr[tid] / pq);
+        }
+      }
+      s_alpha[tid] = a;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < E; ++k) {
+      const int e = k * kSmallThreads + tid, t = e / NY;
+      if (s_live[t]) {
+        const float a = s_alpha[t];
+        const float2 p = ps[e];
+        x[k] = make_float2(fmaf(a, p.x, x[k].x), fmaf(a, p.y, x[k].y));
+        r[k] = make_float2(fmaf(-a, q[k].x, r[k].x), fmaf(-a, q[k].y, r[k].y));
+      }
+      v[k] = (double)r[k].x * r[k].x + (double)r[k].y * r[k].y;
+    }
+    image_sums<NY, T>(v, red, s_tmp);
+    if (tid < T && s_live[tid]) {
+      const double rrn = s_tmp[tid];
+      s_beta[tid] = (float)(rrn / s_rr[tid]);
+      s_rr[tid] = rrn;
+      if (!isfinite(rrn)) status[b0 + tid] = 5;
+      iters_out[(size_t)(b0 + tid) * nx + j] = it + 1;
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int k = 0; k < E; ++k) {
+    const int e = k * kSmallThreads + tid, t = e / NY, y = e % NY, b = b0 + t;
+    if (b < nb) X[(size_t)b * n + (int64_t)y * nx + j] = x[k];
+  }
+  if (tid < T && b0 + tid < nb) {
+    rr0_out[(size_t)(b0 + tid) * nx + j] = s_rr0[tid];
+    rr_out[(size_t)(b0 + tid) * nx + j] = s_rr[tid];
+  }
+}
+
+template <int NY, int T>
+size_t small_smem() {
+  return (size_t)NY * NY * 8 + (size_t)T * NY * 8 + (size_t)T * (NY / 32) * 8 + 3 * T * 8 + 2 * T * 4 + T * 4 + 16;
+}
+
+template <int NY, int T>
+void launch_small(const float2* G, const float2* rhs, float2* X, int nx, int nb, int max_iter, double rtol2,
+                  float lam, double* rr0, double* rr, int* iters, int* status, cudaStream_t s) {
+  const size_t sm = small_smem<NY, T>();
+  auto k = k_colcg_small<NY, T>;
+  cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  k<<<dim3(nx, (nb + T - 1) / T), kSmallThreads, sm, s>>>(G, rhs, X, nx, nb, max_iter, rtol2, lam, rr0, rr, iters,
+                                                          status);
+}
+
+}  // namespace
+
+bool colcg_small_supported(int ny) { return ny == 32 || ny == 64 || ny == 96; }
+
+void launch_colcg_small_build(const float2* smaps, const uint8_t* mask_host, int nc, int ny, int nx, float2* G,
+                              double2* pbuf, cudaStream_t s) {
+  // P[d] = (1/ny) sum_k m_k exp(2 pi i k d / ny), FP64 on the host
+  double2 P[128];
+  const double pi2 = 6.283185307179586476925286766559;
+  for (int d = 0; d < ny; ++d) {
+    double re = 0.0, im = 0.0;
+    for (int k = 0; k < ny; ++k)
+      if (mask_host[k]) {
+        const double a = pi2 * (double)(((int64_t)k * d) % ny) / ny;
+        re += cos(a);
+        im += sin(a);
+      }
+    P[d] = make_double2(re / ny, im / ny);
+  }
+  cudaMemcpyAsync(pbuf, P, ny * sizeof(double2), cudaMemcpyHostToDevice, s);
+  k_colcg_small_build<<<dim3((ny * ny + 255) / 256, nx), 256, 0, s>>>(smaps, pbuf, nc, ny, nx, G);
+  cudaStreamSynchronize(s);  // P lives on the host stack until the copy has run
+}
+
+void launch_colcg_small(const float2* G, const float2* rhs, float2* X, int ny, int nx, int nb, int max_iter,
+                        double rtol2, float lam, double* rr0, double* rr, int* iters, int* status, cudaStream_t s) {
+  if (nb <= 0) return;
+  // images per block: 32 for ny = 32 and 64 (128 blocks for 64 columns and 64
+  // images), 16 for ny = 96 (shared memory)
+  if (ny == 32)
+    launch_small<32, 32>(G, rhs, X, nx, nb, max_iter, rtol2, lam, rr0, rr, iters, status, s);
+  else if (ny == 64)
+    launch_small<64, 16>(G, rhs, X, nx, nb, max_iter, rtol2, lam, rr0, rr, iters, status, s);
+  else if (ny == 96)
+    launch_small<96, 16>(G, rhs, X, nx, nb, max_iter, rtol2, lam, rr0, rr, iters, status, s);
+}
+
+}  // namespace pico

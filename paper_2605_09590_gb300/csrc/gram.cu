@@ -202,6 +202,215 @@ __global__ void k_from_cp(const float* __restrict__ in, float2* __restrict__ out
 }
 
 // ---------------------------------------------------------------------------
+// per-column CG: the epilogue of one CG update (column-CG mode)
+// ---------------------------------------------------------------------------
+// With CG run separately on every readout column j (A^H A is block diagonal
+// over columns), the update of column j needs only sums over that column's
+// ny rows: p^H q for alpha, then ||r||^2 for beta.  The nyt CTAs that hold the
+// row tiles of one (image tile, column) form a thread-block cluster and add
+// their partial sums through distributed shared memory (each CTA sums the nyt
+// partials in rank order, so all of them get the same bits), then every CTA
+// updates x and r on its own rows:
+//   phase A  q = D + lam p (D in tensor memory, p tiles by TMA) -> p^H q partial
+//   exchange alpha = rr / p^H q
+//   phase B  x += alpha p, r -= alpha q on (p, x, r) tiles in shared memory,
+//            stored back by TMA; ||r_new||^2 partial
+//   exchange beta = ||r_new||^2 / rr; the rank-0 CTA writes the column's
+//            rr, beta, done and iteration count for the next launch
+//   a last cluster barrier keeps every CTA alive until its peers have read
+//   its exchange slots.
+// Tiles are 128 images x 32 rows of one plane (128-byte swizzle), two planes
+// (re, im) per vector; phase B keeps up to two (p, x, r) groups in flight in
+// the idle pipeline buffers, phase A up to two p tiles after the first group.
+__device__ __forceinline__ double* xch_of(float* beta_s) { return reinterpret_cast<double*>(beta_s + kGramRows); }
+
+template <int KC>
+__device__ __forceinline__ void colcg_epilogue(uint8_t* sm, int S, uint32_t stage_bytes, uint64_t* pbar, double* xch,
+                                               uint32_t tbase, int NT, int quarter, int row, int k, int j,
+                                               int ytile, int n0, int m0, bool accok, const GramArgs& g,
+                                               const ColCgArgs& cc, const CUtensorMap& mPe, const CUtensorMap& mXe,
+                                               const CUtensorMap& mRe) {
+  constexpr uint32_t kPlane = kGramRows * 128;   // one plane of a 32-row tile: 16 KB
+  constexpr uint32_t kTile = 2 * kPlane;         // re and im planes
+  const int ng = NT / 32;
+  const size_t area = (size_t)S * stage_bytes;
+  const int nbB = area >= 6 * (size_t)kTile ? 2 : 1;
+  const uint32_t aoff = 3 * kTile;
+  const int nbA = (int)min((size_t)2, (area - aoff) / kTile);
+  auto bbuf = [&](int gi) { return sm + (size_t)(gi % nbB) * 3 * kTile; };
+  auto abuf = [&](int gi) { return sm + aoff + (size_t)(gi % nbA) * kTile; };
+  const bool leader = threadIdx.x == 64;
+  auto loadA = [&](int gi) {
+    uint64_t* b = &pbar[gi % nbA];
+    mbar_expect_tx(b, kTile);
+    tma_load_4d(abuf(gi), &mPe, b, n0 + 32 * gi, 0, j, m0);
+    tma_load_4d(abuf(gi) + kPlane, &mPe, b, n0 + 32 * gi, 1, j, m0);
+  };
+  auto loadB = [&](int gi) {
+    uint64_t* b = &pbar[2 + gi % nbB];
+    uint8_t* d = bbuf(gi);
+    mbar_expect_tx(b, 3 * kTile);
+    tma_load_4d(d, &mPe, b, n0 + 32 * gi, 0, j, m0);
+    tma_load_4d(d + kPlane, &mPe, b, n0 + 32 * gi, 1, j, m0);
+    tma_load_4d(d + kTile, &mXe, b, n0 + 32 * gi, 0, j, m0);
+    tma_load_4d(d + kTile + kPlane, &mXe, b, n0 + 32 * gi, 1, j, m0);
+    tma_load_4d(d + 2 * kTile, &mRe, b, n0 + 32 * gi, 0, j, m0);
+    tma_load_4d(d + 2 * kTile + kPlane, &mRe, b, n0 + 32 * gi, 1, j, m0);
+  };
+  const bool inb = k < g.nb;
+  const size_t cidx = (size_t)(inb ? k : 0) * g.nx + j;
+  const bool live = accok && inb && !cc.done[cidx];
+  const double rr = live ? cc.rr[cidx] : 0.0;
+  const int sw = row & 7;  // 16-byte group swizzle of this row
+  const float lam = g.lam;
+
+  // ---- phase A: p^H q over this CTA's rows ----
+  if (leader && accok) {
+    for (int gi = 0; gi < nbA && gi < ng; ++gi) loadA(gi);
+    loadB(0);
+  }
+  double pq = 0.0;
+  for (int gi = 0; gi < ng; ++gi) {
+    const bool pok = accok && mbar_wait(&pbar[gi % nbA], (gi / nbA) & 1);
+    if (accok && !pok) set_err(g.err, 6);
+    const float4* pre = reinterpret_cast<const float4*>(abuf(gi) + (size_t)row * 128);
+    const float4* pim = reinterpret_cast<const float4*>(abuf(gi) + kPlane + (size_t)row * 128);
+    const uint32_t ta = tbase + ((uint32_t)(32 * quarter) << 16) + (uint32_t)(32 * gi);
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      float dr[16], di[16];
+      tmem_ld16x2(ta + 16 * h, ta + (uint32_t)NT + 16 * h, dr, di);
+      if (live && pok) {
+        float acc = 0.f;
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+          const int ph = (4 * h + v) ^ sw;
+          const float4 pr = pre[ph], pi = pim[ph];
+          acc = fmaf(pr.x, fmaf(lam, pr.x, dr[4 * v + 0]), acc);
+          acc = fmaf(pr.y, fmaf(lam, pr.y, dr[4 * v + 1]), acc);
+          acc = fmaf(pr.z, fmaf(lam, pr.z, dr[4 * v + 2]), acc);
+          acc = fmaf(pr.w, fmaf(lam, pr.w, dr[4 * v + 3]), acc);
+          acc = fmaf(pi.x, fmaf(lam, pi.x, di[4 * v + 0]), acc);
+          acc = fmaf(pi.y, fmaf(lam, pi.y, di[4 * v + 1]), acc);
+          acc = fmaf(pi.z, fmaf(lam, pi.z, di[4 * v + 2]), acc);
+          acc = fmaf(pi.w, fmaf(lam, pi.w, di[4 * v + 3]), acc);
+        }
+        pq += (double)acc;
+      }
+    }
+    asm volatile("bar.sync 1, 128;" ::: "memory");  // every row of this p tile has been read
+    if (leader && accok && gi + nbA < ng) loadA(gi + nbA);
+  }
+  // ---- exchange 1: p^H q over the whole column ----
+  const int nyt = g.nyt;
+  double pq_tot = pq;
+  if (nyt > 1) {
+    xch[row] = pq;
+    cluster_sync_all();
+    pq_tot = 0.0;
+    for (int rk = 0; rk < nyt; ++rk) pq_tot += rk == ytile ? xch[row] : ld_dsmem_f64(&xch[row], (uint32_t)rk);
+  }
+  bool upd = live, broke = false;
+  float alpha = 0.f;
+  if (live) {
+    if (!(pq_tot > 0.0) || !isfinite(pq_tot)) {
+      upd = false;
+      broke = true;
+    } else {
+      alpha = (float)(rr / pq_tot);
+    }
+  }
+  // ---- phase B: x += alpha p, r -= alpha q; ||r_new||^2 ----
+  if (leader && accok && nbB > 1 && ng > 1) loadB(1);  // the phase-A buffers are free now
+  double rrn = 0.0;
+  for (int gi = 0; gi < ng; ++gi) {
+    const bool bok = accok && mbar_wait(&pbar[2 + gi % nbB], (gi / nbB) & 1);
+    if (accok && !bok) set_err(g.err, 7);
+    uint8_t* d = bbuf(gi);
+    const float4* pre = reinterpret_cast<const float4*>(d + (size_t)row * 128);
+    const float4* pim = reinterpret_cast<const float4*>(d + kPlane + (size_t)row * 128);
+    float4* xre = reinterpret_cast<float4*>(d + kTile + (size_t)row * 128);
+    float4* xim = reinterpret_cast<float4*>(d + kTile + kPlane + (size_t)row * 128);
+    float4* rre = reinterpret_cast<float4*>(d + 2 * kTile + (size_t)row * 128);
+    float4* rim = reinterpret_cast<float4*>(d + 2 * kTile + kPlane + (size_t)row * 128);
+    const uint32_t ta = tbase + ((uint32_t)(32 * quarter) << 16) + (uint32_t)(32 * gi);
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      float dr[16], di[16];
+      tmem_ld16x2(ta + 16 * h, ta + (uint32_t)NT + 16 * h, dr, di);
+      if (upd && bok) {
+        float acc = 0.f;
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+          const int ph = (4 * h + v) ^ sw;
+          const float pa[4] = {pre[ph].x, pre[ph].y, pre[ph].z, pre[ph].w};
+          const float pb[4] = {pim[ph].x, pim[ph].y, pim[ph].z, pim[ph].w};
+          float xa[4] = {xre[ph].x, xre[ph].y, xre[ph].z, xre[ph].w};
+          float xb[4] = {xim[ph].x, xim[ph].y, xim[ph].z, xim[ph].w};
+          float ra[4] = {rre[ph].x, rre[ph].y, rre[ph].z, rre[ph].w};
+          float rb[4] = {rim[ph].x, rim[ph].y, rim[ph].z, rim[ph].w};
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            xa[e] = fmaf(alpha, pa[e], xa[e]);
+            xb[e] = fmaf(alpha, pb[e], xb[e]);
+            ra[e] = fmaf(-alpha, fmaf(lam, pa[e], dr[4 * v + e]), ra[e]);
+            rb[e] = fmaf(-alpha, fmaf(lam, pb[e], di[4 * v + e]), rb[e]);
+            acc = fmaf(ra[e], ra[e], fmaf(rb[e], rb[e], acc));
+          }
+          xre[ph] = make_float4(xa[0], xa[1], xa[2], xa[3]);
+          xim[ph] = make_float4(xb[0], xb[1], xb[2], xb[3]);
+          rre[ph] = make_float4(ra[0], ra[1], ra[2], ra[3]);
+          rim[ph] = make_float4(rb[0], rb[1], rb[2], rb[3]);
+        }
+        rrn += (double)acc;
+      }
+    }
+    // every row of this group is written before one thread stores the x and r tiles
+    fence_proxy_async_smem();
+    asm volatile("bar.sync 1, 128;" ::: "memory");
+    if (leader && bok) {
+      tma_store_4d(&mXe, d + kTile, n0 + 32 * gi, 0, j, m0);
+      tma_store_4d(&mXe, d + kTile + kPlane, n0 + 32 * gi, 1, j, m0);
+      tma_store_4d(&mRe, d + 2 * kTile, n0 + 32 * gi, 0, j, m0);
+      tma_store_4d(&mRe, d + 2 * kTile + kPlane, n0 + 32 * gi, 1, j, m0);
+      bulk_commit();
+      if (gi + nbB < ng) {
+        bulk_wait_read();
+        loadB(gi + nbB);
+      }
+    }
+  }
+  if (leader) bulk_wait_all();
+  // ---- exchange 2: ||r_new||^2 over the whole column; the next step ----
+  double rr_tot = rrn;
+  if (nyt > 1) {
+    xch[kGramRows + row] = rrn;
+    cluster_sync_all();
+    rr_tot = 0.0;
+    for (int rk = 0; rk < nyt; ++rk)
+      rr_tot += rk == ytile ? xch[kGramRows + row] : ld_dsmem_f64(&xch[kGramRows + row], (uint32_t)rk);
+  }
+  if (ytile == 0 && live) {
+    if (upd && isfinite(rr_tot)) {
+      cc.rr[cidx] = rr_tot;
+      cc.iters[cidx] += 1;
+      const bool stop = !(rr_tot > cc.rtol2 * cc.rr0[cidx]);
+      cc.beta[cidx] = stop ? 0.f : (float)(rr_tot / rr);
+      if (stop) cc.done[cidx] = 1;
+    } else {
+      broke = true;
+    }
+    if (broke) {
+      cc.done[cidx] = 1;
+      cc.beta[cidx] = 0.f;
+      cc.status[k] = 5;
+    }
+  }
+  // no CTA leaves while a peer may still read its exchange slots
+  if (nyt > 1) cluster_sync_all();
+}
+
+// ---------------------------------------------------------------------------
 // the tensor-core normal operator
 // ---------------------------------------------------------------------------
 // CTA (y tile, image tile, column j).  Warp 0: TMA producer.  Warp 1: TMEM
@@ -220,10 +429,11 @@ __global__ void k_from_cp(const float* __restrict__ in, float2* __restrict__ out
 // and the MMAs read A from there: shared memory then carries only the TMA
 // tiles and the B operand reads, which keeps the tensor pipe, not the
 // shared-memory bandwidth, the limit of the main loop.
-template <int KC, bool AT>
+template <int KC, bool AT, bool COL>
 __global__ void __launch_bounds__(kGramThreads, 1)
     k_gram_normal(const __grid_constant__ CUtensorMap mIn, const __grid_constant__ CUtensorMap mPold,
-                  const __grid_constant__ CUtensorMap mPe, const __grid_constant__ CUtensorMap mQe, GramArgs g) {
+                  const __grid_constant__ CUtensorMap mPe, const __grid_constant__ CUtensorMap mQe,
+                  const __grid_constant__ CUtensorMap mRe, GramArgs g, ColCgArgs cc) {
   extern __shared__ uint8_t smraw[];
   uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smraw) + 1023) & ~(uintptr_t)1023);
   const int NT = g.nt, S = g.stages;
@@ -287,7 +497,10 @@ __global__ void __launch_bounds__(kGramThreads, 1)
   if (warp >= 2) {
     const int r = threadIdx.x - 64;
     const int k = m0 + r;
-    beta_s[r] = (use_pold && k < g.nb) ? g.beta[k] : 0.f;
+    if constexpr (COL)
+      beta_s[r] = (use_pold && k < g.nb) ? cc.beta[(size_t)k * g.nx + j] : 0.f;
+    else
+      beta_s[r] = (use_pold && k < g.nb) ? g.beta[k] : 0.f;
   }
   if (warp == 1) tmem_alloc(tslot, g.tmem_cols);
   tc_fence_before();
@@ -374,6 +587,12 @@ __global__ void __launch_bounds__(kGramThreads, 1)
       }
       mma_commit(accf);
     }
+  }
+  if (COL && warp < 2) {
+    // the epilogue's three cluster-wide exchanges: every thread of the cluster takes part
+    if (g.nyt > 1)
+      for (int e = 0; e < 3; ++e) cluster_sync_all();
+  } else if (warp < 2) {
   } else {
     // ---- split p = r + beta p_old into TF32 head / remainder, in place ----
     // The chunks inside this CTA's output rows [n0, n0 + NT) also store p to
@@ -508,6 +727,10 @@ __global__ void __launch_bounds__(kGramThreads, 1)
     const bool accok = mbar_wait(accf, 0);
     if (!accok) set_err(g.err, 4);
     tc_fence_after();
+    if constexpr (COL) {
+      colcg_epilogue<KC>(sm, S, stage_bytes, pbar, xch_of(beta_s), tbase, NT, quarter, row, k, j, ytile, n0, m0,
+                         accok, g, cc, mPe, mQe, mRe);
+    } else {
     const bool inb = k < g.nb;
     const bool valid = accok && inb && !(g.cg && g.done[k]);
     const size_t col = (size_t)(inb ? k : 0) * img2 + (size_t)j * 2 * g.ny;
@@ -649,6 +872,7 @@ __global__ void __launch_bounds__(kGramThreads, 1)
 
     if (valid && g.pq) g.pq[((size_t)k * g.itmax + g.it) * g.PA + (size_t)j * g.nyt + ytile] = pq;
     }
+    }  // !COL
   }
 
   // teardown: every TMA issued has been consumed by the split warps (or they
@@ -659,6 +883,62 @@ __global__ void __launch_bounds__(kGramThreads, 1)
     __syncwarp();
     tc_fence_after();
     tmem_dealloc(tbase, g.tmem_cols);
+  }
+}
+
+// x = 0 and the per-column CG scalars of nb right-hand sides (column-planar r)
+__global__ void __launch_bounds__(64) k_colcg_init(ColCgArgs cc, int ny, int nx) {
+  __shared__ double part[2];
+  const int j = blockIdx.x, b = blockIdx.y;
+  const size_t cidx = (size_t)b * nx + j;
+  const float* rc = cc.r + cidx * 2 * ny;
+  float* xc = cc.x + cidx * 2 * ny;
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < 2 * ny; i += 64) {
+    const double v = (double)rc[i];
+    acc = fma(v, v, acc);
+    xc[i] = 0.f;
+  }
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const double rr = part[0] + part[1];
+    const_cast<double*>(cc.rr0)[cidx] = rr;
+    cc.rr[cidx] = rr;
+    cc.beta[cidx] = 0.f;
+    cc.iters[cidx] = 0;
+    const bool bad = !isfinite(rr);
+    cc.done[cidx] = bad || !(rr > 0.0);
+    if (bad) cc.status[b] = 5;  // a non-finite right-hand side: breakdown, x stays 0
+  }
+}
+
+// *flag = 1 if a column is still iterating (the flag is zeroed before)
+__global__ void k_colcg_any_live(ColCgArgs cc, int n, int* flag) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n && !cc.done[i]) atomicExch(flag, 1);
+}
+
+// per image: most updates of any column; ||r|| / ||b|| over the whole image
+__global__ void k_colcg_report(ColCgArgs cc, int nx, int* iters, double* relres) {
+  const int b = blockIdx.x;
+  double r2 = 0.0, b2 = 0.0;
+  int it = 0;
+  for (int j = threadIdx.x; j < nx; j += 32) {
+    const size_t c = (size_t)b * nx + j;
+    r2 += cc.rr[c];
+    b2 += cc.rr0[c];
+    it = max(it, cc.iters[c]);
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    r2 += __shfl_xor_sync(0xffffffffu, r2, o);
+    b2 += __shfl_xor_sync(0xffffffffu, b2, o);
+    it = max(it, __shfl_xor_sync(0xffffffffu, it, o));
+  }
+  if (threadIdx.x == 0) {
+    iters[b] = it;
+    relres[b] = !isfinite(b2) ? (double)NAN : b2 > 0.0 ? sqrt(r2 / b2) : 0.0;
   }
 }
 
@@ -774,7 +1054,8 @@ size_t gram_smem(int ny, int kc, int* stages) {
   if (S > 8) S = 8;
   if (S < 2) S = 2;
   *stages = S;
-  return 1024 + (size_t)S * stage + (3 * (size_t)S + 9) * 8 + 16 + kGramRows * 4 + 64;
+  // + per-column CG exchange slots (two FP64 sums per image row)
+  return 1024 + (size_t)S * stage + (3 * (size_t)S + 9) * 8 + 16 + kGramRows * 4 + 2 * kGramRows * 8 + 64;
 }
 
 void launch_gram_normal(const GramOp& op, const CUtensorMap& mIn, const CUtensorMap& mPold, GramArgs g,
@@ -783,9 +1064,10 @@ void launch_gram_normal(const GramOp& op, const CUtensorMap& mIn, const CUtensor
   const size_t smem = gram_smem(op.ny, op.kc, &S);
   // the split direction goes to tensor memory when it fits beside the accumulators
   const bool at = op.a_tmem && 2 * op.nt + 4 * op.kc * S <= 512;
-  void (*kern)(const CUtensorMap, const CUtensorMap, const CUtensorMap, const CUtensorMap, GramArgs) =
-      op.kc == 16 ? (at ? k_gram_normal<16, true> : k_gram_normal<16, false>)
-                  : (at ? k_gram_normal<8, true> : k_gram_normal<8, false>);
+  void (*kern)(const CUtensorMap, const CUtensorMap, const CUtensorMap, const CUtensorMap, const CUtensorMap,
+               GramArgs, ColCgArgs) =
+      op.kc == 16 ? (at ? k_gram_normal<16, true, false> : k_gram_normal<16, false, false>)
+                  : (at ? k_gram_normal<8, true, false> : k_gram_normal<8, false, false>);
   // the shared-memory opt-in is per device and kernel; cache it per (thread, device)
   constexpr int kMaxDev = 16;
   static thread_local size_t configured[kMaxDev][4] = {};
@@ -813,7 +1095,73 @@ void launch_gram_normal(const GramOp& op, const CUtensorMap& mIn, const CUtensor
   const float* psrc = g.cg ? g.pnew : g.in;
   g.tma_epi = op.nt % 32 == 0 && g.nb > 0 && gram_encode_e(&mPe, const_cast<float*>(psrc), op.ny, op.nx, g.nb) &&
               gram_encode_e(&mQe, g.q, op.ny, op.nx, g.nb);
-  kern<<<grid, kGramThreads, smem, s>>>(mIn, mPold, mPe, mQe, g);
+  kern<<<grid, kGramThreads, smem, s>>>(mIn, mPold, mPe, mQe, mQe, g, ColCgArgs{});
+}
+
+bool gram_colcg_supported(int ny, int nx) {
+  if (!gram_supported(ny, nx)) return false;
+  const int nt = gram_tile(ny);
+  return nt % 32 == 0 && ny / nt <= 4;
+}
+
+bool launch_gram_colcg(const GramOp& op, const CUtensorMap& mIn, const CUtensorMap& mPold, GramArgs g,
+                       const ColCgArgs& cc, cudaStream_t s) {
+  int S = 0;
+  const size_t smem = gram_smem(op.ny, op.kc, &S);
+  void (*kern)(const CUtensorMap, const CUtensorMap, const CUtensorMap, const CUtensorMap, const CUtensorMap,
+               GramArgs, ColCgArgs) = op.kc == 16 ? k_gram_normal<16, false, true> : k_gram_normal<8, false, true>;
+  constexpr int kMaxDev = 16;
+  static thread_local size_t configured[kMaxDev][2] = {};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  const int ki = op.kc == 16 ? 0 : 1;
+  if (dev < 0 || dev >= kMaxDev || configured[dev][ki] < smem) {
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (dev >= 0 && dev < kMaxDev) configured[dev][ki] = smem;
+  }
+  g.ny = op.ny;
+  g.nx = op.nx;
+  g.nt = op.nt;
+  g.nyt = op.ny / op.nt;
+  g.stages = S;
+  g.G = op.G;
+  g.cg = 1;
+  g.tma_epi = 1;
+  g.tmem_cols = 32;
+  while (g.tmem_cols < 2 * op.nt) g.tmem_cols *= 2;
+  if (g.nb <= 0) return true;
+  // tile maps over exactly the nb images of this launch: p (written by the
+  // main loop's split warps), x and r (read and written by the epilogue)
+  CUtensorMap mPe{}, mXe{}, mRe{};
+  if (!gram_encode_e(&mPe, g.pnew, op.ny, op.nx, g.nb) || !gram_encode_e(&mXe, cc.x, op.ny, op.nx, g.nb) ||
+      !gram_encode_e(&mRe, cc.r, op.ny, op.nx, g.nb))
+    return false;  // nothing launched
+  const unsigned itiles = (unsigned)((g.nb + kGramRows - 1) / kGramRows);
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3((unsigned)g.nyt * itiles, op.nx);
+  cfg.blockDim = dim3(kGramThreads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = (unsigned)g.nyt;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, mIn, mPold, mPe, mXe, mRe, g, cc) == cudaSuccess;
+}
+
+void launch_colcg_init(const ColCgArgs& cg, int ny, int nx, int nb, cudaStream_t s) {
+  if (nb > 0) k_colcg_init<<<dim3(nx, nb), 64, 0, s>>>(cg, ny, nx);
+}
+void launch_colcg_any_live(const ColCgArgs& cg, int nx, int nb, int* flag, cudaStream_t s) {
+  const int n = nx * nb;
+  cudaMemsetAsync(flag, 0, sizeof(int), s);
+  if (n > 0) k_colcg_any_live<<<(n + 255) / 256, 256, 0, s>>>(cg, n, flag);
+}
+void launch_colcg_report(const ColCgArgs& cg, int nx, int nb, int* iters, double* relres, cudaStream_t s) {
+  if (nb > 0) k_colcg_report<<<nb, 32, 0, s>>>(cg, nx, iters, relres);
 }
 
 void launch_to_cp(const float2* in, float* out, int ny, int nx, int nb, cudaStream_t s) {

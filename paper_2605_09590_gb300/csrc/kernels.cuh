@@ -116,6 +116,22 @@ struct GramArgs {
   int ny, nx, nt, nyt, stages, tmem_cols;
   int tma_epi;              // epilogue moves p and q by tensor copies (nt a multiple of 32)
 };
+
+// State of CG run separately on every readout column (phase-encode Cartesian
+// contexts): one step length and one stopping test per (image, column).
+// Arrays are [B][nx], image-major; the solution x and residual r are the
+// context's column-planar X and R.
+struct ColCgArgs {
+  float* x;                 // [B][nx][2][ny] solution, updated in place
+  float* r;                 // [B][nx][2][ny] residual (holds the right-hand side before init)
+  const double* rr0;        // ||r_j||^2 of the right-hand side
+  double* rr;               // ||r_j||^2 before the next update
+  float* beta;              // step of the next direction update (0 before the first)
+  int* done;                // 1 once the column met the stopping rule or broke down
+  int* iters;               // updates taken by the column
+  int* status;              // [B] 5 when any column of the image broke down
+  double rtol2;             // squared relative residual tolerance
+};
 bool gram_supported(int ny, int nx);
 int gram_tile(int ny);
 size_t gram_bytes(int ny, int nx);  // both G planes, head and remainder
@@ -126,7 +142,34 @@ void launch_gram_build(const float2* smaps, const uint8_t* mask_host, int nc, co
 void launch_gram_scalars(const CgArgs& a, int nb, int it, float* beta, int* done, cudaStream_t s);
 void launch_gram_normal(const GramOp& op, const CUtensorMap& mIn, const CUtensorMap& mPold, GramArgs g,
                         cudaStream_t s);
+// Per-column CG on the tensor-core operator.  Supported when the output-row
+// tile is a multiple of 32 and a column spans at most 4 tiles (one thread-
+// block cluster per column and image tile).
+bool gram_colcg_supported(int ny, int nx);
+// x = 0, rr0 = rr = ||b_j||^2, beta = 0, iters = 0, done where b_j = 0 (or
+// non-finite: breakdown, status 5), for the nb right-hand sides in cg.r
+void launch_colcg_init(const ColCgArgs& cg, int ny, int nx, int nb, cudaStream_t s);
+// one CG update on every column of nb images: p = r + beta p_old (it > 0) or
+// r, q = (A^H A + lam) p on the tensor cores, alpha = rr / p^H q, x += alpha p,
+// r -= alpha q, beta = ||r||^2_new / rr -- all in one launch
+// false (nothing launched) if a tile map cannot be encoded
+bool launch_gram_colcg(const GramOp& op, const CUtensorMap& mIn, const CUtensorMap& mPold, GramArgs g,
+                       const ColCgArgs& cg, cudaStream_t s);
+// *flag (device) = 1 if any column of the nb images is still iterating, else 0
+void launch_colcg_any_live(const ColCgArgs& cg, int nx, int nb, int* flag, cudaStream_t s);
+// per image: the most updates any column took, and ||r|| / ||b|| over the image
+void launch_colcg_report(const ColCgArgs& cg, int nx, int nb, int* iters, double* relres, cudaStream_t s);
 void launch_to_cp(const float2* in, float* out, int ny, int nx, int nb, cudaStream_t s);
+
+// ---- colcg_small.cu: per-column CG with the whole solve on chip (ny <= 96) ----
+bool colcg_small_supported(int ny);
+// G_j of every column, plain layout [nx][ny][ny] complex64 (pbuf: ny double2 of device scratch)
+void launch_colcg_small_build(const float2* smaps, const uint8_t* mask_host, int nc, int ny, int nx, float2* G,
+                              double2* pbuf, cudaStream_t s);
+// every CG update of nb right-hand sides rhs [nb][ny][nx] (natural layout) in
+// one launch; x [nb][ny][nx]; rr0 / rr / iters per (image, column) [nb][nx]
+void launch_colcg_small(const float2* G, const float2* rhs, float2* X, int ny, int nx, int nb, int max_iter,
+                        double rtol2, float lam, double* rr0, double* rr, int* iters, int* status, cudaStream_t s);
 void launch_from_cp(const float* in, float2* out, int ny, int nx, int nb, cudaStream_t s);
 
 // ---- spiral.cu: non-Cartesian (Toeplitz normal operator, KB gridding) ----
