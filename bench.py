@@ -55,6 +55,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="knee320_r2")
+    ap.add_argument("--solver", default="global", choices=["global", "columns"],
+                    help="CG of the primary workload: whole image (default) or per readout column")
+    ap.add_argument("--probes", type=int, default=0, help="probes (and replicas) per step; 0 = the workload's")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-t1pct", action="store_true")
@@ -88,9 +91,12 @@ def maybe_relaunch(args):
         sys.exit(f"bench.py: --gpus {args.gpus} does not match WORLD_SIZE={env}")
 
 
-def workload(name):
+def workload(name, probes=0):
+    import dataclasses
     import synth
     w = synth.WORKLOADS[name]
+    if probes:
+        w = dataclasses.replace(w, probes=probes)
     return w, w.inputs()
 
 
@@ -695,9 +701,31 @@ def timed_steps(step, steps, warmup, torch, dist, world, stream, dev_index, ctxs
     return total_ms, per_step, clk, launches, prof
 
 
-def bench_linear(args, w, inp, pico, torch, dist, world, rank, local, steps, warmup, primary, tune_cache):
+def colcg_roofline(w, K, avg_s, launches):
+    """Roofline of the fused per-column CG update (k_gram_normal with the
+    column-CG epilogue), HBM-bound: per image it reads r and p_old (the
+    contraction operand), writes p, reads and writes x and writes r (6 images
+    of 8 bytes per voxel), plus one pass over S; no separate vector kernel
+    runs.  Against the measured copy bandwidth."""
+    mp = measured_peaks()
+    V = w.ny * w.nx * 8
+    alg = 6 * K * V + w.nc * V
+    achieved = alg / avg_s / 1e9
+    traffic, dig = traffic_of(w, K, ("gram.cu", "tc_util.cuh", "kernels.cuh"))
+    return {"bound": "hbm", "achieved": achieved, "peak": mp["hbm_gbs"], "unit": "GB/s",
+            "frac": achieved / mp["hbm_gbs"], "traffic": traffic,
+            "traffic_over_algorithmic": traffic / alg if traffic else None,
+            "kernel": "k_gram_normal<16,0,1> (tcgen05 kind::tf32 column-CG update: operator, step, x / r update "
+                      "and next beta in one launch, 2-CTA clusters)",
+            "kernel_digest": dig, "avg_launch_ms": avg_s * 1e3, "launches": launches,
+            "algorithmic_bytes_per_launch": alg, "peak_note": "measured copy bandwidth (of measured)"}
+
+
+def bench_linear(args, w, inp, pico, torch, dist, world, rank, local, steps, warmup, primary, tune_cache,
+                 solver="global"):
     """One step = PICO map of K probes + PMR map of K replicas on a linear
-    (CG-SENSE) workload; returns (sub-line, operator)."""
+    (CG-SENSE) workload; returns (sub-line, operator).  solver = "columns"
+    runs CG per readout column (phase-encode Cartesian)."""
     import numpy as np
     K = w.probes
     dev = torch.device("cuda", local)
@@ -705,6 +733,8 @@ def bench_linear(args, w, inp, pico, torch, dist, world, rank, local, steps, war
     op = pico.Operator(inp["smaps"], mask=inp.get("mask"), traj=inp.get("traj"), noise_cov=inp["noise_cov"],
                        lam=w.lam, max_batch=K, power_iters=15, stream=stream.cuda_stream)
     tuning = None if args.no_autotune else op.autotune(cache=tune_cache)
+    if solver != "global":
+        op.set_solver(solver)
     maps = [torch.zeros((w.ny, w.nx), dtype=torch.float64, device=dev) for _ in range(4)]
     s, ss, ps, pss = maps
 
@@ -723,11 +753,17 @@ def bench_linear(args, w, inp, pico, torch, dist, world, rank, local, steps, war
     (norm_ms, norm_n), (upd_ms, _), (pmr_ms, _), (acc_ms, _) = prof
     avg_norm_s = norm_ms / max(norm_n, 1) / 1e3
     gram_on = op.info["normal_op"] == 1 and K >= op.tuning["gram_min_batch"]
-    roof = gram_roofline(w, K, avg_norm_s, norm_n) if gram_on else fft_roofline(w, K, avg_norm_s, norm_n)
+    if solver == "columns" and op.info["normal_op"] == 1:
+        roof = colcg_roofline(w, K, avg_norm_s, norm_n)
+    elif solver == "columns":
+        roof = fft_roofline(w, K, avg_norm_s, norm_n)
+        roof["kernel"] = "k_colcg_small (whole per-column CG solve on chip, one launch per solve)"
+    else:
+        roof = gram_roofline(w, K, avg_norm_s, norm_n) if gram_on else fft_roofline(w, K, avg_norm_s, norm_n)
     nsamp = K * world
     line = {
         "value": value, "unit": UNIT, "steps": steps, "warmup": warmup, "ms_per_step": total_ms / steps,
-        "config": arm_config(w, world), "roofline": roof,
+        "config": dict(arm_config(w, world), cg_solver=solver), "roofline": roof,
         "kernel_ms_in_timed_region": {"normal_op_ms": norm_ms, "cg_vector_ms": upd_ms, "pmr_adjoint_ms": pmr_ms,
                                       "accumulate_ms": acc_ms},
         "gpu_launches": launches,
@@ -771,14 +807,16 @@ def bench_linear(args, w, inp, pico, torch, dist, world, rank, local, steps, war
     return line, op
 
 
-def t1pct_linear(op, w, torch, pico, spiral_subset):
+def t1pct_linear(op, w, torch, pico, spiral_subset, arms=None):
     """Time to a 1 %-NRMSE standard-deviation map.  Cartesian: the ablation's
-    three probe families and PMR against the exact diagonal.  Spiral: PICO and
-    PMR with 30 fixed CG iterations and with the paper's solver rule (at most
-    100 iterations, relative residual 1e-2, Sec. 3.2.2)."""
+    three probe families and PMR against the exact diagonal (arms="pico_pmr":
+    PICO and PMR only).  Spiral: PICO and PMR with 30 fixed CG iterations and
+    with the paper's solver rule (at most 100 iterations, relative residual
+    1e-2, Sec. 3.2.2)."""
     K = w.probes
     if w.kind == "cartesian":
-        t1 = measure_time_to_1pct(op, w, torch, pico, step=10)
+        sel = (("pico", pico.PICO_PROBE_PHASE), ("pmr", None)) if arms == "pico_pmr" else None
+        t1 = measure_time_to_1pct(op, w, torch, pico, step=10, arms=sel)
         names = ("pico", "pmr")
     else:
         arms = (("pico", pico.PICO_PROBE_PHASE), ("pmr", None))
@@ -989,7 +1027,7 @@ def main():
         sys.exit(f"bench.py: rank {rank} needs GPU {local}, {torch.cuda.device_count()} visible")
     # the CPU baseline's process pool is spawned before the first GPU call
     cpu_pool = None
-    w, inp = workload(args.workload)
+    w, inp = workload(args.workload, args.probes)
     if rank == 0 and world == 1 and not args.no_cpu and w.kind == "cartesian":
         cpu_pool = OraclePool(w.name)
     torch.cuda.set_device(local)
@@ -1013,7 +1051,7 @@ def main():
         op = None
     else:
         sub, op = bench_linear(args, w, inp, pico, torch, dist, world, rank, local, args.steps, args.warmup,
-                               True, tune_cache)
+                               True, tune_cache, solver=args.solver)
     line = {"metric": METRIC, "n_gpus": world, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "c64", "data": "synthetic"}
     line.update(sub)
@@ -1022,8 +1060,18 @@ def main():
     if op is not None and rank == 0 and world == 1 and not args.no_t1pct and (
             w.kind == "cartesian" or args.t1pct_spiral):
         line["time_to_1pct"] = t1pct_linear(op, w, torch, pico, spiral_subset=0)
+    colcg_ok = op is not None and w.kind == "cartesian" and args.solver == "global" and (
+        op.info["normal_op"] == 1 or w.ny in (32, 64, 96))
     if op is not None:
         op.close()
+    if colcg_ok and not args.no_extra:
+        # the same step with CG run per readout column (same fixed point, other iterates)
+        col, cop = bench_linear(args, w, inp, pico, torch, dist, world, rank, local, args.steps, args.warmup,
+                                False, tune_cache, solver="columns")
+        if rank == 0 and world == 1 and not args.no_t1pct:
+            col["time_to_1pct"] = t1pct_linear(cop, w, torch, pico, spiral_subset=0, arms="pico_pmr")
+        cop.close()
+        line["column_cg"] = col
 
     if rank == 0 and world == 1 and not args.no_extra and args.workload == "knee320_r2":
         ws, inps = workload("spiral240_r2")

@@ -109,8 +109,9 @@ def test_global_solver_is_restored():
 
 
 def test_column_solver_is_refused_where_unsupported():
-    S = synth.coil_maps(64, 64, 4, 0)
-    op = pico.Operator(S, mask=synth.mask_pe(64, 2, 4), power_iters=0, max_batch=8)   # column-FFT context
+    S = synth.coil_maps(48, 40, 4, 0)
+    # ny = 48: neither a tensor-core context (ny < 128) nor an on-chip size (32, 64, 96)
+    op = pico.Operator(S, mask=synth.mask_pe(48, 2, 4), power_iters=0, max_batch=8)
     with pytest.raises(pico.PicoError) as ei:
         op.set_solver("columns")
     assert ei.value.status == pico.PICO_E_UNSUPPORTED
