@@ -152,6 +152,44 @@ def spiral_matrix(S: np.ndarray, traj: np.ndarray) -> np.ndarray:
     return np.concatenate([E * S[c].reshape(-1)[None, :] for c in range(nc)], axis=0)
 
 
+class ToeplitzNormal:
+    """``A^H A`` of the exact-NUDFT spiral encoding applied through its
+    point-spread function (for full-size images, where the NUDFT itself costs
+    minutes per application).
+
+    ``(E^H E z)[r] = sum_r' h(r - r') z[r']`` with
+    ``h(d) = (1/n^2) sum_m exp(+2 pi i k_m . d / n)`` (the entries of
+    ``E^H E`` written out, as in ``pico.dense_normal``); the lags span
+    ``[-(n-1), n-1]^2``, so the sum is a linear convolution that a circular
+    one on the ``2n x 2n`` grid reproduces exactly (convolution theorem, FFT
+    pair of NumPy).  ``apply`` adds the coil sensitivities and ``lam``.
+    """
+
+    def __init__(self, S: np.ndarray, traj: np.ndarray):
+        self.S = np.asarray(S, dtype=np.complex128)
+        n = self.S.shape[1]
+        self.n = n
+        k = np.asarray(traj, dtype=np.float64)
+        d = np.arange(-(n - 1), n, dtype=np.float64)
+        ex = np.exp(2j * np.pi * np.outer(k[:, 0], d) / n)        # [M][dx]
+        ey = np.exp(2j * np.pi * np.outer(k[:, 1], d) / n)        # [M][dy]
+        h = (ey.T @ ex) / n ** 2                                   # h[dy + n-1, dx + n-1]
+        L = 2 * n
+        C = np.zeros((L, L), dtype=np.complex128)
+        C[np.ix_(np.arange(-(n - 1), n) % L, np.arange(-(n - 1), n) % L)] = h
+        self.T = np.fft.fft2(C)
+
+    def apply(self, x: np.ndarray, lam: float = 0.0) -> np.ndarray:
+        n, L = self.n, 2 * self.n
+        out = lam * np.asarray(x, dtype=np.complex128)
+        for c in range(self.S.shape[0]):
+            z = np.zeros((L, L), dtype=np.complex128)
+            z[:n, :n] = self.S[c] * x
+            w = np.fft.ifft2(self.T * np.fft.fft2(z))[:n, :n]
+            out = out + np.conj(self.S[c]) * w
+        return out
+
+
 class Operator:
     """Whitened encoding operator of one acquisition (Cartesian or spiral)."""
 

@@ -86,6 +86,9 @@ struct pico_ctx {
   float* P2 = nullptr;
   float* g_beta = nullptr;
   int* g_done = nullptr;
+  bool gram_f16 = true;         // FP16 operands when the stage shape allows (PICO_GRAM_TF32=1: TF32)
+  double* g_pn = nullptr;       // [B] FP16 form: bound on each direction's entries
+  float* g_pscale = nullptr;    // [B] and its power-of-two operand scale
   int* g_err = nullptr;
   double2* g_pbuf = nullptr;
   pico::CgArgs cg{};
@@ -94,6 +97,8 @@ struct pico_ctx {
   double *col_rr0 = nullptr, *col_rr = nullptr;
   float* col_beta = nullptr;
   int *col_done = nullptr, *col_iters = nullptr;
+  double* col_pn = nullptr;     // FP16 form: bound on each column direction's entries [B][nx]
+  float* col_pscale = nullptr;
   float2* col_G = nullptr;  // small images: G_j of every column, [nx][ny][ny] (whole solve on chip)
   bool col_small = false;
   std::string host_fail;  // a launch that could not be issued (reported by the entry point)
@@ -262,7 +267,8 @@ bool column_mode(const pico_ctx* c) { return c->solver == PICO_SOLVER_COLUMNS &&
 bool column_small(const pico_ctx* c) { return c->solver == PICO_SOLVER_COLUMNS && c->col_small; }
 pico::ColCgArgs col_args(pico_ctx* c) {
   return pico::ColCgArgs{reinterpret_cast<float*>(c->X), reinterpret_cast<float*>(c->R), c->col_rr0, c->col_rr,
-                         c->col_beta, c->col_done, c->col_iters, c->status, c->cg.rtol2};
+                         c->col_beta, c->col_done, c->col_iters, c->status, c->cg.rtol2, c->col_pn,
+                         c->col_pscale};
 }
 // Gram mode: the direction written by CG iteration `it` (two buffers alternate,
 // because the operator reads the previous direction while writing the new one)
@@ -286,7 +292,9 @@ void op_apply(pico_ctx* c, const float2* x, float2* y, int nb, float lam) {
     g.lam = lam;
     g.itmax = c->itmax;
     g.err = c->g_err;
-    Launch L(c, 0);
+    g.pscale = c->g_pscale;
+    Launch L(c, 0, c->gop.f16 ? 2 : 1);
+    if (c->gop.f16) pico::launch_gram_apply_scale(g.in, c->ny, c->nx, nb, c->g_pscale, c->stream);
     pico::launch_gram_normal(c->gop, m, m, g, c->stream);
     return;
   }
@@ -302,7 +310,11 @@ void op_apply(pico_ctx* c, const float2* x, float2* y, int nb, float lam) {
 // CG iteration `it`, operator half (class 0)
 void op_cg_normal(pico_ctx* c, int nb, int it, float lam) {
   if (c->gram_on) {
-    { Launch L(c, 1); pico::launch_gram_scalars(c->cg, nb, it, c->g_beta, c->g_done, c->stream); }
+    {
+      Launch L(c, 1);
+      pico::launch_gram_scalars(c->cg, nb, it, c->g_beta, c->g_done, c->gop.f16 ? c->g_pn : nullptr, c->g_pscale,
+                                c->stream);
+    }
     pico::GramArgs g{};
     g.in = cpf(c->R);
     g.pold = gram_pbuf(c, it + 1);
@@ -310,6 +322,7 @@ void op_cg_normal(pico_ctx* c, int nb, int it, float lam) {
     g.q = cpf(c->Q);
     g.beta = c->g_beta;
     g.done = c->g_done;
+    g.pscale = c->g_pscale;
     g.pq = c->cg.pq_part;
     g.itmax = c->itmax;
     g.PA = c->cg.PA;
@@ -775,12 +788,16 @@ bool want_gram(const pico_operator_desc* d) {
 
 // G planes, second direction buffer and per-image scalars of the Gram mode
 size_t gram_extra_bytes(const pico_operator_desc* d, int64_t B) {
-  return pico::gram_bytes(d->ny, d->nx) + (size_t)B * d->ny * d->nx * 8 + (size_t)B * 8 + (size_t)d->ny * 16 + 16;
+  return pico::gram_bytes(d->ny, d->nx) + (size_t)B * d->ny * d->nx * 8 + (size_t)B * 8 + (size_t)d->ny * 16 + 16 +
+         (size_t)B * 12 + (size_t)d->nx * 4;
 }
 
 // (re)build the stage-tiled G_j for gop.kc and the tensor maps of the CG vectors
 pico_status gram_configure(pico_ctx* c) {
   const int kc = c->gop.kc;
+  // the format G is built in follows the stage shape: FP16 operands need 16-value
+  // stages staged in shared memory
+  c->gop.f16 = c->gram_f16 && kc == 16 && !c->gop.a_tmem;
   pico::launch_gram_build(c->smaps, c->gmask.data(), c->nc, c->gop, c->g_pbuf, c->stream);
   const int B = c->max_batch;
   const bool ok = pico::gram_encode_x(&c->mR, cpf(c->R), c->ny, c->nx, B, kc) &&
@@ -794,10 +811,16 @@ pico_status gram_configure(pico_ctx* c) {
 
 pico_status gram_setup(pico_ctx* c, const pico_operator_desc* d) {
   pico_status st = PICO_OK;
-  if ((st = dalloc(c, &c->gop.G, pico::gram_bytes(c->ny, c->nx) / sizeof(float))) != PICO_OK) return st;
+  float* gbuf = nullptr;  // room for the TF32 form (the FP16 form takes half)
+  if ((st = dalloc(c, &gbuf, pico::gram_bytes(c->ny, c->nx) / sizeof(float))) != PICO_OK) return st;
+  c->gop.G = gbuf;
   if ((st = dalloc(c, &c->P2, (size_t)2 * c->max_batch * c->n)) != PICO_OK) return st;
   if ((st = dalloc(c, &c->g_beta, (size_t)c->max_batch)) != PICO_OK) return st;
   if ((st = dalloc(c, &c->g_done, (size_t)c->max_batch)) != PICO_OK) return st;
+  if ((st = dalloc(c, &c->g_pn, (size_t)c->max_batch)) != PICO_OK) return st;
+  if ((st = dalloc(c, &c->g_pscale, (size_t)c->max_batch)) != PICO_OK) return st;
+  if ((st = dalloc(c, &c->gop.gscale, (size_t)c->nx)) != PICO_OK) return st;
+  if (const char* e = std::getenv("PICO_GRAM_TF32")) c->gram_f16 = std::atoi(e) == 0;
   if (!c->g_err && (st = dalloc(c, &c->g_err, (size_t)4)) != PICO_OK) return st;
   if ((st = dalloc(c, &c->g_pbuf, (size_t)c->ny)) != PICO_OK) return st;
   cudaMemsetAsync(c->g_err, 0, 4 * sizeof(int), c->stream);
@@ -1529,7 +1552,9 @@ pico_status pico_set_solver(pico_ctx* c, int32_t solver) {
         (!c->col_rr && (st = dalloc(c, &c->col_rr, n)) != PICO_OK) ||
         (!c->col_beta && (st = dalloc(c, &c->col_beta, n)) != PICO_OK) ||
         (!c->col_done && (st = dalloc(c, &c->col_done, n)) != PICO_OK) ||
-        (!c->col_iters && (st = dalloc(c, &c->col_iters, n)) != PICO_OK))
+        (!c->col_iters && (st = dalloc(c, &c->col_iters, n)) != PICO_OK) ||
+        (!c->col_pn && (st = dalloc(c, &c->col_pn, n)) != PICO_OK) ||
+        (!c->col_pscale && (st = dalloc(c, &c->col_pscale, n)) != PICO_OK))
       return st;
   }
   clear_graphs(c);
@@ -1605,12 +1630,11 @@ pico_status pico_set_tuning(pico_ctx* c, const pico_tuning* t) {
     return fail(c, PICO_E_INVALID, "tuning out of range (gram_kc 8/16, gram_a_tmem 0/1, probe_batch <= max_batch)");
   clear_graphs(c);
   if (t->gram_min_batch > 0) c->gram_min_batch = t->gram_min_batch;
+  const bool rebuild = (t->gram_kc != 0 && t->gram_kc != c->gop.kc) || t->gram_a_tmem != c->gop.a_tmem;
   c->gop.a_tmem = t->gram_a_tmem;
   c->probe_batch = t->probe_batch;
-  if (t->gram_kc != 0 && t->gram_kc != c->gop.kc) {
-    c->gop.kc = t->gram_kc;
-    if (c->gram) return gram_configure(c);
-  }
+  if (t->gram_kc != 0) c->gop.kc = t->gram_kc;
+  if (rebuild && c->gram) return gram_configure(c);  // G's operand format follows (kc, a_tmem)
   return cuda_check(c, "pico_set_tuning");
 }
 
@@ -1666,8 +1690,8 @@ pico_status pico_autotune(pico_ctx* c, int32_t iters, pico_tuning* out, double* 
     if (k > 0) {
       if (!c->gram) break;
       clear_graphs(c);
-      c->gop.a_tmem = cand_at[k];
-      if (c->gop.kc != cand_kc[k]) {
+      if (c->gop.kc != cand_kc[k] || c->gop.a_tmem != cand_at[k]) {
+        c->gop.a_tmem = cand_at[k];
         c->gop.kc = cand_kc[k];
         if ((st = gram_configure(c)) != PICO_OK) break;
       }

@@ -16,6 +16,8 @@
 // CG vectors of a Gram-mode context live in a column-planar layout
 // [image][x][re|im][y] (so that the contraction index y is contiguous); the
 // kernels here convert to and from the natural [image][y][x] complex layout.
+#include <cuda_fp16.h>
+
 #include <vector>
 
 #include "common.cuh"
@@ -54,6 +56,21 @@ struct GramTile {
   }
 };
 
+// four FP32 values -> FP16 heads (rounded to nearest) and FP16 remainders,
+// each packed as four halves in a uint2 (element 0 in the low half)
+__device__ __forceinline__ uint32_t h2_bits(__half2 h) {
+  uint32_t u;
+  memcpy(&u, &h, sizeof(u));
+  return u;
+}
+__device__ __forceinline__ void split_f16x4(float a0, float a1, float a2, float a3, uint2& hi, uint2& lo) {
+  const __half2 h01 = __floats2half2_rn(a0, a1), h23 = __floats2half2_rn(a2, a3);
+  const float2 f01 = __half22float2(h01), f23 = __half22float2(h23);
+  hi = make_uint2(h2_bits(h01), h2_bits(h23));
+  lo = make_uint2(h2_bits(__floats2half2_rn(a0 - f01.x, a1 - f01.y)),
+                  h2_bits(__floats2half2_rn(a2 - f23.x, a3 - f23.y)));
+}
+
 __device__ __forceinline__ void set_err(int* err, int code) {
   if (err) atomicCAS(err, 0, code);
 }
@@ -72,6 +89,28 @@ __device__ __forceinline__ size_t gt_offset(int j, int y, int yp, int q, int ny,
   const int grp = e >> 2, phys = kc == 16 ? (grp ^ ((r >> 1) & 3)) : (grp ^ ((r >> 2) & 1));
   return ((((size_t)j * (ny / nt) + t) * (ny / kc) + c) * 4 + q) * (size_t)nt * kc + (size_t)r * kc + 4 * phys +
          (e & 3);
+}
+
+// The FP16 form of the same tiling: stages of 16 values of y' (32-byte rows,
+// 32-byte swizzle: the two 16-byte groups of a row swap on rows 4..7 of every
+// 8-row atom), halves instead of floats.
+__device__ __forceinline__ size_t gt_offset_h(int j, int y, int yp, int q, int ny, int nt) {
+  const int t = y / nt, r = y - t * nt, c = yp >> 4, e = yp & 15;
+  const int phys = (e >> 3) ^ ((r >> 2) & 1);
+  return ((((size_t)j * (ny / nt) + t) * (ny / 16) + c) * 4 + q) * (size_t)nt * 16 + (size_t)r * 16 + 8 * phys +
+         (e & 7);
+}
+
+// Power-of-two scale 2^(13 - floor(log2 bound)): a value of magnitude at most
+// `bound` times the scale stays below 2^14 (FP16 holds up to 65504), and the
+// scale itself is exact in FP32.  A zero or non-finite bound gives 1.
+__host__ __device__ __forceinline__ float pow2_scale(double bound) {
+  if (!(bound > 0.0) || !(bound < 1e300)) return 1.f;
+  int e = 0;
+  (void)frexp(bound, &e);            // bound = m 2^e, m in [0.5, 1)
+  int k = 14 - e;                    // bound * 2^k < 2^14
+  k = k > 100 ? 100 : (k < -100 ? -100 : k);
+  return ldexpf(1.f, k);
 }
 
 __global__ void k_gram_build(const float2* __restrict__ S, const double2* __restrict__ P, int nc, int ny, int nx,
@@ -103,10 +142,15 @@ __global__ void k_gram_build(const float2* __restrict__ S, const double2* __rest
 
 // The same G_j with the sensitivities of column j staged in shared memory
 // (block = column j x 32 output rows; all y' per block).
+// F16: G_j scaled by the power of two gscale[j] (pow2_scale of the bound
+// |G_j[y, y']| <= P[0] max_y sum_c |S_c[y, j]|^2, Cauchy-Schwarz with
+// |P[d]| <= P[0]) and split into an FP16 head and FP16 remainder.
+template <bool F16>
 __global__ void __launch_bounds__(256) k_gram_build_smem(const float2* __restrict__ S, const double2* __restrict__ P,
                                                          int nc, int ny, int nx, int nt, int kc,
-                                                         float* __restrict__ G) {
+                                                         void* __restrict__ Gv, float* __restrict__ gscale) {
   extern __shared__ float2 sc[];  // [nc][ny] sensitivities of column j
+  __shared__ float red[8];
   const int j = blockIdx.x, y_lo = blockIdx.y * 32;
   const int64_t n = (int64_t)ny * nx;
   for (int i = threadIdx.x; i < nc * ny; i += blockDim.x) {
@@ -114,6 +158,25 @@ __global__ void __launch_bounds__(256) k_gram_build_smem(const float2* __restric
     sc[i] = S[c * n + (int64_t)y * nx + j];
   }
   __syncthreads();
+  float gs = 1.f;
+  if (F16) {
+    float m = 0.f;
+    for (int y = threadIdx.x; y < ny; y += blockDim.x) {
+      float e = 0.f;
+      for (int c = 0; c < nc; ++c) e = fmaf(sc[c * ny + y].x, sc[c * ny + y].x, fmaf(sc[c * ny + y].y, sc[c * ny + y].y, e));
+      m = fmaxf(m, e);
+    }
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+    __syncthreads();
+    m = 0.f;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = fmaxf(m, red[w]);
+    // 1.01: room for the FP32 rounding of the sums below
+    gs = pow2_scale(1.01 * (double)m * fabs(P[0].x));
+    if (blockIdx.y == 0 && threadIdx.x == 0) gscale[j] = gs;
+  }
+  float* G = static_cast<float*>(Gv);
+  __half* Gh = static_cast<__half*>(Gv);
   for (int t = threadIdx.x; t < 32 * ny; t += blockDim.x) {
     const int y = y_lo + t / ny, yp = t % ny;
     if (y >= ny) break;
@@ -136,18 +199,29 @@ __global__ void __launch_bounds__(256) k_gram_build_smem(const float2* __restric
     const double2 p = P[d];
     const float px = (float)p.x, py = (float)p.y;
     const float gr = fmaf(px, re, -py * im), gi = fmaf(px, im, py * re);
-    float hr, lr, hi_, li;
-    split_tf32(gr, hr, lr);
-    split_tf32(gi, hi_, li);
-    G[gt_offset(j, y, yp, 0, ny, nt, kc)] = hr;
-    G[gt_offset(j, y, yp, 1, ny, nt, kc)] = hi_;
-    G[gt_offset(j, y, yp, 2, ny, nt, kc)] = lr;
-    G[gt_offset(j, y, yp, 3, ny, nt, kc)] = li;
+    if (F16) {
+      const float sr = gr * gs, si = gi * gs;
+      const __half hr = __float2half_rn(sr), hi_ = __float2half_rn(si);
+      Gh[gt_offset_h(j, y, yp, 0, ny, nt)] = hr;
+      Gh[gt_offset_h(j, y, yp, 1, ny, nt)] = hi_;
+      Gh[gt_offset_h(j, y, yp, 2, ny, nt)] = __float2half_rn(sr - __half2float(hr));
+      Gh[gt_offset_h(j, y, yp, 3, ny, nt)] = __float2half_rn(si - __half2float(hi_));
+    } else {
+      float hr, lr, hi_, li;
+      split_tf32(gr, hr, lr);
+      split_tf32(gi, hi_, li);
+      G[gt_offset(j, y, yp, 0, ny, nt, kc)] = hr;
+      G[gt_offset(j, y, yp, 1, ny, nt, kc)] = hi_;
+      G[gt_offset(j, y, yp, 2, ny, nt, kc)] = lr;
+      G[gt_offset(j, y, yp, 3, ny, nt, kc)] = li;
+    }
   }
 }
 
-// per-image CG scalars of iteration it: beta = rr(it) / rr(it-1) (0 at it = 0), done flag
-__global__ void k_gram_scalars(CgArgs a, int it, float* beta, int* done) {
+// per-image CG scalars of iteration it: beta = rr(it) / rr(it-1) (0 at it = 0),
+// done flag, and the bound pn on the new direction's entries (|p| <= ||p|| <=
+// ||r|| + beta ||p_prev||) with its power-of-two FP16 scale
+__global__ void k_gram_scalars(CgArgs a, int it, float* beta, int* done, double* pn, float* pscale) {
   const int b = blockIdx.x;
   const double* base = a.rr_part + (size_t)b * (a.itmax + 1) * a.PB;
   const double rr = warp_sum_parts(base + (size_t)it * a.PB, a.PB);
@@ -155,7 +229,29 @@ __global__ void k_gram_scalars(CgArgs a, int it, float* beta, int* done) {
   const double rrp = it > 0 ? warp_sum_parts(base + (size_t)(it - 1) * a.PB, a.PB) : 1.0;
   if (threadIdx.x == 0) {
     done[b] = !(rr > a.rtol2 * rr0);
-    beta[b] = it > 0 ? (float)(rr / rrp) : 0.f;
+    const float bt = it > 0 ? (float)(rr / rrp) : 0.f;
+    beta[b] = bt;
+    if (pn) {
+      const double p = sqrt(fmax(rr, 0.0)) + (it > 0 ? (double)bt * pn[b] : 0.0);
+      pn[b] = p;
+      pscale[b] = pow2_scale(p);
+    }
+  }
+}
+
+// FP16 operand scale of an operator application: from max |x| over the image
+__global__ void __launch_bounds__(256) k_gram_apply_scale(const float* __restrict__ x, int64_t n2, float* pscale) {
+  __shared__ float red[8];
+  const float* xb = x + (size_t)blockIdx.x * n2;
+  float m = 0.f;
+  for (int64_t i = threadIdx.x; i < n2; i += 256) m = fmaxf(m, fabsf(xb[i]));
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float t = red[0];
+    for (int w = 1; w < 8; ++w) t = fmaxf(t, red[w]);
+    pscale[blockIdx.x] = pow2_scale((double)t);
   }
 }
 
@@ -222,12 +318,14 @@ __global__ void k_from_cp(const float* __restrict__ in, float2* __restrict__ out
 // Tiles are 128 images x 32 rows of one plane (128-byte swizzle), two planes
 // (re, im) per vector; phase B keeps up to two (p, x, r) groups in flight in
 // the idle pipeline buffers, phase A up to two p tiles after the first group.
-__device__ __forceinline__ double* xch_of(float* beta_s) { return reinterpret_cast<double*>(beta_s + kGramRows); }
+__device__ __forceinline__ double* xch_of(float* beta_s) {
+  return reinterpret_cast<double*>(beta_s + 2 * kGramRows);  // after beta and the FP16 row scales
+}
 
 template <int KC>
 __device__ __forceinline__ void colcg_epilogue(uint8_t* sm, int S, uint32_t stage_bytes, uint64_t* pbar, double* xch,
                                                uint32_t tbase, int NT, int quarter, int row, int k, int j,
-                                               int ytile, int n0, int m0, bool accok, const GramArgs& g,
+                                               int ytile, int n0, int m0, bool accok, float fsc, const GramArgs& g,
                                                const ColCgArgs& cc, const CUtensorMap& mPe, const CUtensorMap& mXe,
                                                const CUtensorMap& mRe) {
   constexpr uint32_t kPlane = kGramRows * 128;   // one plane of a 32-row tile: 16 KB
@@ -280,6 +378,11 @@ __device__ __forceinline__ void colcg_epilogue(uint8_t* sm, int S, uint32_t stag
     for (int h = 0; h < 2; ++h) {
       float dr[16], di[16];
       tmem_ld16x2(ta + 16 * h, ta + (uint32_t)NT + 16 * h, dr, di);
+#pragma unroll
+      for (int u = 0; u < 16; ++u) {
+        dr[u] *= fsc;
+        di[u] *= fsc;
+      }
       if (live && pok) {
         float acc = 0.f;
 #pragma unroll
@@ -338,6 +441,11 @@ __device__ __forceinline__ void colcg_epilogue(uint8_t* sm, int S, uint32_t stag
     for (int h = 0; h < 2; ++h) {
       float dr[16], di[16];
       tmem_ld16x2(ta + 16 * h, ta + (uint32_t)NT + 16 * h, dr, di);
+#pragma unroll
+      for (int u = 0; u < 16; ++u) {
+        dr[u] *= fsc;
+        di[u] *= fsc;
+      }
       if (upd && bok) {
         float acc = 0.f;
 #pragma unroll
@@ -395,8 +503,14 @@ __device__ __forceinline__ void colcg_epilogue(uint8_t* sm, int S, uint32_t stag
       cc.rr[cidx] = rr_tot;
       cc.iters[cidx] += 1;
       const bool stop = !(rr_tot > cc.rtol2 * cc.rr0[cidx]);
-      cc.beta[cidx] = stop ? 0.f : (float)(rr_tot / rr);
+      const float bt = stop ? 0.f : (float)(rr_tot / rr);
+      cc.beta[cidx] = bt;
       if (stop) cc.done[cidx] = 1;
+      if (cc.pn) {  // bound on the next direction r + beta p: sqrt(rr_new) + beta pn
+        const double p = sqrt(rr_tot) + (double)bt * cc.pn[cidx];
+        cc.pn[cidx] = p;
+        cc.pscale[cidx] = pow2_scale(p);
+      }
     } else {
       broke = true;
     }
@@ -429,18 +543,21 @@ __device__ __forceinline__ void colcg_epilogue(uint8_t* sm, int S, uint32_t stag
 // and the MMAs read A from there: shared memory then carries only the TMA
 // tiles and the B operand reads, which keeps the tensor pipe, not the
 // shared-memory bandwidth, the limit of the main loop.
-template <int KC, bool AT, bool COL>
+template <int KC, bool AT, bool COL, bool F16>
 __global__ void __launch_bounds__(kGramThreads, 1)
     k_gram_normal(const __grid_constant__ CUtensorMap mIn, const __grid_constant__ CUtensorMap mPold,
                   const __grid_constant__ CUtensorMap mPe, const __grid_constant__ CUtensorMap mQe,
                   const __grid_constant__ CUtensorMap mRe, GramArgs g, ColCgArgs cc) {
+  static_assert(!F16 || (KC == 16 && !AT), "the FP16 split runs with 16-value stages in shared memory");
   extern __shared__ uint8_t smraw[];
   uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smraw) + 1023) & ~(uintptr_t)1023);
   const int NT = g.nt, S = g.stages;
   using T = GramTile<KC>;
+  using H = GramTile<8>;  // FP16 operands: 32-byte rows, 32-byte swizzle (byte-identical to 8 FP32 values)
   constexpr uint32_t kATile = T::kATile;
-  const uint32_t btile = (uint32_t)NT * KC * 4;
-  const uint32_t stage_bytes = 4 * kATile + 4 * btile;
+  constexpr uint32_t kASplit = F16 ? kGramRows * 32 : 0;  // one FP16 plane of the split direction
+  const uint32_t btile = F16 ? (uint32_t)NT * 32 : (uint32_t)NT * KC * 4;
+  const uint32_t stage_bytes = 4 * kATile + 4 * kASplit + 4 * btile;
   uint64_t* bars = reinterpret_cast<uint64_t*>(sm + (size_t)S * stage_bytes);
   uint64_t* full = bars;
   uint64_t* conv = bars + S;
@@ -449,6 +566,7 @@ __global__ void __launch_bounds__(kGramThreads, 1)
   uint64_t* pbar = bars + 3 * S + 1;   // epilogue staging of p: up to 8 buffers, one phase per use
   uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + 3 * S + 9);
   float* beta_s = reinterpret_cast<float*>(tslot + 4);
+  float* ps_s = beta_s + kGramRows;  // FP16: power-of-two scale of each image's direction
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int ytile = blockIdx.x % g.nyt, itile = blockIdx.x / g.nyt, j = blockIdx.y;
@@ -457,11 +575,14 @@ __global__ void __launch_bounds__(kGramThreads, 1)
   const bool use_pold = g.cg && g.it > 0;
 
   auto slotA = [&](int s, int q) { return sm + (size_t)s * stage_bytes + (size_t)q * kATile; };
-  auto slotB = [&](int s, int q) { return sm + (size_t)s * stage_bytes + 4 * kATile + (size_t)q * btile; };
+  auto slotAS = [&](int s, int q) { return sm + (size_t)s * stage_bytes + 4 * kATile + (size_t)q * kASplit; };
+  auto slotB = [&](int s, int q) {
+    return sm + (size_t)s * stage_bytes + 4 * kATile + 4 * kASplit + (size_t)q * btile;
+  };
   // one stage: the A inputs by TMA (r, and p_old after the first iteration),
   // the stage-tiled B block of G_j by one bulk copy
   const uint32_t stage_tx = (use_pold ? 4u : 2u) * kATile + 4u * btile;
-  const float* gsrc = g.G + ((size_t)j * g.nyt + ytile) * nkc * 4 * NT * KC;
+  const uint8_t* gsrc = static_cast<const uint8_t*>(g.G) + ((size_t)j * g.nyt + ytile) * nkc * 4 * btile;
   auto issue = [&](int kc) {
     const int s = kc % S, y0 = kc * KC;
     mbar_expect_tx(&full[s], stage_tx);
@@ -471,7 +592,7 @@ __global__ void __launch_bounds__(kGramThreads, 1)
       tma_load_4d(slotA(s, 2), &mPold, &full[s], y0, 0, j, m0);
       tma_load_4d(slotA(s, 3), &mPold, &full[s], y0, 1, j, m0);
     }
-    bulk_load(slotB(s, 0), gsrc + (size_t)kc * 4 * NT * KC, 4u * btile, &full[s]);
+    bulk_load(slotB(s, 0), gsrc + (size_t)kc * 4 * btile, 4u * btile, &full[s]);
   };
 
   if (threadIdx.x == 0) {
@@ -501,6 +622,12 @@ __global__ void __launch_bounds__(kGramThreads, 1)
       beta_s[r] = (use_pold && k < g.nb) ? cc.beta[(size_t)k * g.nx + j] : 0.f;
     else
       beta_s[r] = (use_pold && k < g.nb) ? g.beta[k] : 0.f;
+    if constexpr (F16) {
+      if constexpr (COL)
+        ps_s[r] = k < g.nb ? cc.pscale[(size_t)k * g.nx + j] : 1.f;
+      else
+        ps_s[r] = k < g.nb ? g.pscale[k] : 1.f;
+    }
   }
   if (warp == 1) tmem_alloc(tslot, g.tmem_cols);
   tc_fence_before();
@@ -553,6 +680,29 @@ __global__ void __launch_bounds__(kGramThreads, 1)
             mma_tf32_ts(dim, Ahi, Blr, id, 1);
             mma_tf32_ts(dim, Ali, Bhr, id, 1);
           }
+          mma_commit(&empty[s]);
+          continue;
+        }
+        if constexpr (F16) {
+          // one K = 16 step per stage: 3 split products x 4 real products
+          const uint32_t hd = idesc_f16(kGramRows, NT, false), hdn = idesc_f16(kGramRows, NT, true);
+          const uint32_t acc0 = kc == 0 ? 0u : 1u;
+          const uint64_t Ahr = H::desc(smem_u32(slotAS(s, 0))), Ahi = H::desc(smem_u32(slotAS(s, 1)));
+          const uint64_t Alr = H::desc(smem_u32(slotAS(s, 2))), Ali = H::desc(smem_u32(slotAS(s, 3)));
+          const uint64_t Bhr = H::desc(smem_u32(slotB(s, 0))), Bhi = H::desc(smem_u32(slotB(s, 1)));
+          const uint64_t Blr = H::desc(smem_u32(slotB(s, 2))), Bli = H::desc(smem_u32(slotB(s, 3)));
+          mma_f16(dre, Ahr, Bhr, hd, acc0);
+          mma_f16(dre, Ahr, Blr, hd, 1);
+          mma_f16(dre, Alr, Bhr, hd, 1);
+          mma_f16(dre, Ahi, Bhi, hdn, 1);
+          mma_f16(dre, Ahi, Bli, hdn, 1);
+          mma_f16(dre, Ali, Bhi, hdn, 1);
+          mma_f16(dim, Ahr, Bhi, hd, acc0);
+          mma_f16(dim, Ahr, Bli, hd, 1);
+          mma_f16(dim, Alr, Bhi, hd, 1);
+          mma_f16(dim, Ahi, Bhr, hd, 1);
+          mma_f16(dim, Ahi, Blr, hd, 1);
+          mma_f16(dim, Ali, Bhr, hd, 1);
           mma_commit(&empty[s]);
           continue;
         }
@@ -693,15 +843,30 @@ __global__ void __launch_bounds__(kGramThreads, 1)
               *reinterpret_cast<float4*>(g.pnew + o + g.ny) = vi;
             }
           }
-          float4 hr, lr, hi4, li;
-          split_tf32(vr.x, hr.x, lr.x); split_tf32(vr.y, hr.y, lr.y);
-          split_tf32(vr.z, hr.z, lr.z); split_tf32(vr.w, hr.w, lr.w);
-          split_tf32(vi.x, hi4.x, li.x); split_tf32(vi.y, hi4.y, li.y);
-          split_tf32(vi.z, hi4.z, li.z); split_tf32(vi.w, hi4.w, li.w);
-          r_re[q] = hr;
-          r_im[q] = hi4;
-          p_re[q] = lr;
-          p_im[q] = li;
+          if constexpr (F16) {
+            // scaled by the image's power of two, split into FP16 head and remainder,
+            // written to the stage's split planes (32-byte rows, 32-byte swizzle)
+            const int rowi = q / (KC / 4), lc = T::chunk(q % (KC / 4), rowi);
+            const float sc = ps_s[rowi];
+            uint2 hre, him, lre, lim;
+            split_f16x4(vr.x * sc, vr.y * sc, vr.z * sc, vr.w * sc, hre, lre);
+            split_f16x4(vi.x * sc, vi.y * sc, vi.z * sc, vi.w * sc, him, lim);
+            const size_t off = (size_t)rowi * 32 + (size_t)(((lc >> 1) ^ ((rowi >> 2) & 1)) * 16) + (lc & 1) * 8;
+            *reinterpret_cast<uint2*>(slotAS(s, 0) + off) = hre;
+            *reinterpret_cast<uint2*>(slotAS(s, 1) + off) = him;
+            *reinterpret_cast<uint2*>(slotAS(s, 2) + off) = lre;
+            *reinterpret_cast<uint2*>(slotAS(s, 3) + off) = lim;
+          } else {
+            float4 hr, lr, hi4, li;
+            split_tf32(vr.x, hr.x, lr.x); split_tf32(vr.y, hr.y, lr.y);
+            split_tf32(vr.z, hr.z, lr.z); split_tf32(vr.w, hr.w, lr.w);
+            split_tf32(vi.x, hi4.x, li.x); split_tf32(vi.y, hi4.y, li.y);
+            split_tf32(vi.z, hi4.z, li.z); split_tf32(vi.w, hi4.w, li.w);
+            r_re[q] = hr;
+            r_im[q] = hi4;
+            p_re[q] = lr;
+            p_im[q] = li;
+          }
         }
       }
       fence_proxy_async_smem();
@@ -727,9 +892,12 @@ __global__ void __launch_bounds__(kGramThreads, 1)
     const bool accok = mbar_wait(accf, 0);
     if (!accok) set_err(g.err, 4);
     tc_fence_after();
+    // FP16 operands were scaled by powers of two (G_j by gscale[j], the image's
+    // direction by ps_s[row]): undo both on the accumulator
+    const float fsc = F16 ? 1.f / (g.gscale[j] * ps_s[row]) : 1.f;
     if constexpr (COL) {
       colcg_epilogue<KC>(sm, S, stage_bytes, pbar, xch_of(beta_s), tbase, NT, quarter, row, k, j, ytile, n0, m0,
-                         accok, g, cc, mPe, mQe, mRe);
+                         accok, fsc, g, cc, mPe, mQe, mRe);
     } else {
     const bool inb = k < g.nb;
     const bool valid = accok && inb && !(g.cg && g.done[k]);
@@ -766,6 +934,13 @@ __global__ void __launch_bounds__(kGramThreads, 1)
         for (int h = 0; h < 2; ++h) {
           float dr[16], di[16];
           tmem_ld16x2(ta + 16 * h, ta + (uint32_t)NT + 16 * h, dr, di);
+          if (F16) {
+#pragma unroll
+            for (int u = 0; u < 16; ++u) {
+              dr[u] *= fsc;
+              di[u] *= fsc;
+            }
+          }
           if (valid && pok) {
             float acc = 0.f;  // p^H q over these 16 rows in FP32, then summed in FP64
 #pragma unroll
@@ -835,6 +1010,13 @@ __global__ void __launch_bounds__(kGramThreads, 1)
         float dr[16], di[16];
         const uint32_t ta = tbase + ((uint32_t)(32 * quarter) << 16) + (uint32_t)(w0 + 16 * c);
         tmem_ld16x2(ta, ta + (uint32_t)NT, dr, di);
+        if (F16) {
+#pragma unroll
+          for (int u = 0; u < 16; ++u) {
+            dr[u] *= fsc;
+            di[u] *= fsc;
+          }
+        }
         if (valid && pok) {
           float4* pr4 = reinterpret_cast<float4*>(prow + 16 * c);
           float4* pi4 = reinterpret_cast<float4*>(prow + W + 16 * c);
@@ -908,6 +1090,10 @@ __global__ void __launch_bounds__(64) k_colcg_init(ColCgArgs cc, int ny, int nx)
     cc.rr[cidx] = rr;
     cc.beta[cidx] = 0.f;
     cc.iters[cidx] = 0;
+    if (cc.pn) {
+      cc.pn[cidx] = sqrt(rr);  // p_0 = r_0
+      cc.pscale[cidx] = pow2_scale(sqrt(rr));
+    }
     const bool bad = !isfinite(rr);
     cc.done[cidx] = bad || !(rr > 0.0);
     if (bad) cc.status[b] = 5;  // a non-finite right-hand side: breakdown, x stays 0
@@ -1031,49 +1217,62 @@ void launch_gram_build(const float2* smaps, const uint8_t* mask_host, int nc, co
   }
   cudaMemcpyAsync(pbuf, P.data(), ny * sizeof(double2), cudaMemcpyHostToDevice, s);
   const size_t sbytes = (size_t)nc * ny * sizeof(float2);
-  if (sbytes <= 200 * 1024) {
-    cudaFuncSetAttribute(k_gram_build_smem, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sbytes);
-    k_gram_build_smem<<<dim3(nx, (ny + 31) / 32), 256, sbytes, s>>>(smaps, pbuf, nc, ny, nx, op.nt, op.kc,
-                                                                     op.G);
+  if (op.f16) {
+    // the FP16 form needs the column's sensitivities in shared memory (its scale bound)
+    cudaFuncSetAttribute(k_gram_build_smem<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sbytes);
+    k_gram_build_smem<true><<<dim3(nx, (ny + 31) / 32), 256, sbytes, s>>>(smaps, pbuf, nc, ny, nx, op.nt, 16,
+                                                                           op.G, op.gscale);
+  } else if (sbytes <= 200 * 1024) {
+    cudaFuncSetAttribute(k_gram_build_smem<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sbytes);
+    k_gram_build_smem<false><<<dim3(nx, (ny + 31) / 32), 256, sbytes, s>>>(smaps, pbuf, nc, ny, nx, op.nt,
+                                                                            op.kc, op.G, op.gscale);
   } else {
     const int64_t tot = (int64_t)ny * ny;
     k_gram_build<<<dim3((unsigned)((tot + 255) / 256), nx), 256, 0, s>>>(smaps, pbuf, nc, ny, nx, op.nt, op.kc,
-                                                                          op.G);
+                                                                          static_cast<float*>(op.G));
   }
   cudaStreamSynchronize(s);  // P lives on the host stack until the copy has run
 }
 
-void launch_gram_scalars(const CgArgs& a, int nb, int it, float* beta, int* done, cudaStream_t s) {
-  k_gram_scalars<<<nb, 32, 0, s>>>(a, it, beta, done);
+void launch_gram_scalars(const CgArgs& a, int nb, int it, float* beta, int* done, double* pn, float* pscale,
+                         cudaStream_t s) {
+  k_gram_scalars<<<nb, 32, 0, s>>>(a, it, beta, done, pn, pscale);
 }
 
-size_t gram_smem(int ny, int kc, int* stages) {
+void launch_gram_apply_scale(const float* x, int ny, int nx, int nb, float* pscale, cudaStream_t s) {
+  if (nb > 0) k_gram_apply_scale<<<nb, 256, 0, s>>>(x, (int64_t)2 * ny * nx, pscale);
+}
+
+size_t gram_smem(int ny, int kc, bool f16, int* stages) {
   const int nt = gram_tile(ny);
-  const size_t stage = 4 * (size_t)kGramRows * kc * 4 + 4 * (size_t)nt * kc * 4;
-  int S = (int)((220 * 1024 - 2048) / stage);
+  const size_t stage = f16 ? 4 * (size_t)kGramRows * 16 * 4 + 4 * (size_t)kGramRows * 32 + 4 * (size_t)nt * 32
+                           : 4 * (size_t)kGramRows * kc * 4 + 4 * (size_t)nt * kc * 4;
+  int S = (int)((220 * 1024 - 2560) / stage);
   if (S > 8) S = 8;
   if (S < 2) S = 2;
   *stages = S;
-  // + per-column CG exchange slots (two FP64 sums per image row)
-  return 1024 + (size_t)S * stage + (3 * (size_t)S + 9) * 8 + 16 + kGramRows * 4 + 2 * kGramRows * 8 + 64;
+  // barriers, TMEM slot, per-row beta and FP16 scale, per-column CG exchange slots (two FP64 sums per row)
+  return 1024 + (size_t)S * stage + (3 * (size_t)S + 9) * 8 + 16 + 2 * kGramRows * 4 + 2 * kGramRows * 8 + 64;
 }
 
 void launch_gram_normal(const GramOp& op, const CUtensorMap& mIn, const CUtensorMap& mPold, GramArgs g,
                         cudaStream_t s) {
+  const bool f16 = op.f16 && op.kc == 16 && !op.a_tmem;
   int S = 0;
-  const size_t smem = gram_smem(op.ny, op.kc, &S);
+  const size_t smem = gram_smem(op.ny, op.kc, f16, &S);
   // the split direction goes to tensor memory when it fits beside the accumulators
-  const bool at = op.a_tmem && 2 * op.nt + 4 * op.kc * S <= 512;
+  const bool at = !f16 && op.a_tmem && 2 * op.nt + 4 * op.kc * S <= 512;
   void (*kern)(const CUtensorMap, const CUtensorMap, const CUtensorMap, const CUtensorMap, const CUtensorMap,
                GramArgs, ColCgArgs) =
-      op.kc == 16 ? (at ? k_gram_normal<16, true, false> : k_gram_normal<16, false, false>)
-                  : (at ? k_gram_normal<8, true, false> : k_gram_normal<8, false, false>);
+      f16 ? k_gram_normal<16, false, false, true>
+          : op.kc == 16 ? (at ? k_gram_normal<16, true, false, false> : k_gram_normal<16, false, false, false>)
+                        : (at ? k_gram_normal<8, true, false, false> : k_gram_normal<8, false, false, false>);
   // the shared-memory opt-in is per device and kernel; cache it per (thread, device)
   constexpr int kMaxDev = 16;
-  static thread_local size_t configured[kMaxDev][4] = {};
+  static thread_local size_t configured[kMaxDev][5] = {};
   int dev = 0;
   cudaGetDevice(&dev);
-  const int ki = (op.kc == 16 ? 0 : 2) + (at ? 1 : 0);
+  const int ki = f16 ? 4 : (op.kc == 16 ? 0 : 2) + (at ? 1 : 0);
   if (dev < 0 || dev >= kMaxDev || configured[dev][ki] < smem) {
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (dev >= 0 && dev < kMaxDev) configured[dev][ki] = smem;
@@ -1084,6 +1283,7 @@ void launch_gram_normal(const GramOp& op, const CUtensorMap& mIn, const CUtensor
   g.nyt = op.ny / op.nt;
   g.stages = S;
   g.G = op.G;
+  g.gscale = op.gscale;
   g.tmem_cols = 32;
   const int need = at ? 2 * op.nt + 4 * op.kc * S : 2 * op.nt;
   while (g.tmem_cols < need) g.tmem_cols *= 2;
@@ -1106,15 +1306,18 @@ bool gram_colcg_supported(int ny, int nx) {
 
 bool launch_gram_colcg(const GramOp& op, const CUtensorMap& mIn, const CUtensorMap& mPold, GramArgs g,
                        const ColCgArgs& cc, cudaStream_t s) {
+  const bool f16 = op.f16 && op.kc == 16;
   int S = 0;
-  const size_t smem = gram_smem(op.ny, op.kc, &S);
+  const size_t smem = gram_smem(op.ny, op.kc, f16, &S);
   void (*kern)(const CUtensorMap, const CUtensorMap, const CUtensorMap, const CUtensorMap, const CUtensorMap,
-               GramArgs, ColCgArgs) = op.kc == 16 ? k_gram_normal<16, false, true> : k_gram_normal<8, false, true>;
+               GramArgs, ColCgArgs) = f16 ? k_gram_normal<16, false, true, true>
+                                          : op.kc == 16 ? k_gram_normal<16, false, true, false>
+                                                        : k_gram_normal<8, false, true, false>;
   constexpr int kMaxDev = 16;
-  static thread_local size_t configured[kMaxDev][2] = {};
+  static thread_local size_t configured[kMaxDev][3] = {};
   int dev = 0;
   cudaGetDevice(&dev);
-  const int ki = op.kc == 16 ? 0 : 1;
+  const int ki = f16 ? 2 : op.kc == 16 ? 0 : 1;
   if (dev < 0 || dev >= kMaxDev || configured[dev][ki] < smem) {
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (dev >= 0 && dev < kMaxDev) configured[dev][ki] = smem;
@@ -1125,6 +1328,7 @@ bool launch_gram_colcg(const GramOp& op, const CUtensorMap& mIn, const CUtensorM
   g.nyt = op.ny / op.nt;
   g.stages = S;
   g.G = op.G;
+  g.gscale = op.gscale;
   g.cg = 1;
   g.tma_epi = 1;
   g.tmem_cols = 32;

@@ -95,10 +95,13 @@ struct GramOp {
   int ny, nx, nt;           // nt: output rows per CTA (divides ny, <= 256)
   int kc;                   // contraction values per pipeline stage (16 or 8)
   int a_tmem;               // 1: the split direction is staged in tensor memory
-  // G_j split into TF32 head and remainder, stored as the kernel's pipeline
-  // stages consume it: [j][y tile][chunk][re hi | im hi | re lo | im lo]
-  // [nt rows][kc values, 16-byte groups swizzled as in shared memory]
-  float* G;
+  int f16;                  // 1 (with kc = 16, a_tmem = 0): FP16 head + remainder operands (kind::f16)
+  // G_j split into a head and a remainder (TF32, or FP16 after scaling by
+  // gscale[j]), stored as the kernel's pipeline stages consume it:
+  // [j][y tile][chunk][re hi | im hi | re lo | im lo][nt rows][kc values,
+  // 16-byte groups swizzled as in shared memory]
+  void* G;
+  float* gscale;            // [nx] power-of-two scale of G_j (FP16 form)
 };
 struct GramArgs {
   const float* in;          // r (CG) or x (apply), column-planar [B][nx][2][ny]
@@ -111,8 +114,11 @@ struct GramArgs {
   int itmax, PA, it, nb, cg;
   float lam;
   int* err;                 // first failure code (bounded waits)
+  const float* pscale;      // FP16 form: power-of-two scale of each image's operand [B]
+                            // (per-column CG: ColCgArgs::pscale instead)
   // filled by the launcher
-  const float* G;
+  const void* G;
+  const float* gscale;
   int ny, nx, nt, nyt, stages, tmem_cols;
   int tma_epi;              // epilogue moves p and q by tensor copies (nt a multiple of 32)
 };
@@ -131,6 +137,8 @@ struct ColCgArgs {
   int* iters;               // updates taken by the column
   int* status;              // [B] 5 when any column of the image broke down
   double rtol2;             // squared relative residual tolerance
+  double* pn;               // bound on the next direction's entries, sqrt(rr) + beta pn
+  float* pscale;            // its power-of-two FP16 scale
 };
 bool gram_supported(int ny, int nx);
 int gram_tile(int ny);
@@ -139,7 +147,12 @@ int gram_pa(int ny, int nx);
 bool gram_encode_x(CUtensorMap* m, float* base, int ny, int nx, int B, int kc);
 void launch_gram_build(const float2* smaps, const uint8_t* mask_host, int nc, const GramOp& op, double2* pbuf,
                        cudaStream_t s);
-void launch_gram_scalars(const CgArgs& a, int nb, int it, float* beta, int* done, cudaStream_t s);
+// per image: beta, the stop flag, and (FP16 operands) the bound pn on the
+// direction's entries, sqrt(rr) + beta pn_prev, with its power-of-two scale
+void launch_gram_scalars(const CgArgs& a, int nb, int it, float* beta, int* done, double* pn, float* pscale,
+                         cudaStream_t s);
+// FP16 operands of an operator application: pscale[b] from max |x_b| (column-planar input)
+void launch_gram_apply_scale(const float* x, int ny, int nx, int nb, float* pscale, cudaStream_t s);
 void launch_gram_normal(const GramOp& op, const CUtensorMap& mIn, const CUtensorMap& mPold, GramArgs g,
                         cudaStream_t s);
 // Per-column CG on the tensor-core operator.  Supported when the output-row

@@ -263,3 +263,42 @@ def test_full_size_variance_map_band(knee):
     assert np.mean(np.abs(z) > 4) < 0.01, np.mean(np.abs(z) > 4)
     assert np.abs(s.cpu().numpy() / K - d).max() / d.max() < 0.2
     assert pico.pico_sync(op.ctx) is None
+
+
+# The default operands are FP16 head + remainder pairs (kind::f16) after
+# power-of-two scaling: G_j by a per-column scale from the bound
+# P[0] max_y sum_c |S_c[y, j]|^2, the direction by a per-image scale from the
+# bound sqrt(r^H r) + beta |p_prev| (CG) or max |x| (an application).
+# PICO_GRAM_TF32=1 selects the TF32 split.  Both keep about 22 significant
+# bits per product; the scales make the FP16 range irrelevant, checked here
+# with sensitivities 1e4 and 1e-4 times the unit-energy maps (G_j entries
+# near 1e8 and 1e-8).
+@pytest.mark.parametrize("scale", [1.0, 1e4, 1e-4])
+def test_fp16_operands_match_the_oracle_and_tf32(scale):
+    ny, nx = 320, 6
+    S, cov, mask = case(ny, nx, 5, acs=6, seed=31)
+    S = (S * scale).astype(np.complex64)
+    kw = dict(mask=mask, noise_cov=cov, lam=0.0, power_iters=0, max_batch=70)
+    f16 = pico.Operator(S, **kw)
+    tf32 = operator_with_env("PICO_GRAM_TF32", "1", S, **kw)
+    oop = O.Operator(S, cov, mask=mask)
+    x = rand_imgs(70, ny, nx, 4)
+    y16, y32 = (o.apply_normal(to_dev(x)).cpu().numpy() for o in (f16, tf32))
+    for b in (0, 69):
+        want = oop.normal(x[b].astype(np.complex128))
+        assert np.linalg.norm(y16[b] - want) / np.linalg.norm(want) < 1e-5
+        assert np.linalg.norm(y32[b] - want) / np.linalg.norm(want) < 1e-5
+    # 30 CG updates: the FP16 and TF32 solves agree with the FP64 CG to the usual 1e-4
+    xs = to_dev(x)
+    for o in (f16, tf32):
+        xc = o.cg(xs, 30, 0.0).cpu().numpy()
+        for b in (0, 69):
+            xo, _, _ = OS.cg(lambda z: oop.normal(z), x[b].astype(np.complex128), 30)
+            assert np.abs(xc[b] - xo).max() / np.abs(xo).max() < 1e-4, (scale, b)
+        assert pico.pico_sync(o.ctx) is None
+    # the per-column CG on FP16 operands as well
+    f16.set_solver("columns")
+    xc = f16.cg(xs, 30, 0.0).cpu().numpy()
+    xo, _, _ = OS.cg_columns(oop, x[[0, 69]].astype(np.complex128), 0.0, 30)
+    for i, b in enumerate((0, 69)):
+        assert np.abs(xc[b] - xo[i]).max() / np.abs(xo[i]).max() < 1e-4, (scale, b)

@@ -146,3 +146,56 @@ def test_full_size_toeplitz_on_sampled_outputs():
             want = np.sum(np.conj(S64[:, yy, xx]) * S64[:, y0, x0]) * h
             got = y[b, yy, xx]
             assert abs(got - want) <= 1e-5 * abs(y[b, y0, x0]) + 1e-4 * abs(want), (b, yy, xx, got, want)
+
+
+def test_full_size_gridding_adjoint_against_exact_nudft():
+    """pico_adjoint (Kaiser-Bessel W = 6, oversampling 2, gather gridding on the
+    480 x 480 grid) on one random whitened k-space vector of the full workload
+    (20 coils x 32768 samples) against the exact NUDFT adjoint."""
+    w = synth.WORKLOADS["spiral240_r2"]
+    inp = w.inputs()
+    S, traj = inp["smaps"], inp["traj"]
+    n, M = w.ny, traj.shape[0]
+    op = pico.Operator(S, traj=traj, lam=0.0, power_iters=0, max_batch=2)
+    g = np.random.default_rng(21)
+    y = (g.standard_normal((1, w.nc, M)) + 1j * g.standard_normal((1, w.nc, M))).astype(np.complex64)
+    x = op.adjoint(torch.from_numpy(y).cuda()).cpu().numpy()[0]
+    oop = O.Operator(S, None, traj=traj)
+    want = oop.adjoint(y[0].astype(np.complex128))
+    err = np.abs(x - want) / np.abs(want).max()
+    # the gridding approximation (W = 6, os = 2): about 1e-4 of the peak, far below at most voxels
+    assert err.max() < 1e-3, err.max()
+    assert np.median(err) < 1e-4, np.median(err)
+    op.close()
+
+
+def test_full_size_pico_probes_same_seed_at_the_bench_launch_shape():
+    """Probes 0 and 255 of one 256-probe batch (lam = 0.1: solve, A^H A, solve;
+    30 CG updates each) against the oracle's same-seed products with the exact
+    Toeplitz-form operator.  The GPU's per-probe product is the difference of
+    two running-sum maps (every image of a batch is processed on its own, so
+    the products do not depend on the batch); per voxel
+    |d_gpu - d_oracle| <= 1e-4 max(|u_k|, 0.1 median |u|), u = Sigma v."""
+    w = synth.WORKLOADS["spiral240_r2"]
+    inp = w.inputs()
+    S, traj = inp["smaps"], inp["traj"]
+    n, K, seed = w.ny, w.probes, 3131
+    op = pico.Operator(S, traj=traj, lam=w.lam, power_iters=15, max_batch=K)
+    lam = op.info["lambda_phys"]
+    s_all, _ = op.variance_sums(seed, K, w.max_iter, 0.0)                  # the bench's launch shape
+    s_wo_last, _ = op.variance_sums(seed, K - 1, w.max_iter, 0.0)
+    s_wo_first, _ = op.variance_sums(seed, K - 1, w.max_iter, 0.0, probe_begin=1)
+    op.sync()
+    d_gpu = {K - 1: (s_all - s_wo_last).cpu().numpy(), 0: (s_all - s_wo_first).cpu().numpy()}
+    op.close()
+    T = O.ToeplitzNormal(S, traj)
+    lmax = OS.power_method(lambda x: T.apply(x), (n, n), 15)
+    assert abs(lam - w.lam * 1.01 * lmax) <= 1e-5 * lam
+    for i in (0, K - 1):
+        v = ORNG.probe(seed, i, n * n).reshape(n, n)
+        x1, _, _ = OS.cg(lambda z: T.apply(z, lam), v, w.max_iter)
+        u, _, _ = OS.cg(lambda z: T.apply(z, lam), T.apply(x1), w.max_iter)
+        d_o = np.real(np.conj(v) * u)
+        scale = np.maximum(np.abs(u), 0.1 * np.median(np.abs(u)))
+        err = np.abs(d_gpu[i] - d_o) / scale
+        assert err.max() < 1e-4, (i, err.max())

@@ -434,3 +434,16 @@ def test_pico_with_column_cg_band_against_exact_diagonal():
     s1, _ = pico.pico(op, 11, 0, 3, 0.0, 200, 1e-12, solver="columns")
     s2, _ = pico.pico(op, 11, 0, 3, 0.0, 200, 1e-12)
     assert np.allclose(s1, s2, rtol=1e-9, atol=1e-12)
+
+
+def test_spiral_toeplitz_normal_equals_exact_nudft_normal():
+    n = 24
+    S = synth.coil_maps(n, n, 3, 7)
+    traj = synth.spiral_traj(n, 4, 160, 1)
+    T = ops.ToeplitzNormal(S, traj)
+    op = ops.Operator(S, None, traj=traj)
+    g = np.random.default_rng(8)
+    for lam in (0.0, 0.3):
+        x = g.standard_normal((n, n)) + 1j * g.standard_normal((n, n))
+        want = op.normal(x, lam)
+        assert np.allclose(T.apply(x, lam), want, rtol=1e-11, atol=1e-12 * np.abs(want).max())
