@@ -797,7 +797,7 @@ pico_status gram_configure(pico_ctx* c) {
   const int kc = c->gop.kc;
   // the format G is built in follows the stage shape: FP16 operands need 16-value
   // stages staged in shared memory
-  c->gop.f16 = c->gram_f16 && kc == 16 && !c->gop.a_tmem;
+  c->gop.f16 = c->gram_f16 && kc == 16 && !c->gop.a_tmem && (size_t)c->nc * c->ny * 8 <= 200 * 1024;
   pico::launch_gram_build(c->smaps, c->gmask.data(), c->nc, c->gop, c->g_pbuf, c->stream);
   const int B = c->max_batch;
   const bool ok = pico::gram_encode_x(&c->mR, cpf(c->R), c->ny, c->nx, B, kc) &&
