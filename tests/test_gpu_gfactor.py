@@ -13,10 +13,9 @@ the GPU, combined by pico_gfactor, against the oracle.
     the delta-method bound of that band.
 * Spiral 64 x 64 (the reference reading for lam > 0: all interleaves, lam = 0,
   same coils; R = interleaves / kept interleaves): the GPU maps equal the
-  oracle's same-seed maps to 1e-4 of the exact diagonal and the g maps agree to
-  2e-3 wherever both 8-probe maps exceed 5 % of their exact values; the
-  256-probe g map is within sampling error of the g of the exact dense
-  covariances.
+  oracle's same-seed maps to 1e-4 of the largest exact variance at every voxel,
+  the g maps agree to the bound that follows from it, and the 256-probe g map
+  is within sampling error of the g of the exact dense covariances.
 """
 import numpy as np
 import pytest
@@ -114,13 +113,17 @@ def test_spiral_gfactor_with_unregularised_full_reference():
     da, dr = np.real(np.diag(Sa)).reshape(n, n), np.real(np.diag(Sr)).reshape(n, n)
     assert np.abs(sa8 - oa).max() / Ka < 1e-4 * da.max()
     assert np.abs(sr8 - orf).max() / Ka < 1e-4 * dr.max()
-    # g from the same-seed maps wherever both 8-probe maps exceed 5 % of their exact
-    # value: the maps agree to 1e-4 of the exact diagonal, so g (a square root of
-    # their ratio) agrees to 0.5e-4 (da / a + dr / r) <= 2e-3 there
-    ok = (oa / Ka > 0.05 * da) & (orf / Ka > 0.05 * dr)
-    g_o = OP.gfactor(np.where(ok, oa / Ka, 1.0), np.where(ok, orf / Ka, 1.0), float(L) / (L // R))
+    # g from the same-seed maps: the maps agree to ea = 1e-4 max(da) and er = 1e-4
+    # max(dr) at every voxel, so g (a square root of their ratio) agrees to
+    # 1/2 (ea / a + er / r) relative -- checked (with a factor 2) wherever both
+    # errors are below 10 % of the 8-probe values
+    a, r = oa / Ka, orf / Ka
+    ea, er = 1e-4 * da.max(), 1e-4 * dr.max()
+    ok = (a > 10 * ea) & (r > 10 * er)
+    g_o = OP.gfactor(np.where(ok, a, 1.0), np.where(ok, r, 1.0), float(L) / (L // R))
+    bound = 0.5 * (ea / np.where(ok, a, 1.0) + er / np.where(ok, r, 1.0))
     assert ok.mean() > 0.3
-    assert (np.abs(g8 - g_o) / g_o)[ok].max() < 2e-3
+    assert np.all((np.abs(g8 - g_o) <= 2 * bound * g_o)[ok])
     # the 256-probe g map against the g of the exact covariances (sampling error only)
     g_ex = OP.gfactor(da, dr, float(L) / (L // R))
     assert np.median(np.abs(g - g_ex) / g_ex) < 0.05

@@ -93,8 +93,13 @@ def operator_with_env(var, val, *args, **kw):
 def test_tensor_memory_operand_matches_shared_memory_operand(ny, nx):
     S, cov, mask = case(ny, nx, 4, acs=6, seed=ny)
     x = to_dev(rand_imgs(130, ny, nx, 3))
-    ops = [operator_with_env("PICO_GRAM_ATMEM", v, S, mask=mask, noise_cov=cov, lam=0.02, power_iters=0,
-                             max_batch=130) for v in ("1", "0")]
+    # both with the TF32 split (the FP16 operands are staged in shared memory only)
+    os.environ["PICO_GRAM_TF32"] = "1"
+    try:
+        ops = [operator_with_env("PICO_GRAM_ATMEM", v, S, mask=mask, noise_cov=cov, lam=0.02, power_iters=0,
+                                 max_batch=130) for v in ("1", "0")]
+    finally:
+        del os.environ["PICO_GRAM_TF32"]
     ya, yb = (o.apply_normal(x) for o in ops)
     assert ((ya - yb).abs().max() / yb.abs().max()).item() < 1e-6
     xa, ia, ra = ops[0].cg(x, 12, 0.0, stats=True)
