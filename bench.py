@@ -155,10 +155,14 @@ def kernel_digest(*names):
 
 
 # dram__bytes_read.sum + dram__bytes_write.sum per launch of the dominant
-# kernel from one ncu capture (the summaries in the profiles folder), keyed by
-# (workload, images per launch, digest of the kernel sources at capture time):
-# a changed kernel no longer matches and its traffic is reported as null.
-TRAFFIC = {}
+# kernel from one ncu capture (the summaries in the profiles folder; two
+# full-size launches averaged, a one-pass metric set), keyed by (workload,
+# images per launch, kernel, digest of the kernel sources at capture time): a
+# changed kernel no longer matches and its traffic is reported as null.
+TRAFFIC = {
+    ("knee320_r2", 256, "gram", "90524d46254e97cb"): 713.701632e6 + 376.994048e6,
+    ("knee320_r2", 256, "colcg", "90524d46254e97cb"): 1009.139072e6 + 577.829120e6,
+}
 
 
 def measured_peaks():
@@ -166,9 +170,9 @@ def measured_peaks():
         return json.load(f)
 
 
-def traffic_of(w, K, kernel_files):
+def traffic_of(w, K, kernel, kernel_files):
     dig = kernel_digest(*kernel_files)
-    return TRAFFIC.get((w.name, K, dig)), dig
+    return TRAFFIC.get((w.name, K, kernel, dig)), dig
 
 
 def gram_roofline(w, K, avg_s, launches):
@@ -180,24 +184,25 @@ def gram_roofline(w, K, avg_s, launches):
     streams instead of S are not algorithmic bytes; they show up in `traffic`.
     The tensor view is kept as a secondary key: nx dense complex
     (ny x ny) x (ny x K) products, 8 ny^2 nx flops per image, issued as three
-    TF32 products (dense-equivalent work, not the method's own flop count)."""
+    FP16 products (dense-equivalent work, not the method's own flop count)."""
     mp = measured_peaks()
     alg = alg_bytes_normal(w, K)
     achieved = alg / avg_s / 1e9
-    traffic, dig = traffic_of(w, K, ("gram.cu", "tc_util.cuh", "kernels.cuh"))
+    traffic, dig = traffic_of(w, K, "gram", ("gram.cu", "tc_util.cuh", "kernels.cuh"))
     cplx = 8.0 * w.ny * w.ny * w.nx * K
-    tf32_peak = mp["bf16_tflops"] * 1.1 / 2.25
     return {"bound": "hbm", "achieved": achieved, "peak": mp["hbm_gbs"], "unit": "GB/s",
             "frac": achieved / mp["hbm_gbs"], "traffic": traffic,
             "traffic_over_algorithmic": traffic / alg if traffic else None,
-            "kernel": "k_gram_normal (tcgen05 kind::tf32, 3-term split, fused CG direction update, TMA epilogue)",
+            "kernel": "k_gram_normal<16,0,0,1> (tcgen05 kind::f16, FP16 head + remainder of scaled operands, "
+                      "fused CG direction update, TMA epilogue)",
             "kernel_digest": dig, "avg_launch_ms": avg_s * 1e3, "launches": launches,
             "algorithmic_bytes_per_launch": alg,
             "peak_note": "measured copy bandwidth (of measured)",
-            "tensor_dense_equivalent": {"achieved_TFLOPs": 3.0 * cplx / avg_s / 1e12, "peak_TFLOPs": tf32_peak,
-                                        "frac": 3.0 * cplx / avg_s / 1e12 / tf32_peak,
-                                        "note": "3 TF32 products per complex term of the dense per-column "
-                                                "Gram contraction; peak = measured bf16 burst x 1.1/2.25"}}
+            "tensor_dense_equivalent": {"achieved_TFLOPs": 3.0 * cplx / avg_s / 1e12, "peak_TFLOPs": mp["bf16_tflops"],
+                                        "frac": 3.0 * cplx / avg_s / 1e12 / mp["bf16_tflops"],
+                                        "note": "3 FP16 products per complex term of the dense per-column "
+                                                "Gram contraction; peak = measured bf16 burst (the FP16 dense "
+                                                "rate is the same)"}}
 
 
 def fft_roofline(w, K, avg_s, launches):
@@ -209,7 +214,7 @@ def fft_roofline(w, K, avg_s, launches):
     achieved = flops / avg_s / 1e12
     peak = N_SM * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
     files = ("cart_impl.cuh", "kernels.cuh") if w.kind == "cartesian" else ("spiral_impl.cuh", "kernels.cuh")
-    traffic, dig = traffic_of(w, K, files)
+    traffic, dig = traffic_of(w, K, "fft", files)
     alg = alg_bytes_normal(w, K)
     return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
             "traffic": traffic, "kernel_digest": dig,
@@ -711,11 +716,11 @@ def colcg_roofline(w, K, avg_s, launches):
     V = w.ny * w.nx * 8
     alg = 6 * K * V + w.nc * V
     achieved = alg / avg_s / 1e9
-    traffic, dig = traffic_of(w, K, ("gram.cu", "tc_util.cuh", "kernels.cuh"))
+    traffic, dig = traffic_of(w, K, "colcg", ("gram.cu", "tc_util.cuh", "kernels.cuh"))
     return {"bound": "hbm", "achieved": achieved, "peak": mp["hbm_gbs"], "unit": "GB/s",
             "frac": achieved / mp["hbm_gbs"], "traffic": traffic,
             "traffic_over_algorithmic": traffic / alg if traffic else None,
-            "kernel": "k_gram_normal<16,0,1> (tcgen05 kind::tf32 column-CG update: operator, step, x / r update "
+            "kernel": "k_gram_normal<16,0,1,1> (tcgen05 kind::f16 column-CG update: operator, step, x / r update "
                       "and next beta in one launch, 2-CTA clusters)",
             "kernel_digest": dig, "avg_launch_ms": avg_s * 1e3, "launches": launches,
             "algorithmic_bytes_per_launch": alg, "peak_note": "measured copy bandwidth (of measured)"}
