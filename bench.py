@@ -226,6 +226,28 @@ def fft_roofline(w, K, avg_s, launches):
                     "frac": alg / avg_s / 1e9 / mp["hbm_gbs"], "algorithmic_bytes_per_launch": alg}}
 
 
+def onchip_roofline(w, K, avg_s, launches, solver):
+    """Roofline of the on-chip CG solve of small phase-encode images (one launch
+    per solve of K images): FP32 work of the dense per-column products,
+    8 ny^2 nx flops per image and update, max_iter updates, against the FP32
+    FMA peak; the HBM view (the right-hand sides in, the solutions out, G_j
+    once) is secondary -- the workload fits in L2 and is latency-bound."""
+    mp = measured_peaks()
+    flops = 8.0 * w.ny * w.ny * w.nx * K * w.max_iter
+    peak = N_SM * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    V = w.ny * w.nx * 8
+    byts = 2 * K * V + w.nx * w.ny * w.ny * 8
+    return {"bound": "alu", "achieved": flops / avg_s / 1e12, "peak": peak, "unit": "TFLOP/s",
+            "frac": flops / avg_s / 1e12 / peak, "traffic": None,
+            "kernel": ("k_colcg_small<NY,T,GLOBAL> (whole CG solve on chip, one cooperative launch per solve, "
+                       "grid barriers between the column sums)" if solver == "global" else
+                       "k_colcg_small<NY,T> (whole per-column CG solve on chip, one launch per solve)"),
+            "avg_launch_ms": avg_s * 1e3, "launches": launches,
+            "peak_note": "FP32 FMA peak 152 SM x 128 lanes x 2 x 2070 MHz (nominal max clock)",
+            "hbm": {"achieved_GBps": byts / avg_s / 1e9, "peak_GBps": mp["hbm_gbs"],
+                    "frac": byts / avg_s / 1e9 / mp["hbm_gbs"]}}
+
+
 def normal_ops_per_probe(w):
     """Normal-operator applications per probe: one CG solve (lam = 0) or two
     solves and one A^H A (lam > 0)."""
@@ -760,9 +782,8 @@ def bench_linear(args, w, inp, pico, torch, dist, world, rank, local, steps, war
     gram_on = op.info["normal_op"] == 1 and K >= op.tuning["gram_min_batch"]
     if solver == "columns" and op.info["normal_op"] == 1:
         roof = colcg_roofline(w, K, avg_norm_s, norm_n)
-    elif solver == "columns":
-        roof = fft_roofline(w, K, avg_norm_s, norm_n)
-        roof["kernel"] = "k_colcg_small (whole per-column CG solve on chip, one launch per solve)"
+    elif op.info["normal_op"] == 3:
+        roof = onchip_roofline(w, K, avg_norm_s, norm_n, solver)
     else:
         roof = gram_roofline(w, K, avg_norm_s, norm_n) if gram_on else fft_roofline(w, K, avg_norm_s, norm_n)
     nsamp = K * world

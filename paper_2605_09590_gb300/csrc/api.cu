@@ -101,6 +101,8 @@ struct pico_ctx {
   float* col_pscale = nullptr;
   float2* col_G = nullptr;  // small images: G_j of every column, [nx][ny][ny] (whole solve on chip)
   bool col_small = false;
+  bool onchip = false;       // small phase-encode images: every CG solve runs on chip (either solver)
+  pico::SmallGlobal sglob{};  // whole-image CG on chip: column partials and the grid barrier
   std::string host_fail;  // a launch that could not be issued (reported by the entry point)
   size_t device_bytes = 0, budget = 0;
   bool async_alloc = false;  // stream-ordered cudaMallocAsync / cudaFreeAsync (serving contexts)
@@ -442,16 +444,20 @@ void cg_iterations(pico_ctx* c, int nb, int max_iter, double rtol, float lam) {
   }
 }
 
-// the whole per-column CG solve of small images: one launch, rhs in R, x to X (natural layout)
+// the whole CG solve of small images on chip (per column, or the whole image
+// with grid barriers): rhs in R, x to X (natural layout)
 void run_cg_small(pico_ctx* c, int nb, int max_iter, double rtol, float lam) {
   Launch L(c, 0);
-  pico::launch_colcg_small(c->col_G, c->R, c->X, c->ny, c->nx, nb, max_iter, rtol * rtol, lam, c->col_rr0,
-                           c->col_rr, c->col_iters, c->status, c->stream);
+  const pico::SmallGlobal* glob = c->solver == PICO_SOLVER_COLUMNS ? nullptr : &c->sglob;
+  if (!pico::launch_colcg_small(c->col_G, c->R, c->X, c->ny, c->nx, nb, max_iter, rtol * rtol, lam, c->col_rr0,
+                                c->col_rr, c->col_iters, c->status, glob, c->stream))
+    c->host_fail = "on-chip CG launch failed (cooperative launch of the whole-image solve)";
 }
+bool small_path(const pico_ctx* c) { return c->onchip || column_small(c); }
 
 pico_status run_cg(pico_ctx* c, int nb, int max_iter, double rtol, float lam) {
   c->cg.rtol2 = rtol * rtol;
-  if (column_small(c)) {
+  if (small_path(c)) {
     run_cg_small(c, nb, max_iter, rtol, lam);
     return cuda_check(c, "cg");
   }
@@ -484,7 +490,7 @@ pico_status run_cg_from_probe(pico_ctx* c, int nb, int max_iter, double rtol, fl
                               int64_t begin, int kind) {
   c->cg.rtol2 = rtol * rtol;
   init_from_probe(c, nb, seed, begin, kind);
-  if (column_small(c)) {
+  if (small_path(c)) {
     run_cg_small(c, nb, max_iter, rtol, lam);
     return cuda_check(c, "cg");
   }
@@ -786,10 +792,47 @@ bool want_gram(const pico_operator_desc* d) {
   return d->ny >= 128 && pico::gram_supported(d->ny, d->nx);
 }
 
+// Small phase-encode Cartesian images (ny = 32, 64, 96): the CG solves run on
+// chip (G_j and the vectors in shared memory, one cooperative launch per
+// solve); PICO_NORMAL_OP=fft keeps the column-FFT path.
+bool want_onchip(const pico_operator_desc* d) {
+  if (d->kind != PICO_CARTESIAN || d->mask_2d) return false;
+  const char* e = std::getenv("PICO_NORMAL_OP");
+  if (e && std::string(e) == "fft") return false;
+  return pico::colcg_small_supported(d->ny);
+}
+size_t onchip_extra_bytes(const pico_operator_desc* d, int64_t B) {
+  return (size_t)d->nx * d->ny * d->ny * 8 + (size_t)d->ny * 16 + (size_t)B * d->nx * (8 + 8 + 4 + 8 + 8) + 8;
+}
+
 // G planes, second direction buffer and per-image scalars of the Gram mode
 size_t gram_extra_bytes(const pico_operator_desc* d, int64_t B) {
   return pico::gram_bytes(d->ny, d->nx) + (size_t)B * d->ny * d->nx * 8 + (size_t)B * 8 + (size_t)d->ny * 16 + 16 +
          (size_t)B * 12 + (size_t)d->nx * 4;
+}
+
+// Small phase-encode images: G_j of every column (plain layout) and the
+// per-(image, column) state of the on-chip solves; `global` adds the column
+// partials and grid-barrier words of the whole-image solve.
+pico_status small_setup(pico_ctx* c, bool global) {
+  pico_status st = PICO_OK;
+  const size_t n = (size_t)c->max_batch * c->nx;
+  if (!c->col_G) {
+    if ((st = dalloc(c, &c->col_G, (size_t)c->nx * c->ny * c->ny)) != PICO_OK) return st;
+    if (!c->g_pbuf && (st = dalloc(c, &c->g_pbuf, (size_t)c->ny)) != PICO_OK) return st;
+    pico::launch_colcg_small_build(c->smaps, c->gmask.data(), c->nc, c->ny, c->nx, c->col_G, c->g_pbuf, c->stream);
+  }
+  if ((!c->col_rr0 && (st = dalloc(c, &c->col_rr0, n)) != PICO_OK) ||
+      (!c->col_rr && (st = dalloc(c, &c->col_rr, n)) != PICO_OK) ||
+      (!c->col_iters && (st = dalloc(c, &c->col_iters, n)) != PICO_OK))
+    return st;
+  if (global && !c->sglob.bar) {
+    if ((st = dalloc(c, &c->sglob.part_pq, n)) != PICO_OK || (st = dalloc(c, &c->sglob.part_rr, n)) != PICO_OK ||
+        (st = dalloc(c, &c->sglob.bar, (size_t)2)) != PICO_OK)
+      return st;
+    c->sglob.err = c->g_err;
+  }
+  return cuda_check(c, "on-chip CG set-up");
 }
 
 // (re)build the stage-tiled G_j for gop.kc and the tensor maps of the CG vectors
@@ -914,6 +957,7 @@ pico_status init_impl(const pico_operator_desc* d, void* cuda_stream, size_t hbm
       return fail(c, PICO_E_UNSUPPORTED, "ny has no FFT split in this build");
     PA = pico::cart_normal_tiles(c->nx);
     extra = (size_t)c->ny * 13 + (size_t)c->nx * 8;
+    if (want_onchip(d)) extra += onchip_extra_bytes(d, B);
     if (want_gram(d)) {
       c->pa_gram = pico::gram_pa(c->ny, c->nx);
       c->pa_fft = PA;
@@ -1046,6 +1090,11 @@ pico_status init_impl(const pico_operator_desc* d, void* cuda_stream, size_t hbm
   }
   // the dense Gram operator takes over the CG normal operator once lambda_max is known
   if (!c->mask2d && c->kind == PICO_CARTESIAN && want_gram(d)) TRY(gram_setup(c, d));
+  // small phase-encode images: every solve runs on chip, G_j in shared memory
+  if (want_onchip(d)) {
+    TRY(small_setup(c, true));
+    c->onchip = true;
+  }
   if (cudaStreamSynchronize(c->stream) != cudaSuccess) return cuda_check(c, "pico_init");
   if ((st = cuda_check(c, "pico_init")) != PICO_OK) return st;
 #undef TRY
@@ -1068,6 +1117,7 @@ size_t footprint_bytes(const pico_operator_desc* d, bool with_kbuf) {
     PA = cart_normal_tiles(d->nx);
     extra = (int64_t)d->ny * 13 + (int64_t)d->nx * 8;
     kbuf = B * nc * n * 8;
+    if (want_onchip(d)) extra += (int64_t)onchip_extra_bytes(d, B);
     if (want_gram(d)) {
       PA = std::max<int64_t>(PA, gram_pa(d->ny, d->nx));
       extra += (int64_t)gram_extra_bytes(d, B);
@@ -1104,7 +1154,7 @@ pico_status pico_get_info(const pico_ctx* c, pico_info* info) {
   info->max_iter_cap = c->itmax;
   info->nsamp = c->nsamp;
   info->device_bytes = c->device_bytes;
-  info->normal_op = c->gram ? 1 : (c->kind == PICO_CARTESIAN && !c->mask2d) ? 0 : 2;
+  info->normal_op = c->gram ? 1 : c->onchip ? 3 : (c->kind == PICO_CARTESIAN && !c->mask2d) ? 0 : 2;
   return PICO_OK;
 }
 
@@ -1155,7 +1205,7 @@ pico_status pico_cg_batch(pico_ctx* c, const void* rhs, void* x, int32_t nbatch,
       cudaMemcpyAsync(xb, c->X, (size_t)nb * bytes_img, cudaMemcpyDeviceToDevice, c->stream);
     }
     if (iters_out || relres_out) {
-      if (column_mode(c) || column_small(c)) {
+      if (column_mode(c) || small_path(c)) {
         Launch L(c, 3);
         pico::launch_colcg_report(col_args(c), c->nx, nb, c->d_iters, c->d_relres, c->stream);
       } else {
@@ -1538,12 +1588,9 @@ pico_status pico_set_solver(pico_ctx* c, int32_t solver) {
       return fail(c, PICO_E_UNSUPPORTED,
                   "per-column CG needs a Cartesian phase-encode context with ny = 32, 64 or 96, or one on the "
                   "tensor-core operator whose row tile is a multiple of 32 and at most 4 tiles per column");
-    if (small && !c->col_G) {
-      pico_status st = PICO_OK;
-      if ((st = dalloc(c, &c->col_G, (size_t)c->nx * c->ny * c->ny)) != PICO_OK) return st;
-      if (!c->g_pbuf && (st = dalloc(c, &c->g_pbuf, (size_t)c->ny)) != PICO_OK) return st;
-      pico::launch_colcg_small_build(c->smaps, c->gmask.data(), c->nc, c->ny, c->nx, c->col_G, c->g_pbuf,
-                                     c->stream);
+    if (small) {
+      const pico_status st = small_setup(c, false);
+      if (st != PICO_OK) return st;
     }
     c->col_small = small;
     const size_t n = (size_t)c->max_batch * c->nx;
@@ -1640,6 +1687,12 @@ pico_status pico_set_tuning(pico_ctx* c, const pico_tuning* t) {
 
 pico_status pico_autotune(pico_ctx* c, int32_t iters, pico_tuning* out, double* times_us, int32_t ntimes) {
   if (!c || !c->smaps) return PICO_E_INVALID;
+  if (c->onchip) {  // the on-chip solve has no launch shape to choose: report the current tuning
+    if (times_us)
+      for (int i = 0; i < ntimes; ++i) times_us[i] = NAN;
+    if (out) pico_get_tuning(c, out);
+    return PICO_OK;
+  }
   if (iters == 0) iters = 4;
   if (iters < 2 || iters > 32 || iters > c->itmax) return fail(c, PICO_E_INVALID, "autotune iters must be 2..32");
   constexpr int kCand = 4, kNb = 6;

@@ -67,15 +67,59 @@ __device__ __forceinline__ void image_sums(const double (&v)[NY * T / kSmallThre
   __syncthreads();
 }
 
+// Grid-wide barrier of a cooperative launch (all blocks resident): the last
+// block to arrive resets the counter and advances the generation; the others
+// wait for the generation to change, for at most about two seconds, after
+// which the wait records error 11 and reports false (the caller then leaves
+// its loop; the other blocks' own bounded waits end the same way).
+__device__ __forceinline__ bool grid_barrier(unsigned* count, unsigned* gen, unsigned nblocks, int* err, int* sh_ok) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned* vgen = gen;
+    const unsigned g = *vgen;
+    __threadfence();  // this block's partial sums are visible before it arrives
+    bool ok = true;
+    if (atomicAdd(count, 1u) == nblocks - 1) {
+      atomicExch(count, 0u);
+      __threadfence();
+      atomicAdd(gen, 1u);
+    } else {
+      uint64_t t0;
+      asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+      for (;;) {
+        if (*vgen != g) break;
+        uint64_t t1;
+        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t1));
+        if (t1 - t0 > 2000000000ull) {
+          ok = false;
+          if (err) atomicCAS(err, 0, 11);
+          break;
+        }
+      }
+    }
+    __threadfence();
+    *sh_ok = ok;
+  }
+  __syncthreads();
+  return *sh_ok != 0;
+}
+
 // Block = (column j, images b0 .. b0 + T - 1).  rhs and x are natural-layout
 // images [B][NY][nx]; rr0 / rr / iters receive the column's ||b_j||^2, final
 // ||r_j||^2 and update count per image ([B][nx]).
-template <int NY, int T>
+// GLOBAL: CG on the whole image instead of per column -- the per-column sums
+// of every image go to part_pq / part_rr ([B][nx]), a grid barrier of the
+// cooperative launch follows, and every block adds an image's nx column sums
+// in column order, so all blocks take the same alpha and beta (Eq. 6 CG with
+// the operator applied column by column).
+template <int NY, int T, bool GLOBAL>
 __global__ void __launch_bounds__(kSmallThreads) k_colcg_small(const float2* __restrict__ G, const float2* __restrict__ rhs,
                                                             float2* __restrict__ X, int nx, int nb, int max_iter,
                                                             double rtol2, float lam, double* __restrict__ rr0_out,
                                                             double* __restrict__ rr_out, int* __restrict__ iters_out,
-                                                            int* __restrict__ status) {
+                                                            int* __restrict__ status, double* __restrict__ part_pq,
+                                                            double* __restrict__ part_rr, unsigned* __restrict__ bar,
+                                                            int* __restrict__ err) {
   constexpr int E = NY * T / kSmallThreads;  // elements (image, row) per thread
   static_assert(NY % 32 == 0 && (NY * T) % kSmallThreads == 0, "tile shape");
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -90,9 +134,25 @@ __global__ void __launch_bounds__(kSmallThreads) k_colcg_small(const float2* __r
   float* s_beta = s_alpha + T;
   int* s_live = reinterpret_cast<int*>(s_beta + T);
   int* s_any = s_live + T;
+  int* s_ok = s_any + 1;
 
   const int j = blockIdx.x, b0 = blockIdx.y * T, tid = threadIdx.x;
   const int64_t n = (int64_t)NY * nx;
+  const unsigned nblocks = gridDim.x * gridDim.y;
+  // GLOBAL: replace each image's column sum in `col` by the sum over all columns
+  auto whole_image = [&](double* col, double* part) -> bool {
+    if (!GLOBAL) return true;
+    if (threadIdx.x < T && b0 + (int)threadIdx.x < nb) part[(size_t)(b0 + threadIdx.x) * nx + j] = col[threadIdx.x];
+    const bool ok = grid_barrier(bar, bar + 1, nblocks, err, s_ok);
+    if (threadIdx.x < T && b0 + (int)threadIdx.x < nb) {
+      double a = 0.0;
+      const double* pp = part + (size_t)(b0 + threadIdx.x) * nx;
+      for (int jj = 0; jj < nx; ++jj) a += __ldcg(pp + jj);  // L2: other blocks wrote these since the last read
+      col[threadIdx.x] = a;
+    }
+    __syncthreads();
+    return ok;
+  };
   for (int i = tid; i < NY * NY; i += kSmallThreads) Gs[i] = G[(size_t)j * NY * NY + i];
   // this thread's elements: image t = e / NY, row y = e % NY (a warp's 32 share t)
   float2 x[E], r[E], q[E];
@@ -105,6 +165,12 @@ __global__ void __launch_bounds__(kSmallThreads) k_colcg_small(const float2* __r
     v[k] = (double)r[k].x * r[k].x + (double)r[k].y * r[k].y;
   }
   image_sums<NY, T>(v, red, s_rr0);
+  if (tid < T && b0 + tid < nb) {  // this column's ||b_j||^2 (and ||r_j||^2 until an update)
+    rr0_out[(size_t)(b0 + tid) * nx + j] = s_rr0[tid];
+    rr_out[(size_t)(b0 + tid) * nx + j] = s_rr0[tid];
+  }
+  __syncthreads();
+  bool alive = whole_image(s_rr0, part_rr);
   if (tid < T) {
     const double rr = s_rr0[tid];
     s_rr[tid] = rr;
@@ -115,7 +181,7 @@ __global__ void __launch_bounds__(kSmallThreads) k_colcg_small(const float2* __r
     }
   }
   __syncthreads();
-  for (int it = 0; it < max_iter; ++it) {
+  for (int it = 0; it < max_iter && alive; ++it) {
     // which systems take this update (block-uniform "any" decides whether to go on)
     if (tid == 0) *s_any = 0;
     __syncthreads();
@@ -126,7 +192,10 @@ __global__ void __launch_bounds__(kSmallThreads) k_colcg_small(const float2* __r
       if (live) *s_any = 1;
     }
     __syncthreads();
-    if (!*s_any) break;
+    // every block of a launch whose images all stopped leaves together; with
+    // GLOBAL and several image groups the blocks keep the same number of
+    // barriers by running the remaining updates as no-ops
+    if (!*s_any && (!GLOBAL || gridDim.y == 1)) break;
     // p = r + beta p
 #pragma unroll
     for (int k = 0; k < E; ++k) {
@@ -156,6 +225,7 @@ __global__ void __launch_bounds__(kSmallThreads) k_colcg_small(const float2* __r
       v[k] = (double)pe.x * q[k].x + (double)pe.y * q[k].y;
     }
     image_sums<NY, T>(v, red, s_tmp);
+    if (!whole_image(s_tmp, part_pq)) break;
     if (tid < T) {
       float a = 0.f;
       if (s_live[tid]) {
@@ -183,6 +253,9 @@ __global__ void __launch_bounds__(kSmallThreads) k_colcg_small(const float2* __r
       v[k] = (double)r[k].x * r[k].x + (double)r[k].y * r[k].y;
     }
     image_sums<NY, T>(v, red, s_tmp);
+    if (tid < T && b0 + tid < nb) rr_out[(size_t)(b0 + tid) * nx + j] = s_tmp[tid];  // this column's ||r_j||^2
+    __syncthreads();
+    if (!whole_image(s_tmp, part_rr)) break;
     if (tid < T && s_live[tid]) {
       const double rrn = s_tmp[tid];
       s_beta[tid] = (float)(rrn / s_rr[tid]);
@@ -197,10 +270,7 @@ __global__ void __launch_bounds__(kSmallThreads) k_colcg_small(const float2* __r
     const int e = k * kSmallThreads + tid, t = e / NY, y = e % NY, b = b0 + t;
     if (b < nb) X[(size_t)b * n + (int64_t)y * nx + j] = x[k];
   }
-  if (tid < T && b0 + tid < nb) {
-    rr0_out[(size_t)(b0 + tid) * nx + j] = s_rr0[tid];
-    rr_out[(size_t)(b0 + tid) * nx + j] = s_rr[tid];
-  }
+  if (!GLOBAL && tid < T && b0 + tid < nb) rr_out[(size_t)(b0 + tid) * nx + j] = s_rr[tid];
 }
 
 template <int NY, int T>
@@ -209,13 +279,49 @@ size_t small_smem() {
 }
 
 template <int NY, int T>
-void launch_small(const float2* G, const float2* rhs, float2* X, int nx, int nb, int max_iter, double rtol2,
-                  float lam, double* rr0, double* rr, int* iters, int* status, cudaStream_t s) {
+bool launch_small(const float2* G, const float2* rhs, float2* X, int nx, int nb, int max_iter, double rtol2,
+                  float lam, double* rr0, double* rr, int* iters, int* status, const SmallGlobal* glob,
+                  cudaStream_t s) {
   const size_t sm = small_smem<NY, T>();
-  auto k = k_colcg_small<NY, T>;
+  if (!glob) {
+    auto k = k_colcg_small<NY, T, false>;
+    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k<<<dim3(nx, (nb + T - 1) / T), kSmallThreads, sm, s>>>(G, rhs, X, nx, nb, max_iter, rtol2, lam, rr0, rr, iters,
+                                                            status, nullptr, nullptr, nullptr, nullptr);
+    return true;
+  }
+  // whole-image CG: a cooperative launch (every block resident for the grid
+  // barriers); batches whose blocks do not all fit run as several launches
+  auto k = k_colcg_small<NY, T, true>;
   cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  k<<<dim3(nx, (nb + T - 1) / T), kSmallThreads, sm, s>>>(G, rhs, X, nx, nb, max_iter, rtol2, lam, rr0, rr, iters,
-                                                          status);
+  int dev = 0, nsm = 0, per = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k, kSmallThreads, sm) != cudaSuccess) return false;
+  const int groups = (per * nsm) / nx;  // image groups of T per launch
+  if (groups < 1) return false;
+  for (int c0 = 0; c0 < nb; c0 += groups * T) {
+    const int cn = nb - c0 < groups * T ? nb - c0 : groups * T;
+    cudaMemsetAsync(glob->bar, 0, 2 * sizeof(unsigned), s);
+    const float2* rhs_c = rhs + (size_t)c0 * NY * nx;
+    float2* X_c = X + (size_t)c0 * NY * nx;
+    double* rr0_c = rr0 + (size_t)c0 * nx;
+    double* rr_c = rr + (size_t)c0 * nx;
+    int* it_c = iters + (size_t)c0 * nx;
+    int* st_c = status + c0;
+    double* pq_c = glob->part_pq + (size_t)c0 * nx;
+    double* pr_c = glob->part_rr + (size_t)c0 * nx;
+    unsigned* bar = glob->bar;
+    int* err = glob->err;
+    int cnb = cn;
+    void* args[] = {(void*)&G, (void*)&rhs_c, (void*)&X_c, (void*)&nx, (void*)&cnb, (void*)&max_iter,
+                    (void*)&rtol2, (void*)&lam, (void*)&rr0_c, (void*)&rr_c, (void*)&it_c, (void*)&st_c,
+                    (void*)&pq_c, (void*)&pr_c, (void*)&bar, (void*)&err};
+    if (cudaLaunchCooperativeKernel((const void*)k, dim3(nx, (cn + T - 1) / T), dim3(kSmallThreads), args, sm, s) !=
+        cudaSuccess)
+      return false;
+  }
+  return true;
 }
 
 }  // namespace
@@ -242,17 +348,16 @@ void launch_colcg_small_build(const float2* smaps, const uint8_t* mask_host, int
   cudaStreamSynchronize(s);  // P lives on the host stack until the copy has run
 }
 
-void launch_colcg_small(const float2* G, const float2* rhs, float2* X, int ny, int nx, int nb, int max_iter,
-                        double rtol2, float lam, double* rr0, double* rr, int* iters, int* status, cudaStream_t s) {
-  if (nb <= 0) return;
-  // images per block: 32 for ny = 32 and 64 (128 blocks for 64 columns and 64
-  // images), 16 for ny = 96 (shared memory)
-  if (ny == 32)
-    launch_small<32, 32>(G, rhs, X, nx, nb, max_iter, rtol2, lam, rr0, rr, iters, status, s);
-  else if (ny == 64)
-    launch_small<64, 16>(G, rhs, X, nx, nb, max_iter, rtol2, lam, rr0, rr, iters, status, s);
-  else if (ny == 96)
-    launch_small<96, 16>(G, rhs, X, nx, nb, max_iter, rtol2, lam, rr0, rr, iters, status, s);
+bool launch_colcg_small(const float2* G, const float2* rhs, float2* X, int ny, int nx, int nb, int max_iter,
+                        double rtol2, float lam, double* rr0, double* rr, int* iters, int* status,
+                        const SmallGlobal* glob, cudaStream_t s) {
+  if (nb <= 0) return true;
+  // images per block: 32 for ny = 32, 16 for ny = 64 (128 blocks for 64
+  // columns and 32 images) and ny = 96 (shared memory)
+  if (ny == 32) return launch_small<32, 32>(G, rhs, X, nx, nb, max_iter, rtol2, lam, rr0, rr, iters, status, glob, s);
+  if (ny == 64) return launch_small<64, 16>(G, rhs, X, nx, nb, max_iter, rtol2, lam, rr0, rr, iters, status, glob, s);
+  if (ny == 96) return launch_small<96, 16>(G, rhs, X, nx, nb, max_iter, rtol2, lam, rr0, rr, iters, status, glob, s);
+  return false;
 }
 
 }  // namespace pico

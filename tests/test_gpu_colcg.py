@@ -173,7 +173,7 @@ def test_small_images_whole_solve_on_chip_matches_the_oracle(ny, nx, nc, nb, lam
     S = synth.coil_maps(ny, nx, nc, 2)
     mask = synth.mask_pe(ny, 2, 0 if ny == 64 else 4)
     op = pico.Operator(S, mask=mask, lam=lam, power_iters=0, max_batch=nb)
-    assert op.info["normal_op"] == 0
+    assert op.info["normal_op"] == 3
     op.set_solver("columns")
     rhs = rand_imgs(nb, ny, nx, 6)
     x, iters, relres = op.cg(torch.from_numpy(rhs).cuda(), 30, 0.0, stats=True)
@@ -205,4 +205,31 @@ def test_small_images_pico_and_pmr_maps_same_seed():
     d, _, _ = OP.column_exact(oop)
     assert (np.abs(s.cpu().numpy() - so) / K / d).max() < 1e-4
     assert (np.abs(pm.cpu().numpy() - po) / K / d).max() < 1e-4
+    op.close()
+
+
+@pytest.mark.parametrize("ny,nx,nc,nb,lam", [(64, 64, 8, 32, 0.0), (32, 24, 4, 70, 0.05), (96, 20, 6, 9, 0.0)])
+def test_small_images_whole_image_cg_on_chip_matches_the_oracle(ny, nx, nc, nb, lam):
+    """The default (whole-image) CG of small phase-encode images on chip: one
+    cooperative launch per solve, per-column partial sums added across the
+    grid between grid barriers; the same CG as the oracle's solvers.cg."""
+    S = synth.coil_maps(ny, nx, nc, 5)
+    mask = synth.mask_pe(ny, 2, 4)
+    op = pico.Operator(S, mask=mask, lam=lam, power_iters=0, max_batch=nb)
+    assert op.info["normal_op"] == 3 and op.solver == pico.PICO_SOLVER_GLOBAL
+    oop = O.Operator(S, None, mask=mask)
+    rhs = rand_imgs(nb, ny, nx, 8)
+    x, iters, relres = op.cg(torch.from_numpy(rhs).cuda(), 30, 0.0, stats=True)
+    op.sync()
+    x = x.cpu().numpy()
+    for b in sorted({0, nb // 2, nb - 1}):
+        xo, ito, relo = OS.cg(lambda z: oop.normal(z, lam), rhs[b].astype(np.complex128), 30, 0.0)
+        assert np.abs(x[b] - xo).max() / np.abs(xo).max() < 1e-4, b
+        assert iters[b] == ito and abs(relres[b] - relo) <= 1e-3 * relo + 1e-6
+    # stopping rule: every image of the batch on its own
+    x2, it2, rel2 = op.cg(torch.from_numpy(rhs).cuda(), 100, 1e-3, stats=True)
+    op.sync()
+    for b in (0, nb - 1):
+        _, ito, _ = OS.cg(lambda z: oop.normal(z, lam), rhs[b].astype(np.complex128), 100, 1e-3)
+        assert abs(int(it2[b]) - ito) <= 1 and rel2[b] <= 1e-3
     op.close()

@@ -115,7 +115,9 @@ def test_path_selection():
     assert pico.Operator(S, mask=mask, noise_cov=cov, power_iters=0).info["normal_op"] == 1
     assert fft_path_operator(S, mask=mask, noise_cov=cov, power_iters=0).info["normal_op"] == 0
     S, cov, mask = case(64, 64, 4)
-    assert pico.Operator(S, mask=mask, noise_cov=cov, power_iters=0).info["normal_op"] == 0
+    # ny = 64: the solves run on chip (dense G_j in shared memory); PICO_NORMAL_OP=fft keeps the column FFTs
+    assert pico.Operator(S, mask=mask, noise_cov=cov, power_iters=0).info["normal_op"] == 3
+    assert fft_path_operator(S, mask=mask, noise_cov=cov, power_iters=0).info["normal_op"] == 0
 
 
 # (ny, nx): one and two output-row tiles, ragged column counts, several tile widths
