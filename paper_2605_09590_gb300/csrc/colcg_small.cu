@@ -144,11 +144,18 @@ __global__ void __launch_bounds__(kSmallThreads) k_colcg_small(const float2* __r
     if (!GLOBAL) return true;
     if (threadIdx.x < T && b0 + (int)threadIdx.x < nb) part[(size_t)(b0 + threadIdx.x) * nx + j] = col[threadIdx.x];
     const bool ok = grid_barrier(bar, bar + 1, nblocks, err, s_ok);
-    if (threadIdx.x < T && b0 + (int)threadIdx.x < nb) {
+    // warp w adds the nx column sums of images w, w + 8, ...: lane l loads columns
+    // l, l + 32, ... (from L2: other blocks wrote them since the last read), then
+    // a fixed shuffle tree -- the same order in every block
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int t = w; t < T; t += kSmallThreads / 32) {
       double a = 0.0;
-      const double* pp = part + (size_t)(b0 + threadIdx.x) * nx;
-      for (int jj = 0; jj < nx; ++jj) a += __ldcg(pp + jj);  // L2: other blocks wrote these since the last read
-      col[threadIdx.x] = a;
+      if (b0 + t < nb) {
+        const double* pp = part + (size_t)(b0 + t) * nx;
+        for (int jj = lane; jj < nx; jj += 32) a += __ldcg(pp + jj);
+      }
+      a = warp_sum_d(a);
+      if (lane == 0 && b0 + t < nb) col[t] = a;
     }
     __syncthreads();
     return ok;

@@ -63,7 +63,9 @@ def test_gram_chunk_change_rebuilds_the_operator():
         want = oop.normal(x[b].astype(np.complex128))
         for y in (y16, y8):
             assert np.linalg.norm(y[b] - want) / np.linalg.norm(want) < 1e-5
-    assert np.abs(y8 - y16).max() / np.abs(y16).max() < 1e-6
+    # kc = 16 runs the FP16 head + remainder split, kc = 8 the TF32 split: the same
+    # ~22 significant bits per product, rounded differently
+    assert np.abs(y8 - y16).max() / np.abs(y16).max() < 1e-5
 
 
 def test_autotune_choices_follow_its_measurements():

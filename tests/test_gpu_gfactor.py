@@ -11,11 +11,13 @@ the GPU, combined by pico_gfactor, against the oracle.
     alias blocks), the fully sampled reference map is exact (one probe,
     diagonal covariance), and the GPU g map agrees with the closed-form g to
     the delta-method bound of that band.
-* Spiral 64 x 64 (the reference reading for lam > 0: all interleaves, lam = 0,
-  same coils; R = interleaves / kept interleaves): the GPU maps equal the
-  oracle's same-seed maps to 1e-4 of the largest exact variance at every voxel,
-  the g maps agree to the bound that follows from it, and the 256-probe g map
-  is within sampling error of the g of the exact dense covariances.
+* Spiral 64 x 64 (the reference reading for lam > 0: all interleaves, the same
+  coils and the same physical Tikhonov weight -- without it the reference is
+  singular, the spiral leaves the k-space corners unsampled; R = interleaves /
+  kept interleaves): the GPU maps equal the oracle's same-seed maps to 1e-4 of
+  the largest exact variance at every voxel, the g maps agree to the bound that
+  follows from it, and the 256-probe g map is within sampling error of the g of
+  the exact dense covariances.
 """
 import numpy as np
 import pytest
@@ -87,29 +89,29 @@ def test_cartesian_gfactor_same_seed_and_closed_form():
 
 
 def test_spiral_gfactor_with_unregularised_full_reference():
-    n, nc, L, ns = 64, 6, 8, 512
+    n, nc, L, ns = 64, 6, 16, 512
     S = synth.coil_maps(n, n, nc, 4)
     R = 2
     traj_acc = synth.spiral_traj(n, L, ns, R)
     traj_ref = synth.spiral_traj(n, L, ns, 1)
+    oacc = O.Operator(S, None, traj=traj_acc)
+    oref = O.Operator(S, None, traj=traj_ref)
+    lam_a, _ = OP.lambda_phys(oacc, 0.1)                # one physical weight for both reconstructions
     K, seed = 256, 909
-    acc = pico.Operator(S, traj=traj_acc, lam=0.1, power_iters=15, max_batch=K)
-    ref = pico.Operator(S, traj=traj_ref, lam=0.0, power_iters=15, max_batch=K)
+    acc = pico.Operator(S, traj=traj_acc, lam=lam_a, power_iters=0, max_batch=K)
+    ref = pico.Operator(S, traj=traj_ref, lam=lam_a, power_iters=0, max_batch=K)
     va, sa = _map(acc, seed, K, 60)
     vr, sr = _map(ref, seed + 1, K, 60)
     g = _g(acc, va, vr, float(L) / (L // R))
     # same seed against the oracle's CG maps (a few probes)
     Ka = 8
-    oacc = O.Operator(S, None, traj=traj_acc)
-    oref = O.Operator(S, None, traj=traj_ref)
-    lam_a, _ = OP.lambda_phys(oacc, 0.1)
     va8, sa8 = _map(acc, seed, Ka, 60)
     vr8, sr8 = _map(ref, seed + 1, Ka, 60)
     oa, _ = OP.pico(oacc, seed, 0, Ka, lam_a, 60, 0.0)
-    orf, _ = OP.pico(oref, seed + 1, 0, Ka, 0.0, 60, 0.0)
+    orf, _ = OP.pico(oref, seed + 1, 0, Ka, lam_a, 60, 0.0)
     g8 = _g(acc, va8, vr8, float(L) / (L // R))
     Sa = OP.dense_cov(OP.dense_normal(oacc), lam_a)
-    Sr = OP.dense_cov(OP.dense_normal(oref))
+    Sr = OP.dense_cov(OP.dense_normal(oref), lam_a)
     da, dr = np.real(np.diag(Sa)).reshape(n, n), np.real(np.diag(Sr)).reshape(n, n)
     assert np.abs(sa8 - oa).max() / Ka < 1e-4 * da.max()
     assert np.abs(sr8 - orf).max() / Ka < 1e-4 * dr.max()
