@@ -10,9 +10,11 @@
 // vectors x, r, p, q of a group of images of that column in shared memory and
 // runs every CG update of the solve in one launch: a latency-bound workload
 // (64 x 64 images, 32 probes) then needs one kernel per solve instead of
-// three per update.  Inner products are FP64 (fixed-order reductions, so the
-// result does not depend on the launch shape); each column stops on its own
-// test ||r_j|| <= rtol ||b_j||.
+// three per update.  Inner products take exact float products summed in
+// float-float within a warp and FP64 across warps and columns (fixed-order
+// reductions, so the result does not depend on the launch shape; the FP64
+// pipe, a small fraction of the FP32 rate, would otherwise bound the solve);
+// each column stops on its own test ||r_j|| <= rtol ||b_j||.
 #include "common.cuh"
 #include "kernels.cuh"
 
@@ -45,17 +47,17 @@ __global__ void k_colcg_small_build(const float2* __restrict__ S, const double2*
 
 // Sum over the NY rows of every image of a per-element value held by the
 // thread that owns element e = k * kSmallThreads + tid (image e / NY, row
-// e % NY): a warp's 32 elements belong to one image; warp sums go to
-// red[t][w], then thread t adds its NY / 32 slots in order.
+// e % NY): a warp's 32 elements belong to one image; warp sums (float-float)
+// go to red[t][w] as doubles, then thread t adds its NY / 32 slots in order.
 template <int NY, int T>
-__device__ __forceinline__ void image_sums(const double (&v)[NY * T / kSmallThreads], double* red, double* out) {
+__device__ __forceinline__ void image_sums(const ffloat (&v)[NY * T / kSmallThreads], double* red, double* out) {
   constexpr int E = NY * T / kSmallThreads;
   const int lane = threadIdx.x & 31;
 #pragma unroll
   for (int k = 0; k < E; ++k) {
-    const double s = warp_sum_d(v[k]);
+    const ffloat s = warp_sum_ff(v[k]);
     const int e = k * kSmallThreads + threadIdx.x;
-    if (lane == 0) red[(e / NY) * (NY / 32) + (e % NY) / 32] = s;
+    if (lane == 0) red[(e / NY) * (NY / 32) + (e % NY) / 32] = (double)s.hi + (double)s.lo;
   }
   __syncthreads();
   if (threadIdx.x < T) {
@@ -163,13 +165,13 @@ __global__ void __launch_bounds__(kSmallThreads) k_colcg_small(const float2* __r
   for (int i = tid; i < NY * NY; i += kSmallThreads) Gs[i] = G[(size_t)j * NY * NY + i];
   // this thread's elements: image t = e / NY, row y = e % NY (a warp's 32 share t)
   float2 x[E], r[E], q[E];
-  double v[E];
+  ffloat v[E];
 #pragma unroll
   for (int k = 0; k < E; ++k) {
     const int e = k * kSmallThreads + tid, t = e / NY, y = e % NY, b = b0 + t;
     r[k] = b < nb ? rhs[(size_t)b * n + (int64_t)y * nx + j] : make_float2(0.f, 0.f);
     x[k] = make_float2(0.f, 0.f);
-    v[k] = (double)r[k].x * r[k].x + (double)r[k].y * r[k].y;
+    v[k] = ff_dot2(r[k], r[k]);
   }
   image_sums<NY, T>(v, red, s_rr0);
   if (tid < T && b0 + tid < nb) {  // this column's ||b_j||^2 (and ||r_j||^2 until an update)
@@ -216,20 +218,46 @@ __global__ void __launch_bounds__(kSmallThreads) k_colcg_small(const float2* __r
     __syncthreads();
     // q = (G_j + lam) p: q[y] = sum_y' G[y][y'] p[y'] = sum_y' conj(G[y'][y]) p[y'] (Hermitian);
     // a warp reads G[y'][y .. y+31] (consecutive) and broadcasts p[t][y']
+    if constexpr (kSmallThreads % NY == 0) {
+      // a thread's E elements share the row y = tid % NY (images tid / NY + k * kSmallThreads / NY):
+      // one read of G[y'][y] serves all E, two y' per step (p as float4)
+      constexpr int IPK = kSmallThreads / NY;
+      const int y = tid % NY, t0 = tid / NY;
+      float ar[E], ai[E];
 #pragma unroll
-    for (int k = 0; k < E; ++k) {
-      const int e = k * kSmallThreads + tid, t = e / NY, y = e % NY;
-      const float2* pt = ps + t * NY;
-      float ar = 0.f, ai = 0.f;
-#pragma unroll 8
-      for (int yp = 0; yp < NY; ++yp) {
-        const float2 g = Gs[yp * NY + y], p = pt[yp];
-        ar = fmaf(g.x, p.x, fmaf(g.y, p.y, ar));   // Re(conj(g) p)
-        ai = fmaf(g.x, p.y, fmaf(-g.y, p.x, ai));  // Im(conj(g) p)
+      for (int k = 0; k < E; ++k) ar[k] = ai[k] = 0.f;
+#pragma unroll 4
+      for (int yp = 0; yp < NY; yp += 2) {
+        const float2 g0 = Gs[yp * NY + y], g1 = Gs[(yp + 1) * NY + y];
+#pragma unroll
+        for (int k = 0; k < E; ++k) {
+          const float4 p = *reinterpret_cast<const float4*>(ps + (k * IPK + t0) * NY + yp);
+          ar[k] = fmaf(g1.x, p.z, fmaf(g1.y, p.w, fmaf(g0.x, p.x, fmaf(g0.y, p.y, ar[k]))));
+          ai[k] = fmaf(g1.x, p.w, fmaf(-g1.y, p.z, fmaf(g0.x, p.y, fmaf(-g0.y, p.x, ai[k]))));
+        }
       }
-      const float2 pe = pt[y];
-      q[k] = make_float2(fmaf(lam, pe.x, ar), fmaf(lam, pe.y, ai));
-      v[k] = (double)pe.x * q[k].x + (double)pe.y * q[k].y;
+#pragma unroll
+      for (int k = 0; k < E; ++k) {
+        const float2 pe = ps[(k * IPK + t0) * NY + y];
+        q[k] = make_float2(fmaf(lam, pe.x, ar[k]), fmaf(lam, pe.y, ai[k]));
+        v[k] = ff_dot2(pe, q[k]);
+      }
+    } else {
+#pragma unroll
+      for (int k = 0; k < E; ++k) {
+        const int e = k * kSmallThreads + tid, t = e / NY, y = e % NY;
+        const float2* pt = ps + t * NY;
+        float ar = 0.f, ai = 0.f;
+#pragma unroll 8
+        for (int yp = 0; yp < NY; ++yp) {
+          const float2 g = Gs[yp * NY + y], p = pt[yp];
+          ar = fmaf(g.x, p.x, fmaf(g.y, p.y, ar));   // Re(conj(g) p)
+          ai = fmaf(g.x, p.y, fmaf(-g.y, p.x, ai));  // Im(conj(g) p)
+        }
+        const float2 pe = pt[y];
+        q[k] = make_float2(fmaf(lam, pe.x, ar), fmaf(lam, pe.y, ai));
+        v[k] = ff_dot2(pe, q[k]);
+      }
     }
     image_sums<NY, T>(v, red, s_tmp);
     if (!whole_image(s_tmp, part_pq)) break;
@@ -257,7 +285,7 @@ __global__ void __launch_bounds__(kSmallThreads) k_colcg_small(const float2* __r
         x[k] = make_float2(fmaf(a, p.x, x[k].x), fmaf(a, p.y, x[k].y));
         r[k] = make_float2(fmaf(-a, q[k].x, r[k].x), fmaf(-a, q[k].y, r[k].y));
       }
-      v[k] = (double)r[k].x * r[k].x + (double)r[k].y * r[k].y;
+      v[k] = ff_dot2(r[k], r[k]);
     }
     image_sums<NY, T>(v, red, s_tmp);
     if (tid < T && b0 + tid < nb) rr_out[(size_t)(b0 + tid) * nx + j] = s_tmp[tid];  // this column's ||r_j||^2

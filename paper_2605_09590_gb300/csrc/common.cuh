@@ -95,6 +95,38 @@ __device__ __forceinline__ float warp_sum_f(float v) {
   return v;
 }
 
+// Float-float values hi + lo (|lo| <= ulp(hi) / 2): sums carried to about 44
+// bits on the FP32 pipes, for inner products in latency-bound kernels where the
+// FP64 pipe (a small fraction of the FP32 rate on this part) would set the
+// pace.  The product of two floats is exact as hi + lo with one FMA (Dekker
+// 1971); the sum takes Knuth's TwoSum of the high parts (exact rounding error)
+// and adds the low parts once.  Explicit _rn intrinsics: no contraction.
+struct ffloat {
+  float hi, lo;
+};
+__device__ __forceinline__ ffloat ff_prod(float a, float b) {
+  const float p = __fmul_rn(a, b);
+  return {p, __fmaf_rn(a, b, -p)};
+}
+__device__ __forceinline__ ffloat ff_add(ffloat a, ffloat b) {
+  const float s = __fadd_rn(a.hi, b.hi);
+  const float bb = __fsub_rn(s, a.hi);
+  const float e = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bb)), __fsub_rn(b.hi, bb));
+  const float t = __fadd_rn(e, __fadd_rn(a.lo, b.lo));
+  const float h = __fadd_rn(s, t);
+  return {h, __fsub_rn(t, __fsub_rn(h, s))};
+}
+// Re(conj(a) b) of two complex floats, both products exact before the sum
+__device__ __forceinline__ ffloat ff_dot2(float2 a, float2 b) { return ff_add(ff_prod(a.x, b.x), ff_prod(a.y, b.y)); }
+// xor-butterfly warp sum (the exact TwoSum error makes ff_add commutative
+// bit for bit, so every lane ends with the same value)
+__device__ __forceinline__ ffloat warp_sum_ff(ffloat v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1)
+    v = ff_add(v, ffloat{__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o)});
+  return v;
+}
+
 // Block-wide sum of one double per thread, fixed order; valid in thread 0.
 // `scratch` needs blockDim.x/32 doubles of shared memory.
 __device__ __forceinline__ double block_sum_d(double v, double* scratch) {

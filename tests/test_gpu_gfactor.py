@@ -88,7 +88,7 @@ def test_cartesian_gfactor_same_seed_and_closed_form():
     ref.close()
 
 
-def test_spiral_gfactor_with_unregularised_full_reference():
+def test_spiral_gfactor_with_fully_sampled_reference():
     n, nc, L, ns = 64, 6, 16, 512
     S = synth.coil_maps(n, n, nc, 4)
     R = 2
