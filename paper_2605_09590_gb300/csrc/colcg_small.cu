@@ -49,8 +49,10 @@ __global__ void k_colcg_small_build(const float2* __restrict__ S, const double2*
 // thread that owns element e = k * kSmallThreads + tid (image e / NY, row
 // e % NY): a warp's 32 elements belong to one image; warp sums (float-float)
 // go to red[t][w] as doubles, then thread t adds its NY / 32 slots in order.
+// `un[t]` undoes the power-of-two scaling of image t's values (sum * 2^un[t]).
 template <int NY, int T>
-__device__ __forceinline__ void image_sums(const ffloat (&v)[NY * T / kSmallThreads], double* red, double* out) {
+__device__ __forceinline__ void image_sums(const ffloat (&v)[NY * T / kSmallThreads], double* red, const int* un,
+                                           double* out) {
   constexpr int E = NY * T / kSmallThreads;
   const int lane = threadIdx.x & 31;
 #pragma unroll
@@ -64,9 +66,52 @@ __device__ __forceinline__ void image_sums(const ffloat (&v)[NY * T / kSmallThre
     double s = 0.0;
 #pragma unroll
     for (int w = 0; w < NY / 32; ++w) s += red[threadIdx.x * (NY / 32) + w];
-    out[threadIdx.x] = s;
+    out[threadIdx.x] = s * __longlong_as_double((long long)(1023 + un[threadIdx.x]) << 52);  // exact: |un| <= 240
   }
   __syncthreads();
+}
+
+// Largest |component| over the NY rows of every image (same element ownership
+// as image_sums); thread t < T gets its image's value.
+template <int NY, int T>
+__device__ __forceinline__ float image_max(const float (&v)[NY * T / kSmallThreads], float* red) {
+  constexpr int E = NY * T / kSmallThreads;
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int k = 0; k < E; ++k) {
+    float m = v[k];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    const int e = k * kSmallThreads + threadIdx.x;
+    if (lane == 0) red[(e / NY) * (NY / 32) + (e % NY) / 32] = m;
+  }
+  __syncthreads();
+  float m = 0.f;
+  if (threadIdx.x < T)
+    for (int w = 0; w < NY / 32; ++w) m = fmaxf(m, red[threadIdx.x * (NY / 32) + w]);
+  __syncthreads();
+  return m;
+}
+
+// Power-of-two scaling keeps the float-float products clear of FP32 underflow
+// and overflow: values are multiplied by 2^e before the exact products and the
+// sum by 2^-e afterwards (both exact in the normal range).
+__device__ __forceinline__ int clamp_exp(int e) { return e < -120 ? -120 : (e > 120 ? 120 : e); }
+__device__ __forceinline__ float pow2f(int e) { return __int_as_float((127 + e) << 23); }
+// binary exponent e of a > 0 with a = m 2^e, m in [0.5, 1) (normal doubles;
+// every value here is a sum of squares of floats, far above the subnormals)
+__device__ __forceinline__ int exp_of(double a) {
+  return (int)((__double_as_longlong(a) >> 52) & 0x7ff) - 1022;
+}
+// e with a * 2^e in [0.5, 1) (0 for zero or non-finite a)
+__device__ __forceinline__ int inv_exp(double a) {
+  if (!(a > 0.0) || !isfinite(a)) return 0;
+  return clamp_exp(-exp_of(a));
+}
+// e with ||r|| * 2^e near 1, from rr = ||r||^2
+__device__ __forceinline__ int inv_exp_sqrt(double rr) {
+  if (!(rr > 0.0) || !isfinite(rr)) return 0;
+  return clamp_exp(-(exp_of(rr) >> 1));
 }
 
 // Grid-wide barrier of a cooperative launch (all blocks resident): the last
@@ -115,7 +160,7 @@ __device__ __forceinline__ bool grid_barrier(unsigned* count, unsigned* gen, uns
 // in column order, so all blocks take the same alpha and beta (Eq. 6 CG with
 // the operator applied column by column).
 template <int NY, int T, bool GLOBAL>
-__global__ void __launch_bounds__(kSmallThreads) k_colcg_small(const float2* __restrict__ G, const float2* __restrict__ rhs,
+__global__ void __launch_bounds__(kSmallThreads, 2) k_colcg_small(const float2* __restrict__ G, const float2* __restrict__ rhs,
                                                             float2* __restrict__ X, int nx, int nb, int max_iter,
                                                             double rtol2, float lam, double* __restrict__ rr0_out,
                                                             double* __restrict__ rr_out, int* __restrict__ iters_out,
@@ -137,6 +182,18 @@ __global__ void __launch_bounds__(kSmallThreads) k_colcg_small(const float2* __r
   int* s_live = reinterpret_cast<int*>(s_beta + T);
   int* s_any = s_live + T;
   int* s_ok = s_any + 1;
+  int* s_er = s_ok + 1;    // [T] scale exponent of r and p (from ||r||)
+  int* s_eq = s_er + T;    // [T] scale exponent of q = (G_j + lam) p
+  int* s_unpq = s_eq + T;  // [T] -(er + eq): undoes the scaling of p^H q
+  int* s_unrr = s_unpq + T;  // [T] -2 er: undoes the scaling of r^H r
+  int* s_eg = s_unrr + T;  // exponent that brings max(|G_j|, lam) to [0.5, 1)
+  auto set_scales = [&](int t, double rr) {  // thread t < T, after s_rr[t] changes
+    const int er = inv_exp_sqrt(rr), eq = clamp_exp(er + *s_eg);
+    s_er[t] = er;
+    s_eq[t] = eq;
+    s_unpq[t] = -(er + eq);
+    s_unrr[t] = -2 * er;
+  };
 
   const int j = blockIdx.x, b0 = blockIdx.y * T, tid = threadIdx.x;
   const int64_t n = (int64_t)NY * nx;
@@ -162,18 +219,52 @@ __global__ void __launch_bounds__(kSmallThreads) k_colcg_small(const float2* __r
     __syncthreads();
     return ok;
   };
-  for (int i = tid; i < NY * NY; i += kSmallThreads) Gs[i] = G[(size_t)j * NY * NY + i];
+  float gmax = lam > 0.f ? lam : 0.f;
+  for (int i = tid; i < NY * NY; i += kSmallThreads) {
+    const float2 g = G[(size_t)j * NY * NY + i];
+    Gs[i] = g;
+    gmax = fmaxf(gmax, fmaxf(fabsf(g.x), fabsf(g.y)));
+  }
+  {
+    float* redf = reinterpret_cast<float*>(red);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) gmax = fmaxf(gmax, __shfl_xor_sync(0xffffffffu, gmax, o));
+    if ((tid & 31) == 0) redf[tid >> 5] = gmax;
+    __syncthreads();
+    if (tid == 0) {
+      float m = 0.f;
+      for (int w = 0; w < kSmallThreads / 32; ++w) m = fmaxf(m, redf[w]);
+      *s_eg = inv_exp(m);
+    }
+    __syncthreads();
+  }
   // this thread's elements: image t = e / NY, row y = e % NY (a warp's 32 share t)
   float2 x[E], r[E], q[E];
   ffloat v[E];
+  float am[E];
 #pragma unroll
   for (int k = 0; k < E; ++k) {
     const int e = k * kSmallThreads + tid, t = e / NY, y = e % NY, b = b0 + t;
     r[k] = b < nb ? rhs[(size_t)b * n + (int64_t)y * nx + j] : make_float2(0.f, 0.f);
     x[k] = make_float2(0.f, 0.f);
-    v[k] = ff_dot2(r[k], r[k]);
+    am[k] = fmaxf(fabsf(r[k].x), fabsf(r[k].y));
   }
-  image_sums<NY, T>(v, red, s_rr0);
+  {  // ||b_j||^2 with b scaled by its largest component
+    const float m = image_max<NY, T>(am, reinterpret_cast<float*>(red));
+    if (tid < T) {
+      s_er[tid] = inv_exp(m);
+      s_unrr[tid] = -2 * s_er[tid];
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int k = 0; k < E; ++k) {
+    const int t = (k * kSmallThreads + tid) / NY;
+    const float f = pow2f(s_er[t]);
+    const float2 rs = make_float2(r[k].x * f, r[k].y * f);
+    v[k] = ff_dot2(rs, rs);
+  }
+  image_sums<NY, T>(v, red, s_unrr, s_rr0);
   if (tid < T && b0 + tid < nb) {  // this column's ||b_j||^2 (and ||r_j||^2 until an update)
     rr0_out[(size_t)(b0 + tid) * nx + j] = s_rr0[tid];
     rr_out[(size_t)(b0 + tid) * nx + j] = s_rr0[tid];
@@ -183,6 +274,7 @@ __global__ void __launch_bounds__(kSmallThreads) k_colcg_small(const float2* __r
   if (tid < T) {
     const double rr = s_rr0[tid];
     s_rr[tid] = rr;
+    set_scales(tid, rr);
     s_beta[tid] = 0.f;
     if (b0 + tid < nb) {
       iters_out[(size_t)(b0 + tid) * nx + j] = 0;
@@ -238,9 +330,11 @@ __global__ void __launch_bounds__(kSmallThreads) k_colcg_small(const float2* __r
       }
 #pragma unroll
       for (int k = 0; k < E; ++k) {
-        const float2 pe = ps[(k * IPK + t0) * NY + y];
+        const int t = k * IPK + t0;
+        const float2 pe = ps[t * NY + y];
         q[k] = make_float2(fmaf(lam, pe.x, ar[k]), fmaf(lam, pe.y, ai[k]));
-        v[k] = ff_dot2(pe, q[k]);
+        const float fp = pow2f(s_er[t]), fq = pow2f(s_eq[t]);
+        v[k] = ff_dot2(make_float2(pe.x * fp, pe.y * fp), make_float2(q[k].x * fq, q[k].y * fq));
       }
     } else {
 #pragma unroll
@@ -256,10 +350,11 @@ __global__ void __launch_bounds__(kSmallThreads) k_colcg_small(const float2* __r
         }
         const float2 pe = pt[y];
         q[k] = make_float2(fmaf(lam, pe.x, ar), fmaf(lam, pe.y, ai));
-        v[k] = ff_dot2(pe, q[k]);
+        const float fp = pow2f(s_er[t]), fq = pow2f(s_eq[t]);
+        v[k] = ff_dot2(make_float2(pe.x * fp, pe.y * fp), make_float2(q[k].x * fq, q[k].y * fq));
       }
     }
-    image_sums<NY, T>(v, red, s_tmp);
+    image_sums<NY, T>(v, red, s_unpq, s_tmp);
     if (!whole_image(s_tmp, part_pq)) break;
     if (tid < T) {
       float a = 0.f;
@@ -285,9 +380,11 @@ __global__ void __launch_bounds__(kSmallThreads) k_colcg_small(const float2* __r
         x[k] = make_float2(fmaf(a, p.x, x[k].x), fmaf(a, p.y, x[k].y));
         r[k] = make_float2(fmaf(-a, q[k].x, r[k].x), fmaf(-a, q[k].y, r[k].y));
       }
-      v[k] = ff_dot2(r[k], r[k]);
+      const float f = pow2f(s_er[t]);
+      const float2 rs = make_float2(r[k].x * f, r[k].y * f);
+      v[k] = ff_dot2(rs, rs);
     }
-    image_sums<NY, T>(v, red, s_tmp);
+    image_sums<NY, T>(v, red, s_unrr, s_tmp);
     if (tid < T && b0 + tid < nb) rr_out[(size_t)(b0 + tid) * nx + j] = s_tmp[tid];  // this column's ||r_j||^2
     __syncthreads();
     if (!whole_image(s_tmp, part_rr)) break;
@@ -295,6 +392,7 @@ __global__ void __launch_bounds__(kSmallThreads) k_colcg_small(const float2* __r
       const double rrn = s_tmp[tid];
       s_beta[tid] = (float)(rrn / s_rr[tid]);
       s_rr[tid] = rrn;
+      set_scales(tid, rrn);
       if (!isfinite(rrn)) status[b0 + tid] = 5;
       iters_out[(size_t)(b0 + tid) * nx + j] = it + 1;
     }
@@ -310,7 +408,8 @@ __global__ void __launch_bounds__(kSmallThreads) k_colcg_small(const float2* __r
 
 template <int NY, int T>
 size_t small_smem() {
-  return (size_t)NY * NY * 8 + (size_t)T * NY * 8 + (size_t)T * (NY / 32) * 8 + 3 * T * 8 + 2 * T * 4 + T * 4 + 16;
+  return (size_t)NY * NY * 8 + (size_t)T * NY * 8 + (size_t)T * (NY / 32) * 8 + 3 * T * 8 + 2 * T * 4 + T * 4 + 8 +
+         4 * T * 4 + 16;
 }
 
 template <int NY, int T>
