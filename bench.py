@@ -240,7 +240,7 @@ def onchip_roofline(w, K, avg_s, launches, solver):
     return {"bound": "alu", "achieved": flops / avg_s / 1e12, "peak": peak, "unit": "TFLOP/s",
             "frac": flops / avg_s / 1e12 / peak, "traffic": None,
             "kernel": ("k_colcg_small<NY,T,GLOBAL> (whole CG solve on chip, one cooperative launch per solve, "
-                       "grid barriers between the column sums)" if solver == "global" else
+                       "column sums exchanged within each image group)" if solver == "global" else
                        "k_colcg_small<NY,T> (whole per-column CG solve on chip, one launch per solve)"),
             "avg_launch_ms": avg_s * 1e3, "launches": launches,
             "peak_note": "FP32 FMA peak 152 SM x 128 lanes x 2 x 2070 MHz (nominal max clock)",

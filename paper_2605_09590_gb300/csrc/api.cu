@@ -100,9 +100,10 @@ struct pico_ctx {
   double* col_pn = nullptr;     // FP16 form: bound on each column direction's entries [B][nx]
   float* col_pscale = nullptr;
   float2* col_G = nullptr;  // small images: G_j of every column, [nx][ny][ny] (whole solve on chip)
+  float* col_gmax = nullptr;  // largest |component| of any G_j
   bool col_small = false;
   bool onchip = false;       // small phase-encode images: every CG solve runs on chip (either solver)
-  pico::SmallGlobal sglob{};  // whole-image CG on chip: column partials and the grid barrier
+  pico::SmallGlobal sglob{};  // whole-image CG on chip: column partials and exchange flags
   std::string host_fail;  // a launch that could not be issued (reported by the entry point)
   size_t device_bytes = 0, budget = 0;
   bool async_alloc = false;  // stream-ordered cudaMallocAsync / cudaFreeAsync (serving contexts)
@@ -445,12 +446,13 @@ void cg_iterations(pico_ctx* c, int nb, int max_iter, double rtol, float lam) {
 }
 
 // the whole CG solve of small images on chip (per column, or the whole image
-// with grid barriers): rhs in R, x to X (natural layout)
+// with sum exchanges between the blocks of an image group): rhs in R, x to X
+// (natural layout)
 void run_cg_small(pico_ctx* c, int nb, int max_iter, double rtol, float lam) {
   Launch L(c, 0);
   const pico::SmallGlobal* glob = c->solver == PICO_SOLVER_COLUMNS ? nullptr : &c->sglob;
-  if (!pico::launch_colcg_small(c->col_G, c->R, c->X, c->ny, c->nx, nb, max_iter, rtol * rtol, lam, c->col_rr0,
-                                c->col_rr, c->col_iters, c->status, glob, c->stream))
+  if (!pico::launch_colcg_small(c->col_G, c->col_gmax, c->R, c->X, c->ny, c->nx, nb, max_iter, rtol * rtol, lam,
+                                c->col_rr0, c->col_rr, c->col_iters, c->status, glob, c->stream))
     c->host_fail = "on-chip CG launch failed (cooperative launch of the whole-image solve)";
 }
 bool small_path(const pico_ctx* c) { return c->onchip || column_small(c); }
@@ -802,7 +804,8 @@ bool want_onchip(const pico_operator_desc* d) {
   return pico::colcg_small_supported(d->ny);
 }
 size_t onchip_extra_bytes(const pico_operator_desc* d, int64_t B) {
-  return (size_t)d->nx * d->ny * d->ny * 8 + (size_t)d->ny * 16 + (size_t)B * d->nx * (8 + 8 + 4 + 8 + 8) + 8;
+  return (size_t)d->nx * d->ny * d->ny * 8 + 4 + (size_t)d->ny * 16 + (size_t)B * d->nx * (8 + 8 + 4 + 8 + 8) +
+         (size_t)(B + 15) / 16 * d->nx * 4;
 }
 
 // G planes, second direction buffer and per-image scalars of the Gram mode
@@ -819,16 +822,18 @@ pico_status small_setup(pico_ctx* c, bool global) {
   const size_t n = (size_t)c->max_batch * c->nx;
   if (!c->col_G) {
     if ((st = dalloc(c, &c->col_G, (size_t)c->nx * c->ny * c->ny)) != PICO_OK) return st;
+    if ((st = dalloc(c, &c->col_gmax, (size_t)1)) != PICO_OK) return st;
     if (!c->g_pbuf && (st = dalloc(c, &c->g_pbuf, (size_t)c->ny)) != PICO_OK) return st;
-    pico::launch_colcg_small_build(c->smaps, c->gmask.data(), c->nc, c->ny, c->nx, c->col_G, c->g_pbuf, c->stream);
+    pico::launch_colcg_small_build(c->smaps, c->gmask.data(), c->nc, c->ny, c->nx, c->col_G, c->col_gmax, c->g_pbuf,
+                                   c->stream);
   }
   if ((!c->col_rr0 && (st = dalloc(c, &c->col_rr0, n)) != PICO_OK) ||
       (!c->col_rr && (st = dalloc(c, &c->col_rr, n)) != PICO_OK) ||
       (!c->col_iters && (st = dalloc(c, &c->col_iters, n)) != PICO_OK))
     return st;
-  if (global && !c->sglob.bar) {
+  if (global && !c->sglob.flags) {
     if ((st = dalloc(c, &c->sglob.part_pq, n)) != PICO_OK || (st = dalloc(c, &c->sglob.part_rr, n)) != PICO_OK ||
-        (st = dalloc(c, &c->sglob.bar, (size_t)2)) != PICO_OK)
+        (st = dalloc(c, &c->sglob.flags, (size_t)(c->max_batch + 15) / 16 * c->nx)) != PICO_OK)
       return st;
     c->sglob.err = c->g_err;
   }

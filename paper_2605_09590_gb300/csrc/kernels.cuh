@@ -178,21 +178,22 @@ void launch_to_cp(const float2* in, float* out, int ny, int nx, int nb, cudaStre
 bool colcg_small_supported(int ny);
 // G_j of every column, plain layout [nx][ny][ny] complex64 (pbuf: ny double2 of device scratch)
 void launch_colcg_small_build(const float2* smaps, const uint8_t* mask_host, int nc, int ny, int nx, float2* G,
-                              double2* pbuf, cudaStream_t s);
-// Whole-image CG on the on-chip kernel: per-column partial sums and the grid
-// barrier of a cooperative launch
+                              float* gmax, double2* pbuf, cudaStream_t s);
+// Whole-image CG on the on-chip kernel: per-column partial sums (float-float,
+// scaled) and the exchange flags of the image groups of a cooperative launch
 struct SmallGlobal {
-  double* part_pq;   // [B][nx]
-  double* part_rr;   // [B][nx]
-  unsigned* bar;     // [2] arrival counter and generation
+  float2* part_pq;   // [B][nx]
+  float2* part_rr;   // [B][nx]
+  unsigned* flags;   // [ceil(B / 16)][nx] exchange sequence of each block (zeroed before each launch)
   int* err;          // error word of a bounded wait
 };
 // every CG update of nb right-hand sides rhs [nb][ny][nx] (natural layout) in
 // one launch; x [nb][ny][nx]; rr0 / rr / iters per (image, column) [nb][nx]
-// (column sums).  glob == nullptr: CG per column; otherwise CG on the whole
-// image (cooperative launches).  false if nothing could be launched.
-bool launch_colcg_small(const float2* G, const float2* rhs, float2* X, int ny, int nx, int nb, int max_iter,
-                        double rtol2, float lam, double* rr0, double* rr, int* iters, int* status,
+// (column sums); gmax from launch_colcg_small_build.  glob == nullptr: CG per
+// column; otherwise CG on the whole image (cooperative launches).  false if
+// nothing could be launched.
+bool launch_colcg_small(const float2* G, const float* gmax, const float2* rhs, float2* X, int ny, int nx, int nb,
+                        int max_iter, double rtol2, float lam, double* rr0, double* rr, int* iters, int* status,
                         const SmallGlobal* glob, cudaStream_t s);
 void launch_from_cp(const float* in, float2* out, int ny, int nx, int nb, cudaStream_t s);
 

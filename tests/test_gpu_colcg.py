@@ -211,8 +211,9 @@ def test_small_images_pico_and_pmr_maps_same_seed():
 @pytest.mark.parametrize("ny,nx,nc,nb,lam", [(64, 64, 8, 32, 0.0), (32, 24, 4, 70, 0.05), (96, 20, 6, 9, 0.0)])
 def test_small_images_whole_image_cg_on_chip_matches_the_oracle(ny, nx, nc, nb, lam):
     """The default (whole-image) CG of small phase-encode images on chip: one
-    cooperative launch per solve, per-column partial sums added across the
-    grid between grid barriers; the same CG as the oracle's solvers.cg."""
+    cooperative launch per solve, per-column partial sums exchanged between
+    the blocks of an image group (release / acquire flags); the same CG as the
+    oracle's solvers.cg."""
     S = synth.coil_maps(ny, nx, nc, 5)
     mask = synth.mask_pe(ny, 2, 4)
     op = pico.Operator(S, mask=mask, lam=lam, power_iters=0, max_batch=nb)
