@@ -103,7 +103,7 @@ struct pico_ctx {
   float* col_gmax = nullptr;  // largest |component| of any G_j
   bool col_small = false;
   bool onchip = false;       // small phase-encode images: every CG solve runs on chip (either solver)
-  pico::SmallGlobal sglob{};  // whole-image CG on chip: column partials and exchange flags
+  pico::SmallGlobal sglob{};  // whole-image CG on chip: exchanged column partials
   std::string host_fail;  // a launch that could not be issued (reported by the entry point)
   size_t device_bytes = 0, budget = 0;
   bool async_alloc = false;  // stream-ordered cudaMallocAsync / cudaFreeAsync (serving contexts)
@@ -804,8 +804,7 @@ bool want_onchip(const pico_operator_desc* d) {
   return pico::colcg_small_supported(d->ny);
 }
 size_t onchip_extra_bytes(const pico_operator_desc* d, int64_t B) {
-  return (size_t)d->nx * d->ny * d->ny * 8 + 4 + (size_t)d->ny * 16 + (size_t)B * d->nx * (8 + 8 + 4 + 8 + 8) +
-         (size_t)(B + 15) / 16 * d->nx * 4;
+  return (size_t)d->nx * d->ny * d->ny * 8 + 4 + (size_t)d->ny * 16 + (size_t)B * d->nx * (8 + 8 + 4 + 16 + 16);
 }
 
 // G planes, second direction buffer and per-image scalars of the Gram mode
@@ -831,9 +830,8 @@ pico_status small_setup(pico_ctx* c, bool global) {
       (!c->col_rr && (st = dalloc(c, &c->col_rr, n)) != PICO_OK) ||
       (!c->col_iters && (st = dalloc(c, &c->col_iters, n)) != PICO_OK))
     return st;
-  if (global && !c->sglob.flags) {
-    if ((st = dalloc(c, &c->sglob.part_pq, n)) != PICO_OK || (st = dalloc(c, &c->sglob.part_rr, n)) != PICO_OK ||
-        (st = dalloc(c, &c->sglob.flags, (size_t)(c->max_batch + 15) / 16 * c->nx)) != PICO_OK)
+  if (global && !c->sglob.part_pq) {
+    if ((st = dalloc(c, &c->sglob.part_pq, n)) != PICO_OK || (st = dalloc(c, &c->sglob.part_rr, n)) != PICO_OK)
       return st;
     c->sglob.err = c->g_err;
   }

@@ -121,27 +121,22 @@ __device__ __forceinline__ float ff_div(ffloat a, ffloat b) {
   return q1 + rem / b.hi;
 }
 
-__device__ __forceinline__ void st_release_gpu(unsigned* p, unsigned v) {
-  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+// Exchange words: (sequence << 32) | payload, written and read as single
+// 64-bit strong (relaxed, GPU-scope) accesses, so a reader that sees the
+// sequence it waits for sees the payload written with it.
+__device__ __forceinline__ void st_word(unsigned long long* p, unsigned seq, unsigned payload) {
+  const unsigned long long w = ((unsigned long long)seq << 32) | payload;
+  asm volatile("st.relaxed.gpu.global.b64 [%0], %1;" ::"l"(p), "l"(w) : "memory");
 }
-__device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p) {
-  unsigned v;
-  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
+__device__ __forceinline__ unsigned long long ld_word(const unsigned long long* p) {
+  unsigned long long w;
+  asm volatile("ld.relaxed.gpu.global.b64 %0, [%1];" : "=l"(w) : "l"(p) : "memory");
+  return w;
 }
-// wait until *f >= seq, for at most about two seconds (then error 11, false)
-__device__ __forceinline__ bool wait_flag(const unsigned* f, unsigned seq, int* err) {
-  uint64_t t0;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
-  while (ld_acquire_gpu(f) < seq) {
-    uint64_t t1;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t1));
-    if (t1 - t0 > 2000000000ull) {
-      if (err) atomicCAS(err, 0, 11);
-      return false;
-    }
-  }
-  return true;
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
 }
 
 // Block = (column j, images b0 .. b0 + T - 1).  rhs and x are natural-layout
@@ -149,20 +144,22 @@ __device__ __forceinline__ bool wait_flag(const unsigned* f, unsigned seq, int* 
 // ||r_j||^2 and update count per image ([B][nx]).  gmax: the largest |G_j|
 // component over every column (sets the scale of q).
 // GLOBAL: CG on the whole image instead of per column.  The blocks of one
-// image group exchange their column sums: each writes its T sums to
-// part[B][nx] and publishes the exchange's sequence number in its flag
-// (release); each waits for the flags of the group's nx blocks (acquire) and
-// adds an image's nx sums in column order, so every block of the group takes
-// the same alpha and beta (Eq. 6 CG with the operator applied column by
-// column).  Groups are independent; a cooperative launch keeps all blocks
-// resident.
+// image group exchange their column sums: each publishes its T sums in
+// part[B][nx] as two tagged words per sum (the exchange's sequence number in
+// the high half); each waits until the group's nx sums of an image carry the
+// current sequence and adds them in column order, so every block of the group
+// takes the same alpha and beta (Eq. 6 CG with the operator applied column by
+// column).  An entry is overwritten two exchanges later, after its readers
+// have published the exchange in between (whose values depend on what they
+// read).  Groups are independent; a cooperative launch keeps all blocks
+// resident, and every wait gives up after about two seconds (error 11).
 template <int NY, int T, bool GLOBAL>
 __global__ void __launch_bounds__(kSmallThreads, 2)
     k_colcg_small(const float2* __restrict__ G, const float* __restrict__ gmax, const float2* __restrict__ rhs,
                   float2* __restrict__ X, int nx, int nb, int max_iter, double rtol2, float lam,
                   double* __restrict__ rr0_out, double* __restrict__ rr_out, int* __restrict__ iters_out,
-                  int* __restrict__ status, float2* __restrict__ part_pq, float2* __restrict__ part_rr,
-                  unsigned* __restrict__ flags, int* __restrict__ err) {
+                  int* __restrict__ status, ulonglong2* __restrict__ part_pq, ulonglong2* __restrict__ part_rr,
+                  int* __restrict__ err) {
   constexpr int E = NY * T / kSmallThreads;  // elements (image, row) per thread
   static_assert(NY % 32 == 0 && (NY * T) % kSmallThreads == 0, "tile shape");
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -183,50 +180,92 @@ __global__ void __launch_bounds__(kSmallThreads, 2)
   int* s_iters = s_eq + T;
   int* s_any = s_iters + T;
   int* s_ok = s_any + 1;
+  unsigned* s_xw = reinterpret_cast<unsigned*>(s_ok + 1);  // [2T] words being published
 
   const int j = blockIdx.x, b0 = blockIdx.y * T, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (tid == 0) *s_ok = 1;
   const int64_t n = (int64_t)NY * nx;
-  unsigned* gflags = flags ? flags + (size_t)blockIdx.y * nx : nullptr;  // this image group's flags
   unsigned seq = 0;
-  // GLOBAL: publish this block's T column sums, wait for the group, replace
-  // each by the sum over the nx columns (warp w adds images w, w + 8, ...:
-  // lane l loads columns l, l + 32, ... from L2, then a fixed shuffle tree)
-  auto publish_wait = [&](const float2* own, float2* part) -> bool {
-    if (tid < T && b0 + tid < nb) part[(size_t)(b0 + tid) * nx + j] = own[tid];
-    __syncthreads();
+  // GLOBAL: publish this block's T column sums (two 32-bit halves each), wait
+  // for the group's, and combine each image's nx sums in column order: warp w
+  // takes images w, w + 8, ...; lane l columns l, l + 32, ... (loads of up to
+  // four entries in flight, reissued until they carry the sequence), then a
+  // fixed shuffle tree.  add(acc, hi, lo) folds one entry; done(t, acc) stores.
+  auto exchange = [&](const unsigned* w_hi, const unsigned* w_lo, ulonglong2* part, auto zero, auto add,
+                      auto done) -> bool {
     ++seq;
-    if (tid == 0) {
-      __threadfence();
-      st_release_gpu(gflags + j, seq);
+    if (tid < T && b0 + tid < nb) {
+      ulonglong2* e = part + (size_t)(b0 + tid) * nx + j;
+      st_word(&e->x, seq, w_hi[tid]);
+      st_word(&e->y, seq, w_lo[tid]);
     }
-    if (warp == 0) {
-      bool ok = true;
-      for (int jj = lane; jj < nx; jj += 32) ok = wait_flag(gflags + jj, seq, err) && ok;
-      ok = __all_sync(0xffffffffu, ok);
-      if (lane == 0) *s_ok = ok;
+    constexpr int IW = T / (kSmallThreads / 32);  // images per warp
+    const int nj = (nx + 31) / 32, ne = IW * nj;  // entries per lane
+    decltype(zero) accs[IW];
+#pragma unroll
+    for (int i = 0; i < IW; ++i) accs[i] = zero;
+    bool ok = true;
+    const uint64_t t0 = global_ns();
+    for (int e0 = 0; e0 < ne; e0 += 4) {
+      unsigned long long w0[4], w1[4];
+      bool ready = false;
+      while (!ready) {
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+          const int e = e0 + m, i = e / nj, jj = lane + 32 * (e % nj), b = b0 + warp + 8 * i;
+          if (e < ne && jj < nx && b < nb) {
+            const ulonglong2* pe = part + (size_t)b * nx + jj;
+            w0[m] = ld_word(&pe->x);
+            w1[m] = ld_word(&pe->y);
+          } else {
+            w0[m] = w1[m] = (unsigned long long)seq << 32;
+          }
+        }
+        ready = true;
+#pragma unroll
+        for (int m = 0; m < 4; ++m) ready = ready && (unsigned)(w0[m] >> 32) == seq && (unsigned)(w1[m] >> 32) == seq;
+        if (!ready && global_ns() - t0 > 2000000000ull) {
+          if (err) atomicCAS(err, 0, 11);
+          ok = false;
+          break;
+        }
+      }
+      if (!ok) break;
+#pragma unroll
+      for (int m = 0; m < 4; ++m) {
+        const int e = e0 + m, i = e / nj, jj = lane + 32 * (e % nj), b = b0 + warp + 8 * i;
+        if (e < ne && jj < nx && b < nb) {
+#pragma unroll
+          for (int ii = 0; ii < IW; ++ii)
+            if (ii == i) accs[ii] = add(accs[ii], (unsigned)w0[m], (unsigned)w1[m]);
+        }
+      }
     }
+#pragma unroll
+    for (int i = 0; i < IW; ++i) done(warp + 8 * i, accs[i]);
+    ok = __all_sync(0xffffffffu, ok);
+    if (lane == 0 && !ok) *s_ok = 0;
     __syncthreads();
     return *s_ok != 0;
   };
-  auto whole_image = [&](ffloat* col, float2* part) -> bool {
+  auto whole_image = [&](ffloat* col, ulonglong2* part) -> bool {
     if (!GLOBAL) return true;
-    const bool ok = publish_wait(reinterpret_cast<const float2*>(col), part);
-    for (int t = warp; t < T; t += kSmallThreads / 32) {
-      ffloat a{0.f, 0.f};
-      if (b0 + t < nb) {
-        const float2* pp = part + (size_t)(b0 + t) * nx;
-        for (int jj = lane; jj < nx; jj += 32) {
-          const float2 c = __ldcg(pp + jj);
-          a = ff_add(a, ffloat{c.x, c.y});
-        }
-      }
-      a = warp_sum_ff(a);
-      if (lane == 0 && b0 + t < nb) col[t] = a;
+    const unsigned* hl = reinterpret_cast<const unsigned*>(col);  // col[t] = {hi, lo}: words 2t, 2t + 1
+    unsigned* hi_w = reinterpret_cast<unsigned*>(s_xw);
+    unsigned* lo_w = hi_w + T;
+    if (tid < T) {  // read back by the same thread: no barrier needed
+      hi_w[tid] = hl[2 * tid];
+      lo_w[tid] = hl[2 * tid + 1];
     }
-    __syncthreads();
+    const bool ok = exchange(
+        hi_w, lo_w, part, ffloat{0.f, 0.f},
+        [](ffloat a, unsigned h, unsigned l) { return ff_add(a, ffloat{__uint_as_float(h), __uint_as_float(l)}); },
+        [&](int t, ffloat a) {
+          a = warp_sum_ff(a);
+          if (lane == 0 && b0 + t < nb) col[t] = a;
+        });
     return ok;
   };
-
   for (int i = tid; i < NY * NY; i += kSmallThreads) Gs[i] = G[(size_t)j * NY * NY + i];
   const int eg = inv_exp(fmaxf(*gmax, lam));  // brings the largest entry of G_j + lam I to [0.5, 1)
   // this thread's elements: image t = e / NY, row y = e % NY (a warp's 32 share t)
@@ -249,17 +288,18 @@ __global__ void __launch_bounds__(kSmallThreads, 2)
     }
     bool ok = true;
     if (GLOBAL) {
-      ok = publish_wait(reinterpret_cast<const float2*>(s_rr0), reinterpret_cast<float2*>(part_rr));
-      for (int t = warp; t < T; t += kSmallThreads / 32) {
-        double a = 0.0;
-        if (b0 + t < nb) {
-          const double* pp = reinterpret_cast<const double*>(part_rr) + (size_t)(b0 + t) * nx;
-          for (int jj = lane; jj < nx; jj += 32) a += __ldcg(pp + jj);
-        }
-        a = warp_sum_d(a);
-        if (lane == 0 && b0 + t < nb) s_rr0[t] = a;
+      if (tid < T) {  // the double's high and low 32 bits
+        s_xw[tid] = (unsigned)__double2hiint(s_rr0[tid]);
+        s_xw[T + tid] = (unsigned)__double2loint(s_rr0[tid]);
       }
       __syncthreads();
+      ok = exchange(
+          s_xw, s_xw + T, part_rr, 0.0,
+          [](double a, unsigned h, unsigned l) { return a + __hiloint2double((int)h, (int)l); },
+          [&](int t, double a) {
+            a = warp_sum_d(a);
+            if (lane == 0 && b0 + t < nb) s_rr0[t] = a;
+          });
     }
     if (tid < T) {
       const double rr = s_rr0[tid];
@@ -413,7 +453,7 @@ __global__ void __launch_bounds__(kSmallThreads, 2)
 template <int NY, int T>
 size_t small_smem() {
   return (size_t)NY * NY * 8 + (size_t)T * NY * 8 + (size_t)T * (NY / 32) * 8 + 3 * T * 8 + 2 * T * 8 + 2 * T * 4 +
-         5 * T * 4 + 16;
+         5 * T * 4 + 8 + 2 * T * 4 + 16;
 }
 
 template <int NY, int T>
@@ -425,7 +465,7 @@ bool launch_small(const float2* G, const float* gmax, const float2* rhs, float2*
     auto k = k_colcg_small<NY, T, false>;
     cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     k<<<dim3(nx, (nb + T - 1) / T), kSmallThreads, sm, s>>>(G, gmax, rhs, X, nx, nb, max_iter, rtol2, lam, rr0, rr,
-                                                            iters, status, nullptr, nullptr, nullptr, nullptr);
+                                                            iters, status, nullptr, nullptr, nullptr);
     return true;
   }
   // whole-image CG: a cooperative launch (every block resident for the
@@ -441,21 +481,22 @@ bool launch_small(const float2* G, const float* gmax, const float2* rhs, float2*
   for (int c0 = 0; c0 < nb; c0 += groups * T) {
     const int cn = nb - c0 < groups * T ? nb - c0 : groups * T;
     const int ng = (cn + T - 1) / T;
-    cudaMemsetAsync(glob->flags, 0, (size_t)ng * nx * sizeof(unsigned), s);
+    // sequence 0 everywhere: no entry of an earlier launch passes for this one's
+    cudaMemsetAsync(glob->part_pq + (size_t)c0 * nx, 0, (size_t)cn * nx * sizeof(ulonglong2), s);
+    cudaMemsetAsync(glob->part_rr + (size_t)c0 * nx, 0, (size_t)cn * nx * sizeof(ulonglong2), s);
     const float2* rhs_c = rhs + (size_t)c0 * NY * nx;
     float2* X_c = X + (size_t)c0 * NY * nx;
     double* rr0_c = rr0 + (size_t)c0 * nx;
     double* rr_c = rr + (size_t)c0 * nx;
     int* it_c = iters + (size_t)c0 * nx;
     int* st_c = status + c0;
-    float2* pq_c = glob->part_pq + (size_t)c0 * nx;
-    float2* pr_c = glob->part_rr + (size_t)c0 * nx;
-    unsigned* flags = glob->flags;
+    ulonglong2* pq_c = glob->part_pq + (size_t)c0 * nx;
+    ulonglong2* pr_c = glob->part_rr + (size_t)c0 * nx;
     int* err = glob->err;
     int cnb = cn;
     void* args[] = {(void*)&G,     (void*)&gmax,  (void*)&rhs_c, (void*)&X_c,   (void*)&nx,    (void*)&cnb,
                     (void*)&max_iter, (void*)&rtol2, (void*)&lam,  (void*)&rr0_c, (void*)&rr_c,  (void*)&it_c,
-                    (void*)&st_c,  (void*)&pq_c,  (void*)&pr_c,  (void*)&flags, (void*)&err};
+                    (void*)&st_c,  (void*)&pq_c,  (void*)&pr_c,  (void*)&err};
     if (cudaLaunchCooperativeKernel((const void*)k, dim3(nx, ng), dim3(kSmallThreads), args, sm, s) != cudaSuccess)
       return false;
   }

@@ -179,13 +179,12 @@ bool colcg_small_supported(int ny);
 // G_j of every column, plain layout [nx][ny][ny] complex64 (pbuf: ny double2 of device scratch)
 void launch_colcg_small_build(const float2* smaps, const uint8_t* mask_host, int nc, int ny, int nx, float2* G,
                               float* gmax, double2* pbuf, cudaStream_t s);
-// Whole-image CG on the on-chip kernel: per-column partial sums (float-float,
-// scaled) and the exchange flags of the image groups of a cooperative launch
+// Whole-image CG on the on-chip kernel: per-column partial sums exchanged
+// between the blocks of an image group (two tagged 64-bit words per sum)
 struct SmallGlobal {
-  float2* part_pq;   // [B][nx]
-  float2* part_rr;   // [B][nx]
-  unsigned* flags;   // [ceil(B / 16)][nx] exchange sequence of each block (zeroed before each launch)
-  int* err;          // error word of a bounded wait
+  ulonglong2* part_pq;  // [B][nx]
+  ulonglong2* part_rr;  // [B][nx]
+  int* err;             // error word of a bounded wait
 };
 // every CG update of nb right-hand sides rhs [nb][ny][nx] (natural layout) in
 // one launch; x [nb][ny][nx]; rr0 / rr / iters per (image, column) [nb][nx]
