@@ -748,6 +748,45 @@ def colcg_roofline(w, K, avg_s, launches):
             "algorithmic_bytes_per_launch": alg, "peak_note": "measured copy bandwidth (of measured)"}
 
 
+def persist_rows(ny):
+    """Rows per CTA of the whole-solve per-column kernel (0: not used)."""
+    if ny % 16:
+        return 0
+    for nt in (80, 64, 48, 32):
+        if ny % nt == 0 and 2 <= ny // nt <= 8:
+            return nt
+    return 0
+
+
+def persist_roofline(w, K, avg_s, launches):
+    """Roofline of the per-column CG with the whole solve in one launch
+    (k_colcg_persist: a cluster owns a column and 128 images, x, r, p stay on
+    chip).  Tensor-bound: every update issues 12 FP16 MMAs of M 128 x N NT x
+    K 16 per 16-row chunk (the FP16 head + remainder split of the complex
+    product, dense-equivalent work) for every (column, image tile, row block),
+    max_iter updates per launch, against the measured sustained dense bf16
+    peak (the kernel runs for milliseconds inside a long step; FP16 runs at the
+    bf16 rate).  The HBM view: the right-hand sides in and the solutions out
+    (2 images of 8 bytes per voxel) and G once."""
+    mp = measured_peaks()
+    nt = persist_rows(w.ny)
+    tiles = -(-K // 128)
+    flops = float(w.max_iter) * w.nx * tiles * (w.ny // nt) * (w.ny // 16) * 12 * 2 * 128 * nt * 16
+    achieved = flops / avg_s / 1e12
+    V = w.ny * w.nx * 8
+    byts = 2 * K * V + 8 * w.nx * w.ny * w.ny
+    peak = mp["bf16_tflops_sustained"]
+    return {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak, "traffic": None,
+            "kernel": "k_colcg_persist<%d> (whole per-column CG solve per launch: clusters of %d CTAs own a column "
+                      "and 128 images, x / p / accumulator in tensor memory, r in shared memory, tcgen05 "
+                      "kind::f16)" % (nt, w.ny // nt),
+            "avg_launch_ms": avg_s * 1e3, "launches": launches, "mma_flops_per_launch": flops,
+            "peak_note": "measured sustained dense bf16 GEMM peak (of measured); FP16 MMAs run at the bf16 rate",
+            "hbm": {"achieved_GBps": byts / avg_s / 1e9, "peak_GBps": mp["hbm_gbs"],
+                    "frac": byts / avg_s / 1e9 / mp["hbm_gbs"], "bytes_per_launch": byts}}
+
+
 def bench_linear(args, w, inp, pico, torch, dist, world, rank, local, steps, warmup, primary, tune_cache,
                  solver="global"):
     """One step = PICO map of K probes + PMR map of K replicas on a linear
@@ -781,7 +820,9 @@ def bench_linear(args, w, inp, pico, torch, dist, world, rank, local, steps, war
     avg_norm_s = norm_ms / max(norm_n, 1) / 1e3
     gram_on = op.info["normal_op"] == 1 and K >= op.tuning["gram_min_batch"]
     if solver == "columns" and op.info["normal_op"] == 1:
-        roof = colcg_roofline(w, K, avg_norm_s, norm_n)
+        persist = persist_rows(w.ny) > 0 and os.environ.get("PICO_COLCG_PERSIST", "1") != "0" and \
+            os.environ.get("PICO_GRAM_TF32", "0") == "0"
+        roof = persist_roofline(w, K, avg_norm_s, norm_n) if persist else colcg_roofline(w, K, avg_norm_s, norm_n)
     elif op.info["normal_op"] == 3:
         roof = onchip_roofline(w, K, avg_norm_s, norm_n, solver)
     else:

@@ -99,6 +99,12 @@ struct pico_ctx {
   int *col_done = nullptr, *col_iters = nullptr;
   double* col_pn = nullptr;     // FP16 form: bound on each column direction's entries [B][nx]
   float* col_pscale = nullptr;
+  // larger phase-encode images: the whole per-column solve in one launch
+  // (a cluster owns a column and 128 images; G_j tiled for its row blocks)
+  bool persist_off = false;     // PICO_COLCG_PERSIST=0, TF32 operands, or the buffers do not fit
+  void* per_G = nullptr;
+  float* per_gscale = nullptr;
+  uint8_t* per_split = nullptr;  // the split directions the cluster's CTAs share
   float2* col_G = nullptr;  // small images: G_j of every column, [nx][ny][ny] (whole solve on chip)
   float* col_gmax = nullptr;  // largest |component| of any G_j
   bool col_small = false;
@@ -445,6 +451,46 @@ void cg_iterations(pico_ctx* c, int nb, int max_iter, double rtol, float lam) {
   }
 }
 
+// Per-column CG with the whole solve in one launch (FP16 operands, ny a
+// multiple of a supported row block): G_j in the cluster's row tiling and the
+// shared split-direction buffer, built on first use.  false: the per-update
+// kernels run instead.
+bool persist_setup(pico_ctx* c) {
+  if (c->per_G) return true;
+  if (c->persist_off || !c->gram || !c->gram_f16 || (size_t)c->nc * c->ny * 8 > 200 * 1024) return false;
+  const int nt = pico::colcg_persist_rows(c->ny);
+  if (!nt) return (c->persist_off = true, false);
+  const size_t gbytes = (size_t)8 * c->nx * c->ny * c->ny;  // four FP16 planes
+  const size_t sbytes = pico::colcg_persist_split_bytes(c->ny, c->nx, c->max_batch);
+  if (c->budget && c->device_bytes + gbytes + sbytes + 4 * (size_t)c->nx > c->budget) return (c->persist_off = true, false);
+  const std::string keep = c->err;
+  if (dalloc(c, reinterpret_cast<uint8_t**>(&c->per_G), gbytes) != PICO_OK ||
+      dalloc(c, &c->per_gscale, (size_t)c->nx) != PICO_OK || dalloc(c, &c->per_split, sbytes) != PICO_OK) {
+    c->err = keep;  // not an error of the call: the per-update kernels take over
+    c->per_G = nullptr;
+    return (c->persist_off = true, false);
+  }
+  pico::GramOp op{};
+  op.ny = c->ny;
+  op.nx = c->nx;
+  op.nt = nt;
+  op.kc = 16;
+  op.a_tmem = 0;
+  op.f16 = 1;
+  op.G = c->per_G;
+  op.gscale = c->per_gscale;
+  pico::launch_gram_build(c->smaps, c->gmask.data(), c->nc, op, c->g_pbuf, c->stream);
+  return true;
+}
+bool persist_path(pico_ctx* c) { return column_mode(c) && persist_setup(c); }
+void run_cg_persist(pico_ctx* c, int nb, int max_iter, double rtol, float lam) {
+  Launch L(c, 0);
+  if (!pico::launch_colcg_persist(c->per_G, c->per_gscale, cpf(c->R), reinterpret_cast<float*>(c->X), c->per_split,
+                                  c->col_rr0, c->col_rr, c->col_iters, c->status, c->g_err, c->ny, c->nx, nb,
+                                  max_iter, rtol * rtol, lam, c->stream))
+    c->host_fail = "per-column CG launch failed (cluster launch of the whole solve)";
+}
+
 // the whole CG solve of small images on chip (per column, or the whole image
 // with sum exchanges between the blocks of an image group): rhs in R, x to X
 // (natural layout)
@@ -461,6 +507,10 @@ pico_status run_cg(pico_ctx* c, int nb, int max_iter, double rtol, float lam) {
   c->cg.rtol2 = rtol * rtol;
   if (small_path(c)) {
     run_cg_small(c, nb, max_iter, rtol, lam);
+    return cuda_check(c, "cg");
+  }
+  if (persist_path(c)) {
+    run_cg_persist(c, nb, max_iter, rtol, lam);
     return cuda_check(c, "cg");
   }
   if (column_mode(c)) {
@@ -494,6 +544,10 @@ pico_status run_cg_from_probe(pico_ctx* c, int nb, int max_iter, double rtol, fl
   init_from_probe(c, nb, seed, begin, kind);
   if (small_path(c)) {
     run_cg_small(c, nb, max_iter, rtol, lam);
+    return cuda_check(c, "cg");
+  }
+  if (persist_path(c)) {
+    run_cg_persist(c, nb, max_iter, rtol, lam);
     return cuda_check(c, "cg");
   }
   if (column_mode(c)) {
@@ -867,6 +921,7 @@ pico_status gram_setup(pico_ctx* c, const pico_operator_desc* d) {
   if ((st = dalloc(c, &c->g_pscale, (size_t)c->max_batch)) != PICO_OK) return st;
   if ((st = dalloc(c, &c->gop.gscale, (size_t)c->nx)) != PICO_OK) return st;
   if (const char* e = std::getenv("PICO_GRAM_TF32")) c->gram_f16 = std::atoi(e) == 0;
+  if (const char* e = std::getenv("PICO_COLCG_PERSIST")) c->persist_off = std::atoi(e) == 0;
   if (!c->g_err && (st = dalloc(c, &c->g_err, (size_t)4)) != PICO_OK) return st;
   if ((st = dalloc(c, &c->g_pbuf, (size_t)c->ny)) != PICO_OK) return st;
   cudaMemsetAsync(c->g_err, 0, 4 * sizeof(int), c->stream);

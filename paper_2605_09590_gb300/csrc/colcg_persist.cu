@@ -1,0 +1,563 @@
+// Per-column CG with the whole solve in one launch, for Cartesian phase-encode
+// images with a tensor-core Gram operator (ny = CS * NT rows, CS <= 8).
+//
+// With a phase-encode mask A^H A is block diagonal over the readout columns
+// (Sec. 2.1.3 with M = M_y (x) I), so CG on Eq. 6 splits into independent
+// column systems (G_j + lam I) x_j = b_j, each converging on its own (the
+// stopping rule ||r_j|| <= rtol ||b_j|| per column).  A cluster of CS CTAs
+// owns one column j and a tile of 128 images for every iteration of the
+// solve; CTA `rank` holds rows [rank NT, rank NT + NT) of x, r and p:
+//   x, p (FP32) and the accumulator D in tensor memory (one image per lane),
+//   r (FP32) in shared memory,
+// so the CG vectors never leave the chip between iterations.  Per iteration:
+//   main loop   D = sum_k p[k] G_j[rows, k] on tcgen05 (kind::f16, FP16 head
+//               + remainder of p and G after power-of-two scaling, 12 MMAs of
+//               M 128 x N NT x K 16 per 16-row chunk).  The A operand (the
+//               split direction of all ny rows) comes from a global buffer in
+//               which every CTA of the cluster leaves its own rows' chunks
+//               (L2-resident), the B operand from the stage-tiled G_j;
+//   phase A     q = D / (gscale ps) + lam p, the p^H q partial of the CTA's rows;
+//   exchange 1  p^H q over the column (distributed shared memory, rank order);
+//   phase B     x += alpha p, r -= alpha q, the ||r||^2 partial;
+//   exchange 2  ||r||^2 over the column, beta, the stopping rule;
+//   phase C     p = r + beta p, its FP16 split written for the next main loop.
+// Every CTA of a cluster adds the partials in rank order, so all of them take
+// the same alpha, beta and stopping decisions (and leave the loop together).
+// Inner products: FP32 partial sums of 16 rows (as in the one-update kernel),
+// float-float across chunks and CTAs; values scaled by the direction's
+// power-of-two FP16 scale, so no FP32 underflow.  Every mbarrier wait is
+// bounded (about 2 s, then an error code); an error ends the solve on every
+// CTA of the cluster at the same iteration (flags exchanged after the last
+// cluster barrier of each iteration).
+#include <cuda_fp16.h>
+
+#include "common.cuh"
+#include "f16_split.cuh"
+#include "kernels.cuh"
+#include "tc_util.cuh"
+
+namespace pico {
+
+namespace {
+
+using namespace tc;
+
+constexpr int kPM = 128;                    // images per cluster (MMA M, one per tensor-memory lane)
+constexpr int kPThreads = 192;              // warp 0 loads, warp 1 MMA, warps 2-5 epilogue
+constexpr uint32_t kPlaneA = kPM * 32;      // one FP16 plane of a 16-row chunk: 4 KB
+constexpr uint32_t kChunkA = 4 * kPlaneA;   // [re head | im head | re rem | im rem]: 16 KB
+
+struct PersistArgs {
+  const void* G;         // FP16 stage-tiled G_j for row blocks of NT
+  const float* gscale;   // [nx] power-of-two scale of G_j
+  const float* R;        // right-hand sides, column-planar [B][nx][2][ny]
+  float* X;              // solutions, same layout
+  uint8_t* psplit;       // [nx][tiles][ny / 16] chunks of kChunkA bytes
+  double* rr0;           // [B][nx] ||b_j||^2
+  double* rr;            // [B][nx] final ||r_j||^2
+  int* iters;            // [B][nx] updates taken
+  int* status;           // [B] 5 on breakdown
+  int* err;              // first failure code of a bounded wait
+  int ny, nx, nb, tiles, max_iter, stages;
+  double rtol2;
+  float lam;
+};
+
+// descriptor of a K-major FP16 tile with 32-byte rows (16 values), 8-row
+// atoms, 32-byte swizzle
+__device__ __forceinline__ uint64_t desc32(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+  d |= (uint64_t)1u << 16;
+  d |= (uint64_t)((8u * 32u) >> 4) << 32;
+  d |= (uint64_t)1u << 46;
+  d |= (uint64_t)6u << 61;
+  return d;
+}
+
+__device__ __forceinline__ void set_err(int* err, int code) {
+  if (err) atomicCAS(err, 0, code);
+}
+
+// float-float value at the same shared-memory offset in the CTA of cluster rank `rank`
+__device__ __forceinline__ ffloat ld_dsmem_ff(const ffloat* local, uint32_t rank) {
+  uint32_t ra;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(ra) : "r"(smem_u32(local)), "r"(rank));
+  float h, l;
+  asm volatile("ld.shared::cluster.v2.f32 {%0, %1}, [%2];" : "=f"(h), "=f"(l) : "r"(ra) : "memory");
+  return ffloat{h, l};
+}
+__device__ __forceinline__ int ld_dsmem_i32(const int* local, uint32_t rank) {
+  uint32_t ra;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(ra) : "r"(smem_u32(local)), "r"(rank));
+  int v;
+  asm volatile("ld.shared::cluster.s32 %0, [%1];" : "=r"(v) : "r"(ra) : "memory");
+  return v;
+}
+
+// float-float sum at a power-of-two scale 2^e, as a double
+__device__ __forceinline__ double ff_unscale(ffloat a, int e) {
+  return ldexp((double)a.hi + (double)a.lo, -e);
+}
+__device__ __forceinline__ int exp2_of(float pow2) { return (int)((__float_as_uint(pow2) >> 23) & 0xff) - 127; }
+// a / b to about float precision (b.hi > 0)
+__device__ __forceinline__ float ff_div(ffloat a, ffloat b) {
+  const float q1 = a.hi / b.hi;
+  const float rem = fmaf(-q1, b.hi, a.hi) + a.lo - q1 * b.lo;
+  return q1 + rem / b.hi;
+}
+__device__ __forceinline__ ffloat ff_scale(ffloat a, float pow2) { return ffloat{a.hi * pow2, a.lo * pow2}; }
+
+// the FP16 split of 16 values (one plane pair) of image row i into a chunk:
+// 32-byte rows, the two 16-byte groups swapped on rows 4..7 of every 8-row atom
+__device__ __forceinline__ void store_split16(uint8_t* chunk, int plane_hi, int plane_lo, int i, const float* v,
+                                              float sc) {
+  uint2 h[4], l[4];
+#pragma unroll
+  for (int g = 0; g < 4; ++g) split_f16x4(v[4 * g] * sc, v[4 * g + 1] * sc, v[4 * g + 2] * sc, v[4 * g + 3] * sc, h[g], l[g]);
+  const int sw = (i >> 2) & 1;
+#pragma unroll
+  for (int g = 0; g < 2; ++g) {
+    const size_t off = (size_t)i * 32 + (size_t)((g ^ sw) * 16);
+    *reinterpret_cast<uint4*>(chunk + (size_t)plane_hi * kPlaneA + off) =
+        make_uint4(h[2 * g].x, h[2 * g].y, h[2 * g + 1].x, h[2 * g + 1].y);
+    *reinterpret_cast<uint4*>(chunk + (size_t)plane_lo * kPlaneA + off) =
+        make_uint4(l[2 * g].x, l[2 * g].y, l[2 * g + 1].x, l[2 * g + 1].y);
+  }
+}
+
+template <int NT>
+__global__ void __launch_bounds__(kPThreads, 1) k_colcg_persist(PersistArgs a) {
+  static_assert(NT % 16 == 0 && 6 * NT <= 512, "row block");
+  constexpr int NCH = NT / 16;               // 16-row chunks of this CTA
+  constexpr uint32_t kB = NT * 128;          // B block: 4 FP16 planes of NT x 16
+  constexpr uint32_t kStage = kChunkA + kB;
+  extern __shared__ uint8_t smraw[];
+  uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smraw) + 1023) & ~(uintptr_t)1023);
+  const int S = a.stages;
+  float* r_re = reinterpret_cast<float*>(sm + (size_t)S * kStage);  // [NT][128]
+  float* r_im = r_re + NT * kPM;
+  ffloat* xpq = reinterpret_cast<ffloat*>(r_im + NT * kPM);  // [128] exchange slots
+  ffloat* xrr = xpq + kPM;
+  int* xab = reinterpret_cast<int*>(xrr + kPM);  // [0] sticky error flag, [1..2] any-live by iteration parity
+  uint64_t* full = reinterpret_cast<uint64_t*>(xab + 4);
+  uint64_t* empty = full + S;
+  uint64_t* accf = empty + S;
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(accf + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t rank = cluster_ctarank();
+  const int CS = a.ny / NT;
+  const int tile = blockIdx.x / CS, j = blockIdx.y;
+  const int n0 = (int)rank * NT, m0 = tile * kPM;
+  const int nkc = a.ny / 16, kc0 = n0 / 16;
+  const uint8_t* gsrc = static_cast<const uint8_t*>(a.G) + ((size_t)j * CS + rank) * nkc * kB;
+  uint8_t* pcol = a.psplit + ((size_t)j * a.tiles + tile) * nkc * kChunkA;  // this (column, tile)'s chunks
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < S; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(accf, 1);
+    fence_mbar_init();
+    xab[0] = 0;
+    xab[1] = 0;
+    xab[2] = 0;
+  }
+  if (warp == 1) tmem_alloc(tslot, 512);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tbase = *tslot;
+
+  // epilogue thread state: image i of the tile (tensor-memory lane i)
+  const bool epi = warp >= 2;
+  const int quarter = warp & 3, i = 32 * quarter + lane, img = m0 + i;
+  const bool valid = epi && img < a.nb;
+  const uint32_t tl = tbase + ((uint32_t)(32 * quarter) << 16);
+  const uint32_t tD = tl, tX = tl + 2 * NT, tP = tl + 4 * NT;  // re at +0, im at +NT
+  const float gsi = epi ? 1.f / a.gscale[j] : 1.f;
+  const float lam = a.lam;
+  double rr0 = 0.0, rrd = 0.0;
+  ffloat rrs{0.f, 0.f};  // ||r||^2 scaled by ps^2
+  float pn = 0.f, ps = 1.f;
+  bool live = false, broke = false;
+  int iters = 0;
+
+  // ---- start: r = b, x = 0, p = r; ||b_j||^2; the split of p for the first main loop ----
+  if (epi) {
+    const float* bre = a.R + ((size_t)(valid ? img : 0) * a.nx + j) * 2 * a.ny + n0;
+    const float* bim = bre + a.ny;
+    float mx = 0.f;
+#pragma unroll
+    for (int c = 0; c < NCH; ++c) {
+      float vr[16], vi[16];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const float4 w = valid ? reinterpret_cast<const float4*>(bre + 16 * c)[u] : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float4 z = valid ? reinterpret_cast<const float4*>(bim + 16 * c)[u] : make_float4(0.f, 0.f, 0.f, 0.f);
+        vr[4 * u] = w.x; vr[4 * u + 1] = w.y; vr[4 * u + 2] = w.z; vr[4 * u + 3] = w.w;
+        vi[4 * u] = z.x; vi[4 * u + 1] = z.y; vi[4 * u + 2] = z.z; vi[4 * u + 3] = z.w;
+      }
+      float zero[16];
+#pragma unroll
+      for (int u = 0; u < 16; ++u) {
+        r_re[(16 * c + u) * kPM + i] = vr[u];
+        r_im[(16 * c + u) * kPM + i] = vi[u];
+        mx = fmaxf(mx, fmaxf(fabsf(vr[u]), fabsf(vi[u])));
+        zero[u] = 0.f;
+      }
+      tmem_st16(tP + 16 * c, vr);
+      tmem_st16(tP + NT + 16 * c, vi);
+      tmem_st16(tX + 16 * c, zero);
+      tmem_st16(tX + NT + 16 * c, zero);
+    }
+    tmem_wait_st();
+    // this CTA's ||b||^2 over its rows, scaled by its largest entry (float-float)
+    const float sb = pow2_scale_f(mx);
+    ffloat acc{0.f, 0.f};
+    for (int c = 0; c < NCH; ++c) {
+      float f = 0.f;
+#pragma unroll
+      for (int u = 0; u < 16; ++u) {
+        const float br = r_re[(16 * c + u) * kPM + i] * sb, bi = r_im[(16 * c + u) * kPM + i] * sb;
+        f = fmaf(br, br, fmaf(bi, bi, f));
+      }
+      acc = ff_add(acc, ffloat{f, 0.f});
+    }
+    const double part = ff_unscale(acc, 2 * exp2_of(sb));
+    reinterpret_cast<double*>(xrr)[i] = part;
+  }
+  cluster_sync_all();
+  if (epi) {
+    for (int rk = 0; rk < CS; ++rk) {
+      uint32_t ra;
+      asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(ra) : "r"(smem_u32(&xrr[i])), "r"((uint32_t)rk));
+      double v;
+      asm volatile("ld.shared::cluster.f64 %0, [%1];" : "=d"(v) : "r"(ra) : "memory");
+      rr0 += v;
+    }
+    rrd = rr0;
+    const bool bad = !isfinite(rr0);
+    live = valid && !bad && rr0 > 0.0;
+    if (valid && bad) broke = true;
+    pn = sqrtf((float)rr0);
+    ps = pow2_scale_f(pn);
+    {
+      const double v = rr0 * (double)ps * (double)ps;
+      const float h = (float)v;
+      rrs = ffloat{h, (float)(v - (double)h)};
+    }
+    // the split of p = b for this CTA's chunks
+    for (int c = 0; c < NCH; ++c) {
+      float vr[16], vi[16];
+#pragma unroll
+      for (int u = 0; u < 16; ++u) {
+        vr[u] = r_re[(16 * c + u) * kPM + i];
+        vi[u] = r_im[(16 * c + u) * kPM + i];
+      }
+      uint8_t* ch = pcol + (size_t)(kc0 + c) * kChunkA;
+      store_split16(ch, 0, 2, i, vr, ps);
+      store_split16(ch, 1, 3, i, vi, ps);
+    }
+    fence_proxy_async_global();  // generic writes of the split, read by the peers' bulk copies
+    if (live) xab[1] = 1;  // any live system in this tile (benign race: every writer stores 1)
+  }
+  tc_fence_before();
+  cluster_sync_all();
+  tc_fence_after();
+  bool any_live = xab[1] != 0;
+  bool abort = false;
+  if (threadIdx.x == 0) xab[2] = 0;
+
+  int issued = 0;      // stages issued by the producer (all iterations)
+  int committed = 0;   // accumulator commits by the MMA thread
+  for (int it = 0; it < a.max_iter && any_live && !abort; ++it) {
+    // ---- main loop ----
+    if (warp == 0 && lane == 0) {
+      fence_proxy_async_global();
+      for (int kc = 0; kc < nkc; ++kc) {
+        const int gidx = it * nkc + kc, s = gidx % S;
+        if (gidx >= S && !mbar_wait(&empty[s], ((gidx / S) - 1) & 1)) {
+          set_err(a.err, 21);
+          xab[0] = 1;
+          break;
+        }
+        uint8_t* st = sm + (size_t)s * kStage;
+        mbar_expect_tx(&full[s], kStage);
+        bulk_load(st, pcol + (size_t)kc * kChunkA, kChunkA, &full[s]);
+        bulk_load(st + kChunkA, gsrc + (size_t)kc * kB, kB, &full[s]);
+        issued = gidx + 1;
+      }
+    } else if (warp == 1 && lane == 0) {
+      const uint32_t hd = idesc_f16(kPM, NT, false), hdn = idesc_f16(kPM, NT, true);
+      const uint32_t dre = tbase, dim = tbase + NT;
+      for (int kc = 0; kc < nkc; ++kc) {
+        const int gidx = it * nkc + kc, s = gidx % S;
+        if (!mbar_wait(&full[s], (gidx / S) & 1)) {
+          set_err(a.err, 22);
+          xab[0] = 1;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t sa = smem_u32(sm + (size_t)s * kStage), sbb = sa + kChunkA;
+        const uint32_t acc0 = kc == 0 ? 0u : 1u;
+        const uint64_t Ahr = desc32(sa), Ahi = desc32(sa + kPlaneA);
+        const uint64_t Alr = desc32(sa + 2 * kPlaneA), Ali = desc32(sa + 3 * kPlaneA);
+        const uint64_t Bhr = desc32(sbb), Bhi = desc32(sbb + NT * 32);
+        const uint64_t Blr = desc32(sbb + 2 * NT * 32), Bli = desc32(sbb + 3 * NT * 32);
+        // D_re += p_re G_re^T - p_im G_im^T ; D_im += p_re G_im^T + p_im G_re^T
+        mma_f16(dre, Ahr, Bhr, hd, acc0);
+        mma_f16(dre, Ahr, Blr, hd, 1);
+        mma_f16(dre, Alr, Bhr, hd, 1);
+        mma_f16(dre, Ahi, Bhi, hdn, 1);
+        mma_f16(dre, Ahi, Bli, hdn, 1);
+        mma_f16(dre, Ali, Bhi, hdn, 1);
+        mma_f16(dim, Ahr, Bhi, hd, acc0);
+        mma_f16(dim, Ahr, Bli, hd, 1);
+        mma_f16(dim, Alr, Bhi, hd, 1);
+        mma_f16(dim, Ahi, Bhr, hd, 1);
+        mma_f16(dim, Ahi, Blr, hd, 1);
+        mma_f16(dim, Ali, Bhr, hd, 1);
+        mma_commit(&empty[s]);
+      }
+      mma_commit(accf);
+      ++committed;
+    }
+    // ---- phase A: q = D / (gscale ps) + lam p; p^H q (scaled by ps^2) ----
+    const float fsc = gsi / ps;
+    if (epi) {
+      if (!mbar_wait(accf, it & 1)) {
+        set_err(a.err, 23);
+        xab[0] = 1;
+      }
+      tc_fence_after();
+      ffloat pq{0.f, 0.f};
+#pragma unroll 1
+      for (int c = 0; c < NCH; ++c) {
+        float dr[16], di[16], pr[16], pi[16];
+        tmem_ld16x2(tD + 16 * c, tD + NT + 16 * c, dr, di);
+        tmem_ld16x2(tP + 16 * c, tP + NT + 16 * c, pr, pi);
+        float f = 0.f;
+#pragma unroll
+        for (int u = 0; u < 16; ++u) {
+          const float qr = fmaf(lam, pr[u], dr[u] * fsc), qi = fmaf(lam, pi[u], di[u] * fsc);
+          f = fmaf(pr[u] * ps, qr * ps, fmaf(pi[u] * ps, qi * ps, f));
+        }
+        pq = ff_add(pq, ffloat{f, 0.f});
+      }
+      xpq[i] = pq;
+    }
+    tc_fence_before();
+    cluster_sync_all();  // exchange 1
+    tc_fence_after();
+    float alpha = 0.f;
+    bool upd = false;
+    if (epi) {
+      ffloat pqt{0.f, 0.f};
+      for (int rk = 0; rk < CS; ++rk) pqt = ff_add(pqt, ld_dsmem_ff(&xpq[i], (uint32_t)rk));
+      if (live) {
+        if (!(pqt.hi > 0.f) || !isfinite(pqt.hi)) {
+          live = false;
+          broke = true;
+        } else {
+          alpha = ff_div(rrs, pqt);
+          upd = true;
+        }
+      }
+      // ---- phase B: x += alpha p, r -= alpha q; ||r||^2 (scaled by ps^2) ----
+      ffloat rn{0.f, 0.f};
+#pragma unroll 1
+      for (int c = 0; c < NCH; ++c) {
+        float f = 0.f;
+        if (upd) {
+          float dr[16], di[16], pr[16], pi[16], xr[16], xi[16];
+          tmem_ld16x2(tD + 16 * c, tD + NT + 16 * c, dr, di);
+          tmem_ld16x2(tP + 16 * c, tP + NT + 16 * c, pr, pi);
+          tmem_ld16x2(tX + 16 * c, tX + NT + 16 * c, xr, xi);
+#pragma unroll
+          for (int u = 0; u < 16; ++u) {
+            const float qr = fmaf(lam, pr[u], dr[u] * fsc), qi = fmaf(lam, pi[u], di[u] * fsc);
+            xr[u] = fmaf(alpha, pr[u], xr[u]);
+            xi[u] = fmaf(alpha, pi[u], xi[u]);
+            float* rre = &r_re[(16 * c + u) * kPM + i];
+            float* rim = &r_im[(16 * c + u) * kPM + i];
+            const float nr = fmaf(-alpha, qr, *rre), ni = fmaf(-alpha, qi, *rim);
+            *rre = nr;
+            *rim = ni;
+            f = fmaf(nr * ps, nr * ps, fmaf(ni * ps, ni * ps, f));
+          }
+          tmem_st16(tX + 16 * c, xr);
+          tmem_st16(tX + NT + 16 * c, xi);
+        }
+        rn = ff_add(rn, ffloat{f, 0.f});
+      }
+      tmem_wait_st();
+      xrr[i] = rn;
+    }
+    tc_fence_before();
+    cluster_sync_all();  // exchange 2
+    tc_fence_after();
+    if (epi) {
+      ffloat rnt{0.f, 0.f};
+      for (int rk = 0; rk < CS; ++rk) rnt = ff_add(rnt, ld_dsmem_ff(&xrr[i], (uint32_t)rk));
+      float beta = 0.f;
+      bool cont = false;
+      if (upd) {
+        const double rn_d = ff_unscale(rnt, 2 * exp2_of(ps));
+        if (!isfinite(rn_d)) {
+          live = false;
+          broke = true;
+        } else {
+          ++iters;
+          rrd = rn_d;
+          const bool stop = !(rn_d > a.rtol2 * rr0);
+          if (stop) {
+            live = false;
+          } else {
+            beta = ff_div(rnt, rrs);
+            cont = true;
+          }
+          rrs = rnt;
+        }
+      }
+      // ---- phase C: p = r + beta p and its split (scale from sqrt(rr) + beta pn) ----
+      if (cont) {
+        pn = sqrtf((float)rrd) + beta * pn;
+        const float psn = pow2_scale_f(pn);
+        rrs = ff_scale(rrs, (psn / ps) * (psn / ps));  // exact: powers of two
+        ps = psn;
+#pragma unroll 1
+        for (int c = 0; c < NCH; ++c) {
+          float pr[16], pi[16];
+          tmem_ld16x2(tP + 16 * c, tP + NT + 16 * c, pr, pi);
+#pragma unroll
+          for (int u = 0; u < 16; ++u) {
+            pr[u] = fmaf(beta, pr[u], r_re[(16 * c + u) * kPM + i]);
+            pi[u] = fmaf(beta, pi[u], r_im[(16 * c + u) * kPM + i]);
+          }
+          tmem_st16(tP + 16 * c, pr);
+          tmem_st16(tP + NT + 16 * c, pi);
+          uint8_t* ch = pcol + (size_t)(kc0 + c) * kChunkA;
+          store_split16(ch, 0, 2, i, pr, ps);
+          store_split16(ch, 1, 3, i, pi, ps);
+        }
+        tmem_wait_st();
+        fence_proxy_async_global();
+        xab[1 + ((it + 1) & 1)] = 1;
+      }
+    }
+    tc_fence_before();
+    cluster_sync_all();  // the split is complete on every CTA; flags are final
+    tc_fence_after();
+    any_live = xab[1 + ((it + 1) & 1)] != 0;
+    bool ab = false;
+    for (int rk = 0; rk < CS; ++rk) ab = ab || ld_dsmem_i32(&xab[0], (uint32_t)rk) != 0;
+    abort = ab;
+    // the other parity's flag is next written in iteration it + 1, after exchange 2
+    if (threadIdx.x == 0) xab[1 + (it & 1)] = 0;
+  }
+
+  // ---- results: x to global, the column's scalars (rank 0) ----
+  if (valid) {
+    float* xre = a.X + ((size_t)img * a.nx + j) * 2 * a.ny + n0;
+    float* xim = xre + a.ny;
+    for (int c = 0; c < NCH; ++c) {
+      float xr[16], xi[16];
+      tmem_ld16x2(tX + 16 * c, tX + NT + 16 * c, xr, xi);
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        reinterpret_cast<float4*>(xre + 16 * c)[u] = make_float4(xr[4 * u], xr[4 * u + 1], xr[4 * u + 2], xr[4 * u + 3]);
+        reinterpret_cast<float4*>(xim + 16 * c)[u] = make_float4(xi[4 * u], xi[4 * u + 1], xi[4 * u + 2], xi[4 * u + 3]);
+      }
+    }
+    if (rank == 0) {
+      const size_t cidx = (size_t)img * a.nx + j;
+      a.rr0[cidx] = rr0;
+      a.rr[cidx] = rrd;
+      a.iters[cidx] = iters;
+      if (broke) a.status[img] = 5;
+    }
+  }
+  // teardown: no bulk copy or MMA of this CTA in flight, no peer still reading
+  // this CTA's shared memory, then the tensor memory is freed
+  if (warp == 0 && lane == 0) {
+    for (int g = issued - S < 0 ? 0 : issued - S; g < issued; ++g)
+      if (!mbar_wait(&full[g % S], (g / S) & 1)) set_err(a.err, 24);
+  }
+  if (warp == 1 && lane == 0 && committed > 0 && !mbar_wait(accf, (committed - 1) & 1)) set_err(a.err, 25);
+  tc_fence_before();
+  cluster_sync_all();
+  if (warp == 1) {
+    __syncwarp();
+    tc_fence_after();
+    tmem_dealloc(tbase, 512);
+  }
+}
+
+template <int NT>
+size_t persist_smem(int* stages) {
+  const size_t stage = kChunkA + (size_t)NT * 128;
+  const size_t fixed = 1024 + (size_t)2 * NT * kPM * 4 + 2 * kPM * 8 + 16 + 64;
+  int S = (int)((225 * 1024 - fixed) / (stage + 16));
+  if (S > 6) S = 6;
+  *stages = S;
+  return fixed + (size_t)S * (stage + 16);
+}
+
+template <int NT>
+bool launch_nt(const PersistArgs& a0, cudaStream_t s) {
+  PersistArgs a = a0;
+  int S = 0;
+  const size_t smem = persist_smem<NT>(&S);
+  if (S < 2) return false;
+  a.stages = S;
+  auto kern = k_colcg_persist<NT>;
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return false;
+  const int CS = a.ny / NT;
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3((unsigned)(CS * a.tiles), (unsigned)a.nx);
+  cfg.blockDim = dim3(kPThreads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = (unsigned)CS;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, a) == cudaSuccess;
+}
+
+}  // namespace
+
+int colcg_persist_rows(int ny) {
+  if (ny % 16 != 0) return 0;
+  for (int nt : {80, 64, 48, 32})
+    if (ny % nt == 0 && ny / nt >= 2 && ny / nt <= 8) return nt;
+  return 0;
+}
+
+size_t colcg_persist_split_bytes(int ny, int nx, int B) {
+  return (size_t)nx * ((B + kPM - 1) / kPM) * (ny / 16) * kChunkA;
+}
+
+bool launch_colcg_persist(const void* G, const float* gscale, const float* R, float* X, uint8_t* psplit, double* rr0,
+                          double* rr, int* iters, int* status, int* err, int ny, int nx, int nb, int max_iter,
+                          double rtol2, float lam, cudaStream_t s) {
+  if (nb <= 0) return true;
+  const int nt = colcg_persist_rows(ny);
+  PersistArgs a{G, gscale, R, X, psplit, rr0, rr, iters, status, err, ny, nx, nb, (nb + kPM - 1) / kPM,
+                max_iter, 0, rtol2, lam};
+  switch (nt) {
+    case 80: return launch_nt<80>(a, s);
+    case 64: return launch_nt<64>(a, s);
+    case 48: return launch_nt<48>(a, s);
+    case 32: return launch_nt<32>(a, s);
+    default: return false;
+  }
+}
+
+}  // namespace pico

@@ -21,6 +21,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "f16_split.cuh"
 #include "kernels.cuh"
 #include "tc_util.cuh"
 
@@ -56,21 +57,6 @@ struct GramTile {
   }
 };
 
-// four FP32 values -> FP16 heads (rounded to nearest) and FP16 remainders,
-// each packed as four halves in a uint2 (element 0 in the low half)
-__device__ __forceinline__ uint32_t h2_bits(__half2 h) {
-  uint32_t u;
-  memcpy(&u, &h, sizeof(u));
-  return u;
-}
-__device__ __forceinline__ void split_f16x4(float a0, float a1, float a2, float a3, uint2& hi, uint2& lo) {
-  const __half2 h01 = __floats2half2_rn(a0, a1), h23 = __floats2half2_rn(a2, a3);
-  const float2 f01 = __half22float2(h01), f23 = __half22float2(h23);
-  hi = make_uint2(h2_bits(h01), h2_bits(h23));
-  lo = make_uint2(h2_bits(__floats2half2_rn(a0 - f01.x, a1 - f01.y)),
-                  h2_bits(__floats2half2_rn(a2 - f23.x, a3 - f23.y)));
-}
-
 __device__ __forceinline__ void set_err(int* err, int code) {
   if (err) atomicCAS(err, 0, code);
 }
@@ -99,18 +85,6 @@ __device__ __forceinline__ size_t gt_offset_h(int j, int y, int yp, int q, int n
   const int phys = (e >> 3) ^ ((r >> 2) & 1);
   return ((((size_t)j * (ny / nt) + t) * (ny / 16) + c) * 4 + q) * (size_t)nt * 16 + (size_t)r * 16 + 8 * phys +
          (e & 7);
-}
-
-// Power-of-two scale 2^(13 - floor(log2 bound)): a value of magnitude at most
-// `bound` times the scale stays below 2^14 (FP16 holds up to 65504), and the
-// scale itself is exact in FP32.  A zero or non-finite bound gives 1.
-__host__ __device__ __forceinline__ float pow2_scale(double bound) {
-  if (!(bound > 0.0) || !(bound < 1e300)) return 1.f;
-  int e = 0;
-  (void)frexp(bound, &e);            // bound = m 2^e, m in [0.5, 1)
-  int k = 14 - e;                    // bound * 2^k < 2^14
-  k = k > 100 ? 100 : (k < -100 ? -100 : k);
-  return ldexpf(1.f, k);
 }
 
 __global__ void k_gram_build(const float2* __restrict__ S, const double2* __restrict__ P, int nc, int ny, int nx,

@@ -177,6 +177,16 @@ void launch_to_cp(const float2* in, float* out, int ny, int nx, int nb, cudaStre
 // ---- colcg_small.cu: per-column CG with the whole solve on chip (ny <= 96) ----
 bool colcg_small_supported(int ny);
 // G_j of every column, plain layout [nx][ny][ny] complex64 (pbuf: ny double2 of device scratch)
+// Per-column CG of phase-encode images with the whole solve in one launch:
+// clusters of ny / NT CTAs (NT = colcg_persist_rows(ny), 0 if unsupported)
+// own a column and 128 images; G in the FP16 stage tiling of row blocks of NT
+// (launch_gram_build with nt = NT); psplit of colcg_persist_split_bytes().
+// R, X column-planar; rr0 / rr / iters per (image, column).
+int colcg_persist_rows(int ny);
+size_t colcg_persist_split_bytes(int ny, int nx, int B);
+bool launch_colcg_persist(const void* G, const float* gscale, const float* R, float* X, uint8_t* psplit, double* rr0,
+                          double* rr, int* iters, int* status, int* err, int ny, int nx, int nb, int max_iter,
+                          double rtol2, float lam, cudaStream_t s);
 void launch_colcg_small_build(const float2* smaps, const uint8_t* mask_host, int nc, int ny, int nx, float2* G,
                               float* gmax, double2* pbuf, cudaStream_t s);
 // Whole-image CG on the on-chip kernel: per-column partial sums exchanged

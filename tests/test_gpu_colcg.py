@@ -69,6 +69,40 @@ def test_column_cg_solutions_match_the_oracle(ny, nx, nc, nb, lam):
     op.close()
 
 
+@pytest.mark.parametrize("ny,nx,nc,nb,lam", [(320, 12, 6, 130, 0.01), (256, 10, 4, 5, 0.0), (128, 16, 4, 9, 0.0)])
+def test_whole_solve_launch_matches_per_update_launches(ny, nx, nc, nb, lam, monkeypatch):
+    """ny = 320, 256, 128 (clusters of 4, 4 and 2 CTAs): the per-column solve
+    runs as one launch per batch with x, r and p on chip for every iteration;
+    PICO_COLCG_PERSIST=0 selects one fused launch per update instead.  The same
+    CG on the same FP16 operands: the two agree to rounding (2e-5 of max|x|),
+    and the one-launch solve matches the oracle per element."""
+    S = synth.coil_maps(ny, nx, nc, 11)
+    cov = synth.noise_cov(nc, 11)
+    mask = synth.mask_pe(ny, 2, 8)
+    rhs = rand_imgs(nb, ny, nx, 12)
+    xs, counts = [], []
+    for v in ("1", "0"):
+        monkeypatch.setenv("PICO_COLCG_PERSIST", v)
+        op = pico.Operator(S, mask=mask, noise_cov=cov, lam=lam, power_iters=0, max_batch=nb)
+        op.set_solver("columns")
+        d = torch.from_numpy(rhs).cuda()
+        op.cg(d, 30, 0.0)
+        op.sync()
+        pico.pico_launch_count(op.ctx, reset=True)
+        x = op.cg(d, 30, 0.0)
+        op.sync()
+        counts.append(pico.pico_launch_count(op.ctx))
+        xs.append(x.cpu().numpy())
+        op.close()
+    assert np.abs(xs[0] - xs[1]).max() / np.abs(xs[1]).max() < 2e-5
+    assert counts[0] + 25 <= counts[1]              # one launch per solve instead of one per update
+    oop = O.Operator(S, cov, mask=mask)
+    check = sorted({0, nb - 1})
+    xo, _, _ = OS.cg_columns(oop, rhs[check].astype(np.complex128), lam, 30)
+    for i, b in enumerate(check):
+        assert np.abs(xs[0][b] - xo[i]).max() / np.abs(xo[i]).max() < 1e-4, b
+
+
 def test_column_cg_stopping_rule_and_report():
     op, oop = column_operator(320, 16, 6)
     rhs = rand_imgs(4, 320, 16, 5)
