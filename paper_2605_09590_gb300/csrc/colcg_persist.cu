@@ -332,6 +332,7 @@ __global__ void __launch_bounds__(kPThreads, 1) k_colcg_persist(PersistArgs a) {
         set_err(a.err, 23);
         xab[0] = 1;
       }
+      __syncwarp();  // the tensor-memory loads below are warp-collective
       tc_fence_after();
       ffloat pq{0.f, 0.f};
 #pragma unroll 1
@@ -367,33 +368,38 @@ __global__ void __launch_bounds__(kPThreads, 1) k_colcg_persist(PersistArgs a) {
         }
       }
       // ---- phase B: x += alpha p, r -= alpha q; ||r||^2 (scaled by ps^2) ----
+      // tensor-memory loads and stores are warp-collective: every lane takes
+      // part whenever one lane of its warp updates (the others store back
+      // what they loaded)
       ffloat rn{0.f, 0.f};
+      if (__any_sync(0xffffffffu, upd)) {
 #pragma unroll 1
-      for (int c = 0; c < NCH; ++c) {
-        float f = 0.f;
-        if (upd) {
+        for (int c = 0; c < NCH; ++c) {
+          float f = 0.f;
           float dr[16], di[16], pr[16], pi[16], xr[16], xi[16];
           tmem_ld16x2(tD + 16 * c, tD + NT + 16 * c, dr, di);
           tmem_ld16x2(tP + 16 * c, tP + NT + 16 * c, pr, pi);
           tmem_ld16x2(tX + 16 * c, tX + NT + 16 * c, xr, xi);
+          if (upd) {
 #pragma unroll
-          for (int u = 0; u < 16; ++u) {
-            const float qr = fmaf(lam, pr[u], dr[u] * fsc), qi = fmaf(lam, pi[u], di[u] * fsc);
-            xr[u] = fmaf(alpha, pr[u], xr[u]);
-            xi[u] = fmaf(alpha, pi[u], xi[u]);
-            float* rre = &r_re[(16 * c + u) * kPM + i];
-            float* rim = &r_im[(16 * c + u) * kPM + i];
-            const float nr = fmaf(-alpha, qr, *rre), ni = fmaf(-alpha, qi, *rim);
-            *rre = nr;
-            *rim = ni;
-            f = fmaf(nr * ps, nr * ps, fmaf(ni * ps, ni * ps, f));
+            for (int u = 0; u < 16; ++u) {
+              const float qr = fmaf(lam, pr[u], dr[u] * fsc), qi = fmaf(lam, pi[u], di[u] * fsc);
+              xr[u] = fmaf(alpha, pr[u], xr[u]);
+              xi[u] = fmaf(alpha, pi[u], xi[u]);
+              float* rre = &r_re[(16 * c + u) * kPM + i];
+              float* rim = &r_im[(16 * c + u) * kPM + i];
+              const float nr = fmaf(-alpha, qr, *rre), ni = fmaf(-alpha, qi, *rim);
+              *rre = nr;
+              *rim = ni;
+              f = fmaf(nr * ps, nr * ps, fmaf(ni * ps, ni * ps, f));
+            }
           }
           tmem_st16(tX + 16 * c, xr);
           tmem_st16(tX + NT + 16 * c, xi);
+          rn = ff_add(rn, ffloat{f, 0.f});
         }
-        rn = ff_add(rn, ffloat{f, 0.f});
+        tmem_wait_st();
       }
-      tmem_wait_st();
       xrr[i] = rn;
     }
     tc_fence_before();
@@ -428,24 +434,30 @@ __global__ void __launch_bounds__(kPThreads, 1) k_colcg_persist(PersistArgs a) {
         const float psn = pow2_scale_f(pn);
         rrs = ff_scale(rrs, (psn / ps) * (psn / ps));  // exact: powers of two
         ps = psn;
+      }
+      if (__any_sync(0xffffffffu, cont)) {  // warp-collective, as in phase B
 #pragma unroll 1
         for (int c = 0; c < NCH; ++c) {
           float pr[16], pi[16];
           tmem_ld16x2(tP + 16 * c, tP + NT + 16 * c, pr, pi);
+          if (cont) {
 #pragma unroll
-          for (int u = 0; u < 16; ++u) {
-            pr[u] = fmaf(beta, pr[u], r_re[(16 * c + u) * kPM + i]);
-            pi[u] = fmaf(beta, pi[u], r_im[(16 * c + u) * kPM + i]);
+            for (int u = 0; u < 16; ++u) {
+              pr[u] = fmaf(beta, pr[u], r_re[(16 * c + u) * kPM + i]);
+              pi[u] = fmaf(beta, pi[u], r_im[(16 * c + u) * kPM + i]);
+            }
           }
           tmem_st16(tP + 16 * c, pr);
           tmem_st16(tP + NT + 16 * c, pi);
-          uint8_t* ch = pcol + (size_t)(kc0 + c) * kChunkA;
-          store_split16(ch, 0, 2, i, pr, ps);
-          store_split16(ch, 1, 3, i, pi, ps);
+          if (cont) {
+            uint8_t* ch = pcol + (size_t)(kc0 + c) * kChunkA;
+            store_split16(ch, 0, 2, i, pr, ps);
+            store_split16(ch, 1, 3, i, pi, ps);
+          }
         }
         tmem_wait_st();
         fence_proxy_async_global();
-        xab[1 + ((it + 1) & 1)] = 1;
+        if (cont) xab[1 + ((it + 1) & 1)] = 1;
       }
     }
     tc_fence_before();
@@ -460,18 +472,24 @@ __global__ void __launch_bounds__(kPThreads, 1) k_colcg_persist(PersistArgs a) {
   }
 
   // ---- results: x to global, the column's scalars (rank 0) ----
-  if (valid) {
-    float* xre = a.X + ((size_t)img * a.nx + j) * 2 * a.ny + n0;
+  if (epi) {  // every epilogue lane loads (warp-collective); valid lanes store
+    float* xre = a.X + ((size_t)(valid ? img : 0) * a.nx + j) * 2 * a.ny + n0;
     float* xim = xre + a.ny;
     for (int c = 0; c < NCH; ++c) {
       float xr[16], xi[16];
       tmem_ld16x2(tX + 16 * c, tX + NT + 16 * c, xr, xi);
+      if (valid) {
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        reinterpret_cast<float4*>(xre + 16 * c)[u] = make_float4(xr[4 * u], xr[4 * u + 1], xr[4 * u + 2], xr[4 * u + 3]);
-        reinterpret_cast<float4*>(xim + 16 * c)[u] = make_float4(xi[4 * u], xi[4 * u + 1], xi[4 * u + 2], xi[4 * u + 3]);
+        for (int u = 0; u < 4; ++u) {
+          reinterpret_cast<float4*>(xre + 16 * c)[u] =
+              make_float4(xr[4 * u], xr[4 * u + 1], xr[4 * u + 2], xr[4 * u + 3]);
+          reinterpret_cast<float4*>(xim + 16 * c)[u] =
+              make_float4(xi[4 * u], xi[4 * u + 1], xi[4 * u + 2], xi[4 * u + 3]);
+        }
       }
     }
+  }
+  if (valid) {
     if (rank == 0) {
       const size_t cidx = (size_t)img * a.nx + j;
       a.rr0[cidx] = rr0;
