@@ -43,7 +43,7 @@ namespace {
 using namespace tc;
 
 constexpr int kPM = 128;                    // images per cluster (MMA M, one per tensor-memory lane)
-constexpr int kPThreads = 192;              // warp 0 loads, warp 1 MMA, warps 2-5 epilogue
+constexpr int kPThreads = 320;              // warp 0 loads, warp 1 MMA, warps 2-9 epilogue (two halves)
 constexpr uint32_t kPlaneA = kPM * 32;      // one FP16 plane of a 16-row chunk: 4 KB
 constexpr uint32_t kChunkA = 4 * kPlaneA;   // [re head | im head | re rem | im rem]: 16 KB
 
@@ -108,28 +108,23 @@ __device__ __forceinline__ float ff_div(ffloat a, ffloat b) {
 }
 __device__ __forceinline__ ffloat ff_scale(ffloat a, float pow2) { return ffloat{a.hi * pow2, a.lo * pow2}; }
 
-// the FP16 split of 16 values (one plane pair) of image row i into a chunk:
-// 32-byte rows, the two 16-byte groups swapped on rows 4..7 of every 8-row atom
-__device__ __forceinline__ void store_split16(uint8_t* chunk, int plane_hi, int plane_lo, int i, const float* v,
-                                              float sc) {
-  uint2 h[4], l[4];
-#pragma unroll
-  for (int g = 0; g < 4; ++g) split_f16x4(v[4 * g] * sc, v[4 * g + 1] * sc, v[4 * g + 2] * sc, v[4 * g + 3] * sc, h[g], l[g]);
-  const int sw = (i >> 2) & 1;
-#pragma unroll
-  for (int g = 0; g < 2; ++g) {
-    const size_t off = (size_t)i * 32 + (size_t)((g ^ sw) * 16);
-    *reinterpret_cast<uint4*>(chunk + (size_t)plane_hi * kPlaneA + off) =
-        make_uint4(h[2 * g].x, h[2 * g].y, h[2 * g + 1].x, h[2 * g + 1].y);
-    *reinterpret_cast<uint4*>(chunk + (size_t)plane_lo * kPlaneA + off) =
-        make_uint4(l[2 * g].x, l[2 * g].y, l[2 * g + 1].x, l[2 * g + 1].y);
-  }
+// the FP16 split of 8 values (one plane pair) of image row i into logical
+// 16-byte group g of a chunk: 32-byte rows, the two groups swapped on rows
+// 4..7 of every 8-row atom (32-byte swizzle)
+__device__ __forceinline__ void store_split8(uint8_t* chunk, int plane_hi, int plane_lo, int i, int g, const float* v,
+                                             float sc) {
+  uint2 h0, l0, h1, l1;
+  split_f16x4(v[0] * sc, v[1] * sc, v[2] * sc, v[3] * sc, h0, l0);
+  split_f16x4(v[4] * sc, v[5] * sc, v[6] * sc, v[7] * sc, h1, l1);
+  const size_t off = (size_t)i * 32 + (size_t)((g ^ ((i >> 2) & 1)) * 16);
+  *reinterpret_cast<uint4*>(chunk + (size_t)plane_hi * kPlaneA + off) = make_uint4(h0.x, h0.y, h1.x, h1.y);
+  *reinterpret_cast<uint4*>(chunk + (size_t)plane_lo * kPlaneA + off) = make_uint4(l0.x, l0.y, l1.x, l1.y);
 }
 
 template <int NT>
 __global__ void __launch_bounds__(kPThreads, 1) k_colcg_persist(PersistArgs a) {
   static_assert(NT % 16 == 0 && 6 * NT <= 512, "row block");
-  constexpr int NCH = NT / 16;               // 16-row chunks of this CTA
+  constexpr int NO = NT / 8;                 // 8-row octets of this CTA; epilogue half h takes o = h, h + 2, ...
   constexpr uint32_t kB = NT * 128;          // B block: 4 FP16 planes of NT x 16
   constexpr uint32_t kStage = kChunkA + kB;
   extern __shared__ uint8_t smraw[];
@@ -137,9 +132,9 @@ __global__ void __launch_bounds__(kPThreads, 1) k_colcg_persist(PersistArgs a) {
   const int S = a.stages;
   float* r_re = reinterpret_cast<float*>(sm + (size_t)S * kStage);  // [NT][128]
   float* r_im = r_re + NT * kPM;
-  ffloat* xpq = reinterpret_cast<ffloat*>(r_im + NT * kPM);  // [128] exchange slots
-  ffloat* xrr = xpq + kPM;
-  int* xab = reinterpret_cast<int*>(xrr + kPM);  // [0] sticky error flag, [1..2] any-live by iteration parity
+  ffloat* xpq = reinterpret_cast<ffloat*>(r_im + NT * kPM);  // [2 halves][128] exchange slots
+  ffloat* xrr = xpq + 2 * kPM;
+  int* xab = reinterpret_cast<int*>(xrr + 2 * kPM);  // [0] sticky error flag, [1..2] any-live by iteration parity
   uint64_t* full = reinterpret_cast<uint64_t*>(xab + 4);
   uint64_t* empty = full + S;
   uint64_t* accf = empty + S;
@@ -171,8 +166,10 @@ __global__ void __launch_bounds__(kPThreads, 1) k_colcg_persist(PersistArgs a) {
   tc_fence_after();
   const uint32_t tbase = *tslot;
 
-  // epilogue thread state: image i of the tile (tensor-memory lane i)
+  // epilogue thread state: image i of the tile (tensor-memory lane i), rows of
+  // the octets of half h
   const bool epi = warp >= 2;
+  const int h = (warp - 2) >> 2;
   const int quarter = warp & 3, i = 32 * quarter + lane, img = m0 + i;
   const bool valid = epi && img < a.nb;
   const uint32_t tl = tbase + ((uint32_t)(32 * quarter) << 16);
@@ -184,60 +181,69 @@ __global__ void __launch_bounds__(kPThreads, 1) k_colcg_persist(PersistArgs a) {
   float pn = 0.f, ps = 1.f;
   bool live = false, broke = false;
   int iters = 0;
+  // sum of the 2 CS partials of image i in (rank, half) order: the same bits on every CTA and half
+  auto gather = [&](const ffloat* slots) {
+    ffloat t{0.f, 0.f};
+    for (int rk = 0; rk < CS; ++rk) {
+      t = ff_add(t, ld_dsmem_ff(&slots[i], (uint32_t)rk));
+      t = ff_add(t, ld_dsmem_ff(&slots[kPM + i], (uint32_t)rk));
+    }
+    return t;
+  };
 
   // ---- start: r = b, x = 0, p = r; ||b_j||^2; the split of p for the first main loop ----
   if (epi) {
     const float* bre = a.R + ((size_t)(valid ? img : 0) * a.nx + j) * 2 * a.ny + n0;
     const float* bim = bre + a.ny;
     float mx = 0.f;
+    const float zero[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    for (int o = h; o < NO; o += 2) {
+      float vr[8], vi[8];
 #pragma unroll
-    for (int c = 0; c < NCH; ++c) {
-      float vr[16], vi[16];
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const float4 w = valid ? reinterpret_cast<const float4*>(bre + 16 * c)[u] : make_float4(0.f, 0.f, 0.f, 0.f);
-        const float4 z = valid ? reinterpret_cast<const float4*>(bim + 16 * c)[u] : make_float4(0.f, 0.f, 0.f, 0.f);
+      for (int u = 0; u < 2; ++u) {
+        const float4 w = valid ? reinterpret_cast<const float4*>(bre + 8 * o)[u] : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float4 z = valid ? reinterpret_cast<const float4*>(bim + 8 * o)[u] : make_float4(0.f, 0.f, 0.f, 0.f);
         vr[4 * u] = w.x; vr[4 * u + 1] = w.y; vr[4 * u + 2] = w.z; vr[4 * u + 3] = w.w;
         vi[4 * u] = z.x; vi[4 * u + 1] = z.y; vi[4 * u + 2] = z.z; vi[4 * u + 3] = z.w;
       }
-      float zero[16];
 #pragma unroll
-      for (int u = 0; u < 16; ++u) {
-        r_re[(16 * c + u) * kPM + i] = vr[u];
-        r_im[(16 * c + u) * kPM + i] = vi[u];
+      for (int u = 0; u < 8; ++u) {
+        r_re[(8 * o + u) * kPM + i] = vr[u];
+        r_im[(8 * o + u) * kPM + i] = vi[u];
         mx = fmaxf(mx, fmaxf(fabsf(vr[u]), fabsf(vi[u])));
-        zero[u] = 0.f;
       }
-      tmem_st16(tP + 16 * c, vr);
-      tmem_st16(tP + NT + 16 * c, vi);
-      tmem_st16(tX + 16 * c, zero);
-      tmem_st16(tX + NT + 16 * c, zero);
+      tmem_st8(tP + 8 * o, vr);
+      tmem_st8(tP + NT + 8 * o, vi);
+      tmem_st8(tX + 8 * o, zero);
+      tmem_st8(tX + NT + 8 * o, zero);
     }
     tmem_wait_st();
-    // this CTA's ||b||^2 over its rows, scaled by its largest entry (float-float)
+    // this half's ||b||^2 over its rows, scaled by its largest entry (float-float)
     const float sb = pow2_scale_f(mx);
     ffloat acc{0.f, 0.f};
-    for (int c = 0; c < NCH; ++c) {
+    for (int o = h; o < NO; o += 2) {
       float f = 0.f;
 #pragma unroll
-      for (int u = 0; u < 16; ++u) {
-        const float br = r_re[(16 * c + u) * kPM + i] * sb, bi = r_im[(16 * c + u) * kPM + i] * sb;
+      for (int u = 0; u < 8; ++u) {
+        const float br = r_re[(8 * o + u) * kPM + i] * sb, bi = r_im[(8 * o + u) * kPM + i] * sb;
         f = fmaf(br, br, fmaf(bi, bi, f));
       }
       acc = ff_add(acc, ffloat{f, 0.f});
     }
-    const double part = ff_unscale(acc, 2 * exp2_of(sb));
-    reinterpret_cast<double*>(xrr)[i] = part;
+    reinterpret_cast<double*>(xrr)[h * kPM + i] = ff_unscale(acc, 2 * exp2_of(sb));
   }
   cluster_sync_all();
   if (epi) {
-    for (int rk = 0; rk < CS; ++rk) {
-      uint32_t ra;
-      asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(ra) : "r"(smem_u32(&xrr[i])), "r"((uint32_t)rk));
-      double v;
-      asm volatile("ld.shared::cluster.f64 %0, [%1];" : "=d"(v) : "r"(ra) : "memory");
-      rr0 += v;
-    }
+    for (int rk = 0; rk < CS; ++rk)
+      for (int hh = 0; hh < 2; ++hh) {
+        uint32_t ra;
+        asm volatile("mapa.shared::cluster.u32 %0, %1, %2;"
+                     : "=r"(ra)
+                     : "r"(smem_u32(reinterpret_cast<double*>(xrr) + hh * kPM + i)), "r"((uint32_t)rk));
+        double v;
+        asm volatile("ld.shared::cluster.f64 %0, [%1];" : "=d"(v) : "r"(ra) : "memory");
+        rr0 += v;
+      }
     rrd = rr0;
     const bool bad = !isfinite(rr0);
     live = valid && !bad && rr0 > 0.0;
@@ -246,20 +252,20 @@ __global__ void __launch_bounds__(kPThreads, 1) k_colcg_persist(PersistArgs a) {
     ps = pow2_scale_f(pn);
     {
       const double v = rr0 * (double)ps * (double)ps;
-      const float h = (float)v;
-      rrs = ffloat{h, (float)(v - (double)h)};
+      const float hi = (float)v;
+      rrs = ffloat{hi, (float)(v - (double)hi)};
     }
-    // the split of p = b for this CTA's chunks
-    for (int c = 0; c < NCH; ++c) {
-      float vr[16], vi[16];
+    // the split of p = b for this half's octets
+    for (int o = h; o < NO; o += 2) {
+      float vr[8], vi[8];
 #pragma unroll
-      for (int u = 0; u < 16; ++u) {
-        vr[u] = r_re[(16 * c + u) * kPM + i];
-        vi[u] = r_im[(16 * c + u) * kPM + i];
+      for (int u = 0; u < 8; ++u) {
+        vr[u] = r_re[(8 * o + u) * kPM + i];
+        vi[u] = r_im[(8 * o + u) * kPM + i];
       }
-      uint8_t* ch = pcol + (size_t)(kc0 + c) * kChunkA;
-      store_split16(ch, 0, 2, i, vr, ps);
-      store_split16(ch, 1, 3, i, vi, ps);
+      uint8_t* ch = pcol + (size_t)(kc0 + (o >> 1)) * kChunkA;
+      store_split8(ch, 0, 2, i, o & 1, vr, ps);
+      store_split8(ch, 1, 3, i, o & 1, vi, ps);
     }
     fence_proxy_async_global();  // generic writes of the split, read by the peers' bulk copies
     if (live) xab[1] = 1;  // any live system in this tile (benign race: every writer stores 1)
@@ -336,19 +342,18 @@ __global__ void __launch_bounds__(kPThreads, 1) k_colcg_persist(PersistArgs a) {
       tc_fence_after();
       ffloat pq{0.f, 0.f};
 #pragma unroll 1
-      for (int c = 0; c < NCH; ++c) {
-        float dr[16], di[16], pr[16], pi[16];
-        tmem_ld16x2(tD + 16 * c, tD + NT + 16 * c, dr, di);
-        tmem_ld16x2(tP + 16 * c, tP + NT + 16 * c, pr, pi);
+      for (int o = h; o < NO; o += 2) {
+        float dr[8], di[8], pr[8], pi[8];
+        tmem_ld8x4(tD + 8 * o, tD + NT + 8 * o, tP + 8 * o, tP + NT + 8 * o, dr, di, pr, pi);
         float f = 0.f;
 #pragma unroll
-        for (int u = 0; u < 16; ++u) {
+        for (int u = 0; u < 8; ++u) {
           const float qr = fmaf(lam, pr[u], dr[u] * fsc), qi = fmaf(lam, pi[u], di[u] * fsc);
           f = fmaf(pr[u] * ps, qr * ps, fmaf(pi[u] * ps, qi * ps, f));
         }
         pq = ff_add(pq, ffloat{f, 0.f});
       }
-      xpq[i] = pq;
+      xpq[h * kPM + i] = pq;
     }
     tc_fence_before();
     cluster_sync_all();  // exchange 1
@@ -356,8 +361,7 @@ __global__ void __launch_bounds__(kPThreads, 1) k_colcg_persist(PersistArgs a) {
     float alpha = 0.f;
     bool upd = false;
     if (epi) {
-      ffloat pqt{0.f, 0.f};
-      for (int rk = 0; rk < CS; ++rk) pqt = ff_add(pqt, ld_dsmem_ff(&xpq[i], (uint32_t)rk));
+      const ffloat pqt = gather(xpq);
       if (live) {
         if (!(pqt.hi > 0.f) || !isfinite(pqt.hi)) {
           live = false;
@@ -374,40 +378,38 @@ __global__ void __launch_bounds__(kPThreads, 1) k_colcg_persist(PersistArgs a) {
       ffloat rn{0.f, 0.f};
       if (__any_sync(0xffffffffu, upd)) {
 #pragma unroll 1
-        for (int c = 0; c < NCH; ++c) {
+        for (int o = h; o < NO; o += 2) {
           float f = 0.f;
-          float dr[16], di[16], pr[16], pi[16], xr[16], xi[16];
-          tmem_ld16x2(tD + 16 * c, tD + NT + 16 * c, dr, di);
-          tmem_ld16x2(tP + 16 * c, tP + NT + 16 * c, pr, pi);
-          tmem_ld16x2(tX + 16 * c, tX + NT + 16 * c, xr, xi);
+          float dr[8], di[8], pr[8], pi[8], xr[8], xi[8];
+          tmem_ld8x6(tD + 8 * o, tD + NT + 8 * o, tP + 8 * o, tP + NT + 8 * o, tX + 8 * o, tX + NT + 8 * o, dr, di,
+                     pr, pi, xr, xi);
           if (upd) {
 #pragma unroll
-            for (int u = 0; u < 16; ++u) {
+            for (int u = 0; u < 8; ++u) {
               const float qr = fmaf(lam, pr[u], dr[u] * fsc), qi = fmaf(lam, pi[u], di[u] * fsc);
               xr[u] = fmaf(alpha, pr[u], xr[u]);
               xi[u] = fmaf(alpha, pi[u], xi[u]);
-              float* rre = &r_re[(16 * c + u) * kPM + i];
-              float* rim = &r_im[(16 * c + u) * kPM + i];
+              float* rre = &r_re[(8 * o + u) * kPM + i];
+              float* rim = &r_im[(8 * o + u) * kPM + i];
               const float nr = fmaf(-alpha, qr, *rre), ni = fmaf(-alpha, qi, *rim);
               *rre = nr;
               *rim = ni;
               f = fmaf(nr * ps, nr * ps, fmaf(ni * ps, ni * ps, f));
             }
           }
-          tmem_st16(tX + 16 * c, xr);
-          tmem_st16(tX + NT + 16 * c, xi);
+          tmem_st8(tX + 8 * o, xr);
+          tmem_st8(tX + NT + 8 * o, xi);
           rn = ff_add(rn, ffloat{f, 0.f});
         }
         tmem_wait_st();
       }
-      xrr[i] = rn;
+      xrr[h * kPM + i] = rn;
     }
     tc_fence_before();
     cluster_sync_all();  // exchange 2
     tc_fence_after();
     if (epi) {
-      ffloat rnt{0.f, 0.f};
-      for (int rk = 0; rk < CS; ++rk) rnt = ff_add(rnt, ld_dsmem_ff(&xrr[i], (uint32_t)rk));
+      const ffloat rnt = gather(xrr);
       float beta = 0.f;
       bool cont = false;
       if (upd) {
@@ -437,22 +439,22 @@ __global__ void __launch_bounds__(kPThreads, 1) k_colcg_persist(PersistArgs a) {
       }
       if (__any_sync(0xffffffffu, cont)) {  // warp-collective, as in phase B
 #pragma unroll 1
-        for (int c = 0; c < NCH; ++c) {
-          float pr[16], pi[16];
-          tmem_ld16x2(tP + 16 * c, tP + NT + 16 * c, pr, pi);
+        for (int o = h; o < NO; o += 2) {
+          float pr[8], pi[8];
+          tmem_ld8x2(tP + 8 * o, tP + NT + 8 * o, pr, pi);
           if (cont) {
 #pragma unroll
-            for (int u = 0; u < 16; ++u) {
-              pr[u] = fmaf(beta, pr[u], r_re[(16 * c + u) * kPM + i]);
-              pi[u] = fmaf(beta, pi[u], r_im[(16 * c + u) * kPM + i]);
+            for (int u = 0; u < 8; ++u) {
+              pr[u] = fmaf(beta, pr[u], r_re[(8 * o + u) * kPM + i]);
+              pi[u] = fmaf(beta, pi[u], r_im[(8 * o + u) * kPM + i]);
             }
           }
-          tmem_st16(tP + 16 * c, pr);
-          tmem_st16(tP + NT + 16 * c, pi);
+          tmem_st8(tP + 8 * o, pr);
+          tmem_st8(tP + NT + 8 * o, pi);
           if (cont) {
-            uint8_t* ch = pcol + (size_t)(kc0 + c) * kChunkA;
-            store_split16(ch, 0, 2, i, pr, ps);
-            store_split16(ch, 1, 3, i, pi, ps);
+            uint8_t* ch = pcol + (size_t)(kc0 + (o >> 1)) * kChunkA;
+            store_split8(ch, 0, 2, i, o & 1, pr, ps);
+            store_split8(ch, 1, 3, i, o & 1, pi, ps);
           }
         }
         tmem_wait_st();
@@ -471,32 +473,28 @@ __global__ void __launch_bounds__(kPThreads, 1) k_colcg_persist(PersistArgs a) {
     if (threadIdx.x == 0) xab[1 + (it & 1)] = 0;
   }
 
-  // ---- results: x to global, the column's scalars (rank 0) ----
+  // ---- results: x to global, the column's scalars (rank 0, half 0) ----
   if (epi) {  // every epilogue lane loads (warp-collective); valid lanes store
     float* xre = a.X + ((size_t)(valid ? img : 0) * a.nx + j) * 2 * a.ny + n0;
     float* xim = xre + a.ny;
-    for (int c = 0; c < NCH; ++c) {
-      float xr[16], xi[16];
-      tmem_ld16x2(tX + 16 * c, tX + NT + 16 * c, xr, xi);
+    for (int o = h; o < NO; o += 2) {
+      float xr[8], xi[8];
+      tmem_ld8x2(tX + 8 * o, tX + NT + 8 * o, xr, xi);
       if (valid) {
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          reinterpret_cast<float4*>(xre + 16 * c)[u] =
-              make_float4(xr[4 * u], xr[4 * u + 1], xr[4 * u + 2], xr[4 * u + 3]);
-          reinterpret_cast<float4*>(xim + 16 * c)[u] =
-              make_float4(xi[4 * u], xi[4 * u + 1], xi[4 * u + 2], xi[4 * u + 3]);
+        for (int u = 0; u < 2; ++u) {
+          reinterpret_cast<float4*>(xre + 8 * o)[u] = make_float4(xr[4 * u], xr[4 * u + 1], xr[4 * u + 2], xr[4 * u + 3]);
+          reinterpret_cast<float4*>(xim + 8 * o)[u] = make_float4(xi[4 * u], xi[4 * u + 1], xi[4 * u + 2], xi[4 * u + 3]);
         }
       }
     }
   }
-  if (valid) {
-    if (rank == 0) {
-      const size_t cidx = (size_t)img * a.nx + j;
-      a.rr0[cidx] = rr0;
-      a.rr[cidx] = rrd;
-      a.iters[cidx] = iters;
-      if (broke) a.status[img] = 5;
-    }
+  if (valid && rank == 0 && h == 0) {
+    const size_t cidx = (size_t)img * a.nx + j;
+    a.rr0[cidx] = rr0;
+    a.rr[cidx] = rrd;
+    a.iters[cidx] = iters;
+    if (broke) a.status[img] = 5;
   }
   // teardown: no bulk copy or MMA of this CTA in flight, no peer still reading
   // this CTA's shared memory, then the tensor memory is freed
@@ -517,7 +515,7 @@ __global__ void __launch_bounds__(kPThreads, 1) k_colcg_persist(PersistArgs a) {
 template <int NT>
 size_t persist_smem(int* stages) {
   const size_t stage = kChunkA + (size_t)NT * 128;
-  const size_t fixed = 1024 + (size_t)2 * NT * kPM * 4 + 2 * kPM * 8 + 16 + 64;
+  const size_t fixed = 1024 + (size_t)2 * NT * kPM * 4 + 4 * kPM * 8 + 16 + 64;
   int S = (int)((225 * 1024 - fixed) / (stage + 16));
   if (S > 6) S = 6;
   *stages = S;
