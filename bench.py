@@ -159,9 +159,11 @@ def kernel_digest(*names):
 # full-size launches averaged, a one-pass metric set), keyed by (workload,
 # images per launch, kernel, digest of the kernel sources at capture time): a
 # changed kernel no longer matches and its traffic is reported as null.
+GRAM_FILES = ("gram.cu", "tc_util.cuh", "kernels.cuh", "f16_split.cuh")
+PERSIST_FILES = ("colcg_persist.cu", "tc_util.cuh", "kernels.cuh", "f16_split.cuh")
 TRAFFIC = {
-    ("knee320_r2", 256, "gram", "90524d46254e97cb"): 713.701632e6 + 376.994048e6,
-    ("knee320_r2", 256, "colcg", "90524d46254e97cb"): 1009.139072e6 + 577.829120e6,
+    ("knee320_r2", 256, "gram", "8fd4b6b46356da2c"): (713.479680e6 + 379.019776e6 + 708.991744e6 + 374.740992e6) / 2,
+    ("knee320_r2", 256, "persist", "35d7a1516b1bd69e"): (473.900288e6 + 375.552256e6 + 473.232128e6 + 372.398848e6) / 2,
 }
 
 
@@ -188,7 +190,7 @@ def gram_roofline(w, K, avg_s, launches):
     mp = measured_peaks()
     alg = alg_bytes_normal(w, K)
     achieved = alg / avg_s / 1e9
-    traffic, dig = traffic_of(w, K, "gram", ("gram.cu", "tc_util.cuh", "kernels.cuh"))
+    traffic, dig = traffic_of(w, K, "gram", GRAM_FILES)
     cplx = 8.0 * w.ny * w.ny * w.nx * K
     return {"bound": "hbm", "achieved": achieved, "peak": mp["hbm_gbs"], "unit": "GB/s",
             "frac": achieved / mp["hbm_gbs"], "traffic": traffic,
@@ -738,7 +740,7 @@ def colcg_roofline(w, K, avg_s, launches):
     V = w.ny * w.nx * 8
     alg = 6 * K * V + w.nc * V
     achieved = alg / avg_s / 1e9
-    traffic, dig = traffic_of(w, K, "colcg", ("gram.cu", "tc_util.cuh", "kernels.cuh"))
+    traffic, dig = traffic_of(w, K, "colcg", GRAM_FILES)
     return {"bound": "hbm", "achieved": achieved, "peak": mp["hbm_gbs"], "unit": "GB/s",
             "frac": achieved / mp["hbm_gbs"], "traffic": traffic,
             "traffic_over_algorithmic": traffic / alg if traffic else None,
@@ -776,8 +778,10 @@ def persist_roofline(w, K, avg_s, launches):
     V = w.ny * w.nx * 8
     byts = 2 * K * V + 8 * w.nx * w.ny * w.ny
     peak = mp["bf16_tflops_sustained"]
+    traffic, dig = traffic_of(w, K, "persist", PERSIST_FILES)
     return {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-            "frac": achieved / peak, "traffic": None,
+            "frac": achieved / peak, "traffic": traffic, "kernel_digest": dig,
+            "traffic_over_hbm_bytes": traffic / byts if traffic else None,
             "kernel": "k_colcg_persist<%d> (whole per-column CG solve per launch: clusters of %d CTAs own a column "
                       "and 128 images, x / p / accumulator in tensor memory, r in shared memory, tcgen05 "
                       "kind::f16)" % (nt, w.ny // nt),

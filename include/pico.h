@@ -151,15 +151,24 @@ pico_status pico_cg_batch(pico_ctx* ctx, const void* rhs_dev, void* x_dev, int32
  *                        (the exact solution); the iterates after a fixed number
  *                        of updates differ from the global CG's (each column's
  *                        iterate minimises that column's error in its own energy
- *                        norm, so no column converges slower).  Every update is
+ *                        norm, so no column converges slower).  With FP16
+ *                        operands and ny a multiple of a row block of 80,
+ *                        64, 48 or 32 rows with at most 8 blocks (ny = 128,
+ *                        160, 192, 256, 320, 384, 512, ...) a whole solve is
+ *                        one launch (x, r, p stay on chip for every update;
+ *                        PICO_COLCG_PERSIST=0 in the environment at
+ *                        pico_init turns this off); otherwise every update is
  *                        one fused launch on the tensor cores.  relres_out of
  *                        pico_cg_batch is ||r|| / ||rhs|| over the image and
  *                        iters_out the most updates any column took.
  * PICO_E_UNSUPPORTED for PICO_SOLVER_COLUMNS unless the context runs the
  * tensor-core operator (pico_info.normal_op == 1) with a row tile that is a
- * multiple of 32 and at most 4 tiles per column (e.g. ny = 128, 160, 192, 256,
- * 320, 384, 512).  Drops the context's captured CUDA graphs; allocates
- * 28 bytes per (image, column) on first use. */
+ * multiple of 32 and at most 4 tiles per column, or keeps its solves on chip
+ * (normal_op == 3).  Drops the context's captured CUDA graphs; allocates
+ * 28 bytes per (image, column) on first use, and for the one-launch solve
+ * the FP16 G_j in its row tiling (8 nx ny^2 bytes) and the shared split
+ * direction (ny / 16 x 16 KB per column and 128-image tile), unless that
+ * would pass the context's hbm_budget (then the per-update kernel runs). */
 pico_status pico_set_solver(pico_ctx* ctx, int32_t solver);
 pico_status pico_get_solver(const pico_ctx* ctx, int32_t* solver);
 

@@ -2,19 +2,22 @@
 
 With a phase-encode mask A^H A is block diagonal over the readout columns, so
 the normal equations split into nx independent ny x ny systems; the context
-then runs CG on every column with its own step lengths and stopping test, one
-fused tensor-core launch per update (x and r updated in the operator's
-epilogue, the column's sums added across the row tiles of a thread-block
-cluster).  The oracle is ``oracle.solvers.cg_columns`` (the same CG on every
+then runs CG on every column with its own step lengths and stopping test:
+for ny >= 128 the whole solve in one launch (a thread-block cluster owns a
+column and 128 images; x, r, p on chip for every update), or one fused
+tensor-core launch per update (PICO_COLCG_PERSIST=0: x and r updated in the
+operator's epilogue, the column's sums added across the row tiles of a
+cluster); for ny = 32, 64, 96 the whole solve on chip in shared memory.  The oracle is ``oracle.solvers.cg_columns`` (the same CG on every
 column's dense block, FP64), pinned in tests/test_oracle_pins.py.
 
 Tolerances: the solutions after 30 updates agree per element to
 1e-4 max|x| (FP32 against FP64, the same bound as the whole-image CG); PICO
 maps per voxel to 1e-4 of the exact diagonal Sigma_kk (the spec bar for
-identical probe seeds).  Cases cover one row tile (ny = 128, no cluster), two
-(ny = 320: a cluster of 2, both phase-B buffers), two with a single phase-B
-buffer (ny = 384), ragged image tiles (batches that are not multiples of 128)
-and the bench's full launch shape (320 x 320, 15 coils, 256 probes).
+identical probe seeds).  Cases cover clusters of 2, 4 and 6 CTAs (ny = 128,
+320, 384; 256 in the comparison with the per-update kernel), ragged image
+tiles (batches that are not multiples of 128, warps with finished and
+unused lanes) and the bench's full launch shape (320 x 320, 15 coils, 256
+probes).
 """
 import numpy as np
 import pytest
