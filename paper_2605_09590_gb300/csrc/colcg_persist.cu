@@ -125,6 +125,7 @@ template <int NT>
 __global__ void __launch_bounds__(kPThreads, 1) k_colcg_persist(PersistArgs a) {
   static_assert(NT % 16 == 0 && 6 * NT <= 512, "row block");
   constexpr int NO = NT / 8;                 // 8-row octets of this CTA; epilogue half h takes o = h, h + 2, ...
+  constexpr int NCH = NT / 16;               // 16-row chunks of this CTA (its own main-loop stages)
   constexpr uint32_t kB = NT * 128;          // B block: 4 FP16 planes of NT x 16
   constexpr uint32_t kStage = kChunkA + kB;
   extern __shared__ uint8_t smraw[];
@@ -189,6 +190,70 @@ __global__ void __launch_bounds__(kPThreads, 1) k_colcg_persist(PersistArgs a) {
       t = ff_add(t, ld_dsmem_ff(&slots[kPM + i], (uint32_t)rk));
     }
     return t;
+  };
+
+  // Main-loop stage t of update `it` takes chunk (kc0 + t) mod ny/16: this
+  // CTA's own chunks come first, so that they can be loaded and multiplied
+  // while the cluster barrier that publishes the peers' chunks completes.
+  int issued = 0;     // stages issued by the producer (all updates)
+  int committed = 0;  // accumulator commits by the MMA thread
+  auto produce = [&](int it, int t0, int t1) -> bool {  // producer thread: stages t0 .. t1 - 1
+    for (int t = t0; t < t1; ++t) {
+      const int gidx = it * nkc + t, s = gidx % S, kc = (kc0 + t) % nkc;
+      if (gidx >= S && !mbar_wait(&empty[s], ((gidx / S) - 1) & 1)) {
+        set_err(a.err, 21);
+        return false;
+      }
+      uint8_t* st = sm + (size_t)s * kStage;
+      mbar_expect_tx(&full[s], kStage);
+      bulk_load(st, pcol + (size_t)kc * kChunkA, kChunkA, &full[s]);
+      bulk_load(st + kChunkA, gsrc + (size_t)kc * kB, kB, &full[s]);
+      issued = gidx + 1;
+    }
+    return true;
+  };
+  auto consume = [&](int it, int t0, int t1) -> bool {  // MMA thread: stages t0 .. t1 - 1
+    const uint32_t hd = idesc_f16(kPM, NT, false), hdn = idesc_f16(kPM, NT, true);
+    const uint32_t dre = tbase, dim = tbase + NT;
+    for (int t = t0; t < t1; ++t) {
+      const int gidx = it * nkc + t, s = gidx % S;
+      if (!mbar_wait(&full[s], (gidx / S) & 1)) {
+        set_err(a.err, 22);
+        return false;
+      }
+      tc_fence_after();
+      const uint32_t sa = smem_u32(sm + (size_t)s * kStage), sbb = sa + kChunkA;
+      const uint32_t acc0 = t == 0 ? 0u : 1u;
+      const uint64_t Ahr = desc32(sa), Ahi = desc32(sa + kPlaneA);
+      const uint64_t Alr = desc32(sa + 2 * kPlaneA), Ali = desc32(sa + 3 * kPlaneA);
+      const uint64_t Bhr = desc32(sbb), Bhi = desc32(sbb + NT * 32);
+      const uint64_t Blr = desc32(sbb + 2 * NT * 32), Bli = desc32(sbb + 3 * NT * 32);
+      // D_re += p_re G_re^T - p_im G_im^T ; D_im += p_re G_im^T + p_im G_re^T
+      mma_f16(dre, Ahr, Bhr, hd, acc0);
+      mma_f16(dre, Ahr, Blr, hd, 1);
+      mma_f16(dre, Alr, Bhr, hd, 1);
+      mma_f16(dre, Ahi, Bhi, hdn, 1);
+      mma_f16(dre, Ahi, Bli, hdn, 1);
+      mma_f16(dre, Ali, Bhi, hdn, 1);
+      mma_f16(dim, Ahr, Bhi, hd, acc0);
+      mma_f16(dim, Ahr, Bli, hd, 1);
+      mma_f16(dim, Alr, Bhi, hd, 1);
+      mma_f16(dim, Ahi, Bhr, hd, 1);
+      mma_f16(dim, Ahi, Blr, hd, 1);
+      mma_f16(dim, Ali, Bhr, hd, 1);
+      mma_commit(&empty[s]);
+    }
+    return true;
+  };
+  // after this CTA's split of update `it` is complete (block barrier), between
+  // the arrive and the wait of the cluster barrier: the own stages of `it`.
+  // A failure here is published before the next exchange, so that every CTA
+  // of the cluster reads the same error flags after the same barrier.
+  bool late_err = false;
+  auto early = [&](int it) {
+    if (it >= a.max_iter) return;
+    if (warp == 0 && lane == 0) late_err = !produce(it, 0, NCH);
+    else if (warp == 1 && lane == 0) late_err = !consume(it, 0, NCH);
   };
 
   // ---- start: r = b, x = 0, p = r; ||b_j||^2; the split of p for the first main loop ----
@@ -267,67 +332,28 @@ __global__ void __launch_bounds__(kPThreads, 1) k_colcg_persist(PersistArgs a) {
       store_split8(ch, 0, 2, i, o & 1, vr, ps);
       store_split8(ch, 1, 3, i, o & 1, vi, ps);
     }
-    fence_proxy_async_global();  // generic writes of the split, read by the peers' bulk copies
+    fence_proxy_async_global();  // generic writes of the split, read by the bulk copies
     if (live) xab[1] = 1;  // any live system in this tile (benign race: every writer stores 1)
   }
   tc_fence_before();
-  cluster_sync_all();
+  __syncthreads();           // this CTA's split of the first direction is complete
+  cluster_arrive_release();  // ... and published to the peers
+  early(0);
+  cluster_wait_acquire();
   tc_fence_after();
   bool any_live = xab[1] != 0;
   bool abort = false;
   if (threadIdx.x == 0) xab[2] = 0;
 
-  int issued = 0;      // stages issued by the producer (all iterations)
-  int committed = 0;   // accumulator commits by the MMA thread
   for (int it = 0; it < a.max_iter && any_live && !abort; ++it) {
-    // ---- main loop ----
+    // ---- main loop: the peers' chunks (the own ones are in flight since the last barrier) ----
     if (warp == 0 && lane == 0) {
+      if (late_err) xab[0] = 1;
       fence_proxy_async_global();
-      for (int kc = 0; kc < nkc; ++kc) {
-        const int gidx = it * nkc + kc, s = gidx % S;
-        if (gidx >= S && !mbar_wait(&empty[s], ((gidx / S) - 1) & 1)) {
-          set_err(a.err, 21);
-          xab[0] = 1;
-          break;
-        }
-        uint8_t* st = sm + (size_t)s * kStage;
-        mbar_expect_tx(&full[s], kStage);
-        bulk_load(st, pcol + (size_t)kc * kChunkA, kChunkA, &full[s]);
-        bulk_load(st + kChunkA, gsrc + (size_t)kc * kB, kB, &full[s]);
-        issued = gidx + 1;
-      }
+      if (!produce(it, NCH, nkc)) xab[0] = 1;
     } else if (warp == 1 && lane == 0) {
-      const uint32_t hd = idesc_f16(kPM, NT, false), hdn = idesc_f16(kPM, NT, true);
-      const uint32_t dre = tbase, dim = tbase + NT;
-      for (int kc = 0; kc < nkc; ++kc) {
-        const int gidx = it * nkc + kc, s = gidx % S;
-        if (!mbar_wait(&full[s], (gidx / S) & 1)) {
-          set_err(a.err, 22);
-          xab[0] = 1;
-          break;
-        }
-        tc_fence_after();
-        const uint32_t sa = smem_u32(sm + (size_t)s * kStage), sbb = sa + kChunkA;
-        const uint32_t acc0 = kc == 0 ? 0u : 1u;
-        const uint64_t Ahr = desc32(sa), Ahi = desc32(sa + kPlaneA);
-        const uint64_t Alr = desc32(sa + 2 * kPlaneA), Ali = desc32(sa + 3 * kPlaneA);
-        const uint64_t Bhr = desc32(sbb), Bhi = desc32(sbb + NT * 32);
-        const uint64_t Blr = desc32(sbb + 2 * NT * 32), Bli = desc32(sbb + 3 * NT * 32);
-        // D_re += p_re G_re^T - p_im G_im^T ; D_im += p_re G_im^T + p_im G_re^T
-        mma_f16(dre, Ahr, Bhr, hd, acc0);
-        mma_f16(dre, Ahr, Blr, hd, 1);
-        mma_f16(dre, Alr, Bhr, hd, 1);
-        mma_f16(dre, Ahi, Bhi, hdn, 1);
-        mma_f16(dre, Ahi, Bli, hdn, 1);
-        mma_f16(dre, Ali, Bhi, hdn, 1);
-        mma_f16(dim, Ahr, Bhi, hd, acc0);
-        mma_f16(dim, Ahr, Bli, hd, 1);
-        mma_f16(dim, Alr, Bhi, hd, 1);
-        mma_f16(dim, Ahi, Bhr, hd, 1);
-        mma_f16(dim, Ahi, Blr, hd, 1);
-        mma_f16(dim, Ali, Bhr, hd, 1);
-        mma_commit(&empty[s]);
-      }
+      if (late_err) xab[0] = 1;
+      if (!consume(it, NCH, nkc)) xab[0] = 1;
       mma_commit(accf);
       ++committed;
     }
@@ -463,7 +489,10 @@ __global__ void __launch_bounds__(kPThreads, 1) k_colcg_persist(PersistArgs a) {
       }
     }
     tc_fence_before();
-    cluster_sync_all();  // the split is complete on every CTA; flags are final
+    __syncthreads();           // this CTA's split is complete and the accumulator read for the last time
+    cluster_arrive_release();  // the split is published; flags are final
+    early(it + 1);             // the own stages of the next update (discarded if the solve ends here)
+    cluster_wait_acquire();
     tc_fence_after();
     any_live = xab[1 + ((it + 1) & 1)] != 0;
     bool ab = false;
@@ -502,7 +531,11 @@ __global__ void __launch_bounds__(kPThreads, 1) k_colcg_persist(PersistArgs a) {
     for (int g = issued - S < 0 ? 0 : issued - S; g < issued; ++g)
       if (!mbar_wait(&full[g % S], (g / S) & 1)) set_err(a.err, 24);
   }
-  if (warp == 1 && lane == 0 && committed > 0 && !mbar_wait(accf, (committed - 1) & 1)) set_err(a.err, 25);
+  if (warp == 1 && lane == 0) {  // also covers MMAs of an update that did not run (its own stages)
+    mma_commit(accf);
+    ++committed;
+    if (!mbar_wait(accf, (committed - 1) & 1)) set_err(a.err, 25);
+  }
   tc_fence_before();
   cluster_sync_all();
   if (warp == 1) {

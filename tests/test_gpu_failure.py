@@ -4,7 +4,8 @@
   reports PICO_E_BREAKDOWN at pico_sync, that system keeps x = 0, every other
   system of the batch is solved as if it were alone, and the context stays
   usable (the next clean batch reports PICO_OK and gives the same solutions).
-  Checked on the column-FFT, tensor-core Gram and Toeplitz (spiral) operators.
+  Checked on the column-FFT, tensor-core Gram and Toeplitz (spiral) operators;
+  under per-column CG only the column holding the NaN breaks down.
 * pico_inject_error sets a device status word from the host exactly as a
   kernel would; pico_sync reports the class (a timeout before a breakdown,
   both named in the message) and clears the words.
@@ -72,6 +73,39 @@ def test_nan_rhs_is_a_breakdown_and_the_context_stays_usable(kind):
     assert torch.equal(x[keep], clean[keep])
     again = op.cg(rhs, 20, 0.0)
     op.sync()                                   # cleared: no error is reported twice
+    assert torch.equal(again, clean)
+    op.close()
+
+
+@pytest.mark.parametrize("ny,nx", [(128, 32), (64, 48)])
+def test_nan_rhs_breaks_down_only_its_column_under_per_column_cg(ny, nx):
+    """Per-column CG (ny = 128: the whole solve in one cluster launch; ny = 64:
+    on chip): a NaN in column 5 of image 2 breaks down that column's system
+    only -- PICO_E_BREAKDOWN at pico_sync, x = 0 in that column, every other
+    column and image as in the clean batch, and the context stays usable."""
+    S = synth.coil_maps(ny, nx, 4, 1)
+    op = pico.Operator(S, mask=synth.mask_pe(ny, 2, 8), power_iters=0, max_batch=8)
+    if ny == 128:
+        op.set_tuning(gram_min_batch=1)
+    op.set_solver("columns")
+    nb = 6
+    rhs = _rhs(nb, ny, nx, 12)
+    clean = op.cg(rhs, 20, 0.0)
+    op.sync()
+    bad = rhs.clone()
+    bad[2, 3, 5] = float("nan")
+    x, iters, relres = op.cg(bad, 20, 0.0, stats=True)
+    with pytest.raises(pico.PicoError) as ei:
+        op.sync()
+    assert ei.value.status == pico.PICO_E_BREAKDOWN
+    assert torch.all(x[2][:, 5] == 0)
+    assert np.isnan(relres[2])
+    others = [j for j in range(nx) if j != 5]
+    assert torch.equal(x[2][:, others], clean[2][:, others])
+    keep = [0, 1, 3, 4, 5]
+    assert torch.equal(x[keep], clean[keep])
+    again = op.cg(rhs, 20, 0.0)
+    op.sync()
     assert torch.equal(again, clean)
     op.close()
 
