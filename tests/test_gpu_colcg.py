@@ -77,8 +77,10 @@ def test_whole_solve_launch_matches_per_update_launches(ny, nx, nc, nb, lam, mon
     """ny = 320, 256, 128 (clusters of 4, 4 and 2 CTAs): the per-column solve
     runs as one launch per batch with x, r and p on chip for every iteration;
     PICO_COLCG_PERSIST=0 selects one fused launch per update instead.  The same
-    CG on the same FP16 operands: the two agree to rounding (2e-5 of max|x|),
-    and the one-launch solve matches the oracle per element."""
+    CG on the same FP16 operands, summed in other orders (the one-launch
+    kernel takes each CTA's own rows of the contraction first): after 30
+    updates the two agree to 1e-4 of max|x|, the bar both meet against the
+    oracle, which the one-launch solve is checked against per element."""
     S = synth.coil_maps(ny, nx, nc, 11)
     cov = synth.noise_cov(nc, 11)
     mask = synth.mask_pe(ny, 2, 8)
@@ -97,7 +99,7 @@ def test_whole_solve_launch_matches_per_update_launches(ny, nx, nc, nb, lam, mon
         counts.append(pico.pico_launch_count(op.ctx))
         xs.append(x.cpu().numpy())
         op.close()
-    assert np.abs(xs[0] - xs[1]).max() / np.abs(xs[1]).max() < 2e-5
+    assert np.abs(xs[0] - xs[1]).max() / np.abs(xs[1]).max() < 1e-4
     assert counts[0] + 25 <= counts[1]              # one launch per solve instead of one per update
     oop = O.Operator(S, cov, mask=mask)
     check = sorted({0, nb - 1})
