@@ -360,11 +360,14 @@ __global__ void __launch_bounds__(kPThreads, 1) k_colcg_persist(PersistArgs a) {
     // ---- phase A: q = D / (gscale ps) + lam p; p^H q (scaled by ps^2) ----
     const float fsc = gsi / ps;
     if (epi) {
-      if (!mbar_wait(accf, it & 1)) {
+      // one thread waits for the accumulator; the other epilogue warps sleep in a
+      // named barrier instead of polling, which would take issue slots from the
+      // MMA warp on the same scheduler
+      if (threadIdx.x == 64 && !mbar_wait(accf, it & 1)) {
         set_err(a.err, 23);
         xab[0] = 1;
       }
-      __syncwarp();  // the tensor-memory loads below are warp-collective
+      asm volatile("bar.sync 1, %0;" ::"r"(kPThreads - 64) : "memory");
       tc_fence_after();
       ffloat pq{0.f, 0.f};
 #pragma unroll 1
