@@ -12,7 +12,7 @@ column's dense block, FP64), pinned in tests/test_oracle_pins.py.
 
 Tolerances: the solutions after 30 updates agree per element to
 1e-4 max|x| (FP32 against FP64, the same bound as the whole-image CG); PICO
-maps per voxel to 1e-4 of the exact diagonal Sigma_kk (the spec bar for
+maps per voxel to 1e-4 of the exact diagonal Sigma_kk (the parity bar for
 identical probe seeds).  Cases cover clusters of 2, 4 and 6 CTAs (ny = 128,
 320, 384; 256 in the comparison with the per-update kernel), ragged image
 tiles (batches that are not multiples of 128, warps with finished and
