@@ -3,10 +3,12 @@
 ``python gen_dft.py OUT.cuh`` writes ``DFT<N, SIGN>::run(float2* v)`` for every
 size in ``SIZES``: an in-place DFT of ``N`` complex values held in registers,
 ``X_k = sum_n x_n exp(SIGN * 2 pi i n k / N)`` (unnormalised, natural order in
-and out).  Composite sizes are split recursively (mixed-radix Cooley-Tukey,
-``n = n1 + N1 n2``, ``k = k2 + N2 k1``) down to radix-2/3/4/5 butterflies
-written from the DFT definition; twiddle factors are numeric literals computed
-here in double precision.
+and out).  Composite sizes are split recursively down to radix-2/3/4/5
+butterflies written from the DFT definition: sizes with coprime factors by the
+Good-Thomas prime-factor mapping (no twiddle factors between the stages),
+prime powers by mixed-radix Cooley-Tukey (``n = n1 + N1 n2``, ``k = k2 + N2
+k1``) with twiddle factors as numeric literals computed here in double
+precision.
 
 Every emitted codelet is executed symbolically in float64 during generation
 and compared with a direct DFT; generation fails if any differs.
@@ -176,6 +178,9 @@ class Gen:
             return list(x)
         if N in (2, 3, 4, 5):
             return {2: self.bf2, 3: self.bf3, 4: self.bf4, 5: self.bf5}[N](x, sign)
+        split = coprime_split(N)
+        if split:
+            return self.dft_pfa(x, sign, *split)
         N1 = next(r for r in (4, 2, 3, 5) if N % r == 0)   # outer radix
         N2 = N // N1
         Y = []
@@ -188,6 +193,39 @@ class Gen:
             for k1 in range(N1):
                 X[k2 + N2 * k1] = z[k1]
         return X
+
+
+def coprime_split(N: int):
+    """(N1, N2) with N = N1 N2, gcd(N1, N2) = 1, N1 the power-of-two part (or
+    the smallest prime-power factor), or None for a prime power."""
+    f = 1
+    while N % (2 * f) == 0:
+        f *= 2
+    if f == 1:
+        p = next(q for q in range(3, N + 1) if N % q == 0)
+        f = p
+        while N % (f * p) == 0:
+            f *= p
+    return (f, N // f) if 1 < f < N else None
+
+
+def _dft_pfa(self, x, sign, N1, N2):
+    """Good-Thomas prime-factor split for coprime N1, N2: input n = (n1 N2 +
+    n2 N1) mod N, output k = the number with k = k1 (mod N1) and k = k2 (mod
+    N2) (Chinese remainder theorem); the exponent n k / N then separates into
+    n1 k1 / N1 + n2 k2 / N2, so no twiddle factors appear between the stages."""
+    N = N1 * N2
+    Y = [self.dft([x[(n1 * N2 + n2 * N1) % N] for n2 in range(N2)], sign) for n1 in range(N1)]
+    X = [None] * N
+    for k2 in range(N2):
+        z = self.dft([Y[n1][k2] for n1 in range(N1)], sign)
+        for k1 in range(N1):
+            k = next(kk for kk in range(k2, N, N2) if kk % N1 == k1)
+            X[k] = z[k1]
+    return X
+
+
+Gen.dft_pfa = _dft_pfa
 
 
 def codelet(N: int, sign: int, rng, nz: int | None = None) -> tuple[str, int]:
