@@ -317,7 +317,9 @@ __global__ void __launch_bounds__(kSmallThreads, 2)
     }
     if (tid == 0) *s_any = ok;
     __syncthreads();
-    if (!*s_any) max_iter = 0;
+    const bool go = *s_any != 0;
+    __syncthreads();  // every thread has read the flag before the loop's first reset of it
+    if (!go) max_iter = 0;
   }
   for (int it = 0; it < max_iter; ++it) {
     // which systems take this update (every block of a group decides alike)
