@@ -42,6 +42,9 @@ struct pico_ctx {
   int* h_flag = nullptr;      // pinned host copy
   float* cg_alpha = nullptr;  // [B] per-system step of the current CG iteration
   int* cg_state = nullptr;    // [B] 0 update, 1 converged, 2 breakdown
+  float* cg_alpha2 = nullptr;  // [B] the same for odd iterations (tensor-core path: x advanced per pair)
+  int* cg_state2 = nullptr;
+  bool pair_x = true;          // PICO_CG_PAIR_X=0: x advanced every iteration on the tensor-core path
   double* d_relres = nullptr;
   double* d_norm = nullptr;
   double* d_adapt = nullptr;
@@ -356,6 +359,20 @@ void op_cg_normal(pico_ctx* c, int nb, int it, float lam) {
 // The CG iterations of one batch: 2 * max_iter kernels (normal operator + update).
 // Replayed from a CUDA graph (captured on a private stream the second time a
 // (nb, max_iter, rtol, lam) combination is used) unless profiling is on.
+// the paired x update of the tensor-core path (x advanced once per two
+// iterations; the per-system step of iteration it in the set of its parity)
+bool pair_path(const pico_ctx* c) { return c->gram_on && c->pair_x && c->n % 2 == 0 && !column_mode(c); }
+float* pair_alpha(pico_ctx* c, int it) { return (it & 1) ? c->cg_alpha2 : c->cg_alpha; }
+int* pair_state(pico_ctx* c, int it) { return (it & 1) ? c->cg_state2 : c->cg_state; }
+// after iterations [0, last]: a solve that ended on an even iteration still
+// owes x its last step
+void pair_flush(pico_ctx* c, int nb, int last) {
+  if (!pair_path(c) || last < 0 || (last & 1)) return;
+  Launch L(c, 1);
+  pico::launch_cg_flush_pair(gram_cg(c, last), nb, pair_alpha(c, last), pair_state(c, last),
+                             reinterpret_cast<const float2*>(gram_pbuf(c, last)), c->stream);
+}
+
 // CG iterations [it0, it1) of one batch: 2-3 kernels per iteration (normal
 // operator, step, update), replayed from a CUDA graph (captured on a private
 // stream the second time a (nb, it0, it1, rtol, lam) combination is used)
@@ -386,6 +403,14 @@ void cg_range(pico_ctx* c, int nb, int it0, int it1, double rtol, float lam) {
       {
         Launch L(c, 1, 2);
         const pico::CgArgs a = c->gram_on ? gram_cg(c, it) : c->cg;
+        if (pair_path(c)) {
+          // the Gram path keeps p of it - 1 (the other direction buffer) through it:
+          // x advances once per pair of iterations
+          if (pico::launch_cg_step_pair(a, nb, it, pair_alpha(c, it), pair_state(c, it), pair_alpha(c, it + 1),
+                                        pair_state(c, it + 1),
+                                        reinterpret_cast<const float2*>(gram_pbuf(c, it + 1)), c->stream))
+            continue;
+        }
         if (!pico::launch_cg_step(a, nb, it, c->cg_alpha, c->cg_state, c->stream)) {
           L.count(-1);
           pico::launch_cg_update(a, nb, it, c->stream);
@@ -432,10 +457,15 @@ void cg_range(pico_ctx* c, int nb, int it0, int it1, double rtol, float lam) {
 constexpr int kStopChunk = 4;
 void cg_iterations(pico_ctx* c, int nb, int max_iter, double rtol, float lam) {
   c->cg.rtol2 = rtol * rtol;
-  if (!(rtol > 0.0) || !c->h_flag) return cg_range(c, nb, 0, max_iter, rtol, lam);
+  if (!(rtol > 0.0) || !c->h_flag) {
+    cg_range(c, nb, 0, max_iter, rtol, lam);
+    return pair_flush(c, nb, max_iter - 1);
+  }
+  int last = -1;  // last iteration run
   for (int it0 = 0; it0 < max_iter; it0 += kStopChunk) {
     const int it1 = std::min(max_iter, it0 + kStopChunk);
     cg_range(c, nb, it0, it1, rtol, lam);
+    last = it1 - 1;
     if (it1 == max_iter) break;
     if (column_mode(c)) {
       { Launch L(c, 1); pico::launch_colcg_any_live(col_args(c), c->nx, nb, c->d_flag, c->stream); }
@@ -449,6 +479,7 @@ void cg_iterations(pico_ctx* c, int nb, int max_iter, double rtol, float lam) {
     if (cudaStreamSynchronize(c->stream) != cudaSuccess) return;
     if (*c->h_flag) break;
   }
+  pair_flush(c, nb, last);
 }
 
 // Per-column CG with the whole solve in one launch (FP16 operands, ny a
@@ -1083,6 +1114,9 @@ pico_status init_impl(const pico_operator_desc* d, void* cuda_stream, size_t hbm
   TRY(dalloc(c, &c->status, (size_t)B));
   TRY(dalloc(c, &c->d_iters, (size_t)B));
   TRY(dalloc(c, &c->cg_alpha, (size_t)B));
+  TRY(dalloc(c, &c->cg_alpha2, (size_t)B));
+  TRY(dalloc(c, &c->cg_state2, (size_t)B));
+  if (const char* e = std::getenv("PICO_CG_PAIR_X")) c->pair_x = std::atoi(e) != 0;
   TRY(dalloc(c, &c->d_flag, (size_t)1));
   TRY(dalloc(c, &c->cg_done, (size_t)B));
   if (cudaMallocHost(&c->h_flag, sizeof(int)) != cudaSuccess) {

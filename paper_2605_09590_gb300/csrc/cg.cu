@@ -192,6 +192,81 @@ __global__ void __launch_bounds__(kVecThreads) k_cg_update_v(CgArgs a, int it, c
   if (threadIdx.x == 0) rr_at_w(a, b, it + 1)[blockIdx.x] = s;
 }
 
+// The same update with x advanced once per two iterations, for operators that
+// keep the last two directions (the tensor-core Gram path): mode 0 (iteration
+// it even) updates r only; mode 1 (it odd) applies the pending x += alpha_prev
+// p_prev, then x += alpha p and r -= alpha q; mode 2 only applies the pending
+// x update (after a solve that ended on an even iteration).  The x values are
+// the same bits as with one update per iteration (the same two FMAs per value
+// in the same order); one pass over x is saved per pair of iterations.
+__global__ void __launch_bounds__(kVecThreads)
+    k_cg_update_pair(CgArgs a, int it, const float* __restrict__ alpha_b, const int* __restrict__ state_b,
+                     const float* __restrict__ alpha_prev_b, const int* __restrict__ state_prev_b,
+                     const float2* __restrict__ p_prev, int mode) {
+  __shared__ double scratch[kVecThreads / 32];
+  const int b = blockIdx.y;
+  const int st = mode == 2 ? 1 : state_b[b];
+  const bool pend = mode != 0 && state_prev_b[b] == 0;
+  const bool upd = st == 0;
+  const float alpha = upd ? alpha_b[b] : 0.f, ap = pend ? alpha_prev_b[b] : 0.f;
+  float4* X = reinterpret_cast<float4*>(a.X + (size_t)b * a.n);
+  float4* R = reinterpret_cast<float4*>(a.R + (size_t)b * a.n);
+  const float4* P = reinterpret_cast<const float4*>(a.P + (size_t)b * a.n);
+  const float4* PP = reinterpret_cast<const float4*>(p_prev + (size_t)b * a.n);
+  const float4* Q = reinterpret_cast<const float4*>(a.Q + (size_t)b * a.n);
+  const int64_t n4 = a.n / 2;
+  const bool xpass = pend || (upd && mode == 1);
+  float acc = 0.f;
+#pragma unroll
+  for (int j = 0; j < kVecPerThread / 2; ++j) {
+    const int64_t i = (int64_t)blockIdx.x * (kVecPerBlock / 2) + j * kVecThreads + threadIdx.x;
+    if (i < n4) {
+      if (xpass) {
+        float4 x = X[i];
+        if (pend) {
+          const float4 p = PP[i];
+          x.x = fmaf(ap, p.x, x.x);
+          x.y = fmaf(ap, p.y, x.y);
+          x.z = fmaf(ap, p.z, x.z);
+          x.w = fmaf(ap, p.w, x.w);
+        }
+        if (upd && mode == 1) {
+          const float4 p = P[i];
+          x.x = fmaf(alpha, p.x, x.x);
+          x.y = fmaf(alpha, p.y, x.y);
+          x.z = fmaf(alpha, p.z, x.z);
+          x.w = fmaf(alpha, p.w, x.w);
+        }
+        X[i] = x;
+      }
+      if (upd) {
+        const float4 q = Q[i];
+        float4 r = R[i];
+        r.x = fmaf(-alpha, q.x, r.x);
+        r.y = fmaf(-alpha, q.y, r.y);
+        r.z = fmaf(-alpha, q.z, r.z);
+        r.w = fmaf(-alpha, q.w, r.w);
+        R[i] = r;
+        acc += fmaf(r.x, r.x, r.y * r.y) + fmaf(r.z, r.z, r.w * r.w);
+      }
+    }
+  }
+  if (mode == 2) return;
+  if (st == 1) {
+    if (threadIdx.x == 0) rr_at_w(a, b, it + 1)[blockIdx.x] = rr_at(a, b, it)[blockIdx.x];
+    return;
+  }
+  if (st == 2) {
+    if (threadIdx.x == 0) {
+      rr_at_w(a, b, it + 1)[blockIdx.x] = 0.0;
+      if (blockIdx.x == 0) a.status[b] = 5;
+    }
+    return;
+  }
+  const double sum = block_sum_d((double)acc, scratch);
+  if (threadIdx.x == 0) rr_at_w(a, b, it + 1)[blockIdx.x] = sum;
+}
+
 // flag = 1 when every system of the batch meets the stopping rule at iteration
 // it (or has broken down, which zeroes its r^H r); cleared by any other
 __global__ void k_cg_all_done(CgArgs a, int it, int* flag) {
@@ -353,6 +428,20 @@ bool launch_cg_step(const CgArgs& a, int nb, int it, float* alpha, int* state, c
   k_cg_alpha<<<nb, 32, 0, s>>>(a, it, alpha, state);
   k_cg_update_v<<<dim3(a.PB, nb), kVecThreads, 0, s>>>(a, it, alpha, state);
   return true;
+}
+bool launch_cg_step_pair(const CgArgs& a, int nb, int it, float* alpha, int* state, const float* alpha_prev,
+                         const int* state_prev, const float2* p_prev, cudaStream_t s) {
+  if (a.n % 2) return false;
+  k_cg_alpha<<<nb, 32, 0, s>>>(a, it, alpha, state);
+  k_cg_update_pair<<<dim3(a.PB, nb), kVecThreads, 0, s>>>(a, it, alpha, state, alpha_prev, state_prev, p_prev,
+                                                          it & 1);
+  return true;
+}
+void launch_cg_flush_pair(const CgArgs& a, int nb, const float* alpha_prev, const int* state_prev,
+                          const float2* p_prev, cudaStream_t s) {
+  if (nb > 0)
+    k_cg_update_pair<<<dim3(a.PB, nb), kVecThreads, 0, s>>>(a, 0, alpha_prev, state_prev, alpha_prev, state_prev,
+                                                            p_prev, 2);
 }
 void launch_cg_all_done(const CgArgs& a, int nb, int it, int* flag, cudaStream_t s) {
   cudaMemsetAsync(flag, 0xFF, sizeof(int), s);  // nonzero: all done unless a block clears it

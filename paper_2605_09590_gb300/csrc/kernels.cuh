@@ -43,6 +43,15 @@ void launch_cg_update(const CgArgs& a, int nb, int it, cudaStream_t s);
 // the same update as launch_cg_update with the per-system scalars computed once
 // (two launches, 16-byte accesses); false (nothing launched) when n is odd
 bool launch_cg_step(const CgArgs& a, int nb, int it, float* alpha, int* state, cudaStream_t s);
+// The same with x advanced once per two iterations (operators that keep the
+// previous direction p_prev intact through iteration it): even it updates r,
+// odd it applies the pending x update of it - 1 and its own; alpha / state
+// of it - 1 in alpha_prev / state_prev.  launch_cg_flush_pair applies a
+// pending x update after a solve that ended on an even iteration.
+bool launch_cg_step_pair(const CgArgs& a, int nb, int it, float* alpha, int* state, const float* alpha_prev,
+                         const int* state_prev, const float2* p_prev, cudaStream_t s);
+void launch_cg_flush_pair(const CgArgs& a, int nb, const float* alpha_prev, const int* state_prev,
+                          const float2* p_prev, cudaStream_t s);
 void launch_cg_report(const CgArgs& a, int nb, int max_iter, int* iters, double* relres, cudaStream_t s);
 // *flag (device) != 0 iff every one of the nb systems has stopped at iteration it
 void launch_cg_all_done(const CgArgs& a, int nb, int it, int* flag, cudaStream_t s);

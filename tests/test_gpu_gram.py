@@ -169,6 +169,26 @@ def test_cg_fixed_iterations_matches_oracle(ny, nx, nc, lam):
         assert abs(relres[b] - rr) <= 1e-3 * rr + 1e-6
 
 
+@pytest.mark.parametrize("iters,rtol", [(30, 0.0), (7, 0.0), (30, 1e-3), (9, 1e-6)])
+def test_x_advanced_per_pair_of_iterations_gives_the_same_bits(iters, rtol):
+    """On the tensor-core path x is advanced once per two iterations (the two
+    FMAs of a value in the same order, one pass over x saved); with
+    PICO_CG_PAIR_X=0 it is advanced every iteration.  Solutions, update counts
+    and residuals are the same bits, for even and odd iteration counts, with
+    and without the stopping rule (which runs the iterations in chunks)."""
+    S, cov, mask = case(160, 18, 5, seed=13)
+    rhs = to_dev(rand_imgs(6, 160, 18, 17))
+    out = []
+    for v in ("1", "0"):
+        op = operator_with_env("PICO_CG_PAIR_X", v, S, mask=mask, noise_cov=cov, lam=0.05, power_iters=0, max_batch=8)
+        x, it, rel = op.cg(rhs, iters, rtol, stats=True)
+        op.sync()
+        out.append((x.cpu(), np.array(it), np.array(rel)))
+        op.close()
+    assert torch.equal(out[0][0], out[1][0])
+    assert np.array_equal(out[0][1], out[1][1]) and np.array_equal(out[0][2], out[1][2])
+
+
 def test_cg_stopping_rule_matches_oracle():
     S, cov, mask = case(128, 16, 6, seed=9)
     op = pico.Operator(S, mask=mask, noise_cov=cov, power_iters=0, max_batch=8)
