@@ -179,7 +179,8 @@ __global__ void __launch_bounds__(kPThreads, 1) k_colcg_persist(PersistArgs a) {
   const float lam = a.lam;
   double rr0 = 0.0, rrd = 0.0;
   ffloat rrs{0.f, 0.f};  // ||r||^2 scaled by ps^2
-  float pn = 0.f, ps = 1.f;
+  double pn = 0.0;  // bound on the direction's entries, sqrt(rr) + beta pn (FP64: rr falls far below FP32's range)
+  float ps = 1.f;
   bool live = false, broke = false;
   int iters = 0;
   // sum of the 2 CS partials of image i in (rank, half) order: the same bits on every CTA and half
@@ -313,8 +314,8 @@ __global__ void __launch_bounds__(kPThreads, 1) k_colcg_persist(PersistArgs a) {
     const bool bad = !isfinite(rr0);
     live = valid && !bad && rr0 > 0.0;
     if (valid && bad) broke = true;
-    pn = sqrtf((float)rr0);
-    ps = pow2_scale_f(pn);
+    pn = sqrt(rr0);
+    ps = pow2_scale(pn);
     {
       const double v = rr0 * (double)ps * (double)ps;
       const float hi = (float)v;
@@ -461,8 +462,8 @@ __global__ void __launch_bounds__(kPThreads, 1) k_colcg_persist(PersistArgs a) {
       }
       // ---- phase C: p = r + beta p and its split (scale from sqrt(rr) + beta pn) ----
       if (cont) {
-        pn = sqrtf((float)rrd) + beta * pn;
-        const float psn = pow2_scale_f(pn);
+        pn = sqrt(rrd) + (double)beta * pn;
+        const float psn = pow2_scale(pn);
         rrs = ff_scale(rrs, (psn / ps) * (psn / ps));  // exact: powers of two
         ps = psn;
       }
