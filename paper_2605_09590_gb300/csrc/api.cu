@@ -64,6 +64,7 @@ struct pico_ctx {
   int64_t nsamp = 0;
   float2* Gt = nullptr;  // Toeplitz / 2-D intermediates [B][nc][n][L]
   bool mask2d = false;   // Cartesian with a 2-D sampling mask (normal operator by the 2-D passes, L = n)
+  int toep_rl = 16;      // image rows per block of the Toeplitz / 2-D row passes
   // nonlinear CS state (pico_cs_*)
   bool cs_ready = false;
   int cs_iters = 0, cs_levels = 0;
@@ -650,6 +651,7 @@ pico_status cart2d_setup(pico_ctx* c, const pico_operator_desc* d, int img, int 
   c->sop.tw2 = c->tw2;
   c->sop.That = c->That;
   c->sop.err = c->g_err;
+  c->sop.row_lines = c->toep_rl;
   c->twx = c->tw2;
   c->tw = c->tw2;
   if (cudaStreamSynchronize(c->stream) != cudaSuccess) return cuda_check(c, "2-D mask set-up");
@@ -755,7 +757,8 @@ pico_status spiral_setup(pico_ctx* c, const pico_operator_desc* d, int img, int 
 
   c->sop = pico::SpiralOp{img,      L,         nc,         P1,          P2,           c->smaps,
                           c->tw2,   c->That,   c->deapod,  M,           c->u,         c->cphase,
-                          c->tile_ptr, c->tile_idx, (float)beta, (float)hw, (float)(1.0 / i0b), c->g_err};
+                          c->tile_ptr, c->tile_idx, (float)beta, (float)hw, (float)(1.0 / i0b), c->g_err,
+                          c->toep_rl};
   // Toeplitz kernel: h on the 2N grid (in the Toeplitz buffer), 2-D DFT, real part, scale
   float2* cbuf = c->Gt;  // max_batch * nc * N * 2N >= (2N)^2 complex values
   { Launch Lh(c, 3); pico::launch_toep_h(c->traj, M, img, cbuf, c->stream); }
@@ -888,6 +891,15 @@ bool want_onchip(const pico_operator_desc* d) {
   if (e && std::string(e) == "fft") return false;
   return pico::colcg_small_supported(d->ny);
 }
+// Image rows per block of the Toeplitz / 2-D-mask row passes: 8 (blocks of
+// half the threads, two per SM) unless PICO_TOEP_ROWS=16 in the environment
+// asks for one block of 16 rows per SM.  The p^H q partials per image are one
+// per row block.
+int toep_row_lines() {
+  const char* e = std::getenv("PICO_TOEP_ROWS");
+  return e && std::atoi(e) == 16 ? 16 : 8;
+}
+
 size_t onchip_extra_bytes(const pico_operator_desc* d, int64_t B) {
   return (size_t)d->nx * d->ny * d->ny * 8 + 4 + (size_t)d->ny * 16 + (size_t)B * d->nx * (8 + 8 + 4 + 16 + 16);
 }
@@ -1039,7 +1051,8 @@ pico_status init_impl(const pico_operator_desc* d, void* cuda_stream, size_t hbm
     if (c->ny != c->nx) return fail(c, PICO_E_UNSUPPORTED, "2-D masks need square images");
     if (!pico::grid_split(img, &P1, &P2) || !pico::fft_length_supported(img))
       return fail(c, PICO_E_UNSUPPORTED, "image size has no 2-D FFT split in this build");
-    PA = (img + 15) / 16;
+    c->toep_rl = toep_row_lines();
+    PA = (img + c->toep_rl - 1) / c->toep_rl;
     extra = std::max((size_t)B * nc * n, (size_t)n) * 8 + (size_t)n * 5 + (size_t)img * 8;
   } else if (c->kind == PICO_CARTESIAN) {
     if (!pico::cart_supported(c->ny, c->nx, &N1, &N2, &M1, &M2))
@@ -1059,7 +1072,8 @@ pico_status init_impl(const pico_operator_desc* d, void* cuda_stream, size_t hbm
     if (kbw < 2 || kbw > 8 || (kbw & 1)) return fail(c, PICO_E_UNSUPPORTED, "kb_width must be 2, 4, 6 or 8");
     if (!pico::spiral_supported(img, &P1, &P2))
       return fail(c, PICO_E_UNSUPPORTED, "spiral image size has no 2N grid split in this build");
-    PA = (img + 15) / 16;
+    c->toep_rl = toep_row_lines();
+    PA = (img + c->toep_rl - 1) / c->toep_rl;
     c->nsamp = d->nsamp;
     extra = std::max((size_t)B * nc * img * L, (size_t)L * L) * 8 + (size_t)L * L * 4 + (size_t)img * 4 + (size_t)L * 8 +
             (size_t)c->nsamp * (8 + 8 + 8 + 16) + (size_t)(L / 16) * (L / 16) * 4 + 64;
@@ -1202,7 +1216,7 @@ size_t footprint_bytes(const pico_operator_desc* d, bool with_kbuf) {
   const int64_t PB = (n + kVecPerBlock - 1) / kVecPerBlock;
   int64_t PA, extra, kbuf;
   if (d->kind == PICO_CARTESIAN && d->mask_2d) {
-    PA = (d->ny + 15) / 16;
+    PA = (d->ny + toep_row_lines() - 1) / toep_row_lines();
     extra = std::max(B * nc * n, n) * 8 + n * 5 + (int64_t)d->ny * 8;
     kbuf = B * nc * n * 8;
   } else if (d->kind == PICO_CARTESIAN) {
@@ -1216,7 +1230,7 @@ size_t footprint_bytes(const pico_operator_desc* d, bool with_kbuf) {
     }
   } else {
     const int64_t img = d->ny, L = 2 * img;
-    PA = (img + 15) / 16;
+    PA = (img + toep_row_lines() - 1) / toep_row_lines();
     extra = std::max(B * nc * img * L, L * L) * 8 + L * L * 4 + img * 4 + L * 8 + d->nsamp * 56 +
             (L / 16) * (L / 16) * 4 + 64;
     kbuf = B * nc * 4 * n * 8;

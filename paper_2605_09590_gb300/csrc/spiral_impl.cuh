@@ -47,20 +47,30 @@ __device__ __forceinline__ void cg_scalars(const CgArgs& a, int b, int it, int* 
   }
 }
 
+// Row-pass blocks of RL image rows: RL = 16 (one block of up to 480 threads
+// per SM) or RL = 8 (half the threads, two blocks per SM, so that one block's
+// global loads and stores overlap the other's transforms).
+template <int P1, int P2, int RL>
+struct RowSplit {
+  static constexpr int NT = (RL * (P1 > P2 ? P1 : P2) + 31) / 32 * 32;
+  static constexpr int MINB = RL <= 8 ? 2 : 1;
+  static constexpr size_t buf = (size_t)RL * P2 * Split<P1, P2>::LD * sizeof(float2);
+};
+
 // ---------------------------------------------------------------------------
 // Pass 1: rows of the image, forward transform of S_c . p padded to L = 2N
 // ---------------------------------------------------------------------------
 // PAD: the grid is 2N (Toeplitz embedding, image in the first half of each
 // line); otherwise L = N (2-D Cartesian masks: plain 2-D DFT, no padding).
-template <int P1, int P2, bool CG, bool PAD>
-__global__ void __launch_bounds__(Split<P1, P2>::NT, 1)
+template <int P1, int P2, bool CG, bool PAD, int RL>
+__global__ void __launch_bounds__(RowSplit<P1, P2, RL>::NT, RowSplit<P1, P2, RL>::MINB)
     k_toep_rows_fwd(SpiralOp op, const float2* __restrict__ xin, float2* __restrict__ G, CgArgs a, int it) {
   constexpr int NIN = PAD ? P2 / 2 : P2;  // samples n1 + P1 n2 inside the image: n2 < NIN
   constexpr int L = P1 * P2;
-  constexpr int NT = Split<P1, P2>::NT;
+  constexpr int NT = RowSplit<P1, P2, RL>::NT;
   extern __shared__ __align__(16) unsigned char smraw[];
   float2* buf = reinterpret_cast<float2*>(smraw);
-  float2* tws = buf + kLines * P2 * Split<P1, P2>::LD;
+  float2* tws = buf + RL * P2 * Split<P1, P2>::LD;
   __shared__ float sh_beta;
   __shared__ int sh_done;
   const int t = threadIdx.x, b = blockIdx.y, N = op.n;
@@ -71,12 +81,12 @@ __global__ void __launch_bounds__(Split<P1, P2>::NT, 1)
   if (CG && sh_done) return;
 
   const int ra = t / P1, n1 = t % P1;
-  const bool ajob = t < kLines * P1;
-  const int ya = blockIdx.x * kLines + ra;
+  const bool ajob = t < RL * P1;
+  const int ya = blockIdx.x * RL + ra;
   const bool aval = ajob && ya < N;
   const int rb = t / P2, k2 = t % P2;
-  const bool bjob = t < kLines * P2;
-  const int yb = blockIdx.x * kLines + rb;
+  const bool bjob = t < RL * P2;
+  const int yb = blockIdx.x * RL + rb;
   const bool bval = bjob && yb < N;
   const size_t img = (size_t)b * N * N;
 
@@ -269,16 +279,16 @@ __global__ void __launch_bounds__(P1 * P2, (P1 * P2 <= 320 ? 2 : 1))
 // ---------------------------------------------------------------------------
 // Pass 3: rows: inverse FFT per coil, first N samples, conj(S) combine, + lam p
 // ---------------------------------------------------------------------------
-template <int P1, int P2, bool CG, bool PAD>
-__global__ void __launch_bounds__(Split<P1, P2>::NT, 1)
+template <int P1, int P2, bool CG, bool PAD, int RL>
+__global__ void __launch_bounds__(RowSplit<P1, P2, RL>::NT, RowSplit<P1, P2, RL>::MINB)
     k_toep_rows_inv(SpiralOp op, const float2* __restrict__ G, const float2* __restrict__ xin,
                     float2* __restrict__ yout, float lam, CgArgs a, int it) {
   constexpr int NIN = PAD ? P2 / 2 : P2;
   constexpr int L = P1 * P2;
-  constexpr int NT = Split<P1, P2>::NT;
+  constexpr int NT = RowSplit<P1, P2, RL>::NT;
   extern __shared__ __align__(16) unsigned char smraw[];
   float2* buf = reinterpret_cast<float2*>(smraw);
-  float2* tws = buf + kLines * P2 * Split<P1, P2>::LD;
+  float2* tws = buf + RL * P2 * Split<P1, P2>::LD;
   __shared__ double red[(NT + 31) / 32];
   __shared__ float sh_beta;
   __shared__ int sh_done;
@@ -289,12 +299,12 @@ __global__ void __launch_bounds__(Split<P1, P2>::NT, 1)
   if (CG && sh_done) return;
 
   const int ra = t / P1, n1 = t % P1;
-  const bool ajob = t < kLines * P1;
-  const int ya = blockIdx.x * kLines + ra;
+  const bool ajob = t < RL * P1;
+  const int ya = blockIdx.x * RL + ra;
   const bool aval = ajob && ya < N;
   const int rb = t / P2, k2 = t % P2;
-  const bool bjob = t < kLines * P2;
-  const int yb = blockIdx.x * kLines + rb;
+  const bool bjob = t < RL * P2;
+  const int yb = blockIdx.x * RL + rb;
   const bool bval = bjob && yb < N;
   const size_t img = (size_t)b * N * N;
 
@@ -468,23 +478,54 @@ __global__ void __launch_bounds__(Split<P1, P2>::NT, 1)
 // ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
+// Row passes of RL image rows per block (grid: ceil(n / RL) row blocks per
+// image; the p^H q partials of the inverse pass, one per row block, fill the
+// context's ceil(n / RL) slots).
+template <int P1, int P2, bool PAD, int RL>
+void toep_rows_fwd_launch(const SpiralOp& op, const float2* x, float2* G, int nb, const CgArgs* a, int it,
+                          cudaStream_t s) {
+  using Rs = RowSplit<P1, P2, RL>;
+  const size_t smr = Rs::buf + P1 * P2 * sizeof(float2);
+  const dim3 grow((op.n + RL - 1) / RL, nb);
+  if (a) {
+    auto k1 = k_toep_rows_fwd<P1, P2, true, PAD, RL>;
+    cudaFuncSetAttribute(k1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smr);
+    k1<<<grow, Rs::NT, smr, s>>>(op, nullptr, G, *a, it);
+  } else {
+    CgArgs dummy{};
+    auto k1 = k_toep_rows_fwd<P1, P2, false, PAD, RL>;
+    cudaFuncSetAttribute(k1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smr);
+    k1<<<grow, Rs::NT, smr, s>>>(op, x, G, dummy, 0);
+  }
+}
+template <int P1, int P2, bool PAD, int RL>
+void toep_rows_inv_launch(const SpiralOp& op, const float2* x, float2* y, const float2* G, int nb, float lam,
+                          const CgArgs* a, int it, cudaStream_t s) {
+  using Rs = RowSplit<P1, P2, RL>;
+  const size_t smr = Rs::buf + P1 * P2 * sizeof(float2);
+  const dim3 grow((op.n + RL - 1) / RL, nb);
+  if (a) {
+    auto k3 = k_toep_rows_inv<P1, P2, true, PAD, RL>;
+    cudaFuncSetAttribute(k3, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smr);
+    k3<<<grow, Rs::NT, smr, s>>>(op, G, nullptr, nullptr, lam, *a, it);
+  } else {
+    CgArgs dummy{};
+    auto k3 = k_toep_rows_inv<P1, P2, false, PAD, RL>;
+    cudaFuncSetAttribute(k3, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smr);
+    k3<<<grow, Rs::NT, smr, s>>>(op, G, x, y, lam, dummy, 0);
+  }
+}
+
 template <int P1, int P2, bool PAD>
 void toep_normal_impl(const SpiralOp& op, const float2* x, float2* y, float2* G, int nb, float lam, const CgArgs* a,
                       int it, cudaStream_t s) {
   using Sp = Split<P1, P2>;
   constexpr int L = P1 * P2;
-  const size_t smr = Sp::row_buf + L * sizeof(float2), smc = Sp::col_buf + L * sizeof(float2);
-  const dim3 grow((op.n + kLines - 1) / kLines, nb);
-  CgArgs dummy{};
-  if (a) {
-    auto k1 = k_toep_rows_fwd<P1, P2, true, PAD>;
-    cudaFuncSetAttribute(k1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smr);
-    k1<<<grow, Sp::NT, smr, s>>>(op, nullptr, G, *a, it);
-  } else {
-    auto k1 = k_toep_rows_fwd<P1, P2, false, PAD>;
-    cudaFuncSetAttribute(k1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smr);
-    k1<<<grow, Sp::NT, smr, s>>>(op, x, G, dummy, 0);
-  }
+  const size_t smc = Sp::col_buf + L * sizeof(float2);
+  if (op.row_lines == 8)
+    toep_rows_fwd_launch<P1, P2, PAD, 8>(op, x, G, nb, a, it, s);
+  else
+    toep_rows_fwd_launch<P1, P2, PAD, kLines>(op, x, G, nb, a, it, s);
   // persistent column pass (P1 > P2): N rows staged per item, TMA boxes of at
   // most 256 rows, every TMA destination 128-byte aligned
   bool wide = false;
@@ -512,15 +553,10 @@ void toep_normal_impl(const SpiralOp& op, const float2* x, float2* y, float2* G,
     cudaFuncSetAttribute(k2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smc);
     k2<<<dim3(L / kLines, nb * op.nc), Sp::NT, smc, s>>>(op, G, a ? a->done : nullptr);
   }
-  if (a) {
-    auto k3 = k_toep_rows_inv<P1, P2, true, PAD>;
-    cudaFuncSetAttribute(k3, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smr);
-    k3<<<grow, Sp::NT, smr, s>>>(op, G, nullptr, nullptr, lam, *a, it);
-  } else {
-    auto k3 = k_toep_rows_inv<P1, P2, false, PAD>;
-    cudaFuncSetAttribute(k3, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smr);
-    k3<<<grow, Sp::NT, smr, s>>>(op, G, x, y, lam, dummy, 0);
-  }
+  if (op.row_lines == 8)
+    toep_rows_inv_launch<P1, P2, PAD, 8>(op, x, y, G, nb, lam, a, it, s);
+  else
+    toep_rows_inv_launch<P1, P2, PAD, kLines>(op, x, y, G, nb, lam, a, it, s);
 }
 
 template <int P1, int P2>
