@@ -891,13 +891,13 @@ bool want_onchip(const pico_operator_desc* d) {
   if (e && std::string(e) == "fft") return false;
   return pico::colcg_small_supported(d->ny);
 }
-// Image rows per block of the Toeplitz / 2-D-mask row passes: 8 (blocks of
-// half the threads, two per SM) unless PICO_TOEP_ROWS=16 in the environment
-// asks for one block of 16 rows per SM.  The p^H q partials per image are one
-// per row block.
+// Image rows per block of the Toeplitz / 2-D-mask row passes: 4 (blocks of
+// a quarter of the threads, four per SM) unless PICO_TOEP_ROWS=16 in the
+// environment asks for one block of 16 rows per SM.  The p^H q partials per
+// image are one per row block.
 int toep_row_lines() {
   const char* e = std::getenv("PICO_TOEP_ROWS");
-  return e && std::atoi(e) == 16 ? 16 : 8;
+  return e && std::atoi(e) == 16 ? 16 : 4;
 }
 
 size_t onchip_extra_bytes(const pico_operator_desc* d, int64_t B) {

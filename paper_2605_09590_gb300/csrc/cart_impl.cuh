@@ -30,7 +30,8 @@ struct ColShape {
   static constexpr int N = N1 * N2;
   // threads: one per (column, job), rounded up to whole warps
   static constexpr int NT = (kColTile * (N1 > N2 ? N1 : N2) + 31) / 32 * 32;
-  static constexpr size_t smem = (size_t)N * kColTile * sizeof(float2) + (size_t)N * sizeof(float2) + N * sizeof(float);
+  // [N][kColTile] values, [N] twiddles, [N] sampled-line list
+  static constexpr size_t smem = (size_t)N * kColTile * sizeof(float2) + (size_t)N * sizeof(float2) + N * sizeof(int);
 };
 
 template <int M1, int M2>
@@ -283,6 +284,11 @@ __global__ void __launch_bounds__(NormShape<N1, N2>::NT, 3)
 // noise on the sampled lines, inverse-transform along y:
 //     G[b][c][y][kx] = (1/sqrt(ny nx)) sum_ky mask(ky) n(c, ky, kx) e^{+2 pi i ky y / ny}
 // Noise element index e = (c * ny + ky) * nx + kx of replica rep_begin + b.
+// The draws run first, over the block's sampled lines only (a list built
+// per block), so that every lane of a warp draws: a draw loop over the
+// frequency jobs' own lines idled the lanes whose line is not sampled
+// (with R = 2 half of every warp).  The values wait in shared memory in
+// line order, [ky][column], until the frequency jobs load them.
 // ---------------------------------------------------------------------------
 template <int N1, int N2>
 __global__ void __launch_bounds__(ColShape<N1, N2>::NT, 1)
@@ -293,6 +299,8 @@ __global__ void __launch_bounds__(ColShape<N1, N2>::NT, 1)
   extern __shared__ __align__(16) unsigned char smraw[];
   float2* buf = reinterpret_cast<float2*>(smraw);
   float2* tws = buf + N * kColTile;
+  int* lines = reinterpret_cast<int*>(tws + N);  // sampled ky, ascending
+  __shared__ int nlines;
 
   const int t = threadIdx.x;
   const int col = t % kColTile, job = t / kColTile;
@@ -302,21 +310,42 @@ __global__ void __launch_bounds__(ColShape<N1, N2>::NT, 1)
   const int colg = blockIdx.x * kColTile + col;
   const bool cval = colg < nx;
   for (int i = t; i < N; i += NT) tws[i] = op.tw[i];
+  if (t < 32) {  // warp 0 lists the sampled lines in order
+    int base = 0;
+    for (int k0 = 0; k0 < N; k0 += 32) {
+      const bool m = k0 + t < N && op.mask[k0 + t];
+      const unsigned bal = __ballot_sync(0xffffffffu, m);
+      if (m) lines[base + __popc(bal & ((1u << t) - 1u))] = k0 + t;
+      base += __popc(bal);
+    }
+    if (t == 0) nlines = base;
+  }
+  __syncthreads();
+  const int nl = nlines;
+  {
+    const uint64_t key = splitmix64(seed, (uint64_t)(rep_begin + b));
+    for (int i = t; i < nl * kColTile; i += NT) {
+      const int ky = lines[i / kColTile], cc = i % kColTile, cg = blockIdx.x * kColTile + cc;
+      float2 v = make_float2(0.f, 0.f);
+      if (cg < nx) {
+        const uint64_t e = ((uint64_t)c * ny + ky) * (uint64_t)nx + cg;
+        v = data ? data[((size_t)b * op.nc * ny) * nx + e] : draw_cnoise(key, e, sigma);
+      }
+      buf[ky * kColTile + cc] = v;
+    }
+  }
   __syncthreads();
   const int n1 = job, k2 = job;
+  float2 y[N1];
   if (job < N2) {
-    const uint64_t key = splitmix64(seed, (uint64_t)(rep_begin + b));
-    float2 y[N1];
 #pragma unroll
     for (int k1 = 0; k1 < N1; ++k1) {
       const int ky = k2 + N2 * k1;
-      float2 v = make_float2(0.f, 0.f);
-      if (cval && op.mask[ky]) {
-        const uint64_t e = ((uint64_t)c * ny + ky) * (uint64_t)nx + colg;
-        v = data ? data[((size_t)b * op.nc * ny) * nx + e] : draw_cnoise(key, e, sigma);
-      }
-      y[k1] = v;
+      y[k1] = op.mask[ky] ? buf[ky * kColTile + col] : make_float2(0.f, 0.f);
     }
+  }
+  __syncthreads();  // every line is loaded: the buffer takes the transposed layout
+  if (job < N2) {
     DFT<N1, 1>::run(y);
 #pragma unroll
     for (int m = 0; m < N1; ++m) buf[(k2 * N1 + m) * kColTile + col] = m == 0 ? y[0] : cmul_cb(y[m], tws[m * k2]);

@@ -233,7 +233,7 @@ struct SpiralOp {
   const int* tile_idx;      // samples touching each tile (with the kernel half-width)
   float beta, halfw, inv_i0beta;
   int* err;                 // first failure code of a bounded wait (device), or nullptr
-  int row_lines;            // image rows per block of the Toeplitz row passes: 8 or 16 (0 = 16)
+  int row_lines;            // image rows per block of the Toeplitz row passes: 4 or 16 (0 = 16)
 };
 // 3-D tensor map over `planes` planes of rows x L complex64 values (8-byte
 // elements), boxes of `cols` x `box_rows` values (the column pass's staging)

@@ -48,12 +48,12 @@ __device__ __forceinline__ void cg_scalars(const CgArgs& a, int b, int it, int* 
 }
 
 // Row-pass blocks of RL image rows: RL = 16 (one block of up to 480 threads
-// per SM) or RL = 8 (half the threads, two blocks per SM, so that one block's
-// global loads and stores overlap the other's transforms).
+// per SM) or RL = 4 (a quarter of the threads, four blocks per SM, so that
+// the blocks' global loads and stores overlap one another's transforms).
 template <int P1, int P2, int RL>
 struct RowSplit {
   static constexpr int NT = (RL * (P1 > P2 ? P1 : P2) + 31) / 32 * 32;
-  static constexpr int MINB = RL <= 8 ? 2 : 1;
+  static constexpr int MINB = RL <= 4 ? 4 : RL <= 8 ? 2 : 1;
   static constexpr size_t buf = (size_t)RL * P2 * Split<P1, P2>::LD * sizeof(float2);
 };
 
@@ -522,8 +522,8 @@ void toep_normal_impl(const SpiralOp& op, const float2* x, float2* y, float2* G,
   using Sp = Split<P1, P2>;
   constexpr int L = P1 * P2;
   const size_t smc = Sp::col_buf + L * sizeof(float2);
-  if (op.row_lines == 8)
-    toep_rows_fwd_launch<P1, P2, PAD, 8>(op, x, G, nb, a, it, s);
+  if (op.row_lines == 4)
+    toep_rows_fwd_launch<P1, P2, PAD, 4>(op, x, G, nb, a, it, s);
   else
     toep_rows_fwd_launch<P1, P2, PAD, kLines>(op, x, G, nb, a, it, s);
   // persistent column pass (P1 > P2): N rows staged per item, TMA boxes of at
@@ -553,8 +553,8 @@ void toep_normal_impl(const SpiralOp& op, const float2* x, float2* y, float2* G,
     cudaFuncSetAttribute(k2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smc);
     k2<<<dim3(L / kLines, nb * op.nc), Sp::NT, smc, s>>>(op, G, a ? a->done : nullptr);
   }
-  if (op.row_lines == 8)
-    toep_rows_inv_launch<P1, P2, PAD, 8>(op, x, y, G, nb, lam, a, it, s);
+  if (op.row_lines == 4)
+    toep_rows_inv_launch<P1, P2, PAD, 4>(op, x, y, G, nb, lam, a, it, s);
   else
     toep_rows_inv_launch<P1, P2, PAD, kLines>(op, x, y, G, nb, lam, a, it, s);
 }
