@@ -61,6 +61,8 @@ struct pico_ctx {
   int* tile_ptr = nullptr;
   int* tile_idx = nullptr;
   float* traj = nullptr;
+  float* grid_w = nullptr;  // [nsamp][2][taps] gridding weights of each sample's window
+  int2* grid_o = nullptr;   // [nsamp] first grid index of each window
   int64_t nsamp = 0;
   float2* Gt = nullptr;  // Toeplitz / 2-D intermediates [B][nc][n][L]
   bool mask2d = false;   // Cartesian with a 2-D sampling mask (normal operator by the 2-D passes, L = n)
@@ -759,6 +761,13 @@ pico_status spiral_setup(pico_ctx* c, const pico_operator_desc* d, int img, int 
                           c->tw2,   c->That,   c->deapod,  M,           c->u,         c->cphase,
                           c->tile_ptr, c->tile_idx, (float)beta, (float)hw, (float)(1.0 / i0b), c->g_err,
                           c->toep_rl};
+  // the Kaiser-Bessel window of every sample, once (the gridding of each PMR
+  // replica batch and pico_adjoint look the weights up)
+  if ((st = dalloc(c, &c->grid_w, std::max<size_t>(1, pico::grid_table_floats(M)))) != PICO_OK) return st;
+  if ((st = dalloc(c, &c->grid_o, std::max<size_t>(1, (size_t)M))) != PICO_OK) return st;
+  c->sop.gw = c->grid_w;
+  c->sop.go = c->grid_o;
+  { Launch Lg(c, 3); pico::launch_grid_table(c->sop, c->grid_w, c->grid_o, c->stream); }
   // Toeplitz kernel: h on the 2N grid (in the Toeplitz buffer), 2-D DFT, real part, scale
   float2* cbuf = c->Gt;  // max_batch * nc * N * 2N >= (2N)^2 complex values
   { Launch Lh(c, 3); pico::launch_toep_h(c->traj, M, img, cbuf, c->stream); }
@@ -1076,7 +1085,7 @@ pico_status init_impl(const pico_operator_desc* d, void* cuda_stream, size_t hbm
     PA = (img + c->toep_rl - 1) / c->toep_rl;
     c->nsamp = d->nsamp;
     extra = std::max((size_t)B * nc * img * L, (size_t)L * L) * 8 + (size_t)L * L * 4 + (size_t)img * 4 + (size_t)L * 8 +
-            (size_t)c->nsamp * (8 + 8 + 8 + 16) + (size_t)(L / 16) * (L / 16) * 4 + 64;
+            (size_t)c->nsamp * (8 + 8 + 8 + 16 + 88) + (size_t)(L / 16) * (L / 16) * 4 + 64;
   }
 
   // footprint check before allocating anything
@@ -1231,7 +1240,7 @@ size_t footprint_bytes(const pico_operator_desc* d, bool with_kbuf) {
   } else {
     const int64_t img = d->ny, L = 2 * img;
     PA = (img + toep_row_lines() - 1) / toep_row_lines();
-    extra = std::max(B * nc * img * L, L * L) * 8 + L * L * 4 + img * 4 + L * 8 + d->nsamp * 56 +
+    extra = std::max(B * nc * img * L, L * L) * 8 + L * L * 4 + img * 4 + L * 8 + d->nsamp * (56 + 88) +
             (L / 16) * (L / 16) * 4 + 64;
     kbuf = B * nc * 4 * n * 8;
   }

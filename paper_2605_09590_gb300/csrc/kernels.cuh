@@ -234,6 +234,8 @@ struct SpiralOp {
   float beta, halfw, inv_i0beta;
   int* err;                 // first failure code of a bounded wait (device), or nullptr
   int row_lines;            // image rows per block of the Toeplitz row passes: 4 or 16 (0 = 16)
+  const float* gw;          // [M][2][kMaxTaps] Kaiser-Bessel weights of each sample's window (x, then y)
+  const int2* go;           // [M] wrapped first grid index (x, y) of each sample's window
 };
 // 3-D tensor map over `planes` planes of rows x L complex64 values (8-byte
 // elements), boxes of `cols` x `box_rows` values (the column pass's staging)
@@ -246,6 +248,9 @@ void launch_toep_finalize(const float2* c, int L, float scale, float* That, cuda
 void launch_toep_apply(const SpiralOp& op, const float2* x, float2* y, float2* G, int nb, float lam, cudaStream_t s);
 void launch_toep_cg_normal(const SpiralOp& op, const CgArgs& a, float2* G, int nb, int it, float lam,
                            cudaStream_t s);
+// the per-sample gridding windows (set-up; gw holds grid_table_floats(M) floats)
+size_t grid_table_floats(int64_t M);
+void launch_grid_table(const SpiralOp& op, float* gw, int2* go, cudaStream_t s);
 void launch_grid_pmr(const SpiralOp& op, float2* Qgrid, int nb, uint64_t seed, int64_t rep_begin, float sigma,
                      cudaStream_t s, const float2* data = nullptr);
 void launch_grid_adjoint_rest(const SpiralOp& op, float2* Qgrid, float2* out, int nb, cudaStream_t s);

@@ -100,17 +100,43 @@ __global__ void k_toep_finalize(const float2* c, int64_t count, float scale, flo
 
 // Gather-form Kaiser-Bessel gridding of PMR noise onto the 2n grid.
 // CTA: one 16x16 grid tile, one replica, kCoilGroup coils; thread = grid point.
-// The kernel is separable, phi(dx) phi(dy): for each staged sample the loader
-// threads evaluate the 1-D weights at the integer offsets of its window once
-// (kMaxTaps of them, zero outside |d| <= W/2), and every grid point then only
-// looks its two weights up -- no Bessel evaluation per (point, sample) pair.
+// The kernel is separable, phi(dx) phi(dy), and its 1-D weights at the integer
+// offsets of a sample's window (kMaxTaps of them, zero outside |d| <= W/2)
+// depend on the trajectory alone: k_grid_table evaluates them once per
+// sample at set-up.  Per staged chunk of a tile's samples the block copies
+// their weights and draws their noise (every thread one (sample, coil) pair),
+// then every grid point looks its two weights up -- no Bessel evaluation in
+// the gridding itself.
 constexpr int kCoilGroup = 4;
 constexpr int kMaxTaps = 10;  // window integers for kb_width <= 8, plus one
+
+__global__ void k_grid_table(SpiralOp op, float* __restrict__ gw, int2* __restrict__ go) {
+  const int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= op.M) return;
+  const int L = op.L;
+  const float hw = op.halfw;
+  const int ntaps = min(kMaxTaps, (int)(2.f * hw) + 2);
+  const float2 u = op.u[m];
+  const int ix0 = (int)floorf(u.x - hw), iy0 = (int)floorf(u.y - hw);
+  for (int k = 0; k < kMaxTaps; ++k) {
+    float wx = 0.f, wy = 0.f;
+    if (k < ntaps) {
+      const float dx = (float)(ix0 + k) - u.x, dy = (float)(iy0 + k) - u.y;
+      if (fabsf(dx) <= hw) wx = cyl_bessel_i0f(op.beta * sqrtf(fmaxf(0.f, 1.f - (dx / hw) * (dx / hw)))) * op.inv_i0beta;
+      if (fabsf(dy) <= hw) wy = cyl_bessel_i0f(op.beta * sqrtf(fmaxf(0.f, 1.f - (dy / hw) * (dy / hw)))) * op.inv_i0beta;
+    }
+    gw[m * 2 * kMaxTaps + k] = wx;
+    gw[m * 2 * kMaxTaps + kMaxTaps + k] = wy;
+  }
+  go[m] = make_int2(((ix0 % L) + L) % L, ((iy0 % L) + L) % L);
+}
+
 __global__ void __launch_bounds__(256) k_grid_pmr(SpiralOp op, float2* __restrict__ Q, uint64_t seed,
                                                   int64_t rep_begin, float sigma, const float2* __restrict__ data) {
   __shared__ float s_wx[kChunk][kMaxTaps];
   __shared__ float s_wy[kChunk][kMaxTaps];
   __shared__ int2 s_o[kChunk];               // wrapped first grid index of each window (x, y)
+  __shared__ int s_m[kChunk];                // sample index
   __shared__ float2 s_w[kChunk][kCoilGroup];
   const int L = op.L;
   const int tiles_x = L / 16;
@@ -130,34 +156,28 @@ __global__ void __launch_bounds__(256) k_grid_pmr(SpiralOp op, float2* __restric
     __syncthreads();
     const int cnt = min(kChunk, end - p0);
     if ((int)threadIdx.x < cnt) {
-      const int i = threadIdx.x;
-      const int m = op.tile_idx[p0 + i];
-      const float2 u = op.u[m];
-      const int ix0 = (int)floorf(u.x - hw), iy0 = (int)floorf(u.y - hw);
-      for (int k = 0; k < kMaxTaps; ++k) {
-        float wx = 0.f, wy = 0.f;
-        if (k < ntaps) {
-          const float dx = (float)(ix0 + k) - u.x, dy = (float)(iy0 + k) - u.y;
-          if (fabsf(dx) <= hw)
-            wx = cyl_bessel_i0f(op.beta * sqrtf(fmaxf(0.f, 1.f - (dx / hw) * (dx / hw)))) * op.inv_i0beta;
-          if (fabsf(dy) <= hw)
-            wy = cyl_bessel_i0f(op.beta * sqrtf(fmaxf(0.f, 1.f - (dy / hw) * (dy / hw)))) * op.inv_i0beta;
-        }
-        s_wx[i][k] = wx;
-        s_wy[i][k] = wy;
+      const int m = op.tile_idx[p0 + threadIdx.x];
+      s_m[threadIdx.x] = m;
+      s_o[threadIdx.x] = op.go[m];
+    }
+    __syncthreads();
+    for (int j = threadIdx.x; j < cnt * 2 * kMaxTaps; j += blockDim.x) {
+      const int i = j / (2 * kMaxTaps), k = j - i * (2 * kMaxTaps);
+      const float w = op.gw[(size_t)s_m[i] * (2 * kMaxTaps) + k];
+      if (k < kMaxTaps)
+        s_wx[i][k] = w;
+      else
+        s_wy[i][k - kMaxTaps] = w;
+    }
+    for (int j = threadIdx.x; j < cnt * kCoilGroup; j += blockDim.x) {
+      const int i = j / kCoilGroup, g = j - i * kCoilGroup;
+      const int m = s_m[i], c = c0 + g;
+      float2 v = make_float2(0.f, 0.f);
+      if (c < op.nc) {
+        const uint64_t e = (uint64_t)c * (uint64_t)op.M + (uint64_t)m;
+        v = cmul(data ? data[(size_t)b * op.nc * op.M + e] : draw_cnoise(key, e, sigma), op.cphase[m]);
       }
-      s_o[i] = make_int2(((ix0 % L) + L) % L, ((iy0 % L) + L) % L);
-      const float2 ph = op.cphase[m];
-#pragma unroll
-      for (int g = 0; g < kCoilGroup; ++g) {
-        const int c = c0 + g;
-        float2 v = make_float2(0.f, 0.f);
-        if (c < op.nc) {
-          const uint64_t e = (uint64_t)c * (uint64_t)op.M + (uint64_t)m;
-          v = cmul(data ? data[(size_t)b * op.nc * op.M + e] : draw_cnoise(key, e, sigma), ph);
-        }
-        s_w[i][g] = v;
-      }
+      s_w[i][g] = v;
     }
     __syncthreads();
     for (int i = 0; i < cnt; ++i) {
@@ -244,6 +264,12 @@ void launch_toep_cg_normal(const SpiralOp& op, const CgArgs& a, float2* G, int n
   if (op.P1 == A && op.P2 == B) return launch_toep_normal_t<A, B>(op, nullptr, nullptr, G, nb, lam, &a, it, s);
   PICO_GRID_SIZES(PICO_CASE)
 #undef PICO_CASE
+}
+
+size_t grid_table_floats(int64_t M) { return (size_t)M * 2 * kMaxTaps; }
+
+void launch_grid_table(const SpiralOp& op, float* gw, int2* go, cudaStream_t s) {
+  if (op.M > 0) k_grid_table<<<(unsigned)((op.M + 255) / 256), 256, 0, s>>>(op, gw, go);
 }
 
 void launch_grid_pmr(const SpiralOp& op, float2* Q, int nb, uint64_t seed, int64_t rep_begin, float sigma,
