@@ -162,8 +162,12 @@ def kernel_digest(*names):
 GRAM_FILES = ("gram.cu", "tc_util.cuh", "kernels.cuh", "f16_split.cuh")
 PERSIST_FILES = ("colcg_persist.cu", "tc_util.cuh", "kernels.cuh", "f16_split.cuh")
 TRAFFIC = {
-    ("knee320_r2", 256, "gram", "6728337592ce1c63"): (712.911872e6 + 378.789120e6 + 713.812736e6 + 375.774720e6) / 2,
-    ("knee320_r2", 256, "persist", "913b3ab9ed69752b"): (473.101312e6 + 376.308992e6 + 474.524928e6 + 372.495872e6) / 2,
+    ("knee320_r2", 256, "gram", "580cead29cb443a1"): (713.137664e6 + 378.007808e6 + 711.760128e6 + 374.798592e6) / 2,
+    ("knee320_r2", 256, "persist", "b7cf5961e2e5f7f1"): (473.558528e6 + 375.167488e6 + 473.355264e6 + 371.994624e6) / 2,
+    # one spiral normal operator = k_toep_rows_fwd + k_toep_cols_w + k_toep_rows_inv (two of each averaged)
+    ("spiral240_r2", 256, "fft", "40fe3b9a9e3fec65"): ((4720.102912e6 + 4661.500160e6 + 4719.623168e6 + 4658.126080e6)
+                                                       + (5086.091520e6 + 133.305856e6 + 5086.246656e6 + 133.519616e6)
+                                                       + (474.891264e6 + 4772.518912e6 + 474.142464e6 + 4772.286208e6)) / 2,
 }
 
 
@@ -219,7 +223,7 @@ def fft_roofline(w, K, avg_s, launches):
     traffic, dig = traffic_of(w, K, "fft", files)
     alg = alg_bytes_normal(w, K)
     return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-            "traffic": traffic, "kernel_digest": dig,
+            "traffic": traffic, "traffic_over_algorithmic": traffic / alg if traffic else None, "kernel_digest": dig,
             "kernel": "k_col_normal (fused CG prologue)" if w.kind == "cartesian" else
                       "k_toep_rows_fwd + k_toep_cols_w + k_toep_rows_inv (one normal operator)",
             "avg_launch_ms": avg_s * 1e3, "launches": launches,
